@@ -1,0 +1,330 @@
+"""Benchmark of the Fourier-expansion CLS hot path on GB300.
+
+Workload: the hybrid mixed-type instance (n=2000 variables; 8000 random
+3-clauses, 400 XOR of length 5 with a fair parity, 200 CARD of length 20 with
+threshold >= 10, 100 NAE of length 4), B=1024 restarts per GPU, FP32 state.
+A step is one pass of the whole hot path for all restarts: FE and analytic
+gradient of every constraint, CSR gather and projected step, and the exact
+integer check of the rounded state. Metric: literal-evals/s = (literal
+occurrences) x (restarts) per second of that step.
+
+Timing: W untimed warm-up steps; K timed steps as K/S replays of an S-step
+CUDA graph (S = --steps-per-graph), each replay bracketed by CUDA events on
+the launching stream, with L2 flushed (a 512 MB write) between replays. Under
+torchrun every rank runs its own restarts (weak scaling, no collective on the
+data path); the timed region is bracketed by a barrier and device syncs and
+the max over ranks is reported.
+
+--impl reference times the CPU oracle (FP64 numpy, Poisson-binomial
+recurrence) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("hybrid mixed-type instance n=2000: 8000 3-OR, 400 XOR(5, fair parity), 200 CARD(20)>=10, "
+            "100 NAE(4); B=1024 restarts per GPU")
+METRIC = "FE+grad literal-evals/s"
+UNIT = "literal-evals/s"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fe_grad_traffic.json")
+KERNEL_SOURCES = ["paper_2606_06641_gb300/csrc/fe_short.cuh", "paper_2606_06641_gb300/csrc/kernels.cu"]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu_id], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return None
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_id_for(dev: int) -> str:
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        return f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[dev] if vis else str(dev)
+
+
+def cpu_oracle_sample(inst, B_sample: int, budget_s: float, seed: int = 0):
+    """The oracle's FE + gradient + projected step on B_sample restarts,
+    repeated for about budget_s seconds of host time."""
+    import numpy as np
+
+    from oracle import fe_oracle as O
+    from paper_2606_06641_gb300 import synth
+    x = synth.uniform_x0(inst.n, B_sample, seed).astype(np.float64)
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        x = O.pgd_step(inst, x, 0.1)
+        O.unsat_count(inst, x)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return inst.n_lits * B_sample * reps / el, reps, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2606_06641_gb300 import synth
+    inst = synth.config2(0)
+    B_sample = 8
+    for _ in range(max(args.warmup, 0)):
+        cpu_oracle_sample(inst, B_sample, 0.0)
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        v, _, _ = cpu_oracle_sample(inst, B_sample, 0.0)
+        vals.append(v)
+    el = time.perf_counter() - t_all
+    value = inst.n_lits * B_sample * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{B_sample} of 1024 restarts per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"FP64 oracle step (FE, gradient, projected step, exact check) on "
+                                   f"{B_sample} restarts per step, {args.steps} steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+
+    from paper_2606_06641_gb300 import binding as bd
+    from paper_2606_06641_gb300 import build as _b
+    from paper_2606_06641_gb300 import synth
+    if rank == 0 or world == 1:
+        _b.build()
+    if world > 1:
+        torch.distributed.barrier()
+
+    inst = synth.config2(0)
+    B = args.restarts
+    params = bd.default_params(eta=0.1, verify_every=1)
+    h = bd.load_instance(inst, params)
+    bd.init_restarts(h, B, seed=1000 + rank)
+    stream = torch.cuda.current_stream()
+    S = max(1, min(args.steps_per_graph, args.steps))
+    R = max(1, args.steps // S)
+    K = R * S
+
+    # warm-up: W single steps, then one untimed replay of the timed graph
+    for _ in range(max(args.warmup, 3)):
+        bd.step(h, 1)
+    bd.set_kernel_timing(h, True)
+    bd.step(h, S)
+    torch.cuda.synchronize()
+    bd.set_kernel_timing(h, True)  # reset sums, keep the captured graph
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(R)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(R)]
+    sampler = ClockSampler(gpu_id_for(dev)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.4)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches = 0
+    for r in range(R):
+        flush.fill_(float(r))
+        e0[r].record(stream)
+        bd.step(h, S)
+        e1[r].record(stream)
+        launches += bd.last_launch_count(h)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+    dev_ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1))
+    fe_ms, fe_n, csr_ms, csr_n = bd.kernel_timing(h)
+    bd.set_kernel_timing(h, False)
+    t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    dev_ms = float(t.item())
+
+    L = inst.n_lits
+    value = L * B * K * world / (dev_ms * 1e-3)
+    work = bd.work_per_restart(h) * B          # FP32 lane instructions per step
+    fe_ms_step = fe_ms / K
+    props = torch.cuda.get_device_properties(dev)
+    peaks, peak_src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tinst = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
+    achieved = work / (fe_ms_step * 1e-3) / 1e12 if fe_ms_step > 0 else 0.0
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        with open(TRAFFIC_FILE) as fh:
+            tr = json.load(fh)
+        if tr.get("kernel_source_hash") == kernel_source_hash():
+            traffic = tr.get("bytes_per_step")
+
+    # end to end through the public API: pinned host x in, one step, x and unsat counts out
+    e2e = None
+    if not args.no_e2e:
+        x_host = bd.get_x(h).cpu().pin_memory()
+        for _ in range(2):
+            bd.step_host(h, x_host, x_host)
+        E = max(3, min(args.steps, 30))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(E):
+            bd.step_host(h, x_host, x_host)
+        el = time.perf_counter() - t0
+        e2e = {"value": L * B * E * world / el, "unit": UNIT, "h2d_bytes_per_step": inst.n * B * 4,
+               "d2h_bytes_per_step": inst.n * B * 4 + B * 4}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, reps, el = cpu_oracle_sample(inst, 8, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 oracle step (FE, gradient, projected step, exact check) on 8 of 1024 restarts, "
+                         f"{reps} steps in {el:.1f} s"}
+
+    chunk, rpl = bd.tuning(h)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": max(args.warmup, 3), "ms_per_step": dev_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "restarts": B, "literals": L,
+                       "l2": f"flushed (512 MB write) between timed CUDA-graph replays of {S} steps",
+                       "chunk_restarts": chunk, "restarts_per_lane": rpl, "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
+                         "frac": achieved / peak_tinst if peak_tinst else None, "traffic": traffic,
+                         "kernel": "FE+gradient kernels (all length buckets of a chunk)",
+                         "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
+                                       f"(max SM clock, {peak_src})",
+                         "fe_ms_per_step": fe_ms_step, "csr_ms_per_step": csr_ms / K,
+                         "work_instr_per_step": work},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--restarts", type=int, default=1024)
+    ap.add_argument("--steps-per-graph", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

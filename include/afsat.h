@@ -1,0 +1,214 @@
+/*
+ * afsat.h - C ABI of the GB300 Fourier-expansion continuous-local-search
+ * (CLS) library.
+ *
+ * The library runs the data-parallel hot path of CLS for symmetric
+ * pseudo-Boolean constraints (Sec. 2.1 and Sec. 3 of "Accelerated Fourier
+ * SAT"): for a batch of B restarts it evaluates the Walsh-Fourier expansion
+ * (Eq. 1) of every constraint as products over the k+1 roots of unity combined
+ * with per-type DFT coefficients (Sec. 2.1.2), forms the analytic gradient by
+ * prefix/suffix products, gathers it per variable through a
+ * variable-to-occurrence CSR, takes the projected step of Algorithm 1 on
+ * [-1,1]^n, and verifies sign-rounded assignments exactly in integers.
+ *
+ * Conventions shared by every call:
+ *   - Every function returns AFS_OK (0) or a negative AFS_E_* code; the
+ *     message of the last failure on the calling thread is afs_last_error().
+ *     No C++ exception crosses this boundary.
+ *   - Pointers suffixed _dev are device pointers owned by the caller (for
+ *     example torch tensors' data_ptr()); all other pointers are host memory
+ *     owned by the caller. The library owns every buffer it allocates for a
+ *     handle and releases them in afs_free().
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Device
+ *     work is enqueued on it in order; calls that fill host outputs
+ *     synchronise that stream before returning.
+ *   - Restart-major layout: a state or gradient array holds x[v * B + b] for
+ *     variable v (0-based) and restart b, so that one restart is one lane of a
+ *     warp and the gathers of a constraint's literals are coalesced rows.
+ *   - A handle is not thread safe; distinct handles are independent.
+ */
+#ifndef AFSAT_H
+#define AFSAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define AFS_OK 0
+#define AFS_E_ARG (-1)       /* null pointer, bad size or bad option          */
+#define AFS_E_VAR_RANGE (-2) /* literal 0 or |literal| > n_vars               */
+#define AFS_E_LEN (-3)       /* constraint length 0 or above AFS_MAX_LEN       */
+#define AFS_E_TYPE (-4)      /* unknown constraint type or CARD operator       */
+#define AFS_E_CUDA (-5)      /* a CUDA runtime call failed                     */
+#define AFS_E_TIMEOUT (-6)   /* a bounded device wait gave up                  */
+#define AFS_E_VERIFY (-7)    /* host re-check of a device result disagreed     */
+#define AFS_E_STATE (-8)     /* call out of order (e.g. step before init)      */
+
+#define AFS_MAX_LEN 1024     /* longest constraint accepted                   */
+
+/* ---- constraint records (Table 1; Appendix A type table) ----------------
+ * A literal is True when its value is -1 (Sec. 2.1: True -> -1, False -> +1).
+ * t = number of true literals of a constraint of length k.
+ *   AFS_OR    t >= 1                 AFS_AMO  t <= 1
+ *   AFS_XOR   t odd (parity = 1) or even (parity = 0)
+ *   AFS_NAE   0 < t < k              AFS_EO   t == 1
+ *   AFS_EK    t == param             AFS_CARD t >= param (op = AFS_GE)
+ *                                             t <  param (op = AFS_LT)
+ * CARD thresholds are taken already normalised to >= or < (Appendix A). */
+enum { AFS_OR = 0, AFS_XOR = 1, AFS_NAE = 2, AFS_AMO = 3, AFS_EO = 4, AFS_EK = 5, AFS_CARD = 6 };
+enum { AFS_GE = 0, AFS_LT = 1 };
+
+typedef struct afs_cons {
+  uint8_t type;       /* AFS_OR .. AFS_CARD                                 */
+  uint8_t op;         /* AFS_GE / AFS_LT (CARD only)                        */
+  uint8_t parity;     /* XOR: 1 = odd, 0 = even                             */
+  uint8_t reserved;
+  int32_t param;      /* threshold r for EK and CARD                        */
+  int32_t lit_offset; /* first literal in the `lits` array                  */
+  int32_t len;        /* k, number of literals (1 .. AFS_MAX_LEN)           */
+} afs_cons;
+
+/* ---- options ------------------------------------------------------------ */
+enum { AFS_BASIS_PGF = 0, AFS_BASIS_ESP = 1 };
+enum { AFS_X_F32 = 0, AFS_X_BF16 = 1 };
+
+typedef struct afs_params {
+  float eta;            /* fixed step size of Algorithm 1 (line 3)          */
+  int32_t basis;        /* AFS_BASIS_PGF (default, stable) or AFS_BASIS_ESP  */
+  int32_t x_storage;    /* AFS_X_F32 or AFS_X_BF16 storage of the state x   */
+  int32_t verify_every; /* exact check cadence inside afs_step (0 = never)   */
+  int32_t chunk;        /* restarts per chunk of the step (0 = autotuned)    */
+  int32_t autotune;     /* 1 = time tile shapes per bucket at init           */
+  int32_t use_graph;    /* 1 = replay afs_step as a captured CUDA graph      */
+  int32_t reserved;
+} afs_params;
+
+typedef struct afs_handle afs_handle;
+
+/* Default options: eta = 0.1, PGF basis, FP32 state, verify every step,
+ * autotuned chunk, autotune on, graphs on. */
+void afs_default_params(afs_params* p);
+
+/* ---- instance loading --------------------------------------------------
+ * afs_load_instance: one instance of n_vars variables and m constraints.
+ *   cons[m]: records; constraint c owns lits[cons[c].lit_offset ..
+ *   + cons[c].len). lits[n_lits]: DIMACS literals, +v / -v for variable v in
+ *   1..n_vars. Repeated variables inside a constraint are independent
+ *   literals. Validates every record (AFS_E_VAR_RANGE, AFS_E_LEN, AFS_E_TYPE),
+ *   computes each distinct constraint shape's DFT coefficients in FP64 from
+ *   its truth table (Table 1, Sec. 3.5: exact conjugate roots, integer
+ *   combinatorics with the division deferred, mirrored terms) and rounds
+ *   them to FP32, buckets constraints by length, builds the literal arrays
+ *   and the variable-to-occurrence CSR, and copies them to the device on
+ *   `stream`. *out receives a new handle (free with afs_free). */
+int afs_load_instance(const afs_cons* cons, int32_t m, const int32_t* lits, int64_t n_lits,
+                      int32_t n_vars, const afs_params* p, void* stream, afs_handle** out);
+
+/* afs_load_batch: n_inst independent instances in one handle, run together
+ * in every launch (the batched serving form). Instance i has
+ * n_vars[i] variables, cons_count[i] constraints starting at
+ * cons[cons_begin[i]], and literal offsets relative to lits. Variables of
+ * different instances are disjoint; each instance gets its own B restarts and
+ * its own unsat counts and solved flag. */
+int afs_load_batch(const afs_cons* cons, const int32_t* cons_begin, const int32_t* cons_count,
+                   const int32_t* lits, int64_t n_lits, const int32_t* n_vars, int32_t n_inst,
+                   const afs_params* p, void* stream, afs_handle** out);
+
+void afs_free(afs_handle* h);
+
+/* ---- restarts ----------------------------------------------------------
+ * afs_init_restarts: allocate and set the state for B restarts. With
+ * x0_dev == NULL every x[v][b] is drawn uniformly on [-1,1) by Philox4x32-10
+ * (Salmon et al., SC'11) with counter (b/4, v, instance, 0) and key (seed low
+ * word, seed high word), word b%4 mapped to 2*(w>>8)*2^-24 - 1; otherwise
+ * x0_dev holds x0[v * B + b] (FP32, all variables of the handle in order) and
+ * is copied (rounded to BF16 if the state is stored in BF16). Also clears the
+ * unsat counts and solved flags. For a batch, v runs over all instances'
+ * variables in load order. */
+int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_dev, void* stream);
+
+/* afs_step: nsteps iterations of Algorithm 1 with the fixed step eta for all
+ * restarts: FE and gradient (Sec. 2.1.2), x <- clamp(x - eta * grad, -1, 1),
+ * and the exact check every verify_every steps. Replayed as a captured CUDA
+ * graph when use_graph is set (the first call for a given nsteps captures). */
+int afs_step(afs_handle* h, int32_t nsteps, void* stream);
+
+/* afs_round_and_verify: sign-round every restart (x < 0 -> True), count the
+ * violated constraints exactly (Algorithm 1's unsat count), and report:
+ *   unsat_host[B * n_inst] (nullable)  per instance and restart
+ *   best_host[n_inst]      (nullable)  restart with the fewest violations
+ *                                      (lowest index on ties)
+ *   assign_host[n_total]   (nullable)  +1/-1 values of the best restart of
+ *                                      each instance, variables in load order
+ *   solved_host[n_inst]    (nullable)  1 if some restart satisfies everything
+ * The best assignments are re-checked on the host with independent integer
+ * code; a disagreement returns AFS_E_VERIFY. Synchronises `stream`. */
+int afs_round_and_verify(afs_handle* h, int32_t* unsat_host, int32_t* best_host,
+                         int8_t* assign_host, int32_t* solved_host, void* stream);
+
+/* ---- state access and evaluation ---------------------------------------- */
+/* Copy the state out as FP32 x[v * B + b] into x_dev (device). */
+int afs_get_x(afs_handle* h, float* x_dev, void* stream);
+/* Overwrite the state from FP32 x_dev[v * B + b] (rounded for BF16 storage). */
+int afs_set_x(afs_handle* h, const float* x_dev, void* stream);
+/* Read the per-restart unsat counts of the last in-step check into
+ * unsat_dev[n_inst * B] and the solved restart per instance (INT32_MAX if
+ * none) into solved_dev[n_inst]; either may be NULL. */
+int afs_get_verify(afs_handle* h, int32_t* unsat_dev, int32_t* solved_dev, void* stream);
+
+/* afs_eval_fe_grad: evaluate, for the restarts given in x_dev, every
+ * constraint's expansion fe_dev[c * B + b] (constraints in load order,
+ * nullable) and the objective's gradient grad_dev[v * B + b] (nullable), with
+ * the same kernels as afs_step but without updating anything. x_dtype is
+ * AFS_X_F32 (x_dev is float) or AFS_X_BF16 (x_dev is bfloat16). B may differ
+ * from the handle's restart count. */
+int afs_eval_fe_grad(afs_handle* h, const void* x_dev, int32_t x_dtype, int32_t B, float* fe_dev,
+                     float* grad_dev, void* stream);
+
+/* afs_step_host: one step of the whole hot path through host memory: copies
+ * x_host[v * B + b] (pinned host FP32) to the device, runs one afs_step with
+ * the exact check, and copies back the unsat counts (unsat_host[n_inst * B])
+ * and the new state (x_out_host, nullable). Synchronises `stream`. */
+int afs_step_host(afs_handle* h, const float* x_host, float* x_out_host, int32_t* unsat_host,
+                  void* stream);
+
+/* ---- introspection ------------------------------------------------------ */
+/* Sizes: n_total variables, m constraints, n_lits literals, n_inst, B. */
+int afs_info(const afs_handle* h, int64_t* out6);
+/* Algorithmic FP32 work of one FE+gradient pass over one restart, in FP32
+ * lane instructions (prefix/suffix products at the non-trivial roots). */
+int afs_work_per_restart(const afs_handle* h, double* instr);
+/* Per-launch timing of the FE+gradient kernels, measured with CUDA events
+ * on `stream` during the last afs_step when timing is enabled. */
+int afs_set_kernel_timing(afs_handle* h, int32_t enable);
+int afs_kernel_timing(afs_handle* h, double* fe_ms_total, int64_t* fe_launches, double* csr_ms_total,
+                      int64_t* csr_launches);
+/* Number of kernel launches enqueued by the last afs_step (all kinds). */
+int afs_last_launch_count(const afs_handle* h, int64_t* launches);
+/* The chunk size and per-bucket tile choice in use (after autotuning). */
+int afs_tuning(const afs_handle* h, int32_t* chunk, int32_t* rpl_by_k, int32_t kcap);
+
+/* afs_coef_table: the FP32 coefficient table the kernels use for one
+ * constraint shape (for host-side inspection and tests). form 0 = short
+ * (k <= 32) layout, form 1 = long layout. Writes up to cap floats into out
+ * and the table length into *len. No device work. */
+int afs_coef_table(int32_t type, int32_t k, int32_t op, int32_t param, int32_t parity,
+                   int32_t basis, int32_t form, float* out, int32_t cap, int32_t* len);
+/* afs_esp_coefficients: f_hat(|S| = d) for d = 0..k in FP64 (Eq. 1's
+ * coefficients of a symmetric constraint, computed with exact integer
+ * combinatorics and one deferred power-of-two division). No device work. */
+int afs_esp_coefficients(int32_t type, int32_t k, int32_t op, int32_t param, int32_t parity,
+                         double* out);
+
+const char* afs_last_error(void);
+const char* afs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AFSAT_H */

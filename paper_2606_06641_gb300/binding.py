@@ -1,0 +1,301 @@
+"""Thin Python binding of the C ABI in include/afsat.h (argument marshalling only).
+
+Every computation runs in libafsat's CUDA kernels; this module converts
+instances to ``afs_cons`` records, passes torch tensors' device pointers and
+the current CUDA stream, and turns status codes into exceptions. There is no
+CPU fallback: if the library is missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from .synth import Instance
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libafsat.so")
+
+AFS_OK = 0
+ERRORS = {-1: "AFS_E_ARG", -2: "AFS_E_VAR_RANGE", -3: "AFS_E_LEN", -4: "AFS_E_TYPE", -5: "AFS_E_CUDA",
+          -6: "AFS_E_TIMEOUT", -7: "AFS_E_VERIFY", -8: "AFS_E_STATE"}
+BASIS_PGF, BASIS_ESP = 0, 1
+X_F32, X_BF16 = 0, 1
+MAX_LEN = 1024
+
+CONS_DTYPE = np.dtype([("type", "u1"), ("op", "u1"), ("parity", "u1"), ("reserved", "u1"),
+                       ("param", "<i4"), ("lit_offset", "<i4"), ("len", "<i4")])
+
+# Every symbol declared in include/afsat.h, with (restype, argtypes).
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+SIGNATURES = {
+    "afs_default_params": (None, [_P]),
+    "afs_load_instance": (_I32, [_P, _I32, _P, _I64, _I32, _P, _P, _P]),
+    "afs_load_batch": (_I32, [_P, _P, _P, _P, _I64, _P, _I32, _P, _P, _P]),
+    "afs_free": (None, [_P]),
+    "afs_init_restarts": (_I32, [_P, _I32, ctypes.c_uint64, _P, _P]),
+    "afs_step": (_I32, [_P, _I32, _P]),
+    "afs_round_and_verify": (_I32, [_P, _P, _P, _P, _P, _P]),
+    "afs_get_x": (_I32, [_P, _P, _P]),
+    "afs_set_x": (_I32, [_P, _P, _P]),
+    "afs_get_verify": (_I32, [_P, _P, _P, _P]),
+    "afs_eval_fe_grad": (_I32, [_P, _P, _I32, _I32, _P, _P, _P]),
+    "afs_step_host": (_I32, [_P, _P, _P, _P, _P]),
+    "afs_info": (_I32, [_P, _P]),
+    "afs_work_per_restart": (_I32, [_P, _P]),
+    "afs_set_kernel_timing": (_I32, [_P, _I32]),
+    "afs_kernel_timing": (_I32, [_P, _P, _P, _P, _P]),
+    "afs_last_launch_count": (_I32, [_P, _P]),
+    "afs_tuning": (_I32, [_P, _P, _P, _I32]),
+    "afs_coef_table": (_I32, [_I32, _I32, _I32, _I32, _I32, _I32, _I32, _P, _I32, _P]),
+    "afs_esp_coefficients": (_I32, [_I32, _I32, _I32, _I32, _I32, _P]),
+    "afs_last_error": (ctypes.c_char_p, []),
+    "afs_version": (ctypes.c_char_p, []),
+}
+
+
+class AfsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_float), ("basis", _I32), ("x_storage", _I32), ("verify_every", _I32),
+                ("chunk", _I32), ("autotune", _I32), ("use_graph", _I32), ("reserved", _I32)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libafsat.so from the package tree (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libafsat.so is not built ({LIB_PATH}); run the package build first")
+        l = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(l, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = l
+    return _lib
+
+
+def _check(rc: int) -> None:
+    if rc != AFS_OK:
+        raise AfsError(rc, lib().afs_last_error().decode())
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().afs_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _stream(stream=None) -> int:
+    if isinstance(stream, int):
+        return stream
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def cons_records(inst: Instance) -> np.ndarray:
+    rec = np.zeros(inst.m, dtype=CONS_DTYPE)
+    rec["type"] = inst.ctype
+    rec["op"] = inst.op
+    rec["parity"] = inst.parity
+    rec["param"] = inst.param
+    rec["lit_offset"] = inst.lit_off[:-1]
+    rec["len"] = np.diff(inst.lit_off)
+    return rec
+
+
+class Handle:
+    """One loaded instance (or batch) with its device state."""
+
+    def __init__(self, ptr: int, n: int, m: int, n_inst: int):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.n, self.m, self.n_inst = n, m, n_inst
+        self.B = 0
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                lib().afs_free(self.ptr)
+                self.ptr = ctypes.c_void_p(0)
+        except Exception:
+            pass
+
+    def free(self) -> None:
+        if self.ptr:
+            lib().afs_free(self.ptr)
+            self.ptr = ctypes.c_void_p(0)
+
+
+def load_instance(inst: Instance, params: Optional[Params] = None, stream=None) -> Handle:
+    rec = cons_records(inst)
+    lits = np.ascontiguousarray(inst.lits, dtype=np.int32)
+    out = ctypes.c_void_p()
+    _check(lib().afs_load_instance(rec.ctypes.data, inst.m, lits.ctypes.data, lits.shape[0], inst.n,
+                                   ctypes.byref(params) if params is not None else None, _stream(stream),
+                                   ctypes.byref(out)))
+    return Handle(out.value, inst.n, inst.m, 1)
+
+
+def load_batch(insts: Sequence[Instance], params: Optional[Params] = None, stream=None) -> Handle:
+    recs, lits, begin, count, nv = [], [], [], [], []
+    c0 = l0 = 0
+    for inst in insts:
+        r = cons_records(inst)
+        r["lit_offset"] += l0
+        recs.append(r)
+        lits.append(inst.lits.astype(np.int32))
+        begin.append(c0)
+        count.append(inst.m)
+        nv.append(inst.n)
+        c0 += inst.m
+        l0 += inst.n_lits
+    rec = np.concatenate(recs) if recs else np.zeros(0, CONS_DTYPE)
+    lit = np.ascontiguousarray(np.concatenate(lits) if lits else np.zeros(0, np.int32))
+    begin = np.asarray(begin, np.int32)
+    count = np.asarray(count, np.int32)
+    nv = np.asarray(nv, np.int32)
+    out = ctypes.c_void_p()
+    _check(lib().afs_load_batch(rec.ctypes.data, begin.ctypes.data, count.ctypes.data, lit.ctypes.data,
+                                lit.shape[0], nv.ctypes.data, len(insts),
+                                ctypes.byref(params) if params is not None else None, _stream(stream),
+                                ctypes.byref(out)))
+    return Handle(out.value, int(nv.sum()), int(count.sum()), len(insts))
+
+
+def init_restarts(h: Handle, B: int, seed: int = 0, x0=None, stream=None) -> None:
+    if x0 is not None:
+        assert x0.is_cuda and x0.dtype.itemsize == 4 and x0.is_contiguous() and tuple(x0.shape) == (h.n, B)
+    _check(lib().afs_init_restarts(h.ptr, B, seed, _ptr(x0), _stream(stream)))
+    h.B = B
+
+
+def step(h: Handle, nsteps: int, stream=None) -> None:
+    _check(lib().afs_step(h.ptr, nsteps, _stream(stream)))
+
+
+def round_and_verify(h: Handle, stream=None):
+    """Returns (unsat[n_inst, B], best[n_inst], assignment[n] (+1/-1), solved[n_inst])."""
+    un = np.zeros((h.n_inst, h.B), np.int32)
+    best = np.zeros(h.n_inst, np.int32)
+    asg = np.zeros(h.n, np.int8)
+    sol = np.zeros(h.n_inst, np.int32)
+    _check(lib().afs_round_and_verify(h.ptr, un.ctypes.data, best.ctypes.data, asg.ctypes.data, sol.ctypes.data,
+                                      _stream(stream)))
+    return un, best, asg, sol
+
+
+def get_x(h: Handle, stream=None):
+    import torch
+    out = torch.empty((h.n, h.B), dtype=torch.float32, device="cuda")
+    _check(lib().afs_get_x(h.ptr, _ptr(out), _stream(stream)))
+    return out
+
+
+def set_x(h: Handle, x, stream=None) -> None:
+    assert x.is_cuda and x.dtype.itemsize == 4 and x.is_contiguous() and tuple(x.shape) == (h.n, h.B)
+    _check(lib().afs_set_x(h.ptr, _ptr(x), _stream(stream)))
+
+
+def get_verify(h: Handle, stream=None):
+    import torch
+    un = torch.empty((h.n_inst, h.B), dtype=torch.int32, device="cuda")
+    sol = torch.empty(h.n_inst, dtype=torch.int32, device="cuda")
+    _check(lib().afs_get_verify(h.ptr, _ptr(un), _ptr(sol), _stream(stream)))
+    return un, sol
+
+
+def eval_fe_grad(h: Handle, x, want_fe: bool = True, want_grad: bool = True, stream=None):
+    """FE per constraint [m, B] and objective gradient [n, B] at x [n, B] (float32 or bfloat16)."""
+    import torch
+    assert x.is_cuda and x.is_contiguous() and x.shape[0] == h.n
+    dt = X_BF16 if x.dtype == torch.bfloat16 else X_F32
+    assert dt == X_BF16 or x.dtype == torch.float32
+    B = x.shape[1]
+    fe = torch.empty((h.m, B), dtype=torch.float32, device=x.device) if want_fe else None
+    g = torch.empty((h.n, B), dtype=torch.float32, device=x.device) if want_grad else None
+    _check(lib().afs_eval_fe_grad(h.ptr, _ptr(x), dt, B, _ptr(fe), _ptr(g), _stream(stream)))
+    return fe, g
+
+
+def step_host(h: Handle, x_host, x_out_host=None, stream=None):
+    """One whole step through host memory; returns unsat counts [n_inst, B] (host)."""
+    import torch
+    assert not x_host.is_cuda and x_host.dtype == torch.float32 and tuple(x_host.shape) == (h.n, h.B)
+    un = torch.empty((h.n_inst, h.B), dtype=torch.int32).pin_memory() if not hasattr(h, "_un_pinned") else h._un_pinned
+    h._un_pinned = un
+    _check(lib().afs_step_host(h.ptr, _ptr(x_host), _ptr(x_out_host), _ptr(un), _stream(stream)))
+    return un
+
+
+def info(h: Handle) -> List[int]:
+    out = (ctypes.c_int64 * 6)()
+    _check(lib().afs_info(h.ptr, out))
+    return list(out)
+
+
+def work_per_restart(h: Handle) -> float:
+    v = ctypes.c_double()
+    _check(lib().afs_work_per_restart(h.ptr, ctypes.byref(v)))
+    return v.value
+
+
+def set_kernel_timing(h: Handle, enable: bool) -> None:
+    _check(lib().afs_set_kernel_timing(h.ptr, 1 if enable else 0))
+
+
+def kernel_timing(h: Handle):
+    fe, csr = ctypes.c_double(), ctypes.c_double()
+    nf, nc = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().afs_kernel_timing(h.ptr, ctypes.byref(fe), ctypes.byref(nf), ctypes.byref(csr), ctypes.byref(nc)))
+    return fe.value, nf.value, csr.value, nc.value
+
+
+def last_launch_count(h: Handle) -> int:
+    v = ctypes.c_int64()
+    _check(lib().afs_last_launch_count(h.ptr, ctypes.byref(v)))
+    return v.value
+
+
+def tuning(h: Handle):
+    chunk = ctypes.c_int32()
+    rpl = (ctypes.c_int32 * 33)()
+    _check(lib().afs_tuning(h.ptr, ctypes.byref(chunk), rpl, 33))
+    return chunk.value, {k: rpl[k] for k in range(33) if rpl[k]}
+
+
+def coef_table(ctype: int, k: int, op: int = 0, param: int = 0, parity: int = 1, basis: int = BASIS_PGF,
+               form: int = 0) -> np.ndarray:
+    n = ctypes.c_int32()
+    _check(lib().afs_coef_table(ctype, k, op, param, parity, basis, form, None, 0, ctypes.byref(n)))
+    out = np.zeros(n.value, np.float32)
+    _check(lib().afs_coef_table(ctype, k, op, param, parity, basis, form, out.ctypes.data, n.value, ctypes.byref(n)))
+    return out
+
+
+def esp_coefficients(ctype: int, k: int, op: int = 0, param: int = 0, parity: int = 1) -> np.ndarray:
+    out = np.zeros(k + 1, np.float64)
+    _check(lib().afs_esp_coefficients(ctype, k, op, param, parity, out.ctypes.data))
+    return out
+
+
+def version() -> str:
+    return lib().afs_version().decode()

@@ -1,0 +1,89 @@
+// Internal launch interface between the host library and the CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace afs {
+
+enum XType { XT_F32 = 0, XT_BF16 = 1 };
+
+// One FE+gradient launch over a group of constraints that share a length k
+// and are stored contiguously in bucket order: constraint c of the group owns
+// literals [lit_base + c*k, lit_base + (c+1)*k).
+struct FeGroupArgs {
+  const void* x;            // x[v * x_pitch + b], float or bf16
+  long long x_pitch;
+  int b0;                   // first restart handled by this launch
+  int nb;                   // number of restarts handled
+  const int2* litslot;      // {var << 1 | negated, CSR slot} per literal
+  const int* cons_tab;      // float4 offset of each constraint's table (bucket order)
+  const int* cons_orig;     // load-order index of each constraint (bucket order)
+  const float4* coef;       // coefficient tables
+  int c_begin;              // first constraint of the group (bucket order)
+  int c_count;              // constraints in the group
+  long long lit_base;       // first literal of the group
+  int k;                    // length of every constraint of the group (long group: the longest)
+  const int* cons_k;        // long group: length of each constraint (bucket order)
+  const int* cons_lit;      // long group: first literal of each constraint (even index)
+  float* go;                // go[slot * go_pitch + (b - b0)] = s_i * dFE/dl_i
+  long long go_pitch;
+  float* fe;                // optional fe[orig * fe_pitch + b]
+  long long fe_pitch;
+  int* err;                 // device error word (bounded waits, bounds checks)
+};
+
+// Gather of per-occurrence derivatives per variable and the projected step.
+struct CsrArgs {
+  void* x;                  // x[v * x_pitch + b] (updated in place when grad == nullptr)
+  long long x_pitch;
+  int b0, nb;
+  const int* csr_off;       // slots of variable v: [csr_off[v], csr_off[v+1])
+  int v_begin, v_count;
+  const float* go;
+  long long go_pitch;
+  float eta;
+  float* grad;              // optional: grad[v * grad_pitch + b] (evaluation mode)
+  long long grad_pitch;
+  const int* var_inst;      // instance of each variable
+  const signed char* frozen;  // optional: frozen[inst * B + b] != 0 -> restart is not moved
+  int B;                    // restarts per instance (frozen row length)
+};
+
+// Exact check of the sign-rounded state.
+struct VerifyArgs {
+  const void* x;
+  long long x_pitch;
+  int B;                    // restarts
+  const int* lit_enc;       // load order literals, var << 1 | negated
+  const int* lit_off;       // load order constraint offsets
+  const int* viol_off;      // per constraint offset into viol
+  const unsigned char* viol;  // viol[viol_off[c] + t] = 1 where f(t) = +1
+  const int4* ranges;       // {c_begin, c_end, instance, 0}
+  int n_ranges;
+  int* unsat;               // unsat[inst * B + b]
+};
+
+// Launch wrappers (kernels.cu / short_*.cu).
+// Return false if no kernel exists for (k, rpl).
+bool launch_short_pgf_f32(const FeGroupArgs& a, int rpl, int warps, cudaStream_t s);
+bool launch_short_pgf_bf16(const FeGroupArgs& a, int rpl, int warps, cudaStream_t s);
+bool launch_short_esp_f32(const FeGroupArgs& a, int rpl, int warps, cudaStream_t s);
+bool launch_short_esp_bf16(const FeGroupArgs& a, int rpl, int warps, cudaStream_t s);
+size_t long_smem_bytes(int kmax, bool esp);
+// One-time kernel attribute setup (raises the long kernel's shared-memory cap).
+bool prepare_kernels();
+void launch_fe_long(const FeGroupArgs& a, int xt, int basis, int rt, cudaStream_t s);
+void launch_csr_update(const CsrArgs& a, int xt, cudaStream_t s);
+void launch_verify(const VerifyArgs& a, int xt, cudaStream_t s);
+void launch_solved(const int* unsat, int n_inst, int B, int* solved, signed char* frozen, cudaStream_t s);
+void launch_init_philox(void* x, int xt, long long x_pitch, int n, int B, const int* var_inst,
+                        unsigned long long seed, cudaStream_t s);
+void launch_convert_in(const void* src, int src_xt, long long src_pitch, void* dst, int dst_xt,
+                       long long dst_pitch, int n, int B, cudaStream_t s);
+void launch_gather_column(const void* x, int xt, long long x_pitch, const int* var_list, int count,
+                          const int* col_of, signed char* out, cudaStream_t s);
+// Restarts per lane available for a short group of length k.
+inline int max_rpl_for_k(int k) { return k <= 8 ? 4 : (k <= 16 ? 2 : 1); }
+
+}  // namespace afs

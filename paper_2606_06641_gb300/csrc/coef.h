@@ -1,0 +1,54 @@
+// Load-time coefficient tables for the FE+gradient kernels (host code).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace afs {
+
+enum { BASIS_PGF = 0, BASIS_ESP = 1 };
+enum { FORM_SHORT = 0, FORM_LONG = 1 };
+
+// Constraints with k <= KSHORT use the register (short) kernels and the
+// short table layout; longer ones use the shared-memory (long) kernel.
+constexpr int KSHORT = 32;
+
+struct Shape {
+  int type, k, op, param, parity;
+  bool operator<(const Shape& o) const;
+  bool operator==(const Shape& o) const;
+};
+
+// Number of real (self-conjugate) and complex-pair roots a table carries.
+inline int n_cplx_roots(int k) { return k / 2; }
+inline int n_real_roots(int k, int basis) { return (k & 1) + (basis == BASIS_ESP ? 1 : 0); }
+
+// f(t) in {-1,+1} for t = 0..k (Table 1, Appendix A); -1 = satisfied.
+void truth_table(const Shape& s, std::vector<int8_t>& f);
+
+// FE coefficients in FP64:
+//  PGF basis: ft_j = (1/(k+1)) sum_t f(t) w^{-jt},   FE = sum_j ft_j prod_i (a_j + b_j l_i)
+//             with a_j = (1+w^j)/2, b_j = (1-w^j)/2.
+//  ESP basis: ch_j = (1/(k+1)) sum_d c_d w^{-jd},     FE = sum_j ch_j prod_i (1 + w^j l_i)
+//             with c_d = f_hat(|S| = d).
+// Only j = 0..floor((k+1)/2) are returned (the rest are exact conjugates).
+void dft_coefficients(const Shape& s, int basis, std::vector<double>& re, std::vector<double>& im);
+
+// c_d = f_hat(|S| = d), d = 0..k, from exact integers with one deferred 2^-k.
+void esp_coefficients(const Shape& s, std::vector<double>& c);
+
+// FP32 table in the layout the kernels read (float4 granules):
+//  short form: {c0,0,0,0}, per real root {alpha, E, 0, 0},
+//              per complex root {alpha, gamma, E.re, E.im}
+//     the kernel evaluates  FE   = c0 + sum_r E_r prod_i (l_i + alpha_r)
+//                                     + sum_j Re(E_j prod_i (l_i + alpha_j + i gamma_j))
+//                          dFE/dl_i = sum_r E_r prod_{i'!=i} (...) + sum_j Re(E_j prod_{i'!=i} (...))
+//  long form:  {c0,0,0,0}, per real root {a, b, D, E},
+//              per complex root {a.re, a.im, b.re, b.im}, {D.re, D.im, E.re, E.im}
+//     FE = c0 + sum Re(E prod_i (a + b l_i)),  dFE/dl_i = sum Re(D prod_{i'!=i} (a + b l_i'))
+void build_table(const Shape& s, int basis, int form, std::vector<float>& out);
+
+// Algorithmic FP32 lane instructions of one FE+gradient evaluation of a
+// constraint of length k for one restart (see the kernels' cost model).
+double work_instr(int k);
+
+}  // namespace afs

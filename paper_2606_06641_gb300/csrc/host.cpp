@@ -1,0 +1,981 @@
+// Host side of the C ABI (include/afsat.h): validation, coefficient tables,
+// length buckets, variable-to-occurrence CSR, restart chunks, CUDA-graph
+// replay of the descent loop, the tile autotuner and exact verification.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/afsat.h"
+#include "afsat_internal.h"
+#include "coef.h"
+
+using namespace afs;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail(AFS_E_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                      \
+  } while (0)
+
+#define CKL()                                                                                    \
+  do {                                                                                           \
+    cudaError_t e_ = cudaPeekAtLastError();                                                      \
+    if (e_ != cudaSuccess) {                                                                     \
+      cudaGetLastError();                                                                        \
+      return fail(AFS_E_CUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, __LINE__); \
+    }                                                                                            \
+  } while (0)
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  int alloc(size_t n) {
+    release();
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return fail(AFS_E_CUDA, "cudaMalloc(%zu): %s", n, cudaGetErrorString(e));
+    }
+    bytes = n;
+    return AFS_OK;
+  }
+  template <typename T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+template <typename T>
+int upload(DevBuf& d, const std::vector<T>& h, cudaStream_t s) {
+  int rc = d.alloc(h.size() * sizeof(T));
+  if (rc) return rc;
+  if (!h.empty()) CK(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return AFS_OK;
+}
+
+struct Group {
+  bool is_long;
+  int k;            // length (long group: longest)
+  int c_begin, c_count;
+  long long lit_base;
+  int rpl;
+};
+
+}  // namespace
+
+struct afs_handle {
+  afs_params p{};
+  int n_inst = 0, n = 0, m = 0;
+  long long L = 0;  // literal occurrences (= CSR slots)
+  std::vector<int> inst_vbegin, inst_cbegin;
+  // host copies for the independent re-check
+  std::vector<int> h_lit_enc, h_lit_off, h_viol_off, h_cons_inst, h_var_inst;
+  std::vector<uint8_t> h_viol;
+  // buckets
+  std::vector<Group> groups;
+  double work_per_restart = 0.0;
+  // device instance data
+  DevBuf litslot, cons_tab, cons_orig, cons_k, cons_lit, coef, csr_off, lit_enc, lit_off, viol_off, viol,
+      ranges, var_inst, err;
+  int n_ranges = 0;
+  // restart state
+  int B = 0, xt = XT_F32;
+  long long pitch = 0;
+  int Bc = 0;
+  DevBuf x, go, unsat, solved, frozen, col, assign, stage, eval_go;
+  long long eval_go_cols = 0;
+  // graphs
+  cudaStream_t cap = nullptr;
+  std::map<int, cudaGraphExec_t> graphs, timed_graphs;
+  std::map<int, std::pair<std::vector<std::pair<int, int>>, std::vector<std::pair<int, int>>>> timed_pairs;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> fe_pairs, csr_pairs;
+  double fe_ms = 0, csr_ms = 0;
+  long long fe_n = 0, csr_n = 0;
+  long long last_launches = 0;
+
+  ~afs_handle() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+    for (auto& g : timed_graphs) cudaGraphExecDestroy(g.second);
+    for (auto e : ev_pool) cudaEventDestroy(e);
+    if (cap) cudaStreamDestroy(cap);
+  }
+  void drop_graphs() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+    for (auto& g : timed_graphs) cudaGraphExecDestroy(g.second);
+    graphs.clear();
+    timed_graphs.clear();
+    timed_pairs.clear();
+  }
+};
+
+// ---------------------------------------------------------------------------
+// loading
+// ---------------------------------------------------------------------------
+static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const int32_t* cons_count,
+                        const int32_t* lits, int64_t n_lits, const int32_t* n_vars, int32_t n_inst,
+                        const afs_params* prm, cudaStream_t s, afs_handle** out) {
+  if (!out) return fail(AFS_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_inst <= 0) return fail(AFS_E_ARG, "n_inst must be positive");
+  if (!cons_begin || !cons_count || !n_vars) return fail(AFS_E_ARG, "NULL instance table");
+  if (n_lits < 0 || (n_lits > 0 && !lits)) return fail(AFS_E_ARG, "bad literal array");
+  std::unique_ptr<afs_handle> h(new afs_handle());
+  if (prm) h->p = *prm;
+  else afs_default_params(&h->p);
+  if (h->p.basis != AFS_BASIS_PGF && h->p.basis != AFS_BASIS_ESP) return fail(AFS_E_ARG, "unknown basis");
+  if (h->p.x_storage != AFS_X_F32 && h->p.x_storage != AFS_X_BF16) return fail(AFS_E_ARG, "unknown x storage");
+  h->n_inst = n_inst;
+  h->inst_vbegin.assign(n_inst + 1, 0);
+  h->inst_cbegin.assign(n_inst + 1, 0);
+  long long nt = 0, mt = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    if (n_vars[i] <= 0) return fail(AFS_E_ARG, "instance %d: n_vars must be positive", i);
+    if (cons_count[i] < 0 || cons_begin[i] < 0) return fail(AFS_E_ARG, "instance %d: bad constraint range", i);
+    if (cons_count[i] > 0 && !cons) return fail(AFS_E_ARG, "cons is NULL");
+    h->inst_vbegin[i] = static_cast<int>(nt);
+    h->inst_cbegin[i] = static_cast<int>(mt);
+    nt += n_vars[i];
+    mt += cons_count[i];
+    if (nt > INT_MAX / 2 || mt > INT_MAX / 2) return fail(AFS_E_ARG, "instance too large");
+  }
+  h->inst_vbegin[n_inst] = static_cast<int>(nt);
+  h->inst_cbegin[n_inst] = static_cast<int>(mt);
+  h->n = static_cast<int>(nt);
+  h->m = static_cast<int>(mt);
+
+  // ---- validate records, gather load-order arrays ----
+  const int m = h->m;
+  std::vector<Shape> shape(m);
+  std::vector<int> gk(m), ginst(m);
+  std::vector<long long> goff(m);
+  long long L = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    for (int j = 0; j < cons_count[i]; ++j) {
+      const afs_cons& c = cons[cons_begin[i] + j];
+      const int g = h->inst_cbegin[i] + j;
+      if (c.type > AFS_CARD) return fail(AFS_E_TYPE, "constraint %d: unknown type %d", g, c.type);
+      if (c.type == AFS_CARD && c.op > AFS_LT) return fail(AFS_E_TYPE, "constraint %d: unknown CARD operator", g);
+      if (c.len <= 0 || c.len > AFS_MAX_LEN) return fail(AFS_E_LEN, "constraint %d: length %d", g, c.len);
+      if (c.lit_offset < 0 || static_cast<long long>(c.lit_offset) + c.len > n_lits)
+        return fail(AFS_E_ARG, "constraint %d: literals out of the array", g);
+      for (int t = 0; t < c.len; ++t) {
+        const int lit = lits[c.lit_offset + t];
+        if (lit == 0 || lit > n_vars[i] || lit < -n_vars[i])
+          return fail(AFS_E_VAR_RANGE, "constraint %d: literal %d outside 1..%d", g, lit, n_vars[i]);
+      }
+      Shape sh{c.type, c.len, c.type == AFS_CARD ? c.op : 0,
+               (c.type == AFS_CARD || c.type == AFS_EK) ? c.param : 0, c.type == AFS_XOR ? (c.parity ? 1 : 0) : 0};
+      shape[g] = sh;
+      gk[g] = c.len;
+      ginst[g] = i;
+      goff[g] = c.lit_offset;
+      L += c.len;
+    }
+  }
+  h->L = L;
+  if (L > INT_MAX / 2) return fail(AFS_E_ARG, "too many literals");
+
+  auto enc_of = [&](int inst, int lit) {
+    const int v = h->inst_vbegin[inst] + (lit > 0 ? lit : -lit) - 1;
+    return (v << 1) | (lit < 0 ? 1 : 0);
+  };
+
+  // ---- distinct shapes: coefficient tables (both forms as needed) and truth tables ----
+  std::map<std::pair<Shape, int>, int> tab_index;  // (shape, form) -> float4 offset
+  std::map<Shape, int> viol_index;
+  std::vector<float> coef;
+  std::vector<uint8_t> violv;
+  std::vector<int> cons_tab_load(m), viol_off(m);
+  for (int g = 0; g < m; ++g) {
+    const int form = gk[g] <= KSHORT ? FORM_SHORT : FORM_LONG;
+    auto key = std::make_pair(shape[g], form);
+    auto it = tab_index.find(key);
+    if (it == tab_index.end()) {
+      std::vector<float> t;
+      try {
+        build_table(shape[g], h->p.basis, form, t);
+      } catch (const std::exception& e) {
+        return fail(AFS_E_TYPE, "constraint %d: %s", g, e.what());
+      }
+      const int off = static_cast<int>(coef.size() / 4);
+      coef.insert(coef.end(), t.begin(), t.end());
+      it = tab_index.emplace(key, off).first;
+    }
+    cons_tab_load[g] = it->second;
+    auto vt = viol_index.find(shape[g]);
+    if (vt == viol_index.end()) {
+      std::vector<int8_t> f;
+      truth_table(shape[g], f);
+      const int off = static_cast<int>(violv.size());
+      for (int8_t v : f) violv.push_back(v > 0 ? 1 : 0);
+      vt = viol_index.emplace(shape[g], off).first;
+    }
+    viol_off[g] = vt->second;
+  }
+
+  // ---- bucket order: short constraints by length, then long ones by decreasing length ----
+  std::vector<int> order(m);
+  for (int g = 0; g < m; ++g) order[g] = g;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const bool la = gk[a] > KSHORT, lb = gk[b] > KSHORT;
+    if (la != lb) return !la;
+    if (!la) return gk[a] < gk[b];
+    return gk[a] > gk[b];
+  });
+  std::vector<int> b_tab(m), b_orig(m), b_k(m), b_lit(m);
+  std::vector<int2> litslot;
+  litslot.reserve(L + m);
+  h->work_per_restart = 0.0;
+  for (int pos = 0; pos < m; ++pos) {
+    const int g = order[pos];
+    const int k = gk[g];
+    if (k > KSHORT && (litslot.size() & 1)) litslot.push_back(make_int2(0, 0));  // even start for bulk copies
+    b_tab[pos] = cons_tab_load[g];
+    b_orig[pos] = g;
+    b_k[pos] = k;
+    b_lit[pos] = static_cast<int>(litslot.size());
+    for (int t = 0; t < k; ++t) litslot.push_back(make_int2(enc_of(ginst[g], lits[goff[g] + t]), -1));
+    if (k > KSHORT && (k & 1)) litslot.push_back(make_int2(0, 0));
+    h->work_per_restart += work_instr(k);
+    const bool is_long = k > KSHORT;
+    Group* last = h->groups.empty() ? nullptr : &h->groups.back();
+    if (last && last->is_long == is_long && (is_long || last->k == k)) {
+      last->c_count++;
+    } else {
+      // long constraints form one group sorted by decreasing length: its k is the longest
+      h->groups.push_back(Group{is_long, k, pos, 1, static_cast<long long>(b_lit[pos]), 1});
+    }
+  }
+  // ---- CSR: slots in variable-major order, occurrences of a variable in bucket order ----
+  std::vector<int> csr(h->n + 1, 0);
+  for (const int2& ls : litslot)
+    if (ls.y == -1) csr[(ls.x >> 1) + 1]++;
+  for (int v = 0; v < h->n; ++v) csr[v + 1] += csr[v];
+  {
+    std::vector<int> fill(csr.begin(), csr.end() - 1);
+    for (int pos = 0; pos < m; ++pos) {
+      for (int t = 0; t < b_k[pos]; ++t) {
+        int2& ls = litslot[b_lit[pos] + t];
+        ls.y = fill[ls.x >> 1]++;
+      }
+    }
+  }
+  // ---- exact-check structures (load order) ----
+  h->h_lit_enc.resize(L);
+  h->h_lit_off.assign(m + 1, 0);
+  h->h_cons_inst = ginst;
+  {
+    long long at = 0;
+    for (int g = 0; g < m; ++g) {
+      h->h_lit_off[g] = static_cast<int>(at);
+      for (int t = 0; t < gk[g]; ++t) h->h_lit_enc[at++] = enc_of(ginst[g], lits[goff[g] + t]);
+    }
+    h->h_lit_off[m] = static_cast<int>(at);
+  }
+  h->h_viol_off = viol_off;
+  h->h_viol = violv;
+  std::vector<int4> ranges;
+  for (int i = 0; i < n_inst; ++i) {
+    int c = h->inst_cbegin[i];
+    const int ce = h->inst_cbegin[i + 1];
+    while (c < ce) {
+      int e = c, lits_in = 0;
+      while (e < ce && (e == c || (lits_in + gk[e] <= 128 && e - c < 32))) lits_in += gk[e++];
+      ranges.push_back(make_int4(c, e, i, 0));
+      c = e;
+    }
+  }
+  h->n_ranges = static_cast<int>(ranges.size());
+  h->h_var_inst.resize(h->n);
+  for (int i = 0; i < n_inst; ++i)
+    for (int v = h->inst_vbegin[i]; v < h->inst_vbegin[i + 1]; ++v) h->h_var_inst[v] = i;
+  std::vector<int> var_inst_ext(h->h_var_inst);
+  var_inst_ext.insert(var_inst_ext.end(), h->inst_vbegin.begin(), h->inst_vbegin.end());
+
+  // ---- upload ----
+  int rc;
+  if ((rc = upload(h->litslot, litslot, s))) return rc;
+  if ((rc = upload(h->cons_tab, b_tab, s))) return rc;
+  if ((rc = upload(h->cons_orig, b_orig, s))) return rc;
+  if ((rc = upload(h->cons_k, b_k, s))) return rc;
+  if ((rc = upload(h->cons_lit, b_lit, s))) return rc;
+  if ((rc = upload(h->coef, coef, s))) return rc;
+  if ((rc = upload(h->csr_off, csr, s))) return rc;
+  if ((rc = upload(h->lit_enc, h->h_lit_enc, s))) return rc;
+  if ((rc = upload(h->lit_off, h->h_lit_off, s))) return rc;
+  if ((rc = upload(h->viol_off, viol_off, s))) return rc;
+  if ((rc = upload(h->viol, violv, s))) return rc;
+  if ((rc = upload(h->ranges, ranges, s))) return rc;
+  if ((rc = upload(h->var_inst, var_inst_ext, s))) return rc;
+  std::vector<int> zero1(1, 0);
+  if ((rc = upload(h->err, zero1, s))) return rc;
+  CK(cudaStreamSynchronize(s));
+  CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  if (!prepare_kernels()) return fail(AFS_E_CUDA, "kernel attribute setup: %s", cudaGetErrorString(cudaGetLastError()));
+  *out = h.release();
+  return AFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch planning
+// ---------------------------------------------------------------------------
+static int launch_fe_group(afs_handle* h, const Group& g, const void* x, int xt, long long x_pitch, int b0, int nb,
+                           float* go, long long go_pitch, float* fe, long long fe_pitch, cudaStream_t s) {
+  FeGroupArgs a{};
+  a.x = x;
+  a.x_pitch = x_pitch;
+  a.b0 = b0;
+  a.nb = nb;
+  a.litslot = h->litslot.as<int2>();
+  a.cons_tab = h->cons_tab.as<int>();
+  a.cons_orig = h->cons_orig.as<int>();
+  a.coef = h->coef.as<float4>();
+  a.c_begin = g.c_begin;
+  a.c_count = g.c_count;
+  a.lit_base = g.lit_base;
+  a.k = g.k;
+  a.cons_k = h->cons_k.as<int>();
+  a.cons_lit = h->cons_lit.as<int>();
+  a.go = go;
+  a.go_pitch = go_pitch;
+  a.fe = fe;
+  a.fe_pitch = fe_pitch;
+  a.err = h->err.as<int>();
+  if (g.is_long) {
+    launch_fe_long(a, xt, h->p.basis, 8, s);
+  } else {
+    bool ok;
+    const bool esp = h->p.basis == AFS_BASIS_ESP;
+    const int rpl = esp ? 1 : g.rpl;
+    if (xt == XT_F32) ok = esp ? launch_short_esp_f32(a, rpl, 4, s) : launch_short_pgf_f32(a, rpl, 4, s);
+    else ok = esp ? launch_short_esp_bf16(a, rpl, 4, s) : launch_short_pgf_bf16(a, rpl, 4, s);
+    if (!ok) return fail(AFS_E_ARG, "no short kernel for k=%d rpl=%d", g.k, rpl);
+  }
+  CKL();
+  return AFS_OK;
+}
+
+static int launch_csr(afs_handle* h, void* x, int xt, long long x_pitch, int b0, int nb, const float* go,
+                      long long go_pitch, float eta, float* grad, long long grad_pitch, bool use_frozen,
+                      cudaStream_t s) {
+  CsrArgs a{};
+  a.x = x;
+  a.x_pitch = x_pitch;
+  a.b0 = b0;
+  a.nb = nb;
+  a.csr_off = h->csr_off.as<int>();
+  a.v_begin = 0;
+  a.v_count = h->n;
+  a.go = go;
+  a.go_pitch = go_pitch;
+  a.eta = eta;
+  a.grad = grad;
+  a.grad_pitch = grad_pitch;
+  a.var_inst = h->var_inst.as<int>();
+  a.frozen = use_frozen ? h->frozen.as<signed char>() : nullptr;
+  a.B = h->B;
+  launch_csr_update(a, xt, s);
+  CKL();
+  return AFS_OK;
+}
+
+static int launch_check(afs_handle* h, bool freeze, cudaStream_t s) {
+  CK(cudaMemsetAsync(h->unsat.p, 0, sizeof(int) * static_cast<size_t>(h->n_inst) * h->B, s));
+  VerifyArgs v{};
+  v.x = h->x.p;
+  v.x_pitch = h->pitch;
+  v.B = h->B;
+  v.lit_enc = h->lit_enc.as<int>();
+  v.lit_off = h->lit_off.as<int>();
+  v.viol_off = h->viol_off.as<int>();
+  v.viol = h->viol.as<unsigned char>();
+  v.ranges = h->ranges.as<int4>();
+  v.n_ranges = h->n_ranges;
+  v.unsat = h->unsat.as<int>();
+  launch_verify(v, h->xt, s);
+  CKL();
+  launch_solved(h->unsat.as<int>(), h->n_inst, h->B, h->solved.as<int>(),
+                freeze ? h->frozen.as<signed char>() : nullptr, s);
+  CKL();
+  return AFS_OK;
+}
+
+static cudaEvent_t pool_event(afs_handle* h, int idx) {
+  while (static_cast<int>(h->ev_pool.size()) <= idx) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[idx];
+}
+
+// Enqueue nsteps of the descent loop on s (used both directly and under capture).
+static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool verify, cudaStream_t s, long long* launches) {
+  long long nl = 0;
+  int ev = 0;
+  const int ve = h->p.verify_every;
+  for (int t = 0; t < nsteps; ++t) {
+    for (int b0 = 0; b0 < h->B; b0 += h->Bc) {
+      const int nb = std::min(h->Bc, h->B - b0);
+      if (h->timing) CK(cudaEventRecord(pool_event(h, ev), s));
+      for (const Group& g : h->groups) {
+        int rc = launch_fe_group(h, g, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, nullptr, 0, s);
+        if (rc) return rc;
+        ++nl;
+      }
+      if (h->timing) CK(cudaEventRecord(pool_event(h, ev + 1), s));
+      int rc = launch_csr(h, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, eta, nullptr, 0, true, s);
+      if (rc) return rc;
+      ++nl;
+      if (h->timing) {
+        CK(cudaEventRecord(pool_event(h, ev + 2), s));
+        h->fe_pairs.emplace_back(ev, ev + 1);
+        h->csr_pairs.emplace_back(ev + 1, ev + 2);
+        ev += 3;
+      }
+    }
+    if (verify && ve > 0 && ((t + 1) % ve == 0 || t + 1 == nsteps)) {
+      int rc = launch_check(h, true, s);
+      if (rc) return rc;
+      nl += 2;
+    }
+  }
+  if (launches) *launches = nl;
+  return AFS_OK;
+}
+
+static void collect_timing(afs_handle* h) {
+  if (h->fe_pairs.empty() && h->csr_pairs.empty()) return;
+  if (!h->ev_pool.empty()) cudaEventSynchronize(h->ev_pool[0]);
+  for (auto& pr : h->fe_pairs) {
+    cudaEventSynchronize(h->ev_pool[pr.second]);
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, h->ev_pool[pr.first], h->ev_pool[pr.second]) == cudaSuccess) {
+      h->fe_ms += ms;
+      h->fe_n++;
+    }
+  }
+  for (auto& pr : h->csr_pairs) {
+    cudaEventSynchronize(h->ev_pool[pr.second]);
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, h->ev_pool[pr.first], h->ev_pool[pr.second]) == cudaSuccess) {
+      h->csr_ms += ms;
+      h->csr_n++;
+    }
+  }
+  h->fe_pairs.clear();
+  h->csr_pairs.clear();
+  cudaGetLastError();
+}
+
+static int alloc_go(afs_handle* h, int cols) {
+  const size_t need = sizeof(float) * static_cast<size_t>(std::max<long long>(h->L, 1)) * cols;
+  if (h->go.bytes >= need) return AFS_OK;
+  return h->go.alloc(need);
+}
+
+// Restart chunk that keeps the per-occurrence derivative buffer (L x Bc
+// floats) well inside the 126 MB L2, so the FE kernel's writes are read back
+// by the CSR kernel from L2 instead of HBM.
+static int default_chunk(const afs_handle* h) {
+  const long long Bp = (h->B + 31) / 32 * 32;
+  const double budget = 40.0e6;
+  long long c = static_cast<long long>(budget / (4.0 * std::max<long long>(h->L, 1)));
+  c = std::max<long long>(32, c / 32 * 32);
+  return static_cast<int>(std::min(c, Bp));
+}
+
+static double time_ms(cudaStream_t s, cudaEvent_t a, cudaEvent_t b) {
+  cudaEventSynchronize(b);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+struct TuneKey {
+  int dev, n, m, B, xt, basis;
+  long long L;
+  std::vector<int> ks;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, n, m, B, xt, basis, L, ks) < std::tie(o.dev, o.n, o.m, o.B, o.xt, o.basis, o.L, o.ks);
+  }
+};
+struct TuneVal {
+  int Bc;
+  std::vector<int> rpl;
+};
+static std::map<TuneKey, TuneVal>& tune_cache() {
+  static std::map<TuneKey, TuneVal> c;
+  return c;
+}
+
+// The tile autotuner: per short length bucket the restarts-per-lane tile,
+// then the restart chunk of the whole step, each chosen by CUDA-event timing
+// of real launches (eta = 0 steps leave the state unchanged).
+static int autotune(afs_handle* h, cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  TuneKey key{dev, h->n, h->m, h->B, h->xt, h->p.basis, h->L, {}};
+  for (auto& g : h->groups) key.ks.push_back(g.is_long ? -g.c_count : g.k * 100000 + g.c_count);
+  auto it = tune_cache().find(key);
+  if (it != tune_cache().end()) {
+    h->Bc = it->second.Bc;
+    for (size_t i = 0; i < h->groups.size(); ++i) h->groups[i].rpl = it->second.rpl[i];
+    return alloc_go(h, h->Bc);
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int Bp = (h->B + 31) / 32 * 32;
+  int rc = alloc_go(h, Bp);
+  if (rc) return rc;
+  const int c0 = default_chunk(h);
+  // 1. restarts per lane per short bucket
+  if (h->p.basis == AFS_BASIS_PGF) {
+    for (Group& g : h->groups) {
+      if (g.is_long) continue;
+      double best = 1e30;
+      int best_rpl = 1;
+      for (int rpl = 1; rpl <= max_rpl_for_k(g.k); rpl *= 2) {
+        g.rpl = rpl;
+        double t = 1e30;
+        for (int rep = 0; rep < 3; ++rep) {
+          CK(cudaEventRecord(e0, s));
+          rc = launch_fe_group(h, g, h->x.p, h->xt, h->pitch, 0, std::min(c0, h->B), h->go.as<float>(), c0, nullptr, 0, s);
+          if (rc) return rc;
+          CK(cudaEventRecord(e1, s));
+          t = std::min(t, time_ms(s, e0, e1));
+        }
+        if (t < best * 0.97) {
+          best = t;
+          best_rpl = rpl;
+        }
+      }
+      g.rpl = best_rpl;
+    }
+  }
+  // 2. restart chunk
+  std::vector<int> cands;
+  for (int c = Bp; c >= 32; c /= 2) {
+    cands.push_back(c / 32 * 32);
+    if (cands.size() >= 6) break;
+  }
+  if (std::find(cands.begin(), cands.end(), c0) == cands.end()) cands.push_back(c0);
+  double best = 1e30;
+  int bestc = c0;
+  const bool was_timing = h->timing;
+  h->timing = false;
+  for (int c : cands) {
+    h->Bc = c;
+    double t = 1e30;
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(cudaEventRecord(e0, s));
+      rc = enqueue_steps(h, 2, 0.0f, false, s, nullptr);
+      if (rc) return rc;
+      CK(cudaEventRecord(e1, s));
+      t = std::min(t, time_ms(s, e0, e1));
+    }
+    if (t < best * 0.97) {
+      best = t;
+      bestc = c;
+    }
+  }
+  h->timing = was_timing;
+  h->Bc = bestc;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  TuneVal val{h->Bc, {}};
+  for (auto& g : h->groups) val.rpl.push_back(g.rpl);
+  tune_cache()[key] = val;
+  return AFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void afs_default_params(afs_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->eta = 0.1f;
+  p->basis = AFS_BASIS_PGF;
+  p->x_storage = AFS_X_F32;
+  p->verify_every = 1;
+  p->chunk = 0;
+  p->autotune = 1;
+  p->use_graph = 1;
+}
+
+int afs_load_instance(const afs_cons* cons, int32_t m, const int32_t* lits, int64_t n_lits, int32_t n_vars,
+                      const afs_params* p, void* stream, afs_handle** out) {
+  if (m < 0) return fail(AFS_E_ARG, "m must be >= 0");
+  const int32_t begin = 0;
+  return build_handle(cons, &begin, &m, lits, n_lits, &n_vars, 1, p, static_cast<cudaStream_t>(stream), out);
+}
+
+int afs_load_batch(const afs_cons* cons, const int32_t* cons_begin, const int32_t* cons_count, const int32_t* lits,
+                   int64_t n_lits, const int32_t* n_vars, int32_t n_inst, const afs_params* p, void* stream,
+                   afs_handle** out) {
+  return build_handle(cons, cons_begin, cons_count, lits, n_lits, n_vars, n_inst, p,
+                      static_cast<cudaStream_t>(stream), out);
+}
+
+void afs_free(afs_handle* h) { delete h; }
+
+int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_dev, void* stream) {
+  if (!h) return fail(AFS_E_ARG, "NULL handle");
+  if (B <= 0) return fail(AFS_E_ARG, "B must be positive");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->drop_graphs();
+  h->B = B;
+  h->xt = h->p.x_storage == AFS_X_BF16 ? XT_BF16 : XT_F32;
+  h->pitch = (B + 31) / 32 * 32;
+  const size_t es = h->xt == XT_F32 ? 4 : 2;
+  int rc;
+  if ((rc = h->x.alloc(es * h->pitch * static_cast<size_t>(h->n)))) return rc;
+  CK(cudaMemsetAsync(h->x.p, 0, h->x.bytes, s));
+  const size_t nib = static_cast<size_t>(h->n_inst) * B;
+  if ((rc = h->unsat.alloc(sizeof(int) * nib))) return rc;
+  if ((rc = h->frozen.alloc(nib))) return rc;
+  if ((rc = h->solved.alloc(sizeof(int) * h->n_inst))) return rc;
+  if ((rc = h->col.alloc(sizeof(int) * h->n_inst))) return rc;
+  if ((rc = h->assign.alloc(static_cast<size_t>(h->n)))) return rc;
+  CK(cudaMemsetAsync(h->unsat.p, 0, h->unsat.bytes, s));
+  CK(cudaMemsetAsync(h->frozen.p, 0, h->frozen.bytes, s));
+  CK(cudaMemsetAsync(h->solved.p, 0x7f, h->solved.bytes, s));
+  if (x0_dev) {
+    launch_convert_in(x0_dev, XT_F32, B, h->x.p, h->xt, h->pitch, h->n, B, s);
+  } else {
+    launch_init_philox(h->x.p, h->xt, h->pitch, h->n, B, h->var_inst.as<int>(), seed, s);
+  }
+  CKL();
+  if (h->p.chunk > 0) {
+    h->Bc = std::min<int>(((h->p.chunk + 31) / 32) * 32, static_cast<int>(h->pitch));
+  } else {
+    h->Bc = default_chunk(h);
+  }
+  if ((rc = alloc_go(h, h->Bc))) return rc;
+  if (h->p.autotune) {
+    if ((rc = autotune(h, s))) return rc;
+    if (h->p.chunk > 0) h->Bc = std::min<int>(((h->p.chunk + 31) / 32) * 32, static_cast<int>(h->pitch));
+    if ((rc = alloc_go(h, h->Bc))) return rc;
+  }
+  // the solved flags start clear: the autotuner does not run the exact check
+  CK(cudaMemsetAsync(h->solved.p, 0x7f, h->solved.bytes, s));
+  return AFS_OK;
+}
+
+int afs_step(afs_handle* h, int32_t nsteps, void* stream) {
+  if (!h) return fail(AFS_E_ARG, "NULL handle");
+  if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
+  if (nsteps < 0) return fail(AFS_E_ARG, "nsteps must be >= 0");
+  if (nsteps == 0) return AFS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!h->p.use_graph) {
+    int rc = enqueue_steps(h, nsteps, h->p.eta, true, s, &h->last_launches);
+    if (rc) return rc;
+    if (h->timing) collect_timing(h);
+    return AFS_OK;
+  }
+  // With kernel timing on, the captured graph also carries event-record nodes
+  // around the FE and CSR launches of every chunk; it is cached separately.
+  auto& cache = h->timing ? h->timed_graphs : h->graphs;
+  auto it = cache.find(nsteps);
+  long long nl = 0;
+  if (it == cache.end()) {
+    cudaGraph_t graph;
+    const size_t fe0 = h->fe_pairs.size(), cs0 = h->csr_pairs.size();
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_steps(h, nsteps, h->p.eta, true, h->cap, &nl);
+    cudaError_t ce = cudaStreamEndCapture(h->cap, &graph);
+    if (rc) return rc;
+    if (ce != cudaSuccess) return fail(AFS_E_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+    cudaGraphExec_t exec;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(AFS_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    if (h->timing) {
+      h->timed_pairs[nsteps] = {std::vector<std::pair<int, int>>(h->fe_pairs.begin() + fe0, h->fe_pairs.end()),
+                                std::vector<std::pair<int, int>>(h->csr_pairs.begin() + cs0, h->csr_pairs.end())};
+      h->fe_pairs.resize(fe0);
+      h->csr_pairs.resize(cs0);
+    }
+    it = cache.emplace(nsteps, exec).first;
+  } else {
+    const int chunks = (h->B + h->Bc - 1) / h->Bc;
+    nl = static_cast<long long>(nsteps) * chunks * (static_cast<long long>(h->groups.size()) + 1);
+    if (h->p.verify_every > 0) nl += 2LL * ((nsteps / h->p.verify_every) + (nsteps % h->p.verify_every ? 1 : 0));
+  }
+  h->last_launches = nl;
+  CK(cudaGraphLaunch(it->second, s));
+  if (h->timing) {
+    auto& pr = h->timed_pairs[nsteps];
+    h->fe_pairs.insert(h->fe_pairs.end(), pr.first.begin(), pr.first.end());
+    h->csr_pairs.insert(h->csr_pairs.end(), pr.second.begin(), pr.second.end());
+    CK(cudaStreamSynchronize(s));
+    collect_timing(h);
+  }
+  return AFS_OK;
+}
+
+static int host_unsat(const afs_handle* h, int inst, const int8_t* assign_all) {
+  int cnt = 0;
+  for (int c = h->inst_cbegin[inst]; c < h->inst_cbegin[inst + 1]; ++c) {
+    int t = 0;
+    for (int l = h->h_lit_off[c]; l < h->h_lit_off[c + 1]; ++l) {
+      const int enc = h->h_lit_enc[l];
+      const int val = assign_all[enc >> 1];  // -1 = True, +1 = False
+      const bool neg = (enc & 1) != 0;
+      const bool lit_true = neg ? (val > 0) : (val < 0);
+      t += lit_true ? 1 : 0;
+    }
+    cnt += h->h_viol[h->h_viol_off[c] + t] ? 1 : 0;
+  }
+  return cnt;
+}
+
+int afs_round_and_verify(afs_handle* h, int32_t* unsat_host, int32_t* best_host, int8_t* assign_host,
+                         int32_t* solved_host, void* stream) {
+  if (!h) return fail(AFS_E_ARG, "NULL handle");
+  if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(h->solved.p, 0x7f, h->solved.bytes, s));
+  int rc = launch_check(h, false, s);
+  if (rc) return rc;
+  const size_t nib = static_cast<size_t>(h->n_inst) * h->B;
+  std::vector<int> un(nib);
+  CK(cudaMemcpyAsync(un.data(), h->unsat.p, nib * sizeof(int), cudaMemcpyDeviceToHost, s));
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (err != 0) return fail(AFS_E_TIMEOUT, "a bounded device wait gave up (code %d)", err);
+  std::vector<int> best(h->n_inst);
+  for (int i = 0; i < h->n_inst; ++i) {
+    int bi = 0;
+    for (int b = 1; b < h->B; ++b)
+      if (un[static_cast<size_t>(i) * h->B + b] < un[static_cast<size_t>(i) * h->B + bi]) bi = b;
+    best[i] = bi;
+  }
+  CK(cudaMemcpyAsync(h->col.p, best.data(), sizeof(int) * h->n_inst, cudaMemcpyHostToDevice, s));
+  launch_gather_column(h->x.p, h->xt, h->pitch, h->var_inst.as<int>(), h->n, h->col.as<int>(),
+                       h->assign.as<signed char>(), s);
+  CKL();
+  std::vector<int8_t> asg(h->n);
+  CK(cudaMemcpyAsync(asg.data(), h->assign.p, h->n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int i = 0; i < h->n_inst; ++i) {
+    const int dev_count = un[static_cast<size_t>(i) * h->B + best[i]];
+    const int host_count = host_unsat(h, i, asg.data());
+    if (dev_count != host_count)
+      return fail(AFS_E_VERIFY, "instance %d restart %d: device counts %d violated, host re-check %d", i, best[i],
+                  dev_count, host_count);
+  }
+  if (unsat_host) std::memcpy(unsat_host, un.data(), nib * sizeof(int));
+  if (best_host) std::memcpy(best_host, best.data(), sizeof(int) * h->n_inst);
+  if (assign_host) std::memcpy(assign_host, asg.data(), h->n);
+  if (solved_host)
+    for (int i = 0; i < h->n_inst; ++i) solved_host[i] = un[static_cast<size_t>(i) * h->B + best[i]] == 0 ? 1 : 0;
+  return AFS_OK;
+}
+
+int afs_get_x(afs_handle* h, float* x_dev, void* stream) {
+  if (!h || !x_dev) return fail(AFS_E_ARG, "NULL argument");
+  if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
+  launch_convert_in(h->x.p, h->xt, h->pitch, x_dev, XT_F32, h->B, h->n, h->B, static_cast<cudaStream_t>(stream));
+  CKL();
+  return AFS_OK;
+}
+
+int afs_set_x(afs_handle* h, const float* x_dev, void* stream) {
+  if (!h || !x_dev) return fail(AFS_E_ARG, "NULL argument");
+  if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
+  launch_convert_in(x_dev, XT_F32, h->B, h->x.p, h->xt, h->pitch, h->n, h->B, static_cast<cudaStream_t>(stream));
+  CKL();
+  return AFS_OK;
+}
+
+int afs_get_verify(afs_handle* h, int32_t* unsat_dev, int32_t* solved_dev, void* stream) {
+  if (!h) return fail(AFS_E_ARG, "NULL handle");
+  if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (unsat_dev)
+    CK(cudaMemcpyAsync(unsat_dev, h->unsat.p, sizeof(int) * static_cast<size_t>(h->n_inst) * h->B,
+                       cudaMemcpyDeviceToDevice, s));
+  if (solved_dev) CK(cudaMemcpyAsync(solved_dev, h->solved.p, sizeof(int) * h->n_inst, cudaMemcpyDeviceToDevice, s));
+  return AFS_OK;
+}
+
+int afs_eval_fe_grad(afs_handle* h, const void* x_dev, int32_t x_dtype, int32_t B, float* fe_dev, float* grad_dev,
+                     void* stream) {
+  if (!h || !x_dev) return fail(AFS_E_ARG, "NULL argument");
+  if (B <= 0) return fail(AFS_E_ARG, "B must be positive");
+  if (x_dtype != AFS_X_F32 && x_dtype != AFS_X_BF16) return fail(AFS_E_ARG, "unknown x dtype");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int xt = x_dtype == AFS_X_BF16 ? XT_BF16 : XT_F32;
+  const int cols = std::min<int>((B + 31) / 32 * 32, 256);
+  const size_t need = sizeof(float) * static_cast<size_t>(std::max<long long>(h->L, 1)) * cols;
+  if (h->eval_go.bytes < need) {
+    int rc = h->eval_go.alloc(need);
+    if (rc) return rc;
+  }
+  for (int b0 = 0; b0 < B; b0 += cols) {
+    const int nb = std::min(cols, B - b0);
+    for (const Group& g : h->groups) {
+      int rc = launch_fe_group(h, g, x_dev, xt, B, b0, nb, h->eval_go.as<float>(), cols, fe_dev, B, s);
+      if (rc) return rc;
+    }
+    if (grad_dev) {
+      int rc = launch_csr(h, nullptr, xt, B, b0, nb, h->eval_go.as<float>(), cols, 0.0f, grad_dev, B, false, s);
+      if (rc) return rc;
+    }
+  }
+  return AFS_OK;
+}
+
+int afs_step_host(afs_handle* h, const float* x_host, float* x_out_host, int32_t* unsat_host, void* stream) {
+  if (!h || !x_host || !unsat_host) return fail(AFS_E_ARG, "NULL argument");
+  if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t nb = sizeof(float) * static_cast<size_t>(h->n) * h->B;
+  if (h->stage.bytes < nb) {
+    int rc = h->stage.alloc(nb);
+    if (rc) return rc;
+  }
+  CK(cudaMemcpyAsync(h->stage.p, x_host, nb, cudaMemcpyHostToDevice, s));
+  launch_convert_in(h->stage.p, XT_F32, h->B, h->x.p, h->xt, h->pitch, h->n, h->B, s);
+  CKL();
+  const int ve = h->p.verify_every;
+  if (ve <= 0) h->p.verify_every = 1;
+  int rc = afs_step(h, 1, stream);
+  h->p.verify_every = ve;
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(unsat_host, h->unsat.p, sizeof(int) * static_cast<size_t>(h->n_inst) * h->B,
+                     cudaMemcpyDeviceToHost, s));
+  if (x_out_host) {
+    launch_convert_in(h->x.p, h->xt, h->pitch, h->stage.p, XT_F32, h->B, h->n, h->B, s);
+    CKL();
+    CK(cudaMemcpyAsync(x_out_host, h->stage.p, nb, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  return AFS_OK;
+}
+
+int afs_info(const afs_handle* h, int64_t* out6) {
+  if (!h || !out6) return fail(AFS_E_ARG, "NULL argument");
+  out6[0] = h->n;
+  out6[1] = h->m;
+  out6[2] = h->L;
+  out6[3] = h->n_inst;
+  out6[4] = h->B;
+  out6[5] = static_cast<int64_t>(h->groups.size());
+  return AFS_OK;
+}
+
+int afs_work_per_restart(const afs_handle* h, double* instr) {
+  if (!h || !instr) return fail(AFS_E_ARG, "NULL argument");
+  *instr = h->work_per_restart;
+  return AFS_OK;
+}
+
+int afs_set_kernel_timing(afs_handle* h, int32_t enable) {
+  if (!h) return fail(AFS_E_ARG, "NULL handle");
+  h->timing = enable != 0;
+  h->fe_ms = h->csr_ms = 0;
+  h->fe_n = h->csr_n = 0;
+  h->fe_pairs.clear();
+  h->csr_pairs.clear();
+  return AFS_OK;
+}
+
+int afs_kernel_timing(afs_handle* h, double* fe_ms_total, int64_t* fe_launches, double* csr_ms_total,
+                      int64_t* csr_launches) {
+  if (!h) return fail(AFS_E_ARG, "NULL handle");
+  collect_timing(h);
+  if (fe_ms_total) *fe_ms_total = h->fe_ms;
+  if (fe_launches) *fe_launches = h->fe_n;
+  if (csr_ms_total) *csr_ms_total = h->csr_ms;
+  if (csr_launches) *csr_launches = h->csr_n;
+  return AFS_OK;
+}
+
+int afs_last_launch_count(const afs_handle* h, int64_t* launches) {
+  if (!h || !launches) return fail(AFS_E_ARG, "NULL argument");
+  *launches = h->last_launches;
+  return AFS_OK;
+}
+
+int afs_tuning(const afs_handle* h, int32_t* chunk, int32_t* rpl_by_k, int32_t kcap) {
+  if (!h) return fail(AFS_E_ARG, "NULL handle");
+  if (chunk) *chunk = h->Bc;
+  if (rpl_by_k) {
+    for (int k = 0; k < kcap; ++k) rpl_by_k[k] = 0;
+    for (const Group& g : h->groups)
+      if (!g.is_long && g.k < kcap) rpl_by_k[g.k] = g.rpl;
+  }
+  return AFS_OK;
+}
+
+int afs_coef_table(int32_t type, int32_t k, int32_t op, int32_t param, int32_t parity, int32_t basis, int32_t form,
+                   float* out, int32_t cap, int32_t* len) {
+  if (!len) return fail(AFS_E_ARG, "len is NULL");
+  if (type < 0 || type > AFS_CARD) return fail(AFS_E_TYPE, "unknown type");
+  if (k <= 0 || k > AFS_MAX_LEN) return fail(AFS_E_LEN, "bad length");
+  if (basis != 0 && basis != 1) return fail(AFS_E_ARG, "unknown basis");
+  Shape sh{type, k, type == AFS_CARD ? op : 0, (type == AFS_CARD || type == AFS_EK) ? param : 0,
+           type == AFS_XOR ? (parity ? 1 : 0) : 0};
+  std::vector<float> t;
+  build_table(sh, basis, form ? FORM_LONG : FORM_SHORT, t);
+  *len = static_cast<int32_t>(t.size());
+  if (out) std::memcpy(out, t.data(), sizeof(float) * std::min<size_t>(t.size(), cap > 0 ? cap : 0));
+  return AFS_OK;
+}
+
+int afs_esp_coefficients(int32_t type, int32_t k, int32_t op, int32_t param, int32_t parity, double* out) {
+  if (!out) return fail(AFS_E_ARG, "out is NULL");
+  if (type < 0 || type > AFS_CARD) return fail(AFS_E_TYPE, "unknown type");
+  if (k <= 0 || k > AFS_MAX_LEN) return fail(AFS_E_LEN, "bad length");
+  Shape sh{type, k, type == AFS_CARD ? op : 0, (type == AFS_CARD || type == AFS_EK) ? param : 0,
+           type == AFS_XOR ? (parity ? 1 : 0) : 0};
+  std::vector<double> c;
+  esp_coefficients(sh, c);
+  std::memcpy(out, c.data(), sizeof(double) * c.size());
+  return AFS_OK;
+}
+
+const char* afs_last_error(void) { return g_err.c_str(); }
+const char* afs_version(void) { return "afsat-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,314 @@
+"""GPU parity of the CUDA path against the FP64 CPU oracle (through the C ABI).
+
+Tolerances (FP32 arithmetic against FP64): an expansion value must lie within
+1e-5 * max(1, |FE_ref|) of the oracle; a variable's gradient within
+1e-5 * max(1, sum over its occurrences of |s_i dFE/dl_i|). With BF16 storage
+of x the arithmetic is checked at the dequantised point against the same 1e-5
+and the end-to-end value at the original FP32 point against 2e-2. Integer
+work (unsat counts, sign rounding, the counter-based starting points) must be
+bit-exact.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import fe_oracle as O
+from paper_2606_06641_gb300 import binding as bd
+from paper_2606_06641_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_06641_gb300 import build
+    build.build()
+    yield
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _grad_scale(inst, go_ref):
+    var = np.abs(inst.lits) - 1
+    acc = np.zeros((inst.n, go_ref.shape[1]))
+    np.add.at(acc, var, np.abs(go_ref))
+    return np.maximum(1.0, acc)
+
+
+def _check_eval(inst, x, params=None, tol=TOL, x_dtype=torch.float32, x_ref=None):
+    h = bd.load_instance(inst, params)
+    xd = _dev(x, x_dtype)
+    fe, g = bd.eval_fe_grad(h, xd)
+    torch.cuda.synchronize()
+    xr = x if x_ref is None else x_ref
+    fe_ref, go_ref, g_ref = O.evaluate(inst, xr.astype(np.float64))
+    fe = fe.cpu().numpy()
+    g = g.cpu().numpy()
+    fe_err = np.abs(fe - fe_ref) / np.maximum(1.0, np.abs(fe_ref))
+    g_err = np.abs(g - g_ref) / _grad_scale(inst, go_ref)
+    assert fe_err.max() <= tol, f"FE error {fe_err.max():.3e}"
+    assert g_err.max() <= tol, f"gradient error {g_err.max():.3e}"
+    return fe_err.max(), g_err.max()
+
+
+# ---- expansion and gradient ------------------------------------------------
+@pytest.mark.parametrize("idx", range(4))
+def test_mixed_types_eval(idx):
+    inst = synth.mixed_small(idx, n=60, m=120, kmax=12)
+    for B, gen in ((37, synth.uniform_x0), (70, synth.near_vertex_x0), (5, synth.vertex_x0)):
+        _check_eval(inst, gen(inst.n, B, idx))
+
+
+@pytest.mark.parametrize("k", list(range(1, 33)))
+def test_every_short_length(k):
+    """All 32 register-kernel lengths, several types, ragged restart counts."""
+    for t, op, r, par in ((synth.OR, 0, 0, 1), (synth.XOR, 0, 0, k % 2), (synth.CARD, synth.GE, (k + 1) // 2, 1),
+                          (synth.EK, 0, k // 3, 1), (synth.NAE, 0, 0, 1)):
+        inst = synth.single_type(t, k, 9, max(2 * k, 12), index=k, op=op, param=r, parity=par)
+        _check_eval(inst, synth.uniform_x0(inst.n, 45, k))
+
+
+@pytest.mark.parametrize("k", [33, 40, 63, 64, 65, 100, 128, 255, 256, 512, 1024])
+def test_long_lengths(k):
+    for t, op, r in ((synth.CARD, synth.GE, k // 2), (synth.EK, 0, k // 3), (synth.AMO, 0, 0),
+                     (synth.CARD, synth.LT, 3 * k // 4)):
+        inst = synth.single_type(t, k, 3, k + 7, index=k, op=op, param=r)
+        _check_eval(inst, synth.uniform_x0(inst.n, 19, k))
+        _check_eval(inst, synth.near_vertex_x0(inst.n, 11, k, spread=0.02))
+
+
+def test_mixed_short_and_long_in_one_instance():
+    inst = synth.config3(0, n=2000, n_clauses=3000, n_long=12, kmin=33, kmax=300)
+    _check_eval(inst, synth.uniform_x0(inst.n, 41, 3))
+
+
+def test_duplicate_and_complementary_literals():
+    """Repeated variables are independent literals on both sides."""
+    b = synth._Builder(6)
+    b.add(synth.OR, [1, 1, 2])
+    b.add(synth.XOR, [3, -3, 4, 5], parity=0)
+    b.add(synth.CARD, [1, -1, 2, 2, 6] * 8, synth.GE, 17)
+    _check_eval(b.build(), synth.uniform_x0(6, 33, 1))
+
+
+def test_bf16_storage_variant():
+    inst = synth.mixed_small(7, n=50, m=90, kmax=20)
+    x = synth.uniform_x0(inst.n, 64, 3)
+    xb = torch.from_numpy(x).to(torch.bfloat16)
+    x_deq = xb.to(torch.float32).numpy()
+    # arithmetic at the dequantised point
+    _check_eval(inst, x_deq, x_dtype=torch.bfloat16, x_ref=x_deq)
+    # end to end against the original FP32 point
+    _check_eval(inst, x_deq, x_dtype=torch.bfloat16, x_ref=x, tol=2e-2)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 8, 12])
+def test_esp_basis_short(k):
+    """The paper's elementary-symmetric basis is accurate for short constraints."""
+    p = bd.default_params(basis=bd.BASIS_ESP)
+    inst = synth.single_type(synth.CARD, k, 7, 2 * k + 3, index=k, op=synth.GE, param=(k + 1) // 2)
+    _check_eval(inst, synth.uniform_x0(inst.n, 33, k), params=p, tol=5e-5)
+
+
+def test_esp_basis_long_runs_and_degrades():
+    """Long constraints in the paper's basis: scaled products keep every value
+    finite up to k = 100 (no FP32 overflow), while cancellation makes the
+    error grow with k, as the paper's floating-point section describes."""
+    p = bd.default_params(basis=bd.BASIS_ESP)
+    errs = {}
+    for k in (40, 100):
+        inst = synth.single_type(synth.CARD, k, 2, k + 3, index=k, op=synth.GE, param=k // 2)
+        x = synth.uniform_x0(inst.n, 16, k)
+        h = bd.load_instance(inst, p)
+        fe, g = bd.eval_fe_grad(h, _dev(x))
+        fe = fe.cpu().numpy()
+        ref, _, _ = O.evaluate(inst, x.astype(np.float64))
+        errs[k] = np.nanmax(np.abs(fe - ref))
+        if k == 40:
+            assert np.all(np.isfinite(fe))
+    assert errs[100] > errs[40]
+
+
+# ---- exact check ------------------------------------------------------------
+@pytest.mark.parametrize("idx", range(3))
+def test_unsat_counts_bit_exact(idx):
+    inst = synth.mixed_small(idx + 10, n=40, m=150, kmax=40)
+    for B, x in ((50, synth.uniform_x0(inst.n, 50, idx)), (33, synth.vertex_x0(inst.n, 33, idx))):
+        x = x.copy()
+        x[0, :5] = 0.0
+        x[1, :5] = -0.0
+        h = bd.load_instance(inst)
+        bd.init_restarts(h, B, x0=_dev(x))
+        un, best, asg, sol = bd.round_and_verify(h)
+        ref = O.unsat_count(inst, x)
+        np.testing.assert_array_equal(un[0], ref)
+        assert best[0] == int(np.argmin(ref))
+        np.testing.assert_array_equal(asg, O.round_signs(x[:, best[0]]))
+        assert sol[0] == int(ref.min() == 0)
+
+
+def test_philox_starting_points_bit_exact():
+    inst = synth.config1(3)
+    h = bd.load_instance(inst)
+    bd.init_restarts(h, 37, seed=0x1234_5678_9ABC)
+    x = bd.get_x(h).cpu().numpy()
+    np.testing.assert_array_equal(x, O.philox_uniform_x0(0x1234_5678_9ABC, inst.n, 37))
+
+
+def test_batch_starting_points_and_counts_per_instance():
+    insts = [synth.config1(i) for i in range(3)] + [synth.mixed_small(5, n=30, m=40, kmax=9)]
+    h = bd.load_batch(insts)
+    B = 24
+    bd.init_restarts(h, B, seed=99)
+    x = bd.get_x(h).cpu().numpy()
+    un, best, asg, sol = bd.round_and_verify(h)
+    v0 = 0
+    for i, inst in enumerate(insts):
+        xi = x[v0:v0 + inst.n]
+        np.testing.assert_array_equal(xi, O.philox_uniform_x0(99, inst.n, B, stream=i))
+        np.testing.assert_array_equal(un[i], O.unsat_count(inst, xi))
+        v0 += inst.n
+
+
+# ---- descent steps ---------------------------------------------------------
+@pytest.mark.parametrize("graph", [0, 1])
+def test_few_steps_match_oracle(graph):
+    inst = synth.mixed_small(21, n=50, m=100, kmax=24)
+    x0 = synth.uniform_x0(inst.n, 40, 8)
+    eta = 0.05
+    p = bd.default_params(eta=eta, use_graph=graph, autotune=1)
+    h = bd.load_instance(inst, p)
+    bd.init_restarts(h, 40, x0=_dev(x0))
+    x = x0.astype(np.float64)
+    for t in range(3):
+        bd.step(h, 1)
+        x = O.pgd_step(inst, x, eta)
+        got = bd.get_x(h).cpu().numpy()
+        assert np.abs(got - x).max() <= 4 * TOL * (t + 1), np.abs(got - x).max()
+        un, _ = bd.get_verify(h)
+        np.testing.assert_array_equal(un.cpu().numpy()[0], O.unsat_count(inst, got))
+
+
+def test_chunked_step_equals_single_chunk():
+    """Restart chunks only change the launch shape, not the arithmetic."""
+    inst = synth.config2(1)
+    x0 = synth.uniform_x0(inst.n, 200, 4)
+    outs = []
+    for chunk in (32, 96, 256):
+        p = bd.default_params(eta=0.1, chunk=chunk, autotune=0)
+        h = bd.load_instance(inst, p)
+        bd.init_restarts(h, 200, x0=_dev(x0))
+        bd.step(h, 2)
+        outs.append(bd.get_x(h).cpu().numpy())
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+
+
+def test_config2_full_size_sampled():
+    """The hybrid n=2000 instance at B=1024 in the launch configuration of the
+    benchmark (autotuned tiles and chunk, graph replay): one step checked on
+    sampled restarts against the oracle, unsat counts for every restart."""
+    inst = synth.config2(0)
+    B = 1024
+    eta = 0.1
+    x0 = synth.uniform_x0(inst.n, B, 11)
+    h = bd.load_instance(inst, bd.default_params(eta=eta))
+    bd.init_restarts(h, B, x0=_dev(x0))
+    bd.step(h, 1)
+    x1 = bd.get_x(h).cpu().numpy()
+    un, _ = bd.get_verify(h)
+    np.testing.assert_array_equal(un.cpu().numpy()[0], O.unsat_count(inst, x1))
+    cols = np.array([0, 1, 31, 32, 255, 256, 511, 777, 1000, 1023])
+    ref = O.pgd_step(inst, x0[:, cols].astype(np.float64), eta)
+    assert np.abs(x1[:, cols] - ref).max() <= eta * 2 * TOL
+    fe, g = bd.eval_fe_grad(h, _dev(x0[:, cols]))
+    fe_ref, go_ref, g_ref = O.evaluate(inst, x0[:, cols].astype(np.float64))
+    assert np.abs(fe.cpu().numpy() - fe_ref).max() <= TOL
+    assert (np.abs(g.cpu().numpy() - g_ref) / _grad_scale(inst, go_ref)).max() <= TOL
+
+
+# ---- solver behaviour and edge cases ---------------------------------------
+def test_never_reports_sat_on_unsat_instances():
+    seen = {True: 0, False: 0}
+    for idx in range(10):
+        inst = synth.random_ksat(14, 70, 3, synth.rng_for(300, idx))
+        sat, _ = O.exhaustive_sat(inst)
+        seen[sat] += 1
+        h = bd.load_instance(inst, bd.default_params(eta=0.2))
+        bd.init_restarts(h, 64, seed=idx)
+        bd.step(h, 100)
+        un, best, asg, sol = bd.round_and_verify(h)
+        if not sat:
+            assert sol[0] == 0 and un.min() > 0
+        if sol[0]:
+            assert O.unsat_count(inst, asg.astype(np.float32)[:, None])[0] == 0
+    assert seen[True] > 0 and seen[False] > 0
+
+
+def test_solved_restarts_are_frozen():
+    inst = synth.random_ksat(20, 60, 3, synth.rng_for(301, 0))
+    h = bd.load_instance(inst, bd.default_params(eta=0.2))
+    bd.init_restarts(h, 32, seed=5)
+    bd.step(h, 200)
+    un, sol = bd.get_verify(h)
+    x_a = bd.get_x(h).cpu().numpy()
+    bd.step(h, 20)
+    x_b = bd.get_x(h).cpu().numpy()
+    solved = un.cpu().numpy()[0] == 0
+    assert solved.any()
+    np.testing.assert_array_equal(x_a[:, solved], x_b[:, solved])
+    assert sol.cpu().numpy()[0] == int(np.nonzero(solved)[0][0])
+
+
+def test_single_restart_and_single_literal():
+    b = synth._Builder(3)
+    b.add(synth.OR, [1])
+    b.add(synth.CARD, [-2], synth.LT, 1)
+    b.add(synth.XOR, [3], parity=0)
+    inst = b.build()
+    _check_eval(inst, synth.uniform_x0(3, 1, 0))
+
+
+def test_empty_constraint_set():
+    b = synth._Builder(4)
+    inst = b.build()
+    h = bd.load_instance(inst)
+    bd.init_restarts(h, 8, seed=1)
+    x0 = bd.get_x(h).cpu().numpy()
+    bd.step(h, 3)
+    np.testing.assert_array_equal(bd.get_x(h).cpu().numpy(), x0)
+    un, best, asg, sol = bd.round_and_verify(h)
+    assert sol[0] == 1 and un.max() == 0
+
+
+def test_step_before_init_is_an_error():
+    h = bd.load_instance(synth.config1(0))
+    with pytest.raises(bd.AfsError) as ei:
+        bd.step(h, 1)
+    assert ei.value.code == -8
+
+
+def test_step_host_matches_device_step():
+    inst = synth.config1(2)
+    B = 64
+    x0 = synth.uniform_x0(inst.n, B, 9)
+    p = bd.default_params(eta=0.1)
+    h1 = bd.load_instance(inst, p)
+    bd.init_restarts(h1, B, x0=_dev(x0))
+    bd.step(h1, 1)
+    x_dev = bd.get_x(h1).cpu().numpy()
+    un_dev, _ = bd.get_verify(h1)
+    h2 = bd.load_instance(inst, p)
+    bd.init_restarts(h2, B, seed=0)
+    xh = torch.from_numpy(x0).pin_memory()
+    xo = torch.empty_like(xh).pin_memory()
+    un = bd.step_host(h2, xh, xo)
+    np.testing.assert_array_equal(xo.numpy(), x_dev)
+    np.testing.assert_array_equal(un.numpy(), un_dev.cpu().numpy())

@@ -1,0 +1,194 @@
+"""CPU tests of the C-ABI library's host logic (no device work).
+
+The library must load and export every symbol that include/afsat.h declares;
+its load-time coefficient tables, evaluated here in FP64 exactly as the
+kernels combine them, must reproduce the oracle's expansion and gradient; its
+exact-integer ESP coefficients must equal the Walsh coefficients computed from
+their definition; and malformed records must be rejected before any CUDA call.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import fe_oracle as O
+from paper_2606_06641_gb300 import binding as bd
+from paper_2606_06641_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built_library():
+    from paper_2606_06641_gb300 import build
+    build.build()
+    yield
+
+
+def _header_symbols():
+    txt = open(os.path.join(ROOT, "include", "afsat.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(afs_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    syms = _header_symbols()
+    assert len(syms) >= 20
+    lib = bd.lib()
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) == set(bd.SIGNATURES), set(syms) ^ set(bd.SIGNATURES)
+    assert "sm_103a" in bd.version()
+
+
+def _eval_short(tab, k, esp, ell):
+    """FE and dFE/dl for ell[B, k] from a short-form table, in float64."""
+    t = tab.astype(np.float64).reshape(-1, 4)
+    fe = np.full(ell.shape[0], t[0, 0])
+    grad = np.zeros_like(ell)
+    nreal = (k & 1) + (1 if esp else 0)
+    for q in range(nreal):
+        alpha, E = t[1 + q, 0], t[1 + q, 1]
+        f = ell + alpha
+        fe += E * f.prod(axis=1)
+        for i in range(k):
+            grad[:, i] += E * np.delete(f, i, axis=1).prod(axis=1)
+    for j in range(k // 2):
+        alpha, gam, er, ei = t[1 + nreal + j]
+        E = er + 1j * ei
+        f = ell + alpha + 1j * gam
+        fe += np.real(E * f.prod(axis=1))
+        for i in range(k):
+            grad[:, i] += np.real(E * np.delete(f, i, axis=1).prod(axis=1))
+    return fe, grad
+
+
+def _eval_long(tab, k, esp, ell):
+    t = tab.astype(np.float64).reshape(-1, 4)
+    fe = np.full(ell.shape[0], t[0, 0])
+    grad = np.zeros_like(ell)
+    nroots = k // 2 + (k & 1) + (1 if esp else 0)
+    for j in range(nroots):
+        ar, ai, br, bi = t[1 + 2 * j]
+        dr, di, er, ei = t[2 + 2 * j]
+        f = (ar + 1j * ai) + (br + 1j * bi) * ell
+        fe += np.real((er + 1j * ei) * f.prod(axis=1))
+        for i in range(k):
+            grad[:, i] += np.real((dr + 1j * di) * np.delete(f, i, axis=1).prod(axis=1))
+    return fe, grad
+
+
+def _shapes(k):
+    out = [(O.T_OR, 0, 0, 1), (O.T_XOR, 0, 0, 1), (O.T_XOR, 0, 0, 0), (O.T_NAE, 0, 0, 1), (O.T_AMO, 0, 0, 1),
+           (O.T_EO, 0, 0, 1)]
+    for r in sorted({0, 1, k // 2, k}):
+        out += [(O.T_EK, 0, r, 1), (O.T_CARD, O.OP_GE, r, 1), (O.T_CARD, O.OP_LT, r, 1)]
+    return out
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 8, 13, 20, 32])
+def test_short_pgf_table_reproduces_oracle(k):
+    rng = np.random.default_rng(k)
+    ell = np.concatenate([rng.uniform(-1, 1, (5, k)), np.sign(rng.uniform(-1, 1, (2, k)))])
+    for (ct, op, r, par) in _shapes(k):
+        tab = bd.coef_table(ct, k, op, r, par, basis=bd.BASIS_PGF, form=0)
+        f = O.truth_table(ct, k, op, r, par)
+        fe, g = _eval_short(tab, k, False, ell)
+        ref_fe, ref_g = O.fe_and_dfe(f, ell)
+        np.testing.assert_allclose(fe, ref_fe, atol=2e-6, rtol=0)
+        np.testing.assert_allclose(g, ref_g, atol=2e-6, rtol=0)
+
+
+@pytest.mark.parametrize("k", [1, 3, 33, 64, 101])
+def test_long_pgf_table_reproduces_oracle(k):
+    rng = np.random.default_rng(50 + k)
+    ell = rng.uniform(-1, 1, (3, k))
+    for (ct, op, r, par) in _shapes(k)[:7]:
+        tab = bd.coef_table(ct, k, op, r, par, basis=bd.BASIS_PGF, form=1)
+        f = O.truth_table(ct, k, op, r, par)
+        fe, g = _eval_long(tab, k, False, ell)
+        ref_fe, ref_g = O.fe_and_dfe(f, ell)
+        np.testing.assert_allclose(fe, ref_fe, atol=5e-6, rtol=0)
+        np.testing.assert_allclose(g, ref_g, atol=5e-6, rtol=0)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 6, 9, 12])
+def test_esp_tables_reproduce_oracle_at_small_k(k):
+    """The paper's basis: prod (1 + w^j l) combined with the DFT of f_hat(|S|=d)."""
+    rng = np.random.default_rng(90 + k)
+    ell = rng.uniform(-1, 1, (4, k))
+    for (ct, op, r, par) in _shapes(k):
+        f = O.truth_table(ct, k, op, r, par)
+        ref_fe, ref_g = O.fe_and_dfe(f, ell)
+        for form, ev in ((0, _eval_short), (1, _eval_long)):
+            tab = bd.coef_table(ct, k, op, r, par, basis=bd.BASIS_ESP, form=form)
+            fe, g = ev(tab, k, True, ell)
+            np.testing.assert_allclose(fe, ref_fe, atol=2e-5, rtol=0)
+            np.testing.assert_allclose(g, ref_g, atol=2e-5, rtol=0)
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 8, 10])
+def test_esp_coefficients_equal_walsh_definition(k):
+    for (ct, op, r, par) in _shapes(k):
+        f = O.truth_table(ct, k, op, r, par)
+        fhat = O.walsh_coefficients(f)
+        c = bd.esp_coefficients(ct, k, op, r, par)
+        masks = np.arange(1 << k)
+        sizes = np.array([bin(mm).count("1") for mm in masks])
+        for d in range(k + 1):
+            np.testing.assert_allclose(fhat[sizes == d], c[d], atol=1e-15)
+
+
+def test_esp_coefficients_exact_at_large_k():
+    """f_hat(|S| = d) of odd parity is 1 at d = k and 0 elsewhere; of CARD >= 1
+    (OR) it is 2^(1-k) for d >= 1 and 2^(1-k) - 1 at d = 0 - exact at any k."""
+    for k in (40, 127, 300):
+        c = bd.esp_coefficients(O.T_XOR, k, 0, 0, 1)
+        want = np.zeros(k + 1)
+        want[k] = 1.0
+        np.testing.assert_array_equal(c, want)
+        c = bd.esp_coefficients(O.T_OR, k)
+        want = np.full(k + 1, 2.0 ** (1 - k))
+        want[0] -= 1.0
+        np.testing.assert_array_equal(c, want)
+
+
+def test_pgf_table_has_exact_conjugate_roots():
+    """Short-form gamma_j = cot(pi j/(k+1)) and the mirrored middle root of an
+    odd length has a purely real weight."""
+    for k in (5, 9, 31):
+        t = bd.coef_table(O.T_CARD, k, O.OP_GE, k // 2).reshape(-1, 4)
+        gam = t[2:, 1]
+        want = 1.0 / np.tan(np.pi * np.arange(1, k // 2 + 1) / (k + 1))
+        np.testing.assert_allclose(gam, want.astype(np.float32), rtol=2e-7)
+        assert t[1, 0] == 0.0 and t[1, 2] == 0.0 and t[1, 3] == 0.0
+
+
+def _bad(inst_kw):
+    b = synth._Builder(5)
+    for rec in inst_kw:
+        b.add(*rec)
+    return b.build()
+
+
+@pytest.mark.parametrize("records,code", [
+    ([(synth.OR, [1, 2, 6])], -2),       # variable beyond n
+    ([(synth.OR, [1, 0, 2])], -2),       # literal zero
+    ([(synth.OR, [])], -3),              # empty constraint
+    ([(9, [1, 2])], -4),                 # unknown type
+    ([(synth.CARD, [1, 2], 7, 1)], -4),  # unknown CARD operator
+])
+def test_invalid_records_rejected_before_device_work(records, code):
+    inst = _bad(records)
+    with pytest.raises(bd.AfsError) as ei:
+        bd.load_instance(inst, stream=0)
+    assert ei.value.code == code
+
+
+def test_overlong_constraint_rejected():
+    b = synth._Builder(2000)
+    b.add(synth.CARD, list(range(1, bd.MAX_LEN + 2)), synth.GE, 3)
+    with pytest.raises(bd.AfsError) as ei:
+        bd.load_instance(b.build(), stream=0)
+    assert ei.value.code == -3
