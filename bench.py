@@ -120,8 +120,8 @@ class ClockSampler:
 def gpu_id_for(dev: int) -> str:
     import torch
     try:
-        pr = torch.cuda.get_device_properties(dev)
-        return f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else f"GPU-{u}"
     except Exception:
         vis = os.environ.get("CUDA_VISIBLE_DEVICES")
         return vis.split(",")[dev] if vis else str(dev)

@@ -449,18 +449,18 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool verify, cuda
   for (int t = 0; t < nsteps; ++t) {
     for (int b0 = 0; b0 < h->B; b0 += h->Bc) {
       const int nb = std::min(h->Bc, h->B - b0);
-      if (h->timing) CK(cudaEventRecord(pool_event(h, ev), s));
+      if (h->timing) CK(cudaEventRecordWithFlags(pool_event(h, ev), s, cudaEventRecordExternal));
       for (const Group& g : h->groups) {
         int rc = launch_fe_group(h, g, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, nullptr, 0, s);
         if (rc) return rc;
         ++nl;
       }
-      if (h->timing) CK(cudaEventRecord(pool_event(h, ev + 1), s));
+      if (h->timing) CK(cudaEventRecordWithFlags(pool_event(h, ev + 1), s, cudaEventRecordExternal));
       int rc = launch_csr(h, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, eta, nullptr, 0, true, s);
       if (rc) return rc;
       ++nl;
       if (h->timing) {
-        CK(cudaEventRecord(pool_event(h, ev + 2), s));
+        CK(cudaEventRecordWithFlags(pool_event(h, ev + 2), s, cudaEventRecordExternal));
         h->fe_pairs.emplace_back(ev, ev + 1);
         h->csr_pairs.emplace_back(ev + 1, ev + 2);
         ev += 3;

@@ -286,13 +286,24 @@ static void launch_long_t(const FeGroupArgs& a, cudaStream_t s) {
   fe_grad_long_kernel<XT, ESP><<<static_cast<unsigned>(blocks), 256, smem, s>>>(a, a.k);
 }
 
+template <typename K>
+static bool raise_smem_cap(K kernel, int optin) {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return false;
+  const int cap = optin - static_cast<int>(fa.sharedSizeBytes);
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) == cudaSuccess;
+}
+
 bool prepare_kernels() {
-  const int cap = 227 * 1024;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+  if (LongLayout(1024).bytes(true) + 64 > static_cast<size_t>(optin)) return false;
   bool ok = true;
-  ok &= cudaFuncSetAttribute(fe_grad_long_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) == cudaSuccess;
-  ok &= cudaFuncSetAttribute(fe_grad_long_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) == cudaSuccess;
-  ok &= cudaFuncSetAttribute(fe_grad_long_kernel<__nv_bfloat16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) == cudaSuccess;
-  ok &= cudaFuncSetAttribute(fe_grad_long_kernel<__nv_bfloat16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) == cudaSuccess;
+  ok &= raise_smem_cap(fe_grad_long_kernel<float, false>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<float, true>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, false>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, true>, optin);
   return ok;
 }
 
