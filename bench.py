@@ -199,7 +199,7 @@ def run_ours(args):
 
     inst = synth.config2(0)
     B = args.restarts
-    params = bd.default_params(eta=0.1, verify_every=1)
+    params = bd.default_params(eta=0.1, verify_every=1, chunk=args.chunk)
     h = bd.load_instance(inst, params)
     bd.init_restarts(h, B, seed=1000 + rank)
     stream = torch.cuda.current_stream()
@@ -317,6 +317,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--restarts", type=int, default=1024)
     ap.add_argument("--steps-per-graph", type=int, default=10)
+    ap.add_argument("--chunk", type=int, default=0, help="restarts per chunk (0 = autotuned)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

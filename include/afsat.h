@@ -80,7 +80,10 @@ typedef struct afs_params {
   float eta;            /* fixed step size of Algorithm 1 (line 3)          */
   int32_t basis;        /* AFS_BASIS_PGF (default, stable) or AFS_BASIS_ESP  */
   int32_t x_storage;    /* AFS_X_F32 or AFS_X_BF16 storage of the state x   */
-  int32_t verify_every; /* exact check cadence inside afs_step (0 = never)   */
+  int32_t verify_every; /* 0 = no exact check inside afs_step; otherwise
+                           every step checks the state it reads and leaves
+                           solved restarts unmoved, and each afs_step call
+                           ends with a check of its final state             */
   int32_t chunk;        /* restarts per chunk of the step (0 = autotuned)    */
   int32_t autotune;     /* 1 = time tile shapes per bucket at init           */
   int32_t use_graph;    /* 1 = replay afs_step as a captured CUDA graph      */
@@ -132,9 +135,13 @@ void afs_free(afs_handle* h);
 int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_dev, void* stream);
 
 /* afs_step: nsteps iterations of Algorithm 1 with the fixed step eta for all
- * restarts: FE and gradient (Sec. 2.1.2), x <- clamp(x - eta * grad, -1, 1),
- * and the exact check every verify_every steps. Replayed as a captured CUDA
- * graph when use_graph is set (the first call for a given nsteps captures). */
+ * restarts: FE and gradient (Sec. 2.1.2), x <- clamp(x - eta * grad, -1, 1).
+ * With verify_every != 0 each iteration also counts, in the same pass, the
+ * violated constraints of the sign-rounded state it reads; a restart with
+ * none is solved and is not moved again (Algorithm 1 returns on is_sat), and
+ * the call ends with an exact check of the final state (afs_get_verify).
+ * Replayed as a captured CUDA graph when use_graph is set (the first call for
+ * a given nsteps and step parity captures). */
 int afs_step(afs_handle* h, int32_t nsteps, void* stream);
 
 /* afs_round_and_verify: sign-round every restart (x < 0 -> True), count the
@@ -155,9 +162,10 @@ int afs_round_and_verify(afs_handle* h, int32_t* unsat_host, int32_t* best_host,
 int afs_get_x(afs_handle* h, float* x_dev, void* stream);
 /* Overwrite the state from FP32 x_dev[v * B + b] (rounded for BF16 storage). */
 int afs_set_x(afs_handle* h, const float* x_dev, void* stream);
-/* Read the per-restart unsat counts of the last in-step check into
- * unsat_dev[n_inst * B] and the solved restart per instance (INT32_MAX if
- * none) into solved_dev[n_inst]; either may be NULL. */
+/* Read the per-restart unsat counts of the check that ended the last afs_step
+ * call (the state it left) into unsat_dev[n_inst * B] and the lowest restart
+ * seen solved per instance since afs_init_restarts (INT32_MAX if none) into
+ * solved_dev[n_inst]; either may be NULL. */
 int afs_get_verify(afs_handle* h, int32_t* unsat_dev, int32_t* solved_dev, void* stream);
 
 /* afs_eval_fe_grad: evaluate, for the restarts given in x_dev, every

@@ -31,7 +31,22 @@ struct FeGroupArgs {
   float* fe;                // optional fe[orig * fe_pitch + b]
   long long fe_pitch;
   int* err;                 // device error word (bounded waits, bounds checks)
+  // fused exact check of the state being read (nullable vflag = no check):
+  // a warp that finds a violated constraint of (inst, b) stores 1 into
+  // vflag[slot * vflag_stride + inst * B + b], slot = blockIdx.x % VFLAG_SLOTS
+  const unsigned long long* cons_vmask;  // short: bit t set where f(t) = +1 (violated)
+  const int* cons_voff;     // long: offset of the constraint's row in viol
+  const unsigned char* viol;
+  const int* cons_inst;     // instance of each constraint (bucket order)
+  int* vflag;
+  long long vflag_stride;
+  int B;
+  int cpw;                  // constraints per warp (short kernel)
 };
+
+// Rows of violation flags: spreading the plain stores of many warps over
+// several rows keeps them off a handful of L2 lines.
+constexpr int VFLAG_SLOTS = 32;
 
 // Gather of per-occurrence derivatives per variable and the projected step.
 struct CsrArgs {
@@ -45,10 +60,24 @@ struct CsrArgs {
   float eta;
   float* grad;              // optional: grad[v * grad_pitch + b] (evaluation mode)
   long long grad_pitch;
-  const int* var_inst;      // instance of each variable
-  const signed char* frozen;  // optional: frozen[inst * B + b] != 0 -> restart is not moved
-  int B;                    // restarts per instance (frozen row length)
+  const int* var_inst;      // instance of each variable, then first variable of each instance
+  int n_vars;               // total variables (offset of the first-variable table in var_inst)
+  // freeze rule (Algorithm 1 returns on is_sat): a restart whose state had no
+  // violated constraint in this step's fused check is left where it is.
+  const signed char* sflag; // nullable: sflag[inst * B + b] = 1 if solved
+  int B;                    // restarts per instance (row length of sflag)
 };
+
+// Per-restart fold of the fused check's flag rows (one thread per restart).
+struct FlagArgs {
+  const int* vflag_cur;     // VFLAG_SLOTS rows of n_inst * B flags
+  int* vflag_next;          // rows cleared for the next step
+  long long stride;         // n_inst * B
+  signed char* sflag;       // 1 where no row flagged a violation
+  int* solved;              // lowest solved restart per instance
+  int n_inst, B, b0, nb;
+};
+void launch_fold_flags(const FlagArgs& a, cudaStream_t s);
 
 // Exact check of the sign-rounded state.
 struct VerifyArgs {
@@ -76,7 +105,7 @@ bool prepare_kernels();
 void launch_fe_long(const FeGroupArgs& a, int xt, int basis, int rt, cudaStream_t s);
 void launch_csr_update(const CsrArgs& a, int xt, cudaStream_t s);
 void launch_verify(const VerifyArgs& a, int xt, cudaStream_t s);
-void launch_solved(const int* unsat, int n_inst, int B, int* solved, signed char* frozen, cudaStream_t s);
+void launch_solved(const int* unsat, int n_inst, int B, int* solved, cudaStream_t s);
 void launch_init_philox(void* x, int xt, long long x_pitch, int n, int B, const int* var_inst,
                         unsigned long long seed, cudaStream_t s);
 void launch_convert_in(const void* src, int src_xt, long long src_pitch, void* dst, int dst_xt,
@@ -85,5 +114,32 @@ void launch_gather_column(const void* x, int xt, long long x_pitch, const int* v
                           const int* col_of, signed char* out, cudaStream_t s);
 // Restarts per lane available for a short group of length k.
 inline int max_rpl_for_k(int k) { return k <= 8 ? 4 : (k <= 16 ? 2 : 1); }
+
+// Programmatic dependent launch: every kernel of the step waits for its
+// predecessor's memory before its first access and lets its successor be
+// scheduled as soon as all of its own CTAs are running, so launch latency
+// overlaps the previous kernel's tail. Off when AFS_PDL=0.
+bool pdl_enabled();
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+#endif
 
 }  // namespace afs

@@ -9,11 +9,18 @@
 //     dFE/dl_i =      sum_roots Re(E prod_{i' != i} (l_i' + alpha + i gamma))
 // (alpha = 0 for the probability-generating basis, gamma = 0 for real roots).
 // The gradient uses prefix and suffix products, so there is no division and
-// zero factors are safe. Each lane owns RPL restarts of one constraint
-// (restart-major x[v][b]: every literal is one coalesced row gather), the
-// k-literal loop is unrolled so prefixes live in registers, and the roots are
-// a runtime loop. Per (literal, complex root) the work is a prefix product
-// (4 FP32 instructions), a suffix product (4) and the gradient combine (2).
+// zero factors are safe. Each lane owns RPL restarts (restart-major x[v][b]:
+// every literal is one coalesced row gather), a warp walks `cpw` consecutive
+// constraints of its group, the k-literal loop is unrolled so prefixes live in
+// registers, and the roots are a runtime loop. Per (literal, complex root) the
+// work is a prefix product (4 FP32 instructions), a suffix product (4) and the
+// gradient combine (2).
+//
+// The same pass performs Algorithm 1's exact check of the state it reads: a
+// literal is true when its variable rounds to True (x < 0) xor it is negated,
+// and the constraint is violated when bit t (true count) of its mask is set.
+// A lane that saw a violation stores 1 into its warp's flag row (one plain
+// store per warp and instance; rows are spread over VFLAG_SLOTS).
 #pragma once
 #include <cuda_bf16.h>
 
@@ -33,18 +40,27 @@ __device__ __forceinline__ float load_x<__nv_bfloat16>(const __nv_bfloat16* p) {
   return __uint_as_float(static_cast<unsigned int>(u) << 16);
 }
 
+// literal truth at the sign-rounded point, from l = s x and the negation bit
+__device__ __forceinline__ int lit_true(float l, int neg) {
+  return neg ? (l <= 0.0f) : (l < 0.0f);
+}
+
 template <int K, int RPL, typename XT, bool SHIFT>
 __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const long long warp = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   constexpr int TW = 32 * RPL;
   const int tiles = (a.nb + TW - 1) / TW;
-  const long long c = warp / tiles;
-  if (c >= a.c_count) return;
-  const int tile = static_cast<int>(warp - c * tiles);
-  const int cb = a.c_begin + static_cast<int>(c);
-  const int2* ls = a.litslot + a.lit_base + c * K;
+  const long long cg = warp / tiles;
+  const long long c_first = cg * a.cpw;
+  if (c_first >= a.c_count) return;
+  const int tile = static_cast<int>(warp - cg * tiles);
+  const int c_last = static_cast<int>(min(static_cast<long long>(a.c_count), c_first + a.cpw));
   const XT* x = static_cast<const XT*>(a.x);
+  const bool check = a.vflag != nullptr;
+  int* vrow = check ? a.vflag + static_cast<long long>(warp % VFLAG_SLOTS) * a.vflag_stride + a.b0 : nullptr;
 
   int bl[RPL];
   bool act[RPL];
@@ -53,121 +69,183 @@ __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
     bl[r] = tile * TW + r * 32 + lane;
     act[r] = bl[r] < a.nb;
   }
+  bool vio[RPL];
+#pragma unroll
+  for (int r = 0; r < RPL; ++r) vio[r] = false;
+  int cur_inst = -1;
 
-  int2 lit[K];
+  for (int c = static_cast<int>(c_first); c < c_last; ++c) {
+    const int cb = a.c_begin + c;
+    const int2* ls = a.litslot + a.lit_base + static_cast<long long>(c) * K;
+    int2 lit[K];
 #pragma unroll
-  for (int i = 0; i < K; ++i) lit[i] = __ldg(ls + i);
+    for (int i = 0; i < K; ++i) lit[i] = __ldg(ls + i);
 
-  float l[RPL][K];
+    float l[RPL][K];
 #pragma unroll
-  for (int i = 0; i < K; ++i) {
-    const long long row = static_cast<long long>(lit[i].x >> 1) * a.x_pitch + a.b0;
+    for (int i = 0; i < K; ++i) {
+      const long long row = static_cast<long long>(lit[i].x >> 1) * a.x_pitch + a.b0;
 #pragma unroll
-    for (int r = 0; r < RPL; ++r) {
-      const float xv = act[r] ? load_x<XT>(x + row + bl[r]) : 0.0f;
-      l[r][i] = (lit[i].x & 1) ? -xv : xv;
-    }
-  }
-
-  const float4* tab = a.coef + __ldg(a.cons_tab + cb);
-  const float4 head = __ldg(tab);
-  float fe[RPL];
-  float g[RPL][K];
-#pragma unroll
-  for (int r = 0; r < RPL; ++r) {
-    fe[r] = head.x;
-#pragma unroll
-    for (int i = 0; i < K; ++i) g[r][i] = 0.0f;
-  }
-  int ti = 1;
-
-  // real roots: factor (l + alpha)
-  constexpr int NREAL = (K & 1) + (SHIFT ? 1 : 0);
-#pragma unroll
-  for (int q = 0; q < NREAL; ++q) {
-    const float4 rc = __ldg(tab + ti + q);
-    const float alpha = rc.x, E = rc.y;
-#pragma unroll
-    for (int r = 0; r < RPL; ++r) {
-      float pre[K];
-      float P = E;
-#pragma unroll
-      for (int i = 0; i < K; ++i) {
-        pre[i] = P;
-        if (i + 1 < K) P *= SHIFT ? (l[r][i] + alpha) : l[r][i];
+      for (int r = 0; r < RPL; ++r) {
+        const float xv = act[r] ? load_x<XT>(x + row + bl[r]) : 0.0f;
+        l[r][i] = (lit[i].x & 1) ? -xv : xv;
       }
-      g[r][K - 1] += pre[K - 1];
-      float S = SHIFT ? (l[r][K - 1] + alpha) : l[r][K - 1];
-#pragma unroll
-      for (int i = K - 2; i >= 0; --i) {
-        g[r][i] = fmaf(pre[i], S, g[r][i]);
-        S *= SHIFT ? (l[r][i] + alpha) : l[r][i];
-      }
-      fe[r] = fmaf(E, S, fe[r]);
     }
-  }
-  ti += NREAL;
 
-  // complex roots: factor (l + alpha) + i gamma
-#pragma unroll 1
-  for (int j = 0; j < K / 2; ++j) {
-    const float4 cc = __ldg(tab + ti + j);
-    const float alpha = cc.x, gam = cc.y;
+    if (check) {
+      const int inst = __ldg(a.cons_inst + cb);
+      if (inst != cur_inst) {
+        if (cur_inst >= 0) {
 #pragma unroll
-    for (int r = 0; r < RPL; ++r) {
-      float pr[K], pi[K];
-      float Pr = cc.z, Pi = cc.w;
-#pragma unroll
-      for (int i = 0; i < K; ++i) {
-        pr[i] = Pr;
-        pi[i] = Pi;
-        if (i + 1 < K) {
-          const float u = SHIFT ? (l[r][i] + alpha) : l[r][i];
-          const float nr = fmaf(Pr, u, -Pi * gam);
-          const float ni = fmaf(Pi, u, Pr * gam);
-          Pr = nr;
-          Pi = ni;
+          for (int r = 0; r < RPL; ++r) {
+            if (act[r] && vio[r]) vrow[static_cast<long long>(cur_inst) * a.B + bl[r]] = 1;
+            vio[r] = false;
+          }
         }
+        cur_inst = inst;
       }
-      g[r][K - 1] += pr[K - 1];
-      float Sr = SHIFT ? (l[r][K - 1] + alpha) : l[r][K - 1];
-      float Si = gam;
+      const unsigned long long vm = __ldg(a.cons_vmask + cb);
 #pragma unroll
-      for (int i = K - 2; i >= 0; --i) {
-        g[r][i] = fmaf(pr[i], Sr, g[r][i]);
-        g[r][i] = fmaf(-pi[i], Si, g[r][i]);
-        const float u = SHIFT ? (l[r][i] + alpha) : l[r][i];
-        const float nr = fmaf(Sr, u, -Si * gam);
-        const float ni = fmaf(Si, u, Sr * gam);
-        Sr = nr;
-        Si = ni;
+      for (int r = 0; r < RPL; ++r) {
+        int t = 0;
+#pragma unroll
+        for (int i = 0; i < K; ++i) t += lit_true(l[r][i], lit[i].x & 1);
+        vio[r] |= ((vm >> t) & 1ull) != 0;
       }
-      fe[r] = fmaf(cc.z, Sr, fmaf(-cc.w, Si, fe[r]));
     }
-  }
+
+    const float4* tab = a.coef + __ldg(a.cons_tab + cb);
+    const float4 head = __ldg(tab);
+    float fe[RPL];
+    float g[RPL][K];
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+      fe[r] = head.x;
+#pragma unroll
+      for (int i = 0; i < K; ++i) g[r][i] = 0.0f;
+    }
+
+    // real roots: factor (l + alpha)
+    constexpr int NREAL = (K & 1) + (SHIFT ? 1 : 0);
+#pragma unroll
+    for (int q = 0; q < NREAL; ++q) {
+      const float4 rc = __ldg(tab + 1 + q);
+      const float alpha = rc.x, E = rc.y;
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        float pre[K];
+        float P = E;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          pre[i] = P;
+          if (i + 1 < K) P *= SHIFT ? (l[r][i] + alpha) : l[r][i];
+        }
+        g[r][K - 1] += pre[K - 1];
+        float S = SHIFT ? (l[r][K - 1] + alpha) : l[r][K - 1];
+#pragma unroll
+        for (int i = K - 2; i >= 0; --i) {
+          g[r][i] = fmaf(pre[i], S, g[r][i]);
+          S *= SHIFT ? (l[r][i] + alpha) : l[r][i];
+        }
+        fe[r] = fmaf(E, S, fe[r]);
+      }
+    }
+
+    // complex roots: factor (l + alpha) + i gamma; RPI roots per iteration
+    // are independent product chains interleaved for instruction-level
+    // parallelism (they share the literal values and the accumulators)
+    constexpr int NC = K / 2;
+    // (two interleaved roots measured slower at k = 20: the register growth
+    // costs more occupancy than the extra chains win back)
+    constexpr int RPI = 1;
+#pragma unroll 1
+    for (int j = 0; j < NC; j += RPI) {
+      float4 cc[RPI];
+      bool on[RPI];
+#pragma unroll
+      for (int q = 0; q < RPI; ++q) {
+        on[q] = (q == 0) || (j + q < NC);
+        cc[q] = on[q] ? __ldg(tab + 1 + NREAL + j + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        float pr[RPI][K], pi[RPI][K];
+        float Pr[RPI], Pi[RPI];
+#pragma unroll
+        for (int q = 0; q < RPI; ++q) {
+          Pr[q] = cc[q].z;
+          Pi[q] = cc[q].w;
+        }
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+#pragma unroll
+          for (int q = 0; q < RPI; ++q) {
+            pr[q][i] = Pr[q];
+            pi[q][i] = Pi[q];
+            if (i + 1 < K) {
+              const float u = SHIFT ? (l[r][i] + cc[q].x) : l[r][i];
+              const float nr = fmaf(Pr[q], u, -Pi[q] * cc[q].y);
+              const float ni = fmaf(Pi[q], u, Pr[q] * cc[q].y);
+              Pr[q] = nr;
+              Pi[q] = ni;
+            }
+          }
+        }
+        float Sr[RPI], Si[RPI];
+#pragma unroll
+        for (int q = 0; q < RPI; ++q) {
+          g[r][K - 1] += pr[q][K - 1];
+          Sr[q] = SHIFT ? (l[r][K - 1] + cc[q].x) : l[r][K - 1];
+          Si[q] = cc[q].y;
+        }
+#pragma unroll
+        for (int i = K - 2; i >= 0; --i) {
+#pragma unroll
+          for (int q = 0; q < RPI; ++q) {
+            g[r][i] = fmaf(pr[q][i], Sr[q], g[r][i]);
+            g[r][i] = fmaf(-pi[q][i], Si[q], g[r][i]);
+            const float u = SHIFT ? (l[r][i] + cc[q].x) : l[r][i];
+            const float nr = fmaf(Sr[q], u, -Si[q] * cc[q].y);
+            const float ni = fmaf(Si[q], u, Sr[q] * cc[q].y);
+            Sr[q] = nr;
+            Si[q] = ni;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < RPI; ++q) fe[r] = fmaf(cc[q].z, Sr[q], fmaf(-cc[q].w, Si[q], fe[r]));
+      }
+    }
 
 #pragma unroll
-  for (int i = 0; i < K; ++i) {
-    float* row = a.go + static_cast<long long>(lit[i].y) * a.go_pitch;
+    for (int i = 0; i < K; ++i) {
+      float* row = a.go + static_cast<long long>(lit[i].y) * a.go_pitch;
 #pragma unroll
-    for (int r = 0; r < RPL; ++r)
-      if (act[r]) row[bl[r]] = (lit[i].x & 1) ? -g[r][i] : g[r][i];
+      for (int r = 0; r < RPL; ++r)
+        if (act[r]) row[bl[r]] = (lit[i].x & 1) ? -g[r][i] : g[r][i];
+    }
+    if (a.fe != nullptr) {
+      const long long orow = static_cast<long long>(__ldg(a.cons_orig + cb)) * a.fe_pitch + a.b0;
+#pragma unroll
+      for (int r = 0; r < RPL; ++r)
+        if (act[r]) a.fe[orow + bl[r]] = fe[r];
+    }
   }
-  if (a.fe != nullptr) {
-    const long long orow = static_cast<long long>(__ldg(a.cons_orig + cb)) * a.fe_pitch + a.b0;
+  if (check && cur_inst >= 0) {
 #pragma unroll
     for (int r = 0; r < RPL; ++r)
-      if (act[r]) a.fe[orow + bl[r]] = fe[r];
+      if (act[r] && vio[r]) vrow[static_cast<long long>(cur_inst) * a.B + bl[r]] = 1;
   }
 }
 
 template <int K, int RPL, typename XT, bool SHIFT>
-void launch_short_k(const FeGroupArgs& a, int warps, cudaStream_t s) {
+void launch_short_k(const FeGroupArgs& a_in, int warps, cudaStream_t s) {
+  FeGroupArgs a = a_in;
+  if (a.cpw < 1) a.cpw = 1;
   const int TW = 32 * RPL;
   const long long tiles = (a.nb + TW - 1) / TW;
-  const long long nwarps = tiles * a.c_count;
+  const long long nwarps = tiles * ((a.c_count + a.cpw - 1) / a.cpw);
   const long long blocks = (nwarps + warps - 1) / warps;
-  fe_grad_short_kernel<K, RPL, XT, SHIFT><<<static_cast<unsigned>(blocks), warps * 32, 0, s>>>(a);
+  launch_pdl(fe_grad_short_kernel<K, RPL, XT, SHIFT>, dim3(static_cast<unsigned>(blocks)), dim3(warps * 32), 0, s, a);
 }
 
 }  // namespace afs

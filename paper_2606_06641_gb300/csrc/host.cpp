@@ -7,6 +7,7 @@
 #include <climits>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -87,7 +88,8 @@ struct Group {
   int k;            // length (long group: longest)
   int c_begin, c_count;
   long long lit_base;
-  int rpl;
+  int rpl;          // restarts per lane (short kernel tile)
+  int cpw;          // constraints per warp (short kernel tile)
 };
 
 }  // namespace
@@ -105,18 +107,22 @@ struct afs_handle {
   double work_per_restart = 0.0;
   // device instance data
   DevBuf litslot, cons_tab, cons_orig, cons_k, cons_lit, coef, csr_off, lit_enc, lit_off, viol_off, viol,
-      ranges, var_inst, err;
+      ranges, var_inst, err, cons_vmask, cons_voff, cons_inst;
   int n_ranges = 0;
   // restart state
   int B = 0, xt = XT_F32;
   long long pitch = 0;
   int Bc = 0;
-  DevBuf x, go, unsat, solved, frozen, col, assign, stage, eval_go;
+  // unsat: counts of the last standalone check; vflag: the fused per-step
+  // check's flag rows (two parities x VFLAG_SLOTS rows); sflag: solved bytes
+  DevBuf x, go, unsat, vflag, sflag, solved, col, assign, stage, eval_go;
+  int parity = 0;
   long long eval_go_cols = 0;
   // graphs
   cudaStream_t cap = nullptr;
-  std::map<int, cudaGraphExec_t> graphs, timed_graphs;
-  std::map<int, std::pair<std::vector<std::pair<int, int>>, std::vector<std::pair<int, int>>>> timed_pairs;
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs, timed_graphs;  // (nsteps, start parity)
+  std::map<std::pair<int, int>, std::pair<std::vector<std::pair<int, int>>, std::vector<std::pair<int, int>>>>
+      timed_pairs;
   // timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -254,7 +260,8 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     if (!la) return gk[a] < gk[b];
     return gk[a] > gk[b];
   });
-  std::vector<int> b_tab(m), b_orig(m), b_k(m), b_lit(m);
+  std::vector<int> b_tab(m), b_orig(m), b_k(m), b_lit(m), b_voff(m), b_inst(m);
+  std::vector<unsigned long long> b_vmask(m, 0ull);
   std::vector<int2> litslot;
   litslot.reserve(L + m);
   h->work_per_restart = 0.0;
@@ -266,6 +273,11 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     b_orig[pos] = g;
     b_k[pos] = k;
     b_lit[pos] = static_cast<int>(litslot.size());
+    b_voff[pos] = viol_off[g];
+    b_inst[pos] = ginst[g];
+    if (k < 64)
+      for (int t = 0; t <= k; ++t)
+        if (violv[viol_off[g] + t]) b_vmask[pos] |= 1ull << t;
     for (int t = 0; t < k; ++t) litslot.push_back(make_int2(enc_of(ginst[g], lits[goff[g] + t]), -1));
     if (k > KSHORT && (k & 1)) litslot.push_back(make_int2(0, 0));
     h->work_per_restart += work_instr(k);
@@ -275,7 +287,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
       last->c_count++;
     } else {
       // long constraints form one group sorted by decreasing length: its k is the longest
-      h->groups.push_back(Group{is_long, k, pos, 1, static_cast<long long>(b_lit[pos]), 1});
+      h->groups.push_back(Group{is_long, k, pos, 1, static_cast<long long>(b_lit[pos]), 1, 1});
     }
   }
   // ---- CSR: slots in variable-major order, occurrences of a variable in bucket order ----
@@ -312,7 +324,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     const int ce = h->inst_cbegin[i + 1];
     while (c < ce) {
       int e = c, lits_in = 0;
-      while (e < ce && (e == c || (lits_in + gk[e] <= 128 && e - c < 32))) lits_in += gk[e++];
+      while (e < ce && (e == c || (lits_in + gk[e] <= 48 && e - c < 8))) lits_in += gk[e++];
       ranges.push_back(make_int4(c, e, i, 0));
       c = e;
     }
@@ -339,6 +351,9 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   if ((rc = upload(h->viol, violv, s))) return rc;
   if ((rc = upload(h->ranges, ranges, s))) return rc;
   if ((rc = upload(h->var_inst, var_inst_ext, s))) return rc;
+  if ((rc = upload(h->cons_vmask, b_vmask, s))) return rc;
+  if ((rc = upload(h->cons_voff, b_voff, s))) return rc;
+  if ((rc = upload(h->cons_inst, b_inst, s))) return rc;
   std::vector<int> zero1(1, 0);
   if ((rc = upload(h->err, zero1, s))) return rc;
   CK(cudaStreamSynchronize(s));
@@ -352,7 +367,8 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
 // launch planning
 // ---------------------------------------------------------------------------
 static int launch_fe_group(afs_handle* h, const Group& g, const void* x, int xt, long long x_pitch, int b0, int nb,
-                           float* go, long long go_pitch, float* fe, long long fe_pitch, cudaStream_t s) {
+                           float* go, long long go_pitch, float* fe, long long fe_pitch, int* vflag,
+                           cudaStream_t s) {
   FeGroupArgs a{};
   a.x = x;
   a.x_pitch = x_pitch;
@@ -373,6 +389,14 @@ static int launch_fe_group(afs_handle* h, const Group& g, const void* x, int xt,
   a.fe = fe;
   a.fe_pitch = fe_pitch;
   a.err = h->err.as<int>();
+  a.cons_vmask = h->cons_vmask.as<unsigned long long>();
+  a.cons_voff = h->cons_voff.as<int>();
+  a.viol = h->viol.as<unsigned char>();
+  a.cons_inst = h->cons_inst.as<int>();
+  a.vflag = vflag;
+  a.vflag_stride = static_cast<long long>(h->n_inst) * h->B;
+  a.B = h->B;
+  a.cpw = g.cpw;
   if (g.is_long) {
     launch_fe_long(a, xt, h->p.basis, 8, s);
   } else {
@@ -387,8 +411,10 @@ static int launch_fe_group(afs_handle* h, const Group& g, const void* x, int xt,
   return AFS_OK;
 }
 
+// CSR gather and step; with `check`, the restarts whose state passed this
+// step's fused exact check are left unmoved and recorded as solved.
 static int launch_csr(afs_handle* h, void* x, int xt, long long x_pitch, int b0, int nb, const float* go,
-                      long long go_pitch, float eta, float* grad, long long grad_pitch, bool use_frozen,
+                      long long go_pitch, float eta, float* grad, long long grad_pitch, bool use_sflag,
                       cudaStream_t s) {
   CsrArgs a{};
   a.x = x;
@@ -404,14 +430,16 @@ static int launch_csr(afs_handle* h, void* x, int xt, long long x_pitch, int b0,
   a.grad = grad;
   a.grad_pitch = grad_pitch;
   a.var_inst = h->var_inst.as<int>();
-  a.frozen = use_frozen ? h->frozen.as<signed char>() : nullptr;
+  a.n_vars = h->n;
   a.B = h->B;
+  a.sflag = use_sflag ? h->sflag.as<signed char>() : nullptr;
   launch_csr_update(a, xt, s);
   CKL();
   return AFS_OK;
 }
 
-static int launch_check(afs_handle* h, bool freeze, cudaStream_t s) {
+// Standalone exact check of the current state into h->unsat, solved flags updated.
+static int launch_check(afs_handle* h, cudaStream_t s) {
   CK(cudaMemsetAsync(h->unsat.p, 0, sizeof(int) * static_cast<size_t>(h->n_inst) * h->B, s));
   VerifyArgs v{};
   v.x = h->x.p;
@@ -426,8 +454,7 @@ static int launch_check(afs_handle* h, bool freeze, cudaStream_t s) {
   v.unsat = h->unsat.as<int>();
   launch_verify(v, h->xt, s);
   CKL();
-  launch_solved(h->unsat.as<int>(), h->n_inst, h->B, h->solved.as<int>(),
-                freeze ? h->frozen.as<signed char>() : nullptr, s);
+  launch_solved(h->unsat.as<int>(), h->n_inst, h->B, h->solved.as<int>(), s);
   CKL();
   return AFS_OK;
 }
@@ -441,22 +468,45 @@ static cudaEvent_t pool_event(afs_handle* h, int idx) {
   return h->ev_pool[idx];
 }
 
-// Enqueue nsteps of the descent loop on s (used both directly and under capture).
-static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool verify, cudaStream_t s, long long* launches) {
+// Enqueue nsteps of the descent loop on s (used both directly and under
+// capture). Step t reads the state x_t: its FE pass also flags x_t's violated
+// constraints (flag rows of parity p), a fold marks the restarts with no flag
+// as solved and clears the rows of parity 1-p, and the CSR pass moves only
+// the unsolved restarts. With `check`, a standalone exact check of the final
+// state ends the sequence.
+static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int parity0, cudaStream_t s,
+                         long long* launches) {
   long long nl = 0;
   int ev = 0;
-  const int ve = h->p.verify_every;
+  const size_t nib = static_cast<size_t>(h->n_inst) * h->B;
   for (int t = 0; t < nsteps; ++t) {
+    const int p = (parity0 + t) & 1;
+    int* vcur = check ? h->vflag.as<int>() + p * VFLAG_SLOTS * nib : nullptr;
     for (int b0 = 0; b0 < h->B; b0 += h->Bc) {
       const int nb = std::min(h->Bc, h->B - b0);
       if (h->timing) CK(cudaEventRecordWithFlags(pool_event(h, ev), s, cudaEventRecordExternal));
       for (const Group& g : h->groups) {
-        int rc = launch_fe_group(h, g, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, nullptr, 0, s);
+        int rc = launch_fe_group(h, g, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, nullptr, 0, vcur, s);
         if (rc) return rc;
         ++nl;
       }
       if (h->timing) CK(cudaEventRecordWithFlags(pool_event(h, ev + 1), s, cudaEventRecordExternal));
-      int rc = launch_csr(h, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, eta, nullptr, 0, true, s);
+      if (check) {
+        FlagArgs f{};
+        f.vflag_cur = vcur;
+        f.vflag_next = h->vflag.as<int>() + (p ^ 1) * VFLAG_SLOTS * nib;
+        f.stride = static_cast<long long>(nib);
+        f.sflag = h->sflag.as<signed char>();
+        f.solved = h->solved.as<int>();
+        f.n_inst = h->n_inst;
+        f.B = h->B;
+        f.b0 = b0;
+        f.nb = nb;
+        launch_fold_flags(f, s);
+        CKL();
+        ++nl;
+      }
+      int rc = launch_csr(h, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, eta, nullptr, 0, check, s);
       if (rc) return rc;
       ++nl;
       if (h->timing) {
@@ -466,11 +516,11 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool verify, cuda
         ev += 3;
       }
     }
-    if (verify && ve > 0 && ((t + 1) % ve == 0 || t + 1 == nsteps)) {
-      int rc = launch_check(h, true, s);
-      if (rc) return rc;
-      nl += 2;
-    }
+  }
+  if (check && nsteps > 0) {
+    int rc = launch_check(h, s);
+    if (rc) return rc;
+    nl += 2;
   }
   if (launches) *launches = nl;
   return AFS_OK;
@@ -532,27 +582,50 @@ struct TuneKey {
     return std::tie(dev, n, m, B, xt, basis, L, ks) < std::tie(o.dev, o.n, o.m, o.B, o.xt, o.basis, o.L, o.ks);
   }
 };
+static bool tune_log() {
+  static const bool on = std::getenv("AFS_TUNE_LOG") != nullptr;
+  return on;
+}
+
 struct TuneVal {
   int Bc;
-  std::vector<int> rpl;
+  std::vector<int> rpl, cpw;
 };
 static std::map<TuneKey, TuneVal>& tune_cache() {
   static std::map<TuneKey, TuneVal> c;
   return c;
 }
 
-// The tile autotuner: per short length bucket the restarts-per-lane tile,
-// then the restart chunk of the whole step, each chosen by CUDA-event timing
-// of real launches (eta = 0 steps leave the state unchanged).
+// Warps of a short group at a tile shape (rpl restarts per lane, cpw constraints per warp).
+static long long group_warps(const Group& g, int nb, int rpl, int cpw) {
+  const long long tiles = (nb + 32 * rpl - 1) / (32 * rpl);
+  return tiles * ((g.c_count + cpw - 1) / cpw);
+}
+
+// Constraints per warp that leaves at least ~32 warps per SM of work.
+static int default_cpw(const Group& g, int nb, int rpl, int sms) {
+  int cpw = 1;
+  while (cpw < 16 && group_warps(g, nb, rpl, cpw * 2) >= 32LL * sms) cpw *= 2;
+  return cpw;
+}
+
+// The tile autotuner: per short length bucket the (restarts-per-lane,
+// constraints-per-warp) tile, then the restart chunk of the whole step, each
+// chosen by CUDA-event timing of real launches (eta = 0 steps leave the state
+// unchanged; the check buffers are cleared afterwards).
 static int autotune(afs_handle* h, cudaStream_t s) {
-  int dev = 0;
+  int dev = 0, sms = 1;
   cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   TuneKey key{dev, h->n, h->m, h->B, h->xt, h->p.basis, h->L, {}};
   for (auto& g : h->groups) key.ks.push_back(g.is_long ? -g.c_count : g.k * 100000 + g.c_count);
   auto it = tune_cache().find(key);
   if (it != tune_cache().end()) {
     h->Bc = it->second.Bc;
-    for (size_t i = 0; i < h->groups.size(); ++i) h->groups[i].rpl = it->second.rpl[i];
+    for (size_t i = 0; i < h->groups.size(); ++i) {
+      h->groups[i].rpl = it->second.rpl[i];
+      h->groups[i].cpw = it->second.cpw[i];
+    }
     return alloc_go(h, h->Bc);
   }
   cudaEvent_t e0, e1;
@@ -561,37 +634,21 @@ static int autotune(afs_handle* h, cudaStream_t s) {
   const int Bp = (h->B + 31) / 32 * 32;
   int rc = alloc_go(h, Bp);
   if (rc) return rc;
-  const int c0 = default_chunk(h);
-  // 1. restarts per lane per short bucket
-  if (h->p.basis == AFS_BASIS_PGF) {
+  const bool pgf = h->p.basis == AFS_BASIS_PGF;
+  auto default_tiles = [&](int chunk) {
     for (Group& g : h->groups) {
       if (g.is_long) continue;
-      double best = 1e30;
-      int best_rpl = 1;
-      for (int rpl = 1; rpl <= max_rpl_for_k(g.k); rpl *= 2) {
-        g.rpl = rpl;
-        double t = 1e30;
-        for (int rep = 0; rep < 3; ++rep) {
-          CK(cudaEventRecord(e0, s));
-          rc = launch_fe_group(h, g, h->x.p, h->xt, h->pitch, 0, std::min(c0, h->B), h->go.as<float>(), c0, nullptr, 0, s);
-          if (rc) return rc;
-          CK(cudaEventRecord(e1, s));
-          t = std::min(t, time_ms(s, e0, e1));
-        }
-        if (t < best * 0.97) {
-          best = t;
-          best_rpl = rpl;
-        }
-      }
-      g.rpl = best_rpl;
+      g.rpl = pgf ? std::min(2, max_rpl_for_k(g.k)) : 1;
+      g.cpw = default_cpw(g, std::min(chunk, h->B), g.rpl, sms);
     }
-  }
-  // 2. restart chunk
+  };
+  // 1. restart chunk, with default tiles: whole steps timed (eta = 0)
   std::vector<int> cands;
   for (int c = Bp; c >= 32; c /= 2) {
     cands.push_back(c / 32 * 32);
     if (cands.size() >= 6) break;
   }
+  const int c0 = default_chunk(h);
   if (std::find(cands.begin(), cands.end(), c0) == cands.end()) cands.push_back(c0);
   double best = 1e30;
   int bestc = c0;
@@ -599,14 +656,16 @@ static int autotune(afs_handle* h, cudaStream_t s) {
   h->timing = false;
   for (int c : cands) {
     h->Bc = c;
+    default_tiles(c);
     double t = 1e30;
     for (int rep = 0; rep < 2; ++rep) {
       CK(cudaEventRecord(e0, s));
-      rc = enqueue_steps(h, 2, 0.0f, false, s, nullptr);
+      rc = enqueue_steps(h, 2, 0.0f, true, 0, s, nullptr);
       if (rc) return rc;
       CK(cudaEventRecord(e1, s));
       t = std::min(t, time_ms(s, e0, e1));
     }
+    if (tune_log()) std::fprintf(stderr, "[afs autotune] chunk %d: %.1f us/step\n", c, 500.0 * t);
     if (t < best * 0.97) {
       best = t;
       bestc = c;
@@ -614,10 +673,45 @@ static int autotune(afs_handle* h, cudaStream_t s) {
   }
   h->timing = was_timing;
   h->Bc = bestc;
+  default_tiles(bestc);
+  // 2. tile shape per short bucket at that chunk: single FE launches timed
+  const int nb = std::min(h->Bc, h->B);
+  int* vcheck = h->vflag.as<int>();
+  for (Group& g : h->groups) {
+    if (g.is_long) continue;
+    double bt = 1e30;
+    int best_rpl = g.rpl, best_cpw = g.cpw;
+    for (int rpl = 1; rpl <= (pgf ? max_rpl_for_k(g.k) : 1); rpl *= 2) {
+      for (int cpw = 1; cpw <= 8; cpw *= 2) {
+        if (cpw > 1 && group_warps(g, nb, rpl, cpw) < 8LL * sms) break;
+        g.rpl = rpl;
+        g.cpw = cpw;
+        double t = 1e30;
+        for (int rep = 0; rep < 3; ++rep) {
+          CK(cudaEventRecord(e0, s));
+          rc = launch_fe_group(h, g, h->x.p, h->xt, h->pitch, 0, nb, h->go.as<float>(), h->Bc, nullptr, 0, vcheck, s);
+          if (rc) return rc;
+          CK(cudaEventRecord(e1, s));
+          t = std::min(t, time_ms(s, e0, e1));
+        }
+        if (tune_log()) std::fprintf(stderr, "[afs autotune] k=%d rpl=%d cpw=%d: %.2f us\n", g.k, rpl, cpw, 1e3 * t);
+        if (t < bt * 0.97) {
+          bt = t;
+          best_rpl = rpl;
+          best_cpw = cpw;
+        }
+      }
+    }
+    g.rpl = best_rpl;
+    g.cpw = best_cpw;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  TuneVal val{h->Bc, {}};
-  for (auto& g : h->groups) val.rpl.push_back(g.rpl);
+  TuneVal val{h->Bc, {}, {}};
+  for (auto& g : h->groups) {
+    val.rpl.push_back(g.rpl);
+    val.cpw.push_back(g.cpw);
+  }
   tune_cache()[key] = val;
   return AFS_OK;
 }
@@ -669,13 +763,20 @@ int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_d
   CK(cudaMemsetAsync(h->x.p, 0, h->x.bytes, s));
   const size_t nib = static_cast<size_t>(h->n_inst) * B;
   if ((rc = h->unsat.alloc(sizeof(int) * nib))) return rc;
-  if ((rc = h->frozen.alloc(nib))) return rc;
+  if ((rc = h->vflag.alloc(2 * VFLAG_SLOTS * sizeof(int) * nib))) return rc;
+  if ((rc = h->sflag.alloc(nib))) return rc;
   if ((rc = h->solved.alloc(sizeof(int) * h->n_inst))) return rc;
   if ((rc = h->col.alloc(sizeof(int) * h->n_inst))) return rc;
   if ((rc = h->assign.alloc(static_cast<size_t>(h->n)))) return rc;
   CK(cudaMemsetAsync(h->unsat.p, 0, h->unsat.bytes, s));
-  CK(cudaMemsetAsync(h->frozen.p, 0, h->frozen.bytes, s));
+  CK(cudaMemsetAsync(h->vflag.p, 0, h->vflag.bytes, s));
+  CK(cudaMemsetAsync(h->sflag.p, 0, h->sflag.bytes, s));
   CK(cudaMemsetAsync(h->solved.p, 0x7f, h->solved.bytes, s));
+  h->parity = 0;
+  for (Group& g : h->groups) {
+    g.rpl = 1;
+    g.cpw = 1;
+  }
   if (x0_dev) {
     launch_convert_in(x0_dev, XT_F32, B, h->x.p, h->xt, h->pitch, h->n, B, s);
   } else {
@@ -693,7 +794,17 @@ int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_d
     if (h->p.chunk > 0) h->Bc = std::min<int>(((h->p.chunk + 31) / 32) * 32, static_cast<int>(h->pitch));
     if ((rc = alloc_go(h, h->Bc))) return rc;
   }
-  // the solved flags start clear: the autotuner does not run the exact check
+  if (!h->p.autotune) {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (Group& g : h->groups)
+      if (!g.is_long) g.cpw = default_cpw(g, std::min(h->Bc, h->B), g.rpl, sms);
+  }
+  // the autotuner's steps leave x unchanged but touch the check buffers and flags
+  CK(cudaMemsetAsync(h->unsat.p, 0, h->unsat.bytes, s));
+  CK(cudaMemsetAsync(h->vflag.p, 0, h->vflag.bytes, s));
+  CK(cudaMemsetAsync(h->sflag.p, 0, h->sflag.bytes, s));
   CK(cudaMemsetAsync(h->solved.p, 0x7f, h->solved.bytes, s));
   return AFS_OK;
 }
@@ -704,8 +815,11 @@ int afs_step(afs_handle* h, int32_t nsteps, void* stream) {
   if (nsteps < 0) return fail(AFS_E_ARG, "nsteps must be >= 0");
   if (nsteps == 0) return AFS_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool check = h->p.verify_every != 0;
+  const int p0 = h->parity;
+  h->parity = (h->parity + nsteps) & 1;
   if (!h->p.use_graph) {
-    int rc = enqueue_steps(h, nsteps, h->p.eta, true, s, &h->last_launches);
+    int rc = enqueue_steps(h, nsteps, h->p.eta, check, p0, s, &h->last_launches);
     if (rc) return rc;
     if (h->timing) collect_timing(h);
     return AFS_OK;
@@ -713,13 +827,14 @@ int afs_step(afs_handle* h, int32_t nsteps, void* stream) {
   // With kernel timing on, the captured graph also carries event-record nodes
   // around the FE and CSR launches of every chunk; it is cached separately.
   auto& cache = h->timing ? h->timed_graphs : h->graphs;
-  auto it = cache.find(nsteps);
+  const auto key = std::make_pair(static_cast<int>(nsteps), p0);
+  auto it = cache.find(key);
   long long nl = 0;
   if (it == cache.end()) {
     cudaGraph_t graph;
     const size_t fe0 = h->fe_pairs.size(), cs0 = h->csr_pairs.size();
     CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_steps(h, nsteps, h->p.eta, true, h->cap, &nl);
+    int rc = enqueue_steps(h, nsteps, h->p.eta, check, p0, h->cap, &nl);
     cudaError_t ce = cudaStreamEndCapture(h->cap, &graph);
     if (rc) return rc;
     if (ce != cudaSuccess) return fail(AFS_E_CUDA, "graph capture: %s", cudaGetErrorString(ce));
@@ -728,21 +843,21 @@ int afs_step(afs_handle* h, int32_t nsteps, void* stream) {
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return fail(AFS_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
     if (h->timing) {
-      h->timed_pairs[nsteps] = {std::vector<std::pair<int, int>>(h->fe_pairs.begin() + fe0, h->fe_pairs.end()),
-                                std::vector<std::pair<int, int>>(h->csr_pairs.begin() + cs0, h->csr_pairs.end())};
+      h->timed_pairs[key] = {std::vector<std::pair<int, int>>(h->fe_pairs.begin() + fe0, h->fe_pairs.end()),
+                             std::vector<std::pair<int, int>>(h->csr_pairs.begin() + cs0, h->csr_pairs.end())};
       h->fe_pairs.resize(fe0);
       h->csr_pairs.resize(cs0);
     }
-    it = cache.emplace(nsteps, exec).first;
+    it = cache.emplace(key, exec).first;
   } else {
     const int chunks = (h->B + h->Bc - 1) / h->Bc;
-    nl = static_cast<long long>(nsteps) * chunks * (static_cast<long long>(h->groups.size()) + 1);
-    if (h->p.verify_every > 0) nl += 2LL * ((nsteps / h->p.verify_every) + (nsteps % h->p.verify_every ? 1 : 0));
+    nl = static_cast<long long>(nsteps) * chunks * (static_cast<long long>(h->groups.size()) + (check ? 2 : 1));
+    if (check) nl += 2;
   }
   h->last_launches = nl;
   CK(cudaGraphLaunch(it->second, s));
   if (h->timing) {
-    auto& pr = h->timed_pairs[nsteps];
+    auto& pr = h->timed_pairs[key];
     h->fe_pairs.insert(h->fe_pairs.end(), pr.first.begin(), pr.first.end());
     h->csr_pairs.insert(h->csr_pairs.end(), pr.second.begin(), pr.second.end());
     CK(cudaStreamSynchronize(s));
@@ -773,7 +888,7 @@ int afs_round_and_verify(afs_handle* h, int32_t* unsat_host, int32_t* best_host,
   if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CK(cudaMemsetAsync(h->solved.p, 0x7f, h->solved.bytes, s));
-  int rc = launch_check(h, false, s);
+  int rc = launch_check(h, s);
   if (rc) return rc;
   const size_t nib = static_cast<size_t>(h->n_inst) * h->B;
   std::vector<int> un(nib);
@@ -854,7 +969,7 @@ int afs_eval_fe_grad(afs_handle* h, const void* x_dev, int32_t x_dtype, int32_t 
   for (int b0 = 0; b0 < B; b0 += cols) {
     const int nb = std::min(cols, B - b0);
     for (const Group& g : h->groups) {
-      int rc = launch_fe_group(h, g, x_dev, xt, B, b0, nb, h->eval_go.as<float>(), cols, fe_dev, B, s);
+      int rc = launch_fe_group(h, g, x_dev, xt, B, b0, nb, h->eval_go.as<float>(), cols, fe_dev, B, nullptr, s);
       if (rc) return rc;
     }
     if (grad_dev) {
@@ -878,7 +993,7 @@ int afs_step_host(afs_handle* h, const float* x_host, float* x_out_host, int32_t
   launch_convert_in(h->stage.p, XT_F32, h->B, h->x.p, h->xt, h->pitch, h->n, h->B, s);
   CKL();
   const int ve = h->p.verify_every;
-  if (ve <= 0) h->p.verify_every = 1;
+  if (ve == 0) h->p.verify_every = 1;
   int rc = afs_step(h, 1, stream);
   h->p.verify_every = ve;
   if (rc) return rc;

@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <cstdlib>
 
 #include "afsat_internal.h"
 #include "fe_short.cuh"
@@ -150,6 +151,8 @@ template <typename XT, bool ESP>
 __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int kmax) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) unsigned long long bar;
+  pdl_wait();
+  pdl_trigger();
   const LongLayout L(kmax);
   const int tiles = (a.nb + LONG_RT - 1) / LONG_RT;
   const int cl = blockIdx.x / tiles;
@@ -206,6 +209,17 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
   int* myce = cke + static_cast<size_t>(w) * L.nseg_max * 32;
   const int nseg = (k + 31) >> 5;
   float fe_part = 0.0f;
+
+  // exact check of the state read (Algorithm 1's unsat count): warp w, restart bt + w
+  if (a.vflag != nullptr) {
+    int t = 0;
+    for (int i = lane; i < k; i += 32) t += lit_true(el[i], lits[i].x & 1);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0 && bt + w < a.nb && __ldg(a.viol + __ldg(a.cons_voff + cb) + t))
+      a.vflag[static_cast<long long>(blockIdx.x % VFLAG_SLOTS) * a.vflag_stride +
+              static_cast<long long>(__ldg(a.cons_inst + cb)) * a.B + a.b0 + bt + w] = 1;
+  }
 
   for (int rg = 0; rg < nroots; rg += 32) {
     const int j = rg + lane;
@@ -283,7 +297,7 @@ static void launch_long_t(const FeGroupArgs& a, cudaStream_t s) {
   const size_t smem = LongLayout(a.k).bytes(ESP);
   const int tiles = (a.nb + LONG_RT - 1) / LONG_RT;
   const long long blocks = static_cast<long long>(tiles) * a.c_count;
-  fe_grad_long_kernel<XT, ESP><<<static_cast<unsigned>(blocks), 256, smem, s>>>(a, a.k);
+  launch_pdl(fe_grad_long_kernel<XT, ESP>, dim3(static_cast<unsigned>(blocks)), dim3(256), smem, s, a, a.k);
 }
 
 template <typename K>
@@ -292,6 +306,14 @@ static bool raise_smem_cap(K kernel, int optin) {
   if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return false;
   const int cap = optin - static_cast<int>(fa.sharedSizeBytes);
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) == cudaSuccess;
+}
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("AFS_PDL");
+    return !(e != nullptr && e[0] == '0');
+  }();
+  return on;
 }
 
 bool prepare_kernels() {
@@ -347,6 +369,8 @@ __device__ __forceinline__ float load_x_rw<__nv_bfloat16>(const __nv_bfloat16* p
 
 template <typename XT>
 __global__ void __launch_bounds__(256) csr_update_kernel(CsrArgs a) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const long long warp = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int tiles = (a.nb + 31) >> 5;
@@ -357,22 +381,33 @@ __global__ void __launch_bounds__(256) csr_update_kernel(CsrArgs a) {
   if (bl >= a.nb) return;
   const int v = a.v_begin + static_cast<int>(vl);
   const int s0 = __ldg(a.csr_off + v), s1 = __ldg(a.csr_off + v + 1);
+  // eight independent loads in flight per lane; the summation order is fixed
+  // by the slot order, so the result does not depend on timing
   const float* col = a.go + bl;
-  float acc0 = 0.f, acc1 = 0.f;
+  float acc[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) acc[u] = 0.f;
   int s = s0;
-  for (; s + 1 < s1; s += 2) {
-    acc0 += __ldg(col + static_cast<long long>(s) * a.go_pitch);
-    acc1 += __ldg(col + static_cast<long long>(s + 1) * a.go_pitch);
+  for (; s + 7 < s1; s += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldg(col + static_cast<long long>(s + u) * a.go_pitch);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] += v[u];
   }
-  if (s < s1) acc0 += __ldg(col + static_cast<long long>(s) * a.go_pitch);
-  const float g = acc0 + acc1;
+  {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = s + u < s1 ? __ldg(col + static_cast<long long>(s + u) * a.go_pitch) : 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] += v[u];
+  }
+  const float g = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
   if (a.grad != nullptr) {
     a.grad[static_cast<long long>(v) * a.grad_pitch + a.b0 + bl] = g;
     return;
   }
-  if (a.frozen != nullptr &&
-      a.frozen[static_cast<long long>(__ldg(a.var_inst + v)) * a.B + a.b0 + bl] != 0)
-    return;
+  if (a.sflag != nullptr && a.sflag[static_cast<long long>(__ldg(a.var_inst + v)) * a.B + a.b0 + bl] != 0) return;
   XT* xp = static_cast<XT*>(a.x) + static_cast<long long>(v) * a.x_pitch + a.b0 + bl;
   const float xn = fminf(fmaxf(fmaf(-a.eta, g, load_x_rw<XT>(xp)), -1.0f), 1.0f);
   store_x<XT>(xp, xn);
@@ -383,8 +418,8 @@ void launch_csr_update(const CsrArgs& a, int xt, cudaStream_t s) {
   const long long nwarps = tiles * a.v_count;
   const long long blocks = (nwarps + 7) / 8;
   if (blocks == 0) return;
-  if (xt == XT_F32) csr_update_kernel<float><<<static_cast<unsigned>(blocks), 256, 0, s>>>(a);
-  else csr_update_kernel<__nv_bfloat16><<<static_cast<unsigned>(blocks), 256, 0, s>>>(a);
+  if (xt == XT_F32) launch_pdl(csr_update_kernel<float>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+  else launch_pdl(csr_update_kernel<__nv_bfloat16>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -395,6 +430,8 @@ void launch_csr_update(const CsrArgs& a, int xt, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 template <typename XT>
 __global__ void __launch_bounds__(256) verify_kernel(VerifyArgs a) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const long long warp = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int tiles = (a.B + 31) >> 5;
@@ -406,12 +443,24 @@ __global__ void __launch_bounds__(256) verify_kernel(VerifyArgs a) {
   const int4 rg = __ldg(a.ranges + rgi);
   const XT* x = static_cast<const XT*>(a.x);
   int count = 0;
+  const XT* xb = x + (act ? b : 0);
   for (int c = rg.x; c < rg.y; ++c) {
     const int l0 = __ldg(a.lit_off + c), l1 = __ldg(a.lit_off + c + 1);
     int t = 0;
-    for (int l = l0; l < l1; ++l) {
+    int l = l0;
+    for (; l + 3 < l1; l += 4) {  // four independent gathers in flight
+      const int e0 = __ldg(a.lit_enc + l), e1 = __ldg(a.lit_enc + l + 1);
+      const int e2 = __ldg(a.lit_enc + l + 2), e3 = __ldg(a.lit_enc + l + 3);
+      const float x0 = load_x<XT>(xb + static_cast<long long>(e0 >> 1) * a.x_pitch);
+      const float x1 = load_x<XT>(xb + static_cast<long long>(e1 >> 1) * a.x_pitch);
+      const float x2 = load_x<XT>(xb + static_cast<long long>(e2 >> 1) * a.x_pitch);
+      const float x3 = load_x<XT>(xb + static_cast<long long>(e3 >> 1) * a.x_pitch);
+      t += (static_cast<int>(x0 < 0.0f) ^ (e0 & 1)) + (static_cast<int>(x1 < 0.0f) ^ (e1 & 1)) +
+           (static_cast<int>(x2 < 0.0f) ^ (e2 & 1)) + (static_cast<int>(x3 < 0.0f) ^ (e3 & 1));
+    }
+    for (; l < l1; ++l) {
       const int enc = __ldg(a.lit_enc + l);
-      const float xv = act ? load_x<XT>(x + static_cast<long long>(enc >> 1) * a.x_pitch + b) : 1.0f;
+      const float xv = load_x<XT>(xb + static_cast<long long>(enc >> 1) * a.x_pitch);
       t += static_cast<int>(xv < 0.0f) ^ (enc & 1);
     }
     count += __ldg(a.viol + __ldg(a.viol_off + c) + t);
@@ -424,26 +473,52 @@ void launch_verify(const VerifyArgs& a, int xt, cudaStream_t s) {
   const long long nwarps = tiles * a.n_ranges;
   const long long blocks = (nwarps + 7) / 8;
   if (blocks == 0) return;
-  if (xt == XT_F32) verify_kernel<float><<<static_cast<unsigned>(blocks), 256, 0, s>>>(a);
-  else verify_kernel<__nv_bfloat16><<<static_cast<unsigned>(blocks), 256, 0, s>>>(a);
+  if (xt == XT_F32) launch_pdl(verify_kernel<float>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+  else launch_pdl(verify_kernel<__nv_bfloat16>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+}
+
+// Fold of the fused check: restart (inst, b) is solved when no warp flagged a
+// violation in any row. Records the lowest solved restart per instance and
+// clears the rows the next step's check writes.
+__global__ void fold_flags_kernel(FlagArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= static_cast<long long>(a.n_inst) * a.nb) return;
+  const int inst = static_cast<int>(i / a.nb);
+  const int b = a.b0 + static_cast<int>(i - static_cast<long long>(inst) * a.nb);
+  const long long ui = static_cast<long long>(inst) * a.B + b;
+  int any = 0;
+#pragma unroll 8
+  for (int s = 0; s < VFLAG_SLOTS; ++s) {
+    any |= a.vflag_cur[s * a.stride + ui];
+    a.vflag_next[s * a.stride + ui] = 0;
+  }
+  a.sflag[ui] = any ? 0 : 1;
+  if (!any) atomicMin(a.solved + inst, b);
+}
+
+void launch_fold_flags(const FlagArgs& a, cudaStream_t s) {
+  const long long n = static_cast<long long>(a.n_inst) * a.nb;
+  if (n == 0) return;
+  launch_pdl(fold_flags_kernel, dim3(static_cast<unsigned>((n + 255) / 256)), dim3(256), 0, s, a);
 }
 
 // A restart with no violated constraint is solved: record the lowest such
-// restart per instance and freeze it (Algorithm 1 returns on is_sat).
-__global__ void solved_kernel(const int* unsat, int n_inst, int B, int* solved, signed char* frozen) {
+// restart per instance.
+__global__ void solved_kernel(const int* unsat, int n_inst, int B, int* solved) {
+  pdl_wait();
+  pdl_trigger();
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= static_cast<long long>(n_inst) * B) return;
   const int inst = static_cast<int>(i / B), b = static_cast<int>(i - static_cast<long long>(inst) * B);
-  if (unsat[i] == 0) {
-    atomicMin(solved + inst, b);
-    if (frozen != nullptr) frozen[i] = 1;
-  }
+  if (unsat[i] == 0) atomicMin(solved + inst, b);
 }
 
-void launch_solved(const int* unsat, int n_inst, int B, int* solved, signed char* frozen, cudaStream_t s) {
+void launch_solved(const int* unsat, int n_inst, int B, int* solved, cudaStream_t s) {
   const long long n = static_cast<long long>(n_inst) * B;
   if (n == 0) return;
-  solved_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(unsat, n_inst, B, solved, frozen);
+  launch_pdl(solved_kernel, dim3(static_cast<unsigned>((n + 255) / 256)), dim3(256), 0, s, unsat, n_inst, B, solved);
 }
 
 // ---------------------------------------------------------------------------
