@@ -177,6 +177,25 @@ int afs_get_verify(afs_handle* h, int32_t* unsat_dev, int32_t* solved_dev, void*
 int afs_eval_fe_grad(afs_handle* h, const void* x_dev, int32_t x_dtype, int32_t B, float* fe_dev,
                      float* grad_dev, void* stream);
 
+/* afs_eval_fe_grad_noalloc: the same outputs as afs_eval_fe_grad for FP32
+ * x_dev[v * B + b], without allocating device memory. The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc at this point
+ * (cudaMalloc/cudaFree synchronise the device and take a driver-wide lock, or
+ * all device memory is already reserved by another allocator). The handle
+ * and the caller's x, fe and grad buffers are the only memory used besides a
+ * fixed 16 MiB file-scope device array inside the library, which every GPU
+ * that loads the library holds until the process exits. Restarts are
+ * processed in chunks of 32..256 columns sized to that array; an instance
+ * whose literal occurrences x 32 restarts x 4 bytes exceed 16 MiB (more than
+ * 131072 occurrences) is rejected with AFS_E_ARG. The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture. All calls share the one array
+ * and its contents carry over from the last call, so calls whose work
+ * overlaps on the GPU (different streams, or different handles at once)
+ * race; serialise them. */
+int afs_eval_fe_grad_noalloc(afs_handle* h, const float* x_dev, int32_t B, float* fe_dev, float* grad_dev,
+                             void* stream);
+
 /* afs_step_host: one step of the whole hot path through host memory: copies
  * x_host[v * B + b] (pinned host FP32) to the device, runs one afs_step with
  * the exact check, and copies back the unsat counts (unsat_host[n_inst * B])

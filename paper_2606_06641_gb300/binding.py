@@ -44,6 +44,7 @@ SIGNATURES = {
     "afs_set_x": (_I32, [_P, _P, _P]),
     "afs_get_verify": (_I32, [_P, _P, _P, _P]),
     "afs_eval_fe_grad": (_I32, [_P, _P, _I32, _I32, _P, _P, _P]),
+    "afs_eval_fe_grad_noalloc": (_I32, [_P, _P, _I32, _P, _P, _P]),
     "afs_step_host": (_I32, [_P, _P, _P, _P, _P]),
     "afs_info": (_I32, [_P, _P]),
     "afs_work_per_restart": (_I32, [_P, _P]),
@@ -234,6 +235,19 @@ def eval_fe_grad(h: Handle, x, want_fe: bool = True, want_grad: bool = True, str
     g = torch.empty((h.n, B), dtype=torch.float32, device=x.device) if want_grad else None
     _check(lib().afs_eval_fe_grad(h.ptr, _ptr(x), dt, B, _ptr(fe), _ptr(g), _stream(stream)))
     return fe, g
+
+
+def eval_fe_grad_noalloc(h: Handle, x, fe=None, grad=None, stream=None):
+    """FE [m, B] and gradient [n, B] at FP32 x [n, B] through the entry point
+    that allocates no device memory (its scratch is a fixed array inside the
+    library). The caller passes the output buffers (either may be None)."""
+    assert x.is_cuda and x.is_contiguous() and x.shape[0] == h.n
+    B = x.shape[1]
+    for out, rows in ((fe, h.m), (grad, h.n)):
+        if out is not None:
+            assert out.is_cuda and out.is_contiguous() and tuple(out.shape) == (rows, B)
+    _check(lib().afs_eval_fe_grad_noalloc(h.ptr, _ptr(x), B, _ptr(fe), _ptr(grad), _stream(stream)))
+    return fe, grad
 
 
 def step_host(h: Handle, x_host, x_out_host=None, stream=None):

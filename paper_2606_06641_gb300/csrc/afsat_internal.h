@@ -112,6 +112,22 @@ void launch_convert_in(const void* src, int src_xt, long long src_pitch, void* d
                        long long dst_pitch, int n, int B, cudaStream_t s);
 void launch_gather_column(const void* x, int xt, long long x_pitch, const int* var_list, int count,
                           const int* col_of, signed char* out, cudaStream_t s);
+}  // namespace afs
+
+struct afs_handle;
+
+namespace afs {
+
+// Records an error message for afs_last_error() and returns `code`.
+int set_error(int code, const char* fmt, ...);
+
+// FE and gradient of FP32 x[v * B + b] into fe/grad (nullable) using the
+// caller-provided occurrence-derivative buffer `scratch` of `cap_floats`
+// floats; allocates nothing. Restarts are processed in column chunks sized
+// to fit the buffer.
+int eval_into_scratch(afs_handle* h, const float* x, int B, float* fe, float* grad, float* scratch,
+                      long long cap_floats, cudaStream_t s);
+
 // Restarts per lane available for a short group of length k.
 inline int max_rpl_for_k(int k) { return k <= 8 ? 4 : (k <= 16 ? 2 : 1); }
 

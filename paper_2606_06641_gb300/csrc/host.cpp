@@ -719,6 +719,41 @@ static int autotune(afs_handle* h, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // ABI
 // ---------------------------------------------------------------------------
+int afs::set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int afs::eval_into_scratch(afs_handle* h, const float* x, int B, float* fe, float* grad, float* scratch,
+                           long long cap_floats, cudaStream_t s) {
+  if (!h || !x || !scratch) return fail(AFS_E_ARG, "NULL argument");
+  if (B <= 0) return fail(AFS_E_ARG, "B must be positive");
+  const long long L = std::max<long long>(h->L, 1);
+  long long cols = std::min<long long>((B + 31) / 32 * 32, 256);
+  while (cols > 32 && L * cols > cap_floats) cols -= 32;
+  if (L * cols > cap_floats)
+    return fail(AFS_E_ARG,
+                "instance has %lld literal occurrences: 32 restarts need %lld bytes of scratch, the buffer holds %lld",
+                h->L, L * 32 * 4, cap_floats * 4);
+  for (int b0 = 0; b0 < B; b0 += static_cast<int>(cols)) {
+    const int nb = std::min(static_cast<int>(cols), B - b0);
+    for (const Group& g : h->groups) {
+      int rc = launch_fe_group(h, g, x, XT_F32, B, b0, nb, scratch, cols, fe, B, nullptr, s);
+      if (rc) return rc;
+    }
+    if (grad) {
+      int rc = launch_csr(h, nullptr, XT_F32, B, b0, nb, scratch, cols, 0.0f, grad, B, false, s);
+      if (rc) return rc;
+    }
+  }
+  return AFS_OK;
+}
+
 extern "C" {
 
 void afs_default_params(afs_params* p) {
