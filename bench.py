@@ -1,12 +1,12 @@
 """Benchmark of the Fourier-expansion CLS hot path on GB300.
 
-Workload: the hybrid mixed-type instance (n=2000 variables; 8000 random
-3-clauses, 400 XOR of length 5 with a fair parity, 200 CARD of length 20 with
-threshold >= 10, 100 NAE of length 4), B=1024 restarts per GPU, FP32 state.
-A step is one pass of the whole hot path for all restarts: FE and analytic
-gradient of every constraint, CSR gather and projected step, and the exact
-integer check of the rounded state. Metric: literal-evals/s = (literal
-occurrences) x (restarts) per second of that step.
+Default workload (``--workload hybrid``): the hybrid mixed-type instance
+(n=2000 variables; 8000 random 3-clauses, 400 XOR of length 5 with a fair
+parity, 200 CARD of length 20 with threshold >= 10, 100 NAE of length 4),
+B=1024 restarts per GPU, FP32 state. A step is one pass of the whole hot path
+for all restarts: FE and analytic gradient of every constraint with the fused
+exact check of the state read, the solved fold, the CSR gather and projected
+step. Metric: literal-evals/s = literal occurrences x restarts x steps / s.
 
 Timing: W untimed warm-up steps; K timed steps as K/S replays of an S-step
 CUDA graph (S = --steps-per-graph), each replay bracketed by CUDA events on
@@ -14,6 +14,17 @@ the launching stream, with L2 flushed (a 512 MB write) between replays. Under
 torchrun every rank runs its own restarts (weak scaling, no collective on the
 data path); the timed region is bracketed by a barrier and device syncs and
 the max over ranks is reported.
+
+The default line also carries ``time_to_solve``: random 3-SAT instances of
+n=50, m=213 solved by plain CLS (one instance at a time, un-captured launches,
+solved flag read every step) and by the batched form (all instances in one
+handle, graph replays), from identical starting points, so both follow the
+same trajectories and reach the same solve rate.
+
+Other workloads: ``long`` (n=10000, 30000 3-clauses + 500 CARD/EK of length
+64..512, B=4096; adds a precision report of the FP32 PGF basis, the paper's
+ESP basis and BF16 state against the FP64 oracle) and ``batch`` (256
+instances of n log-uniform in [100, 20000], B=64 each, one handle).
 
 --impl reference times the CPU oracle (FP64 numpy, Poisson-binomial
 recurrence) on a bounded sample of the same workload.
@@ -32,8 +43,14 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = ("hybrid mixed-type instance n=2000: 8000 3-OR, 400 XOR(5, fair parity), 200 CARD(20)>=10, "
-            "100 NAE(4); B=1024 restarts per GPU")
+WORKLOADS = {
+    "hybrid": ("hybrid mixed-type instance n=2000: 8000 3-OR, 400 XOR(5, fair parity), 200 CARD(20)>=10, "
+               "100 NAE(4); B=1024 restarts per GPU", 1024),
+    "long": ("long-constraint instance n=10000: 30000 3-OR + 500 CARD>=r / EK=r of length U[64,512], "
+             "r U[k/4,3k/4]; B=4096 restarts per GPU", 4096),
+    "batch": ("uneven batch: 256 instances, n log-U[100,20000], m/n U[4.0,4.3], 90% 3-OR, 5% XOR(3..8), "
+              "5% CARD(10..100); B=64 restarts each, one handle", 64),
+}
 METRIC = "FE+grad literal-evals/s"
 UNIT = "literal-evals/s"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fe_grad_traffic.json")
@@ -127,13 +144,25 @@ def gpu_id_for(dev: int) -> str:
         return vis.split(",")[dev] if vis else str(dev)
 
 
-def cpu_oracle_sample(inst, B_sample: int, budget_s: float, seed: int = 0):
-    """The oracle's FE + gradient + projected step on B_sample restarts,
-    repeated for about budget_s seconds of host time."""
+def make_workload(name: str):
+    from paper_2606_06641_gb300 import synth
+    if name == "hybrid":
+        return [synth.config2(0)]
+    if name == "long":
+        return [synth.config3(0)]
+    if name == "batch":
+        return synth.config4(256)
+    raise ValueError(name)
+
+
+def cpu_oracle_sample(insts, B_sample: int, budget_s: float, seed: int = 0):
+    """The oracle's FE + gradient + projected step + exact check on B_sample
+    restarts of the first instance, repeated for about budget_s seconds."""
     import numpy as np
 
     from oracle import fe_oracle as O
     from paper_2606_06641_gb300 import synth
+    inst = insts[0]
     x = synth.uniform_x0(inst.n, B_sample, seed).astype(np.float64)
     reps = 0
     t0 = time.perf_counter()
@@ -151,24 +180,22 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    from paper_2606_06641_gb300 import synth
-    inst = synth.config2(0)
-    B_sample = 8
+    insts = make_workload(args.workload)
+    desc, B_full = WORKLOADS[args.workload]
+    B_sample = 8 if args.workload == "hybrid" else 2
     for _ in range(max(args.warmup, 0)):
-        cpu_oracle_sample(inst, B_sample, 0.0)
-    vals = []
+        cpu_oracle_sample(insts, B_sample, 0.0)
     t_all = time.perf_counter()
     for _ in range(args.steps):
-        v, _, _ = cpu_oracle_sample(inst, B_sample, 0.0)
-        vals.append(v)
+        cpu_oracle_sample(insts, B_sample, 0.0)
     el = time.perf_counter() - t_all
-    value = inst.n_lits * B_sample * args.steps / el
+    value = insts[0].n_lits * B_sample * args.steps / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"{B_sample} of 1024 restarts per step"},
+        "config": {"workload": desc, "sample": f"{B_sample} of {B_full} restarts of the first instance per step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"FP64 oracle step (FE, gradient, projected step, exact check) on "
                                    f"{B_sample} restarts per step, {args.steps} steps"},
@@ -178,8 +205,76 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
+def measure_time_to_solve(n_inst: int, B: int, eta: float, max_steps: int, seed: int = 17):
+    """Plain CLS vs the batched form on config-1 style random 3-SAT instances,
+    both from the same Philox starting points."""
     import numpy as np
+    import torch
+
+    from paper_2606_06641_gb300 import binding as bd
+    from paper_2606_06641_gb300 import solver
+    from paper_2606_06641_gb300 import synth
+    insts = [synth.config5(i, "test") for i in range(n_inst)]
+    hb = bd.load_batch(insts, bd.default_params(eta=eta, autotune=0))
+    bd.init_restarts(hb, B, seed=seed)
+    x_all = bd.get_x(hb)
+    hb.free()
+    x0s, v0 = [], 0
+    for inst in insts:
+        x0s.append(x_all[v0:v0 + inst.n].contiguous())
+        v0 += inst.n
+    torch.cuda.synchronize()
+    solver.solve_batched(insts[:2], B, eta, 5, seed=seed)       # warm the library and allocator
+    plain = solver.solve_plain(insts, B, eta, max_steps, x0s=x0s)
+    batched = solver.solve_batched(insts, B, eta, max_steps, x0=x_all, steps_per_poll=10)
+    timeout = plain.total_seconds  # one common budget: the plain run's wall time
+
+    def summary(r):
+        return {"solved": int(r.solved.sum()), "solve_rate": float(r.solved.mean()),
+                "median_s": solver.median_tts(r, timeout), "par2_s": solver.par2(r, timeout),
+                "median_steps_solved": float(np.median(r.steps[r.solved])) if r.solved.any() else None,
+                "wall_s": r.total_seconds}
+    same = bool(np.array_equal(plain.solved, batched.solved))
+    return {"instances": n_inst, "n": 50, "m": 213, "restarts": B, "eta": eta, "max_steps": max_steps,
+            "timeout_s": timeout, "same_solved_set": same,
+            "plain": summary(plain), "batched": summary(batched),
+            "batched_speedup_median": (summary(plain)["median_s"] / summary(batched)["median_s"])
+            if summary(batched)["median_s"] > 0 else None}
+
+
+def precision_report(inst, n_restarts: int = 4):
+    """Max errors of the FE values and gradient against the FP64 oracle for the
+    FP32 PGF basis, the paper's ESP basis with scaled products, and BF16 state
+    (at the original FP32 point), on sampled restarts."""
+    import numpy as np
+    import torch
+
+    from oracle import fe_oracle as O
+    from paper_2606_06641_gb300 import binding as bd
+    from paper_2606_06641_gb300 import synth
+    x = synth.uniform_x0(inst.n, n_restarts, 5)
+    fe_ref, _, g_ref = O.evaluate(inst, x.astype(np.float64))
+    xd = torch.from_numpy(x).cuda()
+    out = {}
+    for name, params, xin in (("pgf_f32", bd.default_params(), xd),
+                              ("esp_scaled_f32", bd.default_params(basis=bd.BASIS_ESP), xd),
+                              ("pgf_bf16_state", bd.default_params(), xd.to(torch.bfloat16))):
+        h = bd.load_instance(inst, params)
+        fe, g = bd.eval_fe_grad(h, xin)
+        fe = fe.cpu().numpy()
+        g = g.cpu().numpy()
+        k = np.diff(inst.lit_off)
+        long_rows = k > 32
+        d_fe = np.abs(fe - fe_ref)
+        d_g = np.abs(g - g_ref)
+        out[name] = {"fe_max_err": float(np.nanmax(np.where(np.isfinite(d_fe), d_fe, np.inf))),
+                     "fe_max_err_long": float(np.nanmax(np.where(np.isfinite(d_fe[long_rows]), d_fe[long_rows], np.inf))),
+                     "grad_max_err": float(np.nanmax(np.where(np.isfinite(d_g), d_g, np.inf)))}
+        h.free()
+    return {"restarts": n_restarts, **out}
+
+
+def run_ours(args):
     import torch
 
     rank, world, local = dist_env()
@@ -191,21 +286,23 @@ def run_ours(args):
 
     from paper_2606_06641_gb300 import binding as bd
     from paper_2606_06641_gb300 import build as _b
-    from paper_2606_06641_gb300 import synth
     if rank == 0 or world == 1:
         _b.build()
     if world > 1:
         torch.distributed.barrier()
 
-    inst = synth.config2(0)
-    B = args.restarts
+    desc, B_default = WORKLOADS[args.workload]
+    B = args.restarts or B_default
+    insts = make_workload(args.workload)
     params = bd.default_params(eta=0.1, verify_every=1, chunk=args.chunk)
-    h = bd.load_instance(inst, params)
+    h = bd.load_instance(insts[0], params) if len(insts) == 1 else bd.load_batch(insts, params)
     bd.init_restarts(h, B, seed=1000 + rank)
     stream = torch.cuda.current_stream()
     S = max(1, min(args.steps_per_graph, args.steps))
     R = max(1, args.steps // S)
     K = R * S
+    L = sum(i.n_lits for i in insts)
+    n_total = sum(i.n for i in insts)
 
     # warm-up: W single steps, then one untimed replay of the timed graph
     for _ in range(max(args.warmup, 3)):
@@ -244,7 +341,6 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     dev_ms = float(t.item())
 
-    L = inst.n_lits
     value = L * B * K * world / (dev_ms * 1e-3)
     work = bd.work_per_restart(h) * B          # FP32 lane instructions per step
     fe_ms_step = fe_ms / K
@@ -257,7 +353,7 @@ def run_ours(args):
     if os.path.exists(TRAFFIC_FILE):
         with open(TRAFFIC_FILE) as fh:
             tr = json.load(fh)
-        if tr.get("kernel_source_hash") == kernel_source_hash():
+        if tr.get("kernel_source_hash") == kernel_source_hash() and tr.get("workload") == args.workload:
             traffic = tr.get("bytes_per_step")
 
     # end to end through the public API: pinned host x in, one step, x and unsat counts out
@@ -272,23 +368,32 @@ def run_ours(args):
         for _ in range(E):
             bd.step_host(h, x_host, x_host)
         el = time.perf_counter() - t0
-        e2e = {"value": L * B * E * world / el, "unit": UNIT, "h2d_bytes_per_step": inst.n * B * 4,
-               "d2h_bytes_per_step": inst.n * B * 4 + B * 4}
+        e2e = {"value": L * B * E * world / el, "unit": UNIT, "h2d_bytes_per_step": n_total * B * 4,
+               "d2h_bytes_per_step": n_total * B * 4 + len(insts) * B * 4}
+    chunk, rpl = bd.tuning(h)
+    h.free()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, reps, el = cpu_oracle_sample(inst, 8, args.cpu_seconds)
+        Bs = 8 if args.workload == "hybrid" else 2
+        v, reps, el = cpu_oracle_sample(insts, Bs, args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"FP64 oracle step (FE, gradient, projected step, exact check) on 8 of 1024 restarts, "
-                         f"{reps} steps in {el:.1f} s"}
+               "sample": f"FP64 oracle step (FE, gradient, projected step, exact check) on {Bs} of {B} restarts"
+                         f" of the first instance, {reps} steps in {el:.1f} s"}
 
-    chunk, rpl = bd.tuning(h)
+    tts = None
+    if rank == 0 and args.workload == "hybrid" and not args.no_tts:
+        tts = measure_time_to_solve(args.tts_instances, 32, args.tts_eta, 500)
+    precision = None
+    if rank == 0 and args.workload == "long" and not args.no_cpu:
+        precision = precision_report(insts[0])
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": max(args.warmup, 3), "ms_per_step": dev_ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "restarts": B, "literals": L,
+            "config": {"workload": desc, "restarts": B, "literals": L, "instances": len(insts),
                        "l2": f"flushed (512 MB write) between timed CUDA-graph replays of {S} steps",
                        "chunk_restarts": chunk, "restarts_per_lane": rpl, "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
@@ -303,6 +408,10 @@ def run_ours(args):
             "clocks": clocks,
             "gpu_launches": launches,
         }
+        if tts is not None:
+            line["time_to_solve"] = tts
+        if precision is not None:
+            line["precision"] = precision
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -315,12 +424,16 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--restarts", type=int, default=1024)
+    ap.add_argument("--workload", default="hybrid", choices=sorted(WORKLOADS))
+    ap.add_argument("--restarts", type=int, default=0, help="restarts per GPU (0 = the workload's)")
     ap.add_argument("--steps-per-graph", type=int, default=10)
     ap.add_argument("--chunk", type=int, default=0, help="restarts per chunk (0 = autotuned)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--tts-instances", type=int, default=128)
+    ap.add_argument("--tts-eta", type=float, default=0.1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tts", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -203,6 +203,45 @@ int afs_eval_fe_grad_noalloc(afs_handle* h, const float* x_dev, int32_t B, float
 int afs_step_host(afs_handle* h, const float* x_host, float* x_out_host, int32_t* unsat_host,
                   void* stream);
 
+/* ---- learned initialiser ----------------------------------------------
+ * The paper has no learned component; this is the benchmark plan's
+ * initialiser: a bipartite variable-constraint message-passing network
+ * (hidden width 64, `layers` rounds) over a loaded handle's instance graph.
+ * Per round the constraints take the signed mean of U h_v over their
+ * literals, then the variables the signed mean of V h_c over their
+ * occurrences, each followed by relu(W [h; message] + b); the output is
+ * mu_v = tanh(w h_v + b) in [-1, 1] (negative = True). Dense products run on
+ * tensor cores with BF16 operands and FP32 accumulation; parameters are one
+ * flat FP32 vector in the order Av[64x4], av, Ac[64x16], ac, then per round
+ * U, V[64x64], Wc[64x128], bc, Wv[64x128], bv, then w[64], b[1]. Features:
+ * f_v = (deg/8, (pos-neg)/deg, 1, 0); f_c = (one-hot type, k/8, param/k,
+ * parity, op, 1, 0...). Per-graph buffers are kept with the handle. */
+typedef struct afs_mpnn afs_mpnn;
+int afs_mpnn_create(int32_t hidden, int32_t layers, uint64_t seed, afs_mpnn** out);
+void afs_mpnn_free(afs_mpnn* net);
+int afs_mpnn_num_params(const afs_mpnn* net, int64_t* n);
+/* copy the flat parameter vector out of / into device memory */
+int afs_mpnn_get_params(afs_mpnn* net, float* theta_dev, void* stream);
+int afs_mpnn_set_params(afs_mpnn* net, const float* theta_dev, void* stream);
+/* mu_dev[n_total] = the network's output for the handle's variables */
+int afs_mpnn_forward(afs_mpnn* net, afs_handle* h, float* mu_dev, void* stream);
+/* Loss = sum_v w_v BCE(p_v, y_v) / wsum with p_v = (1 - mu_v)/2 the predicted
+ * probability that v is True and y_dev[n_total] soft labels in [0, 1]
+ * (w_dev nullable = all ones). Writes the parameter gradient into the net's
+ * gradient buffer (and grad_dev if not NULL) and the loss into *loss_host
+ * (nullable; when given the stream is synchronised). */
+int afs_mpnn_loss_grad(afs_mpnn* net, afs_handle* h, const float* y_dev, const float* w_dev, float wsum,
+                       float* grad_dev, float* loss_host, void* stream);
+/* One Adam step (beta 0.9/0.999, eps 1e-8, bias-corrected) with the last gradient. */
+int afs_mpnn_adam_step(afs_mpnn* net, float lr, void* stream);
+/* Overwrite the handle's restart state (after afs_init_restarts with the
+ * same B): the first round((1-uniform_frac) B) restarts get
+ * x = clamp(mu_v + sigma_b eps, -1, 1), sigma_b ramped from sigma_min to
+ * sigma_max, eps uniform on [-1, 1) from Philox4x32-10 keyed by `seed`; the
+ * remaining restarts stay uniform on [-1, 1) as the fallback. */
+int afs_mpnn_init_restarts(afs_mpnn* net, afs_handle* h, int32_t B, uint64_t seed, float uniform_frac,
+                           float sigma_min, float sigma_max, void* stream);
+
 /* ---- introspection ------------------------------------------------------ */
 /* Sizes: n_total variables, m constraints, n_lits literals, n_inst, B. */
 int afs_info(const afs_handle* h, int64_t* out6);

@@ -46,6 +46,16 @@ SIGNATURES = {
     "afs_eval_fe_grad": (_I32, [_P, _P, _I32, _I32, _P, _P, _P]),
     "afs_eval_fe_grad_noalloc": (_I32, [_P, _P, _I32, _P, _P, _P]),
     "afs_step_host": (_I32, [_P, _P, _P, _P, _P]),
+    "afs_mpnn_create": (_I32, [_I32, _I32, ctypes.c_uint64, _P]),
+    "afs_mpnn_free": (None, [_P]),
+    "afs_mpnn_num_params": (_I32, [_P, _P]),
+    "afs_mpnn_get_params": (_I32, [_P, _P, _P]),
+    "afs_mpnn_set_params": (_I32, [_P, _P, _P]),
+    "afs_mpnn_forward": (_I32, [_P, _P, _P, _P]),
+    "afs_mpnn_loss_grad": (_I32, [_P, _P, _P, _P, ctypes.c_float, _P, _P, _P]),
+    "afs_mpnn_adam_step": (_I32, [_P, ctypes.c_float, _P]),
+    "afs_mpnn_init_restarts": (_I32, [_P, _P, _I32, ctypes.c_uint64, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_float, _P]),
     "afs_info": (_I32, [_P, _P]),
     "afs_work_per_restart": (_I32, [_P, _P]),
     "afs_set_kernel_timing": (_I32, [_P, _I32]),
@@ -258,6 +268,61 @@ def step_host(h: Handle, x_host, x_out_host=None, stream=None):
     h._un_pinned = un
     _check(lib().afs_step_host(h.ptr, _ptr(x_host), _ptr(x_out_host), _ptr(un), _stream(stream)))
     return un
+
+
+class Mpnn:
+    """The learned initialiser's network (parameters live on the device)."""
+
+    def __init__(self, layers: int = 3, seed: int = 0, hidden: int = 64):
+        out = ctypes.c_void_p()
+        _check(lib().afs_mpnn_create(hidden, layers, seed, ctypes.byref(out)))
+        self.ptr = out
+        n = ctypes.c_int64()
+        _check(lib().afs_mpnn_num_params(self.ptr, ctypes.byref(n)))
+        self.n_params = n.value
+        self.layers = layers
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                lib().afs_mpnn_free(self.ptr)
+                self.ptr = ctypes.c_void_p(0)
+        except Exception:
+            pass
+
+    def get_params(self, stream=None):
+        import torch
+        out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        _check(lib().afs_mpnn_get_params(self.ptr, _ptr(out), _stream(stream)))
+        return out
+
+    def set_params(self, theta, stream=None) -> None:
+        assert theta.is_cuda and theta.dtype.itemsize == 4 and theta.numel() == self.n_params
+        _check(lib().afs_mpnn_set_params(self.ptr, _ptr(theta.contiguous()), _stream(stream)))
+
+    def forward(self, h: Handle, stream=None):
+        import torch
+        mu = torch.empty(h.n, dtype=torch.float32, device="cuda")
+        _check(lib().afs_mpnn_forward(self.ptr, h.ptr, _ptr(mu), _stream(stream)))
+        return mu
+
+    def loss_grad(self, h: Handle, y, w=None, want_grad: bool = False, stream=None):
+        """Returns (loss, gradient tensor or None); y and w are device tensors [n]."""
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device="cuda") if want_grad else None
+        loss = ctypes.c_float()
+        wsum = float(w.sum().item()) if w is not None else float(h.n)
+        _check(lib().afs_mpnn_loss_grad(self.ptr, h.ptr, _ptr(y), _ptr(w), wsum, _ptr(g), ctypes.byref(loss),
+                                        _stream(stream)))
+        return loss.value, g
+
+    def adam_step(self, lr: float, stream=None) -> None:
+        _check(lib().afs_mpnn_adam_step(self.ptr, lr, _stream(stream)))
+
+    def init_restarts(self, h: Handle, B: int, seed: int = 0, uniform_frac: float = 0.25,
+                      sigma_min: float = 0.1, sigma_max: float = 0.9, stream=None) -> None:
+        _check(lib().afs_mpnn_init_restarts(self.ptr, h.ptr, B, seed, uniform_frac, sigma_min, sigma_max,
+                                            _stream(stream)))
 
 
 def info(h: Handle) -> List[int]:

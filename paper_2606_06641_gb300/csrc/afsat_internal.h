@@ -78,6 +78,8 @@ struct FlagArgs {
   int n_inst, B, b0, nb;
 };
 void launch_fold_flags(const FlagArgs& a, cudaStream_t s);
+// p[0..n) = v
+void launch_fill_int(int* p, int v, long long n, cudaStream_t s);
 
 // Exact check of the sign-rounded state.
 struct VerifyArgs {
@@ -120,6 +122,28 @@ namespace afs {
 
 // Records an error message for afs_last_error() and returns `code`.
 int set_error(int code, const char* fmt, ...);
+
+// Read-only view of a loaded handle's instance structure (load order) and
+// restart state, for the learned initialiser.
+struct GraphView {
+  int n, m, n_inst;
+  long long L;
+  const int* lit_enc;       // host: var << 1 | negated, load order
+  const int* lit_off;       // host: [m + 1]
+  const int* ctype;         // host: per constraint
+  const int* cop;
+  const int* cparam;
+  const int* cparity;
+  const int* inst_vbegin;   // host: [n_inst + 1]
+  const int* var_inst_dev;  // device: instance of each variable, then first variable per instance
+  void* x;                  // device state (after afs_init_restarts), pitch columns per variable
+  long long pitch;
+  int B, xt;
+};
+int graph_view(const afs_handle* h, GraphView* out);
+// A slot in which other modules keep per-handle device data; released with the handle.
+void* handle_ext(const afs_handle* h);
+void set_handle_ext(afs_handle* h, void* p, void (*release)(void*));
 
 // FE and gradient of FP32 x[v * B + b] into fe/grad (nullable) using the
 // caller-provided occurrence-derivative buffer `scratch` of `cap_floats`

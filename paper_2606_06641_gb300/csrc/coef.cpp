@@ -221,35 +221,39 @@ void build_table(const Shape& s, int basis, int form, std::vector<float>& out) {
       }
     }
   } else {
-    // every root, real or complex, is two granules {a, b}, {D, E}
+    // every root, real or complex, is two granules {A, b}, {D, E} with the
+    // factor written a + b l = A - b (1 - l), A = a + b. In the
+    // probability-generating basis A = 1 exactly, so the FP32 rounding of b
+    // perturbs a factor by eps*|b| (small at the dominant low roots) instead of
+    // eps; with a and b rounded separately that error would add up coherently
+    // over the k factors.
     if (basis == BASIS_PGF) {
       push4(out, cr[0], 0, 0, 0);
       if (odd) {
-        push4(out, 0.0, 0.0, 1.0, 0.0);
+        push4(out, 1.0, 0.0, 1.0, 0.0);
         push4(out, cr[mid], 0.0, cr[mid], 0.0);
       }
       for (int j = 1; j <= k / 2; ++j) {
         double wc, ws;
         unit_root(j, N, wc, ws);
-        const double ar = 0.5 * (1.0 + wc), ai = 0.5 * ws;
         const double br = 0.5 * (1.0 - wc), bi = -0.5 * ws;
         const double dr = 2.0 * (cr[j] * br - ci[j] * bi), di = 2.0 * (cr[j] * bi + ci[j] * br);
-        push4(out, ar, ai, br, bi);
+        push4(out, 1.0, 0.0, br, bi);
         push4(out, dr, di, 2.0 * cr[j], 2.0 * ci[j]);
       }
     } else {
       push4(out, 0.0, 0, 0, 0);
-      push4(out, 1.0, 0.0, 1.0, 0.0);
+      push4(out, 2.0, 0.0, 1.0, 0.0);     // 1 + l
       push4(out, cr[0], 0.0, cr[0], 0.0);
       if (odd) {
-        push4(out, 1.0, 0.0, -1.0, 0.0);
+        push4(out, 0.0, 0.0, -1.0, 0.0);  // 1 - l
         push4(out, -cr[mid], 0.0, cr[mid], 0.0);
       }
       for (int j = 1; j <= k / 2; ++j) {
         double wc, ws;
         unit_root(j, N, wc, ws);
         const double dr = 2.0 * (cr[j] * wc - ci[j] * ws), di = 2.0 * (cr[j] * ws + ci[j] * wc);
-        push4(out, 1.0, 0.0, wc, ws);
+        push4(out, 1.0 + wc, ws, wc, ws);  // 1 + w^j l
         push4(out, dr, di, 2.0 * cr[j], 2.0 * ci[j]);
       }
     }

@@ -42,9 +42,10 @@ void esp_coefficients(const Shape& s, std::vector<double>& c);
 //     the kernel evaluates  FE   = c0 + sum_r E_r prod_i (l_i + alpha_r)
 //                                     + sum_j Re(E_j prod_i (l_i + alpha_j + i gamma_j))
 //                          dFE/dl_i = sum_r E_r prod_{i'!=i} (...) + sum_j Re(E_j prod_{i'!=i} (...))
-//  long form:  {c0,0,0,0}, per real root {a, b, D, E},
-//              per complex root {a.re, a.im, b.re, b.im}, {D.re, D.im, E.re, E.im}
-//     FE = c0 + sum Re(E prod_i (a + b l_i)),  dFE/dl_i = sum Re(D prod_{i'!=i} (a + b l_i'))
+//  long form:  {c0,0,0,0}, per root (real roots first, imaginary parts 0)
+//              {A.re, A.im, b.re, b.im}, {D.re, D.im, E.re, E.im}
+//     with the factor a + b l = A - b (1 - l), A = a + b:
+//     FE = c0 + sum Re(E prod_i F_i),  dFE/dl_i = sum Re(D prod_{i'!=i} F_i')
 void build_table(const Shape& s, int basis, int form, std::vector<float>& out);
 
 // Algorithmic FP32 lane instructions of one FE+gradient evaluation of a

@@ -101,6 +101,10 @@ struct afs_handle {
   std::vector<int> inst_vbegin, inst_cbegin;
   // host copies for the independent re-check
   std::vector<int> h_lit_enc, h_lit_off, h_viol_off, h_cons_inst, h_var_inst;
+  std::vector<int> h_ctype, h_cop, h_cparam, h_cparity;
+  // per-handle data of other modules (the learned initialiser's graph buffers)
+  void* ext = nullptr;
+  void (*ext_release)(void*) = nullptr;
   std::vector<uint8_t> h_viol;
   // buckets
   std::vector<Group> groups;
@@ -136,6 +140,7 @@ struct afs_handle {
     for (auto& g : timed_graphs) cudaGraphExecDestroy(g.second);
     for (auto e : ev_pool) cudaEventDestroy(e);
     if (cap) cudaStreamDestroy(cap);
+    if (ext && ext_release) ext_release(ext);
   }
   void drop_graphs() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.second);
@@ -317,6 +322,16 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     h->h_lit_off[m] = static_cast<int>(at);
   }
   h->h_viol_off = viol_off;
+  h->h_ctype.resize(m);
+  h->h_cop.resize(m);
+  h->h_cparam.resize(m);
+  h->h_cparity.resize(m);
+  for (int g = 0; g < m; ++g) {
+    h->h_ctype[g] = shape[g].type;
+    h->h_cop[g] = shape[g].op;
+    h->h_cparam[g] = shape[g].param;
+    h->h_cparity[g] = shape[g].parity;
+  }
   h->h_viol = violv;
   std::vector<int4> ranges;
   for (int i = 0; i < n_inst; ++i) {
@@ -729,6 +744,35 @@ int afs::set_error(int code, const char* fmt, ...) {
   return code;
 }
 
+int afs::graph_view(const afs_handle* h, GraphView* out) {
+  if (!h || !out) return fail(AFS_E_ARG, "NULL argument");
+  out->n = h->n;
+  out->m = h->m;
+  out->n_inst = h->n_inst;
+  out->L = h->L;
+  out->lit_enc = h->h_lit_enc.data();
+  out->lit_off = h->h_lit_off.data();
+  out->ctype = h->h_ctype.data();
+  out->cop = h->h_cop.data();
+  out->cparam = h->h_cparam.data();
+  out->cparity = h->h_cparity.data();
+  out->inst_vbegin = h->inst_vbegin.data();
+  out->var_inst_dev = h->var_inst.as<int>();
+  out->x = h->x.p;
+  out->pitch = h->pitch;
+  out->B = h->B;
+  out->xt = h->xt;
+  return AFS_OK;
+}
+
+void* afs::handle_ext(const afs_handle* h) { return h ? h->ext : nullptr; }
+
+void afs::set_handle_ext(afs_handle* h, void* p, void (*release)(void*)) {
+  if (h->ext && h->ext_release) h->ext_release(h->ext);
+  h->ext = p;
+  h->ext_release = release;
+}
+
 int afs::eval_into_scratch(afs_handle* h, const float* x, int B, float* fe, float* grad, float* scratch,
                            long long cap_floats, cudaStream_t s) {
   if (!h || !x || !scratch) return fail(AFS_E_ARG, "NULL argument");
@@ -806,7 +850,8 @@ int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_d
   CK(cudaMemsetAsync(h->unsat.p, 0, h->unsat.bytes, s));
   CK(cudaMemsetAsync(h->vflag.p, 0, h->vflag.bytes, s));
   CK(cudaMemsetAsync(h->sflag.p, 0, h->sflag.bytes, s));
-  CK(cudaMemsetAsync(h->solved.p, 0x7f, h->solved.bytes, s));
+  launch_fill_int(h->solved.as<int>(), INT_MAX, h->n_inst, s);
+  CKL();
   h->parity = 0;
   for (Group& g : h->groups) {
     g.rpl = 1;
@@ -840,7 +885,8 @@ int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_d
   CK(cudaMemsetAsync(h->unsat.p, 0, h->unsat.bytes, s));
   CK(cudaMemsetAsync(h->vflag.p, 0, h->vflag.bytes, s));
   CK(cudaMemsetAsync(h->sflag.p, 0, h->sflag.bytes, s));
-  CK(cudaMemsetAsync(h->solved.p, 0x7f, h->solved.bytes, s));
+  launch_fill_int(h->solved.as<int>(), INT_MAX, h->n_inst, s);
+  CKL();
   return AFS_OK;
 }
 
@@ -922,7 +968,8 @@ int afs_round_and_verify(afs_handle* h, int32_t* unsat_host, int32_t* best_host,
   if (!h) return fail(AFS_E_ARG, "NULL handle");
   if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  CK(cudaMemsetAsync(h->solved.p, 0x7f, h->solved.bytes, s));
+  launch_fill_int(h->solved.as<int>(), INT_MAX, h->n_inst, s);
+  CKL();
   int rc = launch_check(h, s);
   if (rc) return rc;
   const size_t nib = static_cast<size_t>(h->n_inst) * h->B;

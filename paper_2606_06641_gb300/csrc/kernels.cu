@@ -99,6 +99,8 @@ __device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
   return v[0];
 }
 
+// el[t] = u_t = 1 - l_t; the factor is A - b u, passed as (ar, ai) = A and
+// (br, bi) = -b so that each component is one FMA.
 template <bool FULL>
 __device__ __forceinline__ void long_segment(const float* el, int n, float ar, float ai, float br, float bi,
                                              float Qr, float Qi, float& Sr, float& Si, float (&v)[32]) {
@@ -143,6 +145,7 @@ struct LongLayout {
     b += 2 * static_cast<size_t>(LONG_RT) * kpad * 4;         // literal values, gradient accumulators
     b += static_cast<size_t>(LONG_RT) * nseg_max * 32 * 8;    // prefix checkpoints
     if (esp) b += static_cast<size_t>(LONG_RT) * nseg_max * 32 * 4;
+    b += static_cast<size_t>(LONG_RT) * kpad;                 // literal truth bytes
     return b;
   }
 };
@@ -169,6 +172,7 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
   float* gs = ell + LONG_RT * L.kpad;
   float2* ck = reinterpret_cast<float2*>(gs + LONG_RT * L.kpad);
   int* cke = reinterpret_cast<int*>(ck + LONG_RT * L.nseg_max * 32);
+  unsigned char* tru = reinterpret_cast<unsigned char*>(cke + (ESP ? LONG_RT * L.nseg_max * 32 : 0));
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const unsigned tab_bytes = static_cast<unsigned>(1 + 2 * nroots) * 16u;
@@ -190,7 +194,8 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
     return;
   }
 
-  // stage l[r][i] = s_i * x[v_i][b]: 8 consecutive threads read one 32-byte row
+  // stage u[r][i] = 1 - s_i x[v_i][b] and the literal's truth at the rounded
+  // point: 8 consecutive threads read one 32-byte row
   const XT* x = static_cast<const XT*>(a.x);
   const int bt = tile * LONG_RT;
   for (int idx = tid; idx < k * LONG_RT; idx += blockDim.x) {
@@ -199,7 +204,9 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
     const int bl = bt + r;
     const float xv =
         bl < a.nb ? load_x<XT>(x + static_cast<long long>(li.x >> 1) * a.x_pitch + a.b0 + bl) : 0.0f;
-    ell[r * L.kpad + i] = (li.x & 1) ? -xv : xv;
+    const float l = (li.x & 1) ? -xv : xv;
+    ell[r * L.kpad + i] = 1.0f - l;
+    tru[r * L.kpad + i] = static_cast<unsigned char>(lit_true(l, li.x & 1));
   }
   __syncthreads();
 
@@ -213,7 +220,8 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
   // exact check of the state read (Algorithm 1's unsat count): warp w, restart bt + w
   if (a.vflag != nullptr) {
     int t = 0;
-    for (int i = lane; i < k; i += 32) t += lit_true(el[i], lits[i].x & 1);
+    const unsigned char* tr = tru + w * L.kpad;
+    for (int i = lane; i < k; i += 32) t += tr[i];
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0 && bt + w < a.nb && __ldg(a.viol + __ldg(a.cons_voff + cb) + t))
@@ -224,9 +232,9 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
   for (int rg = 0; rg < nroots; rg += 32) {
     const int j = rg + lane;
     float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f, dr = 0.f, di = 0.f, er = 0.f, ei = 0.f;
-    if (j < nroots) {
+    if (j < nroots) {  // factor A - b u: keep (A, -b)
       const float4 t0 = tab[1 + 2 * j], t1 = tab[2 + 2 * j];
-      ar = t0.x; ai = t0.y; br = t0.z; bi = t0.w;
+      ar = t0.x; ai = t0.y; br = -t0.z; bi = -t0.w;
       dr = t1.x; di = t1.y; er = t1.z; ei = t1.w;
     }
     // forward: prefix checkpoints at segment starts
@@ -502,6 +510,16 @@ void launch_fold_flags(const FlagArgs& a, cudaStream_t s) {
   const long long n = static_cast<long long>(a.n_inst) * a.nb;
   if (n == 0) return;
   launch_pdl(fold_flags_kernel, dim3(static_cast<unsigned>((n + 255) / 256)), dim3(256), 0, s, a);
+}
+
+__global__ void fill_int_kernel(int* p, int v, long long n) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+void launch_fill_int(int* p, int v, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  fill_int_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(p, v, n);
 }
 
 // A restart with no violated constraint is solved: record the lowest such

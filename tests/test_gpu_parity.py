@@ -249,9 +249,11 @@ def test_never_reports_sat_on_unsat_instances():
         h = bd.load_instance(inst, bd.default_params(eta=0.2))
         bd.init_restarts(h, 64, seed=idx)
         bd.step(h, 100)
+        _, flag = bd.get_verify(h)
         un, best, asg, sol = bd.round_and_verify(h)
         if not sat:
             assert sol[0] == 0 and un.min() > 0
+            assert int(flag.cpu()[0]) == 2 ** 31 - 1  # "no solved restart" is INT32_MAX
         if sol[0]:
             assert O.unsat_count(inst, asg.astype(np.float32)[:, None])[0] == 0
     assert seen[True] > 0 and seen[False] > 0

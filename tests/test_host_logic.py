@@ -70,9 +70,9 @@ def _eval_long(tab, k, esp, ell):
     grad = np.zeros_like(ell)
     nroots = k // 2 + (k & 1) + (1 if esp else 0)
     for j in range(nroots):
-        ar, ai, br, bi = t[1 + 2 * j]
+        Ar, Ai, br, bi = t[1 + 2 * j]
         dr, di, er, ei = t[2 + 2 * j]
-        f = (ar + 1j * ai) + (br + 1j * bi) * ell
+        f = (Ar + 1j * Ai) - (br + 1j * bi) * (1.0 - ell)
         fe += np.real((er + 1j * ei) * f.prod(axis=1))
         for i in range(k):
             grad[:, i] += np.real((dr + 1j * di) * np.delete(f, i, axis=1).prod(axis=1))
