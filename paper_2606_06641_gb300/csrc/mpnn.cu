@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
 
 void gemm(const float* A, long long sa0, long long sa1, const float* B, long long sb0, long long sb1, float* C,
           long long ldc, int M, int N, int K, const float* bias, bool relu, int mode, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return;  // empty product (weight gradients of an empty graph stay zero)
   GemmArgs g{A, sa0, sa1, B, sb0, sb1, C, ldc, M, N, K, bias, relu ? 1 : 0, mode, K};
   int zsplit = 1;
   if (mode == 2) {  // weight gradients: split the long inner dimension over CTAs
