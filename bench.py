@@ -227,19 +227,96 @@ def measure_time_to_solve(n_inst: int, B: int, eta: float, max_steps: int, seed:
     solver.solve_batched(insts[:2], B, eta, 5, seed=seed)       # warm the library and allocator
     plain = solver.solve_plain(insts, B, eta, max_steps, x0s=x0s)
     batched = solver.solve_batched(insts, B, eta, max_steps, x0=x_all, steps_per_poll=10)
-    timeout = plain.total_seconds  # one common budget: the plain run's wall time
+    forms = {"plain": (plain.solved, plain.seconds, plain.steps, plain.total_seconds),
+             "batched": (batched.solved, batched.seconds, batched.steps, batched.total_seconds)}
+    out = tts_summary(forms)
+    out.update({"instances": n_inst, "n": 50, "m": 213, "restarts": B, "eta": eta, "max_steps": max_steps,
+                "same_solved_set": bool(np.array_equal(plain.solved, batched.solved)),
+                "start_points": "identical (Philox, batch convention) for both forms"})
+    return out
 
-    def summary(r):
-        return {"solved": int(r.solved.sum()), "solve_rate": float(r.solved.mean()),
-                "median_s": solver.median_tts(r, timeout), "par2_s": solver.par2(r, timeout),
-                "median_steps_solved": float(np.median(r.steps[r.solved])) if r.solved.any() else None,
-                "wall_s": r.total_seconds}
-    same = bool(np.array_equal(plain.solved, batched.solved))
-    return {"instances": n_inst, "n": 50, "m": 213, "restarts": B, "eta": eta, "max_steps": max_steps,
-            "timeout_s": timeout, "same_solved_set": same,
-            "plain": summary(plain), "batched": summary(batched),
-            "batched_speedup_median": (summary(plain)["median_s"] / summary(batched)["median_s"])
-            if summary(batched)["median_s"] > 0 else None}
+
+def tts_summary(forms):
+    """Time-to-solve at an equal solve rate: with k = half the smallest number
+    of instances any form solved, each form's k-th fastest completion time
+    (from the start of its run) is its median time-to-solve over that common
+    solved fraction. Also the solve rate, median steps over solved instances
+    and total wall time."""
+    import numpy as np
+    kmin = min(int(v[0].sum()) for v in forms.values())
+    k = max(1, kmin // 2)
+    res = {"equal_rate_rank": k}
+    for name, (solved, secs, steps, wall) in forms.items():
+        t = np.sort(np.where(solved, secs, np.inf))
+        res[name] = {"solved": int(solved.sum()), "solve_rate": float(solved.mean()),
+                     "median_tts_s": float(t[k - 1]) if kmin > 0 else None,
+                     "median_steps_solved": float(np.median(steps[solved])) if solved.any() else None,
+                     "wall_s": float(wall)}
+    if "plain" in res and kmin > 0:
+        for name in forms:
+            if name != "plain" and res[name]["median_tts_s"]:
+                res[f"{name}_vs_plain_speedup"] = res["plain"]["median_tts_s"] / res[name]["median_tts_s"]
+    return res
+
+
+def run_learned(args):
+    """Config 5: train the message-passing initialiser on assignments the
+    descent finds for training instances, then solve held-out instances from
+    learned and from uniform starts (and with plain CLS) at equal step budget."""
+    import numpy as np
+    import torch
+
+    from paper_2606_06641_gb300 import binding as bd
+    from paper_2606_06641_gb300 import build as _b
+    from paper_2606_06641_gb300 import learned, solver, synth
+    _b.build()
+    eta, steps = 0.1, 500
+    t0 = time.perf_counter()
+    train = [synth.config5(i, "train") for i in range(args.learned_train)]
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    labels = learned.harvest(train, 64, eta, steps, seed=1)
+    t_harvest = time.perf_counter() - t0
+    batches = learned.make_batches(labels, 64)
+    net = bd.Mpnn(layers=3, seed=7)
+    t0 = time.perf_counter()
+    hist = learned.train(net, batches, args.learned_epochs, 3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    test = [synth.config5(i, "test") for i in range(args.learned_test)]
+    B = 256
+    learned.evaluate(net, test[:4], B, eta, 5, seed=2)  # warm-up
+    res_u = learned.evaluate(None, test, B, eta, steps, seed=3)
+    res_l = learned.evaluate(net, test, B, eta, steps, seed=3)
+    n_plain = min(len(test), args.learned_plain)
+    plain = solver.solve_plain(test[:n_plain], B, eta, steps, seed=3)
+    forms = {"uniform_batched": res_u, "learned_batched": res_l}
+    summ = tts_summary({k: (v[0][:n_plain], v[2][:n_plain], v[1][:n_plain], v[3]) for k, v in forms.items()} |
+                       {"plain": (plain.solved, plain.seconds, plain.steps, plain.total_seconds)})
+    both = res_u[0] & res_l[0]
+    line = {
+        "metric": "median time-to-solve at equal solve rate (learned vs uniform starts vs plain CLS)",
+        "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+        "config": {"workload": "config-1 distribution random 3-SAT n=50 m=213; "
+                               f"{args.learned_train} training instances, {len(test)} held-out, B={B}, "
+                               f"{steps} steps, eta={eta}", "network": "3 rounds, hidden 64, BF16 GEMMs"},
+        "labels": {"labelled_instances": len(labels.insts), "mean_solutions": float(labels.n_solutions.mean())
+                   if len(labels.insts) else 0.0},
+        "train": {"epochs": args.learned_epochs, "loss_first": hist[0] if hist else None,
+                  "loss_last": hist[-1] if hist else None, "train_s": t_train, "harvest_s": t_harvest,
+                  "generate_s": t_gen},
+        "held_out": {
+            "uniform": {"solve_rate": float(res_u[0].mean()), "median_steps": float(np.median(res_u[1][res_u[0]]))
+                        if res_u[0].any() else None, "wall_s": res_u[3]},
+            "learned": {"solve_rate": float(res_l[0].mean()), "median_steps": float(np.median(res_l[1][res_l[0]]))
+                        if res_l[0].any() else None, "wall_s": res_l[3]},
+            "paired_steps_gain_on_both_solved": float(np.median(res_u[1][both] - res_l[1][both])) if both.any()
+            else None,
+        },
+        "time_to_solve_first_instances": summ | {"instances": n_plain},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def precision_report(inst, n_restarts: int = 4):
@@ -424,7 +501,11 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hybrid", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="hybrid", choices=sorted(WORKLOADS) + ["learned"])
+    ap.add_argument("--learned-train", type=int, default=10000)
+    ap.add_argument("--learned-test", type=int, default=512)
+    ap.add_argument("--learned-epochs", type=int, default=30)
+    ap.add_argument("--learned-plain", type=int, default=128, help="held-out instances also run by plain CLS")
     ap.add_argument("--restarts", type=int, default=0, help="restarts per GPU (0 = the workload's)")
     ap.add_argument("--steps-per-graph", type=int, default=10)
     ap.add_argument("--chunk", type=int, default=0, help="restarts per chunk (0 = autotuned)")
@@ -436,7 +517,11 @@ def main():
     ap.add_argument("--no-tts", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
+        if args.workload == "learned":
+            args.workload = "hybrid"
         return run_reference(args)
+    if args.workload == "learned":
+        return run_learned(args)
     return run_ours(args)
 
 

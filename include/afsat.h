@@ -242,6 +242,19 @@ int afs_mpnn_adam_step(afs_mpnn* net, float lr, void* stream);
 int afs_mpnn_init_restarts(afs_mpnn* net, afs_handle* h, int32_t B, uint64_t seed, float uniform_frac,
                            float sigma_min, float sigma_max, void* stream);
 
+/* ---- failure detection -------------------------------------------------
+ * Device waits are bounded: the long-constraint kernel waits for its bulk
+ * copies for at most ~2 s of SM cycles, then records AFS_E_TIMEOUT in the
+ * handle's device status word and returns without touching the outputs.
+ * afs_device_error reads that word into *code (AFS_OK or AFS_E_TIMEOUT),
+ * clears it, and synchronises `stream`; afs_round_and_verify also reports
+ * it. afs_debug_wait_timeout(h, 1) is a test hook: the long kernel then
+ * expects 16 bytes that no copy delivers and gives up after ~10 ms, so the
+ * timeout path can be exercised without a fault; (h, 0) restores normal
+ * operation. Captured step graphs are dropped on every change. */
+int afs_device_error(afs_handle* h, int32_t* code, void* stream);
+int afs_debug_wait_timeout(afs_handle* h, int32_t enable);
+
 /* ---- introspection ------------------------------------------------------ */
 /* Sizes: n_total variables, m constraints, n_lits literals, n_inst, B. */
 int afs_info(const afs_handle* h, int64_t* out6);

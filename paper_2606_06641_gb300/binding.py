@@ -56,6 +56,8 @@ SIGNATURES = {
     "afs_mpnn_adam_step": (_I32, [_P, ctypes.c_float, _P]),
     "afs_mpnn_init_restarts": (_I32, [_P, _P, _I32, ctypes.c_uint64, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_float, _P]),
+    "afs_device_error": (_I32, [_P, _P, _P]),
+    "afs_debug_wait_timeout": (_I32, [_P, _I32]),
     "afs_info": (_I32, [_P, _P]),
     "afs_work_per_restart": (_I32, [_P, _P]),
     "afs_set_kernel_timing": (_I32, [_P, _I32]),
@@ -319,10 +321,21 @@ class Mpnn:
     def adam_step(self, lr: float, stream=None) -> None:
         _check(lib().afs_mpnn_adam_step(self.ptr, lr, _stream(stream)))
 
-    def init_restarts(self, h: Handle, B: int, seed: int = 0, uniform_frac: float = 0.25,
-                      sigma_min: float = 0.1, sigma_max: float = 0.9, stream=None) -> None:
+    def init_restarts(self, h: Handle, B: int, seed: int = 0, uniform_frac: float = 0.5,
+                      sigma_min: float = 0.3, sigma_max: float = 1.5, stream=None) -> None:
         _check(lib().afs_mpnn_init_restarts(self.ptr, h.ptr, B, seed, uniform_frac, sigma_min, sigma_max,
                                             _stream(stream)))
+
+
+def device_error(h: Handle, stream=None) -> int:
+    """AFS_OK or AFS_E_TIMEOUT from the handle's device status word (cleared)."""
+    code = ctypes.c_int32()
+    _check(lib().afs_device_error(h.ptr, ctypes.byref(code), _stream(stream)))
+    return code.value
+
+
+def debug_wait_timeout(h: Handle, enable: bool) -> None:
+    _check(lib().afs_debug_wait_timeout(h.ptr, 1 if enable else 0))
 
 
 def info(h: Handle) -> List[int]:

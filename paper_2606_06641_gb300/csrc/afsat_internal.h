@@ -42,6 +42,9 @@ struct FeGroupArgs {
   long long vflag_stride;
   int B;
   int cpw;                  // constraints per warp (short kernel)
+  int vec;                  // short kernel: a lane's restarts are consecutive (vector loads/stores)
+  long long wait_limit;     // long kernel: SM cycles a bounded barrier wait may take
+  unsigned extra_tx;        // test hook: bytes the long kernel expects beyond its copies (0 normally)
 };
 
 // Rows of violation flags: spreading the plain stores of many warps over

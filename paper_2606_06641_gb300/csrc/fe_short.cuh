@@ -45,7 +45,55 @@ __device__ __forceinline__ int lit_true(float l, int neg) {
   return neg ? (l <= 0.0f) : (l < 0.0f);
 }
 
-template <int K, int RPL, typename XT, bool SHIFT>
+// N consecutive state values with one vector load (N = 2 or 4; 16-byte or
+// 8-byte alignment for FP32, 8- or 4-byte for BF16)
+template <typename XT, int N>
+__device__ __forceinline__ void load_xvec(const XT* p, float (&v)[N]);
+template <>
+__device__ __forceinline__ void load_xvec<float, 2>(const float* p, float (&v)[2]) {
+  const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+  v[0] = t.x;
+  v[1] = t.y;
+}
+template <>
+__device__ __forceinline__ void load_xvec<float, 4>(const float* p, float (&v)[4]) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+template <>
+__device__ __forceinline__ void load_xvec<__nv_bfloat16, 2>(const __nv_bfloat16* p, float (&v)[2]) {
+  const unsigned t = __ldg(reinterpret_cast<const unsigned*>(p));
+  v[0] = __uint_as_float(t << 16);
+  v[1] = __uint_as_float(t & 0xffff0000u);
+}
+template <>
+__device__ __forceinline__ void load_xvec<__nv_bfloat16, 4>(const __nv_bfloat16* p, float (&v)[4]) {
+  const uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+  v[0] = __uint_as_float(t.x << 16);
+  v[1] = __uint_as_float(t.x & 0xffff0000u);
+  v[2] = __uint_as_float(t.y << 16);
+  v[3] = __uint_as_float(t.y & 0xffff0000u);
+}
+template <int N>
+__device__ __forceinline__ void store_fvec(float* p, const float (&v)[N]);
+template <>
+__device__ __forceinline__ void store_fvec<2>(float* p, const float (&v)[2]) {
+  *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+}
+template <>
+__device__ __forceinline__ void store_fvec<4>(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// VEC (with RPL > 1): a lane's RPL restarts are consecutive, so a literal's
+// gather is one vector load and a derivative store one vector store. It needs
+// the state's row pitch, the chunk start and the derivative pitch to be
+// multiples of 32 (the library's own state and buffers); a vector that starts
+// below nb then stays inside the padded row, and values past nb are ignored.
+template <int K, int RPL, typename XT, bool SHIFT, bool VEC>
 __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
   pdl_wait();
   pdl_trigger();
@@ -62,11 +110,12 @@ __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
   const bool check = a.vflag != nullptr;
   int* vrow = check ? a.vflag + static_cast<long long>(warp % VFLAG_SLOTS) * a.vflag_stride + a.b0 : nullptr;
 
+  constexpr bool V = VEC && RPL > 1;
   int bl[RPL];
   bool act[RPL];
 #pragma unroll
   for (int r = 0; r < RPL; ++r) {
-    bl[r] = tile * TW + r * 32 + lane;
+    bl[r] = V ? tile * TW + lane * RPL + r : tile * TW + r * 32 + lane;
     act[r] = bl[r] < a.nb;
   }
   bool vio[RPL];
@@ -85,10 +134,22 @@ __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       const long long row = static_cast<long long>(lit[i].x >> 1) * a.x_pitch + a.b0;
+      if constexpr (V) {
+        float xv[RPL];
+        if (act[0]) {
+          load_xvec<XT, RPL>(x + row + bl[0], xv);
+        } else {
 #pragma unroll
-      for (int r = 0; r < RPL; ++r) {
-        const float xv = act[r] ? load_x<XT>(x + row + bl[r]) : 0.0f;
-        l[r][i] = (lit[i].x & 1) ? -xv : xv;
+          for (int r = 0; r < RPL; ++r) xv[r] = 0.0f;
+        }
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) l[r][i] = (lit[i].x & 1) ? -xv[r] : xv[r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+          const float xv = act[r] ? load_x<XT>(x + row + bl[r]) : 0.0f;
+          l[r][i] = (lit[i].x & 1) ? -xv : xv;
+        }
       }
     }
 
@@ -219,9 +280,18 @@ __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       float* row = a.go + static_cast<long long>(lit[i].y) * a.go_pitch;
+      if constexpr (V) {
+        if (act[0]) {
+          float gv[RPL];
 #pragma unroll
-      for (int r = 0; r < RPL; ++r)
-        if (act[r]) row[bl[r]] = (lit[i].x & 1) ? -g[r][i] : g[r][i];
+          for (int r = 0; r < RPL; ++r) gv[r] = (lit[i].x & 1) ? -g[r][i] : g[r][i];
+          store_fvec<RPL>(row + bl[0], gv);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < RPL; ++r)
+          if (act[r]) row[bl[r]] = (lit[i].x & 1) ? -g[r][i] : g[r][i];
+      }
     }
     if (a.fe != nullptr) {
       const long long orow = static_cast<long long>(__ldg(a.cons_orig + cb)) * a.fe_pitch + a.b0;
@@ -245,7 +315,15 @@ void launch_short_k(const FeGroupArgs& a_in, int warps, cudaStream_t s) {
   const long long tiles = (a.nb + TW - 1) / TW;
   const long long nwarps = tiles * ((a.c_count + a.cpw - 1) / a.cpw);
   const long long blocks = (nwarps + warps - 1) / warps;
-  launch_pdl(fe_grad_short_kernel<K, RPL, XT, SHIFT>, dim3(static_cast<unsigned>(blocks)), dim3(warps * 32), 0, s, a);
+  if constexpr (RPL > 1) {
+    if (a.vec) {
+      launch_pdl(fe_grad_short_kernel<K, RPL, XT, SHIFT, true>, dim3(static_cast<unsigned>(blocks)), dim3(warps * 32),
+                 0, s, a);
+      return;
+    }
+  }
+  launch_pdl(fe_grad_short_kernel<K, RPL, XT, SHIFT, false>, dim3(static_cast<unsigned>(blocks)), dim3(warps * 32), 0,
+             s, a);
 }
 
 }  // namespace afs

@@ -51,6 +51,24 @@ int fail(int code, const char* fmt, ...) {
     }                                                                                            \
   } while (0)
 
+// Concurrent launch of a chunk's length buckets (off when AFS_CONCURRENT=0).
+bool concurrent_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("AFS_CONCURRENT");
+    return !(e != nullptr && e[0] == '0');
+  }();
+  return on;
+}
+
+// Vector tiles in the short FE kernel (off when AFS_VEC=0, for A/B timing).
+bool vec_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("AFS_VEC");
+    return !(e != nullptr && e[0] == '0');
+  }();
+  return on;
+}
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -106,8 +124,12 @@ struct afs_handle {
   void* ext = nullptr;
   void (*ext_release)(void*) = nullptr;
   std::vector<uint8_t> h_viol;
-  // buckets
+  // test hook for the bounded-wait path of the long kernel (0 = normal)
+  long long dbg_wait_limit = 0;
+  unsigned dbg_extra_tx = 0;
+  // buckets, and their launch order (largest work first)
   std::vector<Group> groups;
+  std::vector<int> order;
   double work_per_restart = 0.0;
   // device instance data
   DevBuf litslot, cons_tab, cons_orig, cons_k, cons_lit, coef, csr_off, lit_enc, lit_off, viol_off, viol,
@@ -124,6 +146,12 @@ struct afs_handle {
   long long eval_go_cols = 0;
   // graphs
   cudaStream_t cap = nullptr;
+  // the length buckets of a chunk are launched concurrently on these streams
+  // (forked from and joined back to the step's stream; parallel graph branches)
+  static constexpr int NAUX = 6;
+  cudaStream_t aux[NAUX] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[NAUX] = {};
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs, timed_graphs;  // (nsteps, start parity)
   std::map<std::pair<int, int>, std::pair<std::vector<std::pair<int, int>>, std::vector<std::pair<int, int>>>>
       timed_pairs;
@@ -140,6 +168,11 @@ struct afs_handle {
     for (auto& g : timed_graphs) cudaGraphExecDestroy(g.second);
     for (auto e : ev_pool) cudaEventDestroy(e);
     if (cap) cudaStreamDestroy(cap);
+    for (int i = 0; i < NAUX; ++i) {
+      if (aux[i]) cudaStreamDestroy(aux[i]);
+      if (ev_join[i]) cudaEventDestroy(ev_join[i]);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
     if (ext && ext_release) ext_release(ext);
   }
   void drop_graphs() {
@@ -295,6 +328,15 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
       h->groups.push_back(Group{is_long, k, pos, 1, static_cast<long long>(b_lit[pos]), 1, 1});
     }
   }
+  {
+    std::vector<double> work(h->groups.size(), 0.0);
+    for (size_t gi = 0; gi < h->groups.size(); ++gi)
+      for (int c = h->groups[gi].c_begin; c < h->groups[gi].c_begin + h->groups[gi].c_count; ++c)
+        work[gi] += work_instr(b_k[c]);
+    h->order.resize(h->groups.size());
+    for (size_t gi = 0; gi < h->groups.size(); ++gi) h->order[gi] = static_cast<int>(gi);
+    std::stable_sort(h->order.begin(), h->order.end(), [&](int a, int b) { return work[a] > work[b]; });
+  }
   // ---- CSR: slots in variable-major order, occurrences of a variable in bucket order ----
   std::vector<int> csr(h->n + 1, 0);
   for (const int2& ls : litslot)
@@ -373,6 +415,11 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   if ((rc = upload(h->err, zero1, s))) return rc;
   CK(cudaStreamSynchronize(s));
   CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  for (int i = 0; i < afs_handle::NAUX; ++i) {
+    CK(cudaStreamCreateWithFlags(&h->aux[i], cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming));
+  }
+  CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   if (!prepare_kernels()) return fail(AFS_E_CUDA, "kernel attribute setup: %s", cudaGetErrorString(cudaGetLastError()));
   *out = h.release();
   return AFS_OK;
@@ -412,6 +459,13 @@ static int launch_fe_group(afs_handle* h, const Group& g, const void* x, int xt,
   a.vflag_stride = static_cast<long long>(h->n_inst) * h->B;
   a.B = h->B;
   a.cpw = g.cpw;
+  a.wait_limit = h->dbg_wait_limit;
+  a.extra_tx = h->dbg_extra_tx;
+  // vector tiles need 32-aligned pitches and chunk start (the library's own
+  // state and buffers; an evaluation input qualifies when its B does) and
+  // 16-byte aligned bases
+  a.vec = vec_enabled() && (x_pitch % 32) == 0 && (b0 % 32) == 0 && (go_pitch % 32) == 0 &&
+          (reinterpret_cast<uintptr_t>(x) % 16) == 0 && (reinterpret_cast<uintptr_t>(go) % 16) == 0;
   if (g.is_long) {
     launch_fe_long(a, xt, h->p.basis, 8, s);
   } else {
@@ -500,10 +554,27 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int p
     for (int b0 = 0; b0 < h->B; b0 += h->Bc) {
       const int nb = std::min(h->Bc, h->B - b0);
       if (h->timing) CK(cudaEventRecordWithFlags(pool_event(h, ev), s, cudaEventRecordExternal));
-      for (const Group& g : h->groups) {
-        int rc = launch_fe_group(h, g, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, nullptr, 0, vcur, s);
+      // the first (largest-work) bucket runs on s, the others on forked streams
+      const int G = static_cast<int>(h->groups.size());
+      const bool fork = G > 1 && concurrent_enabled();
+      if (fork) CK(cudaEventRecord(h->ev_fork, s));
+      int used = 0;
+      for (int gi = 0; gi < G; ++gi) {
+        const Group& g = h->groups[h->order[gi]];
+        cudaStream_t st = s;
+        if (fork && gi > 0) {
+          const int a = (gi - 1) % afs_handle::NAUX;
+          if (gi - 1 < afs_handle::NAUX) CK(cudaStreamWaitEvent(h->aux[a], h->ev_fork, 0));
+          st = h->aux[a];
+          used = std::max(used, a + 1);
+        }
+        int rc = launch_fe_group(h, g, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, nullptr, 0, vcur, st);
         if (rc) return rc;
         ++nl;
+      }
+      for (int a = 0; a < used; ++a) {
+        CK(cudaEventRecord(h->ev_join[a], h->aux[a]));
+        CK(cudaStreamWaitEvent(s, h->ev_join[a], 0));
       }
       if (h->timing) CK(cudaEventRecordWithFlags(pool_event(h, ev + 1), s, cudaEventRecordExternal));
       if (check) {
@@ -1087,6 +1158,25 @@ int afs_step_host(afs_handle* h, const float* x_host, float* x_out_host, int32_t
     CK(cudaMemcpyAsync(x_out_host, h->stage.p, nb, cudaMemcpyDeviceToHost, s));
   }
   CK(cudaStreamSynchronize(s));
+  return AFS_OK;
+}
+
+int afs_device_error(afs_handle* h, int32_t* code, void* stream) {
+  if (!h || !code) return fail(AFS_E_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  CK(cudaMemcpyAsync(&v, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemsetAsync(h->err.p, 0, sizeof(int), s));
+  CK(cudaStreamSynchronize(s));
+  *code = v == 0 ? AFS_OK : AFS_E_TIMEOUT;
+  return AFS_OK;
+}
+
+int afs_debug_wait_timeout(afs_handle* h, int32_t enable) {
+  if (!h) return fail(AFS_E_ARG, "NULL handle");
+  h->drop_graphs();
+  h->dbg_extra_tx = enable ? 16u : 0u;         // bytes that no copy will deliver
+  h->dbg_wait_limit = enable ? 20000000LL : 0;  // ~10 ms instead of ~2 s
   return AFS_OK;
 }
 

@@ -183,14 +183,15 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
   }
   __syncthreads();
   if (tid == 0) {
-    mbar_expect_tx(&bar, tab_bytes + lit_bytes);
+    mbar_expect_tx(&bar, tab_bytes + lit_bytes + a.extra_tx);
     bulk_g2s(tab, a.coef + tab_off, tab_bytes, &bar);
     bulk_g2s(lits, a.litslot + litoff, lit_bytes, &bar);
   }
   for (int i = tid; i < LONG_RT * L.kpad; i += blockDim.x) gs[i] = 0.0f;
-  if (!mbar_wait_bounded(&bar, 0, WAIT_LIMIT_CYCLES)) {
+  const long long limit = a.wait_limit > 0 ? a.wait_limit : WAIT_LIMIT_CYCLES;
+  if (!mbar_wait_bounded(&bar, 0, limit)) {
     if (tid == 0) atomicExch(a.err, DEV_ERR_TIMEOUT);
-    mbar_wait_bounded(&bar, 0, WAIT_LIMIT_CYCLES);  // let copies in flight land before exit
+    mbar_wait_bounded(&bar, 0, limit);  // let copies in flight land before exit
     return;
   }
 
@@ -421,7 +422,73 @@ __global__ void __launch_bounds__(256) csr_update_kernel(CsrArgs a) {
   store_x<XT>(xp, xn);
 }
 
+// Step-path variant: each lane owns 4 consecutive restarts, so a warp reads
+// 512 contiguous bytes of every occurrence row (16-byte vector loads) and
+// updates 4 states. Needs the state's row pitch and the chunk start to be
+// multiples of 4 and the buffers 16-byte aligned (true for the library's own
+// state and occurrence buffers); lanes past nb are masked per element.
+template <typename XT>
+__global__ void __launch_bounds__(256) csr_update_vec4_kernel(CsrArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  const int lane = threadIdx.x & 31;
+  const long long warp = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int tiles = (a.nb + 127) >> 7;
+  const long long vl = warp / tiles;
+  if (vl >= a.v_count) return;
+  const int tile = static_cast<int>(warp - vl * tiles);
+  const int bl = tile * 128 + lane * 4;
+  if (bl >= a.nb) return;
+  const int v = a.v_begin + static_cast<int>(vl);
+  const int s0 = __ldg(a.csr_off + v), s1 = __ldg(a.csr_off + v + 1);
+  const float* col = a.go + bl;
+  float4 acc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+  int s = s0;
+  for (; s + 3 < s1; s += 4) {
+    float4 t[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) t[u] = __ldg(reinterpret_cast<const float4*>(col + static_cast<long long>(s + u) * a.go_pitch));
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc[u].x += t[u].x;
+      acc[u].y += t[u].y;
+      acc[u].z += t[u].z;
+      acc[u].w += t[u].w;
+    }
+  }
+  for (; s < s1; ++s) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(col + static_cast<long long>(s) * a.go_pitch));
+    acc[0].x += t.x;
+    acc[0].y += t.y;
+    acc[0].z += t.z;
+    acc[0].w += t.w;
+  }
+  const float g[4] = {(acc[0].x + acc[1].x) + (acc[2].x + acc[3].x), (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y),
+                      (acc[0].z + acc[1].z) + (acc[2].z + acc[3].z), (acc[0].w + acc[1].w) + (acc[2].w + acc[3].w)};
+  const int inst = __ldg(a.var_inst + v);
+  XT* xp = static_cast<XT*>(a.x) + static_cast<long long>(v) * a.x_pitch + a.b0 + bl;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (bl + e >= a.nb) break;
+    if (a.sflag != nullptr && a.sflag[static_cast<long long>(inst) * a.B + a.b0 + bl + e] != 0) continue;
+    const float xn = fminf(fmaxf(fmaf(-a.eta, g[e], load_x_rw<XT>(xp + e)), -1.0f), 1.0f);
+    store_x<XT>(xp + e, xn);
+  }
+}
+
 void launch_csr_update(const CsrArgs& a, int xt, cudaStream_t s) {
+  const bool vec = a.grad == nullptr && (a.go_pitch % 4) == 0 && (a.x_pitch % 4) == 0 && (a.b0 % 4) == 0 &&
+                   (reinterpret_cast<uintptr_t>(a.go) % 16) == 0;
+  if (vec) {
+    const long long tiles = (a.nb + 127) / 128;
+    const long long blocks = (tiles * a.v_count + 7) / 8;
+    if (blocks == 0) return;
+    if (xt == XT_F32) launch_pdl(csr_update_vec4_kernel<float>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+    else launch_pdl(csr_update_vec4_kernel<__nv_bfloat16>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+    return;
+  }
   const long long tiles = (a.nb + 31) / 32;
   const long long nwarps = tiles * a.v_count;
   const long long blocks = (nwarps + 7) / 8;

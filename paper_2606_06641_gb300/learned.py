@@ -89,8 +89,8 @@ def train(net: bd.Mpnn, batches, epochs: int, lr: float, seed: int = 0, log_ever
 
 
 def evaluate(net: Optional[bd.Mpnn], insts: Sequence[Instance], B: int, eta: float, max_steps: int,
-             seed: int = 0, steps_per_poll: int = 10, uniform_frac: float = 0.25,
-             sigma_min: float = 0.1, sigma_max: float = 0.9):
+             seed: int = 0, steps_per_poll: int = 10, uniform_frac: float = 0.5,
+             sigma_min: float = 0.3, sigma_max: float = 1.5):
     """Batched solve of `insts` from learned starts (net given) or uniform starts
     (net None). Returns (solved[bool], steps[int], seconds per instance, total)."""
     import torch

@@ -144,6 +144,35 @@ def solve_batched(insts: Sequence[Instance], B: int, eta: float, max_steps: int,
     return SolveResult(solved, steps, secs, total, asgs)
 
 
+def merge_across_ranks(best_unsat: int, best_restart: int, assignment: np.ndarray):
+    """Replicas on several GPUs solve the same instance from different
+    restarts; the result is the restart with the fewest violated constraints
+    (ties: lowest rank, then lowest restart). One all-reduce of a packed key
+    picks the winner and one broadcast ships its +-1 assignment; this is the
+    only exchange the data-parallel path needs. Works with any
+    torch.distributed backend (CPU tensors with gloo)."""
+    import torch
+    import torch.distributed as dist
+    rank, world = dist.get_rank(), dist.get_world_size()
+    key = torch.tensor([best_unsat * world * (1 << 31) + rank * (1 << 31) + best_restart], dtype=torch.int64)
+    dist.all_reduce(key, op=dist.ReduceOp.MIN)
+    k = int(key.item())
+    win_unsat, rem = divmod(k, world * (1 << 31))
+    win_rank, win_restart = divmod(rem, 1 << 31)
+    buf = torch.from_numpy(np.ascontiguousarray(assignment, dtype=np.int8)).clone()
+    dist.broadcast(buf, src=win_rank)
+    return win_unsat, win_rank, win_restart, buf.numpy()
+
+
+def max_over_ranks(value: float) -> float:
+    """The slowest rank's time (bench timing rule)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def par2(res: SolveResult, timeout_s: float) -> float:
     """PAR-2: mean time with unsolved instances charged twice the timeout."""
     t = np.where(res.solved & (res.seconds <= timeout_s), res.seconds, 2.0 * timeout_s)
