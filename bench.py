@@ -371,9 +371,11 @@ def run_ours(args):
     desc, B_default = WORKLOADS[args.workload]
     B = args.restarts or B_default
     insts = make_workload(args.workload)
-    params = bd.default_params(eta=0.1, verify_every=1, chunk=args.chunk)
+    params = bd.default_params(eta=0.1, verify_every=1, chunk=args.chunk, autotune=0 if args.tiles else 1)
     h = bd.load_instance(insts[0], params) if len(insts) == 1 else bd.load_batch(insts, params)
     bd.init_restarts(h, B, seed=1000 + rank)
+    if args.tiles:
+        bd.set_tiles(h, *bd.parse_tiles(args.tiles))
     stream = torch.cuda.current_stream()
     S = max(1, min(args.steps_per_graph, args.steps))
     R = max(1, args.steps // S)
@@ -448,6 +450,7 @@ def run_ours(args):
         e2e = {"value": L * B * E * world / el, "unit": UNIT, "h2d_bytes_per_step": n_total * B * 4,
                "d2h_bytes_per_step": n_total * B * 4 + len(insts) * B * 4}
     chunk, rpl = bd.tuning(h)
+    tiles = bd.format_tiles(*bd.tiles(h))
     h.free()
 
     cpu = None
@@ -472,7 +475,9 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "restarts": B, "literals": L, "instances": len(insts),
                        "l2": f"flushed (512 MB write) between timed CUDA-graph replays of {S} steps",
-                       "chunk_restarts": chunk, "restarts_per_lane": rpl, "parallelism": f"replicas x{world}"},
+                       "chunk_restarts": chunk, "restarts_per_lane": rpl,
+                       "tiles": tiles, "tiles_source": "given" if args.tiles else "autotuned",
+                       "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
                          "frac": achieved / peak_tinst if peak_tinst else None, "traffic": traffic,
                          "kernel": "FE+gradient kernels (all length buckets of a chunk)",
@@ -509,6 +514,7 @@ def main():
     ap.add_argument("--restarts", type=int, default=0, help="restarts per GPU (0 = the workload's)")
     ap.add_argument("--steps-per-graph", type=int, default=10)
     ap.add_argument("--chunk", type=int, default=0, help="restarts per chunk (0 = autotuned)")
+    ap.add_argument("--tiles", default="", help="fixed chunk and tiles, 'chunk:k=RPLxCPW,...' (no autotuning)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--tts-instances", type=int, default=128)
     ap.add_argument("--tts-eta", type=float, default=0.1)

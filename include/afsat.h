@@ -270,6 +270,20 @@ int afs_kernel_timing(afs_handle* h, double* fe_ms_total, int64_t* fe_launches, 
 int afs_last_launch_count(const afs_handle* h, int64_t* launches);
 /* The chunk size and per-bucket tile choice in use (after autotuning). */
 int afs_tuning(const afs_handle* h, int32_t* chunk, int32_t* rpl_by_k, int32_t kcap);
+/* afs_tiles: as afs_tuning, plus the constraints-per-warp of each short
+ * bucket. rpl_by_k / cpw_by_k (may be NULL) have kcap entries indexed by
+ * constraint length; entries of lengths with no short bucket are 0. */
+int afs_tiles(const afs_handle* h, int32_t* chunk, int32_t* rpl_by_k, int32_t* cpw_by_k, int32_t kcap);
+/* afs_set_tiles: fix the restart chunk and the per-bucket tile shapes after
+ * afs_init_restarts (for example to replay a shape chosen by an earlier
+ * autotuned run, or under a profiler where event timing is not meaningful).
+ * chunk 0 keeps the current chunk, otherwise it is rounded up to a multiple
+ * of 32 and capped at the padded restart count. A zero entry of rpl_by_k or
+ * cpw_by_k (or a NULL array) keeps that bucket's value. rpl must be a power
+ * of two up to the kernel's limit for the length (4 for k <= 8, 2 for
+ * k <= 16, else 1; 1 in the ESP basis) and cpw in 1..64; otherwise nothing
+ * changes and AFS_E_ARG is returned. Cached step graphs are dropped. */
+int afs_set_tiles(afs_handle* h, int32_t chunk, const int32_t* rpl_by_k, const int32_t* cpw_by_k, int32_t kcap);
 
 /* afs_coef_table: the FP32 coefficient table the kernels use for one
  * constraint shape (for host-side inspection and tests). form 0 = short

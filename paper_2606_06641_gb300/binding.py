@@ -64,6 +64,8 @@ SIGNATURES = {
     "afs_kernel_timing": (_I32, [_P, _P, _P, _P, _P]),
     "afs_last_launch_count": (_I32, [_P, _P]),
     "afs_tuning": (_I32, [_P, _P, _P, _I32]),
+    "afs_tiles": (_I32, [_P, _P, _P, _P, _I32]),
+    "afs_set_tiles": (_I32, [_P, _I32, _P, _P, _I32]),
     "afs_coef_table": (_I32, [_I32, _I32, _I32, _I32, _I32, _I32, _I32, _P, _I32, _P]),
     "afs_esp_coefficients": (_I32, [_I32, _I32, _I32, _I32, _I32, _P]),
     "afs_last_error": (ctypes.c_char_p, []),
@@ -372,6 +374,42 @@ def tuning(h: Handle):
     rpl = (ctypes.c_int32 * 33)()
     _check(lib().afs_tuning(h.ptr, ctypes.byref(chunk), rpl, 33))
     return chunk.value, {k: rpl[k] for k in range(33) if rpl[k]}
+
+
+def tiles(h: Handle):
+    """(chunk, {k: (restarts per lane, constraints per warp)}) of the short buckets."""
+    chunk = ctypes.c_int32()
+    rpl = (ctypes.c_int32 * 33)()
+    cpw = (ctypes.c_int32 * 33)()
+    _check(lib().afs_tiles(h.ptr, ctypes.byref(chunk), rpl, cpw, 33))
+    return chunk.value, {k: (rpl[k], cpw[k]) for k in range(33) if rpl[k]}
+
+
+def set_tiles(h: Handle, chunk: int = 0, tiles=None):
+    """Fix the chunk and per-length (rpl, cpw) tile shapes; 0 keeps a value."""
+    rpl = (ctypes.c_int32 * 33)()
+    cpw = (ctypes.c_int32 * 33)()
+    for k, (r, c) in (tiles or {}).items():
+        if not 0 <= int(k) < 33:
+            raise ValueError(f"no short bucket for length {k}")
+        rpl[int(k)] = int(r)
+        cpw[int(k)] = int(c)
+    _check(lib().afs_set_tiles(h.ptr, int(chunk), rpl, cpw, 33))
+
+
+def parse_tiles(spec: str):
+    """'1024:3=4x2,20=1x1' -> (1024, {3: (4, 2), 20: (1, 1)})."""
+    chunk_s, _, rest = spec.partition(":")
+    tiles = {}
+    for item in filter(None, rest.split(",")):
+        k, _, shape = item.partition("=")
+        r, _, c = shape.partition("x")
+        tiles[int(k)] = (int(r), int(c or 0))
+    return int(chunk_s or 0), tiles
+
+
+def format_tiles(chunk: int, tiles) -> str:
+    return f"{chunk}:" + ",".join(f"{k}={r}x{c}" for k, (r, c) in sorted(tiles.items()))
 
 
 def coef_table(ctype: int, k: int, op: int = 0, param: int = 0, parity: int = 1, basis: int = BASIS_PGF,

@@ -1235,6 +1235,52 @@ int afs_tuning(const afs_handle* h, int32_t* chunk, int32_t* rpl_by_k, int32_t k
   return AFS_OK;
 }
 
+int afs_tiles(const afs_handle* h, int32_t* chunk, int32_t* rpl_by_k, int32_t* cpw_by_k, int32_t kcap) {
+  if (!h) return fail(AFS_E_ARG, "NULL handle");
+  if (kcap < 0) return fail(AFS_E_ARG, "negative kcap");
+  if (chunk) *chunk = h->Bc;
+  for (int k = 0; k < kcap; ++k) {
+    if (rpl_by_k) rpl_by_k[k] = 0;
+    if (cpw_by_k) cpw_by_k[k] = 0;
+  }
+  for (const Group& g : h->groups) {
+    if (g.is_long || g.k >= kcap) continue;
+    if (rpl_by_k) rpl_by_k[g.k] = g.rpl;
+    if (cpw_by_k) cpw_by_k[g.k] = g.cpw;
+  }
+  return AFS_OK;
+}
+
+int afs_set_tiles(afs_handle* h, int32_t chunk, const int32_t* rpl_by_k, const int32_t* cpw_by_k, int32_t kcap) {
+  if (!h) return fail(AFS_E_ARG, "NULL handle");
+  if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
+  if (chunk < 0 || kcap < 0) return fail(AFS_E_ARG, "negative chunk or kcap");
+  const bool pgf = h->p.basis == AFS_BASIS_PGF;
+  // validate everything before changing anything
+  for (const Group& g : h->groups) {
+    if (g.is_long || g.k >= kcap) continue;
+    const int r = rpl_by_k ? rpl_by_k[g.k] : 0;
+    const int c = cpw_by_k ? cpw_by_k[g.k] : 0;
+    const int rmax = pgf ? max_rpl_for_k(g.k) : 1;
+    if (r < 0 || r > rmax || (r & (r - 1)))
+      return fail(AFS_E_ARG, "rpl %d not allowed for k=%d (power of two <= %d)", r, g.k, rmax);
+    if (c < 0 || c > 64) return fail(AFS_E_ARG, "cpw %d out of range for k=%d", c, g.k);
+  }
+  if (chunk > 0) {
+    const int bc = std::min<int>((chunk + 31) / 32 * 32, static_cast<int>(h->pitch));
+    int rc = alloc_go(h, bc);
+    if (rc) return rc;
+    h->Bc = bc;
+  }
+  for (Group& g : h->groups) {
+    if (g.is_long || g.k >= kcap) continue;
+    if (rpl_by_k && rpl_by_k[g.k]) g.rpl = rpl_by_k[g.k];
+    if (cpw_by_k && cpw_by_k[g.k]) g.cpw = cpw_by_k[g.k];
+  }
+  h->drop_graphs();
+  return AFS_OK;
+}
+
 int afs_coef_table(int32_t type, int32_t k, int32_t op, int32_t param, int32_t parity, int32_t basis, int32_t form,
                    float* out, int32_t cap, int32_t* len) {
   if (!len) return fail(AFS_E_ARG, "len is NULL");

@@ -216,6 +216,51 @@ def test_chunked_step_equals_single_chunk():
     np.testing.assert_array_equal(outs[0], outs[2])
 
 
+def test_fixed_tiles_match_autotuned_and_oracle():
+    """Every tile shape a caller may fix computes the same step: x after two
+    steps agrees across shapes and with the oracle, and the unsat counts of
+    each are the oracle's for its own state."""
+    inst = synth.config2(1)
+    B = 256
+    x0 = synth.uniform_x0(inst.n, B, 5)
+    ks = sorted(set(int(k) for k in inst.lengths))
+    ref = O.pgd_step(inst, O.pgd_step(inst, x0.astype(np.float64), 0.1), 0.1)
+    outs = []
+    for chunk, rpl, cpw in ((0, None, None), (64, 1, 1), (256, 4, 8), (128, 2, 3)):
+        h = bd.load_instance(inst, bd.default_params(eta=0.1, autotune=0 if rpl else 1))
+        bd.init_restarts(h, B, x0=_dev(x0))
+        if rpl:
+            tiles = {k: (min(rpl, 4 if k <= 8 else 2 if k <= 16 else 1), cpw) for k in ks if k <= 32}
+            bd.set_tiles(h, chunk, tiles)
+            c, got = bd.tiles(h)
+            assert c == chunk and got == tiles
+        bd.step(h, 2)
+        x = bd.get_x(h).cpu().numpy()
+        un, _ = bd.get_verify(h)
+        np.testing.assert_array_equal(un.cpu().numpy()[0], O.unsat_count(inst, x))
+        assert np.abs(x - ref).max() <= 0.1 * 4 * TOL
+        outs.append(x)
+        h.free()
+    for x in outs[1:]:
+        assert np.abs(x - outs[0]).max() <= 1e-6
+
+
+def test_set_tiles_rejects_bad_shapes():
+    inst = synth.config2(1)
+    h = bd.load_instance(inst, bd.default_params(autotune=0))
+    with pytest.raises(RuntimeError):
+        bd.set_tiles(h, 64, {3: (1, 1)})            # before init_restarts
+    bd.init_restarts(h, 64, seed=1)
+    before = bd.tiles(h)
+    with pytest.raises(RuntimeError):
+        bd.set_tiles(h, 0, {20: (2, 1)})            # k=20 allows one restart per lane
+    with pytest.raises(RuntimeError):
+        bd.set_tiles(h, 0, {3: (3, 1)})             # not a power of two
+    with pytest.raises(RuntimeError):
+        bd.set_tiles(h, 0, {3: (1, 65)})
+    assert bd.tiles(h) == before
+
+
 def test_config2_full_size_sampled():
     """The hybrid n=2000 instance at B=1024 in the launch configuration of the
     benchmark (autotuned tiles and chunk, graph replay): one step checked on

@@ -192,3 +192,11 @@ def test_overlong_constraint_rejected():
     with pytest.raises(bd.AfsError) as ei:
         bd.load_instance(b.build(), stream=0)
     assert ei.value.code == -3
+
+
+def test_tile_spec_round_trip():
+    spec = "1024:3=4x2,4=2x1,5=4x1,20=1x1"
+    chunk, tiles = bd.parse_tiles(spec)
+    assert chunk == 1024 and tiles == {3: (4, 2), 4: (2, 1), 5: (4, 1), 20: (1, 1)}
+    assert bd.format_tiles(chunk, tiles) == spec
+    assert bd.parse_tiles("0:") == (0, {})
