@@ -167,6 +167,13 @@ int afs_set_x(afs_handle* h, const float* x_dev, void* stream);
  * seen solved per instance since afs_init_restarts (INT32_MAX if none) into
  * solved_dev[n_inst]; either may be NULL. */
 int afs_get_verify(afs_handle* h, int32_t* unsat_dev, int32_t* solved_dev, void* stream);
+/* afs_get_step_check: the outcome of the exact check inside the last step
+ * that ran one (verify_every != 0), per instance and word of 32 restarts:
+ * bit j of out_dev[inst * W + w] is 1 when restart 32w + j satisfied every
+ * constraint of the instance at the state that step read (those restarts
+ * were left unmoved). W = ceil(B / 32); out_dev holds n_inst * W words
+ * (device memory, written on `stream`). Bits of restarts >= B are 0. */
+int afs_get_step_check(const afs_handle* h, uint32_t* out_dev, int32_t* words_per_inst, void* stream);
 
 /* afs_eval_fe_grad: evaluate, for the restarts given in x_dev, every
  * constraint's expansion fe_dev[c * B + b] (constraints in load order,

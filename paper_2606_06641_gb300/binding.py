@@ -65,6 +65,7 @@ SIGNATURES = {
     "afs_last_launch_count": (_I32, [_P, _P]),
     "afs_tuning": (_I32, [_P, _P, _P, _I32]),
     "afs_tiles": (_I32, [_P, _P, _P, _P, _I32]),
+    "afs_get_step_check": (_I32, [_P, _P, _P, _P]),
     "afs_set_tiles": (_I32, [_P, _I32, _P, _P, _I32]),
     "afs_coef_table": (_I32, [_I32, _I32, _I32, _I32, _I32, _I32, _I32, _P, _I32, _P]),
     "afs_esp_coefficients": (_I32, [_I32, _I32, _I32, _I32, _I32, _P]),
@@ -236,6 +237,19 @@ def get_verify(h: Handle, stream=None):
     sol = torch.empty(h.n_inst, dtype=torch.int32, device="cuda")
     _check(lib().afs_get_verify(h.ptr, _ptr(un), _ptr(sol), _stream(stream)))
     return un, sol
+
+
+def get_step_check(h: Handle, stream=None):
+    """Per instance and restart: True where the last step's exact check found
+    every constraint satisfied (bool tensor [n_inst, B] on the device)."""
+    import torch
+    W = ctypes.c_int32()
+    _check(lib().afs_get_step_check(h.ptr, None, ctypes.byref(W), _stream(stream)))
+    words = torch.empty((h.n_inst, W.value), dtype=torch.int32, device="cuda")
+    _check(lib().afs_get_step_check(h.ptr, _ptr(words), None, _stream(stream)))
+    shifts = torch.arange(32, device="cuda", dtype=torch.int32)
+    bits = (words.unsqueeze(-1) >> shifts) & 1
+    return bits.reshape(h.n_inst, -1)[:, :h.B] != 0
 
 
 def eval_fe_grad(h: Handle, x, want_fe: bool = True, want_grad: bool = True, stream=None):

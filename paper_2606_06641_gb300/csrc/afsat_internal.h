@@ -31,25 +31,11 @@ struct FeGroupArgs {
   float* fe;                // optional fe[orig * fe_pitch + b]
   long long fe_pitch;
   int* err;                 // device error word (bounded waits, bounds checks)
-  // fused exact check of the state being read (nullable vflag = no check):
-  // a warp that finds a violated constraint of (inst, b) stores 1 into
-  // vflag[slot * vflag_stride + inst * B + b], slot = blockIdx.x % VFLAG_SLOTS
-  const unsigned long long* cons_vmask;  // short: bit t set where f(t) = +1 (violated)
-  const int* cons_voff;     // long: offset of the constraint's row in viol
-  const unsigned char* viol;
-  const int* cons_inst;     // instance of each constraint (bucket order)
-  int* vflag;
-  long long vflag_stride;
-  int B;
   int cpw;                  // constraints per warp (short kernel)
   int vec;                  // short kernel: a lane's restarts are consecutive (vector loads/stores)
   long long wait_limit;     // long kernel: SM cycles a bounded barrier wait may take
   unsigned extra_tx;        // test hook: bytes the long kernel expects beyond its copies (0 normally)
 };
-
-// Rows of violation flags: spreading the plain stores of many warps over
-// several rows keeps them off a handful of L2 lines.
-constexpr int VFLAG_SLOTS = 32;
 
 // Gather of per-occurrence derivatives per variable and the projected step.
 struct CsrArgs {
@@ -66,21 +52,48 @@ struct CsrArgs {
   const int* var_inst;      // instance of each variable, then first variable of each instance
   int n_vars;               // total variables (offset of the first-variable table in var_inst)
   // freeze rule (Algorithm 1 returns on is_sat): a restart whose state had no
-  // violated constraint in this step's fused check is left where it is.
-  const signed char* sflag; // nullable: sflag[inst * B + b] = 1 if solved
-  int B;                    // restarts per instance (row length of sflag)
+  // violated constraint in this step's exact check is left where it is.
+  // vcur[inst * W + w] holds the violation bits of this step's check
+  // (nullable: nothing is frozen); the warps of each instance's first
+  // variable record the lowest solved restart in `solved` and clear the
+  // other parity's words vnext for the next step's check.
+  const unsigned* vcur;
+  unsigned* vnext;
+  int* solved;
+  unsigned* sgn;            // nullable: sign words of the new state (layout below)
+  int W;                    // words per variable row of sgn / per instance of vcur
+  int B;                    // restarts per instance
 };
 
-// Per-restart fold of the fused check's flag rows (one thread per restart).
-struct FlagArgs {
-  const int* vflag_cur;     // VFLAG_SLOTS rows of n_inst * B flags
-  int* vflag_next;          // rows cleared for the next step
-  long long stride;         // n_inst * B
-  signed char* sflag;       // 1 where no row flagged a violation
-  int* solved;              // lowest solved restart per instance
-  int n_inst, B, b0, nb;
+// Sign words: bit j of sgn[v * W + w] is 1 when x[v][32w + j] < 0, i.e. when
+// variable v rounds to True in restart 32w + j (padding restarts are 0). The
+// step's CSR pass writes them together with the state; the exact check reads
+// 32 restarts per integer operation from them.
+void launch_pack_signs(const void* x, int xt, long long x_pitch, int n, int B, unsigned* sgn, int W,
+                       cudaStream_t s);
+
+// Bit-sliced exact check of the state in sign words (Algorithm 1's is_sat):
+// one thread per (range of constraints of one instance, word of 32 restarts)
+// counts true literals in bit planes and ORs the violation words of its range
+// into vword[inst * W + w] (which the caller has cleared).
+struct CheckArgs {
+  const unsigned* sgn;
+  int W;                    // words per variable row
+  int w0, wc;               // first word and number of words of this chunk
+  const int* lit_enc;       // load order literals, var << 1 | negated
+  const int* lit_off;       // load order constraint offsets
+  const unsigned long long* em;  // per constraint, k <= 62: counts to test (bit t), bit 63 = complement
+  const int* viol_off;      // k > 62: viol[viol_off[c] + t] = 1 where f(t) = +1
+  const unsigned char* viol;
+  const int4* ranges;       // {c_begin, c_end, instance, 0}
+  int n_ranges;
+  unsigned* vword;
 };
-void launch_fold_flags(const FlagArgs& a, cudaStream_t s);
+void launch_check_bits(const CheckArgs& a, cudaStream_t s);
+
+// Solved bits (1 = no violated constraint) of the violation words of a check,
+// restarts >= B cleared: out[inst * W + w].
+void launch_solved_words(const unsigned* vword, int n_inst, int W, int B, unsigned* out, cudaStream_t s);
 // p[0..n) = v
 void launch_fill_int(int* p, int v, long long n, cudaStream_t s);
 
@@ -144,6 +157,8 @@ struct GraphView {
   int B, xt;
 };
 int graph_view(const afs_handle* h, GraphView* out);
+// Rebuild the sign words after the state was written outside the step.
+int state_written(afs_handle* h, cudaStream_t s);
 // A slot in which other modules keep per-handle device data; released with the handle.
 void* handle_ext(const afs_handle* h);
 void set_handle_ext(afs_handle* h, void* p, void (*release)(void*));

@@ -14,13 +14,10 @@
 // constraints of its group, the k-literal loop is unrolled so prefixes live in
 // registers, and the roots are a runtime loop. Per (literal, complex root) the
 // work is a prefix product (4 FP32 instructions), a suffix product (4) and the
-// gradient combine (2).
-//
-// The same pass performs Algorithm 1's exact check of the state it reads: a
-// literal is true when its variable rounds to True (x < 0) xor it is negated,
-// and the constraint is violated when bit t (true count) of its mask is set.
-// A lane that saw a violation stores 1 into its warp's flag row (one plain
-// store per warp and instance; rows are spread over VFLAG_SLOTS).
+// gradient combine (2). A literal's sign s_i is applied with one multiply per
+// value (l = s x on the way in, s dFE/dl on the way out), and only the
+// negation bits and the slot reads are kept per literal, so a k = 20 tile
+// holds its k literal values, k prefixes and k gradients and little else.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -38,11 +35,6 @@ template <>
 __device__ __forceinline__ float load_x<__nv_bfloat16>(const __nv_bfloat16* p) {
   const unsigned short u = __ldg(reinterpret_cast<const unsigned short*>(p));
   return __uint_as_float(static_cast<unsigned int>(u) << 16);
-}
-
-// literal truth at the sign-rounded point, from l = s x and the negation bit
-__device__ __forceinline__ int lit_true(float l, int neg) {
-  return neg ? (l <= 0.0f) : (l < 0.0f);
 }
 
 // N consecutive state values with one vector load (N = 2 or 4; 16-byte or
@@ -107,8 +99,6 @@ __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
   const int tile = static_cast<int>(warp - cg * tiles);
   const int c_last = static_cast<int>(min(static_cast<long long>(a.c_count), c_first + a.cpw));
   const XT* x = static_cast<const XT*>(a.x);
-  const bool check = a.vflag != nullptr;
-  int* vrow = check ? a.vflag + static_cast<long long>(warp % VFLAG_SLOTS) * a.vflag_stride + a.b0 : nullptr;
 
   constexpr bool V = VEC && RPL > 1;
   int bl[RPL];
@@ -118,22 +108,18 @@ __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
     bl[r] = V ? tile * TW + lane * RPL + r : tile * TW + r * 32 + lane;
     act[r] = bl[r] < a.nb;
   }
-  bool vio[RPL];
-#pragma unroll
-  for (int r = 0; r < RPL; ++r) vio[r] = false;
-  int cur_inst = -1;
 
   for (int c = static_cast<int>(c_first); c < c_last; ++c) {
     const int cb = a.c_begin + c;
     const int2* ls = a.litslot + a.lit_base + static_cast<long long>(c) * K;
-    int2 lit[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) lit[i] = __ldg(ls + i);
-
+    unsigned negm = 0u;
     float l[RPL][K];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-      const long long row = static_cast<long long>(lit[i].x >> 1) * a.x_pitch + a.b0;
+      const int enc = __ldg(&ls[i].x);
+      negm |= static_cast<unsigned>(enc & 1) << i;
+      const float sg = (enc & 1) ? -1.0f : 1.0f;
+      const long long row = static_cast<long long>(enc >> 1) * a.x_pitch + a.b0;
       if constexpr (V) {
         float xv[RPL];
         if (act[0]) {
@@ -143,35 +129,10 @@ __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
           for (int r = 0; r < RPL; ++r) xv[r] = 0.0f;
         }
 #pragma unroll
-        for (int r = 0; r < RPL; ++r) l[r][i] = (lit[i].x & 1) ? -xv[r] : xv[r];
+        for (int r = 0; r < RPL; ++r) l[r][i] = xv[r] * sg;
       } else {
 #pragma unroll
-        for (int r = 0; r < RPL; ++r) {
-          const float xv = act[r] ? load_x<XT>(x + row + bl[r]) : 0.0f;
-          l[r][i] = (lit[i].x & 1) ? -xv : xv;
-        }
-      }
-    }
-
-    if (check) {
-      const int inst = __ldg(a.cons_inst + cb);
-      if (inst != cur_inst) {
-        if (cur_inst >= 0) {
-#pragma unroll
-          for (int r = 0; r < RPL; ++r) {
-            if (act[r] && vio[r]) vrow[static_cast<long long>(cur_inst) * a.B + bl[r]] = 1;
-            vio[r] = false;
-          }
-        }
-        cur_inst = inst;
-      }
-      const unsigned long long vm = __ldg(a.cons_vmask + cb);
-#pragma unroll
-      for (int r = 0; r < RPL; ++r) {
-        int t = 0;
-#pragma unroll
-        for (int i = 0; i < K; ++i) t += lit_true(l[r][i], lit[i].x & 1);
-        vio[r] |= ((vm >> t) & 1ull) != 0;
+        for (int r = 0; r < RPL; ++r) l[r][i] = (act[r] ? load_x<XT>(x + row + bl[r]) : 0.0f) * sg;
       }
     }
 
@@ -279,18 +240,19 @@ __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
 
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-      float* row = a.go + static_cast<long long>(lit[i].y) * a.go_pitch;
+      const float sg = ((negm >> i) & 1u) ? -1.0f : 1.0f;
+      float* row = a.go + static_cast<long long>(__ldg(&ls[i].y)) * a.go_pitch;
       if constexpr (V) {
         if (act[0]) {
           float gv[RPL];
 #pragma unroll
-          for (int r = 0; r < RPL; ++r) gv[r] = (lit[i].x & 1) ? -g[r][i] : g[r][i];
+          for (int r = 0; r < RPL; ++r) gv[r] = g[r][i] * sg;
           store_fvec<RPL>(row + bl[0], gv);
         }
       } else {
 #pragma unroll
         for (int r = 0; r < RPL; ++r)
-          if (act[r]) row[bl[r]] = (lit[i].x & 1) ? -g[r][i] : g[r][i];
+          if (act[r]) row[bl[r]] = g[r][i] * sg;
       }
     }
     if (a.fe != nullptr) {
@@ -299,11 +261,6 @@ __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
       for (int r = 0; r < RPL; ++r)
         if (act[r]) a.fe[orow + bl[r]] = fe[r];
     }
-  }
-  if (check && cur_inst >= 0) {
-#pragma unroll
-    for (int r = 0; r < RPL; ++r)
-      if (act[r] && vio[r]) vrow[static_cast<long long>(cur_inst) * a.B + bl[r]] = 1;
   }
 }
 

@@ -133,16 +133,19 @@ struct afs_handle {
   double work_per_restart = 0.0;
   // device instance data
   DevBuf litslot, cons_tab, cons_orig, cons_k, cons_lit, coef, csr_off, lit_enc, lit_off, viol_off, viol,
-      ranges, var_inst, err, cons_vmask, cons_voff, cons_inst;
-  int n_ranges = 0;
+      ranges, var_inst, err, chk_em, chk_ranges;
+  int n_ranges = 0, n_chk_ranges = 0;
   // restart state
   int B = 0, xt = XT_F32;
   long long pitch = 0;
   int Bc = 0;
-  // unsat: counts of the last standalone check; vflag: the fused per-step
-  // check's flag rows (two parities x VFLAG_SLOTS rows); sflag: solved bytes
-  DevBuf x, go, unsat, vflag, sflag, solved, col, assign, stage, eval_go;
+  int W = 0;  // 32-restart words per variable row (pitch / 32)
+  // unsat: counts of the last standalone check; sgn: sign words of x (n x W);
+  // vword: the per-step check's violation words, two parities of n_inst x W
+  // (step t ORs into parity t & 1 and clears the other for step t + 1)
+  DevBuf x, go, unsat, sgn, vword, solved, col, assign, stage, eval_go;
   int parity = 0;
+  bool step_check_valid = false;  // vword[parity ^ 1] holds the last step's check
   long long eval_go_cols = 0;
   // graphs
   cudaStream_t cap = nullptr;
@@ -152,6 +155,9 @@ struct afs_handle {
   cudaStream_t aux[NAUX] = {};
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[NAUX] = {};
+  // the per-step exact check runs on its own forked stream beside the FE launches
+  cudaStream_t chk = nullptr;
+  cudaEvent_t ev_chk = nullptr;
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs, timed_graphs;  // (nsteps, start parity)
   std::map<std::pair<int, int>, std::pair<std::vector<std::pair<int, int>>, std::vector<std::pair<int, int>>>>
       timed_pairs;
@@ -173,6 +179,8 @@ struct afs_handle {
       if (ev_join[i]) cudaEventDestroy(ev_join[i]);
     }
     if (ev_fork) cudaEventDestroy(ev_fork);
+    if (chk) cudaStreamDestroy(chk);
+    if (ev_chk) cudaEventDestroy(ev_chk);
     if (ext && ext_release) ext_release(ext);
   }
   void drop_graphs() {
@@ -298,8 +306,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     if (!la) return gk[a] < gk[b];
     return gk[a] > gk[b];
   });
-  std::vector<int> b_tab(m), b_orig(m), b_k(m), b_lit(m), b_voff(m), b_inst(m);
-  std::vector<unsigned long long> b_vmask(m, 0ull);
+  std::vector<int> b_tab(m), b_orig(m), b_k(m), b_lit(m);
   std::vector<int2> litslot;
   litslot.reserve(L + m);
   h->work_per_restart = 0.0;
@@ -311,11 +318,6 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     b_orig[pos] = g;
     b_k[pos] = k;
     b_lit[pos] = static_cast<int>(litslot.size());
-    b_voff[pos] = viol_off[g];
-    b_inst[pos] = ginst[g];
-    if (k < 64)
-      for (int t = 0; t <= k; ++t)
-        if (violv[viol_off[g] + t]) b_vmask[pos] |= 1ull << t;
     for (int t = 0; t < k; ++t) litslot.push_back(make_int2(enc_of(ginst[g], lits[goff[g] + t]), -1));
     if (k > KSHORT && (k & 1)) litslot.push_back(make_int2(0, 0));
     h->work_per_restart += work_instr(k);
@@ -387,6 +389,32 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     }
   }
   h->n_ranges = static_cast<int>(ranges.size());
+  // bit-sliced check: counts to test per constraint (the violated ones, or
+  // the satisfied ones with bit 63 set when fewer); ranges of <= 32 literals
+  // and < 32 constraints, a longer constraint alone
+  std::vector<unsigned long long> chk_em(m, 0ull);
+  for (int g = 0; g < m; ++g) {
+    const int k = gk[g];
+    if (k > 62) continue;
+    unsigned long long vm = 0ull;
+    for (int t = 0; t <= k; ++t)
+      if (violv[viol_off[g] + t]) vm |= 1ull << t;
+    const unsigned long long all = (1ull << (k + 1)) - 1ull;
+    const unsigned long long sat = ~vm & all;
+    chk_em[g] = (__builtin_popcountll(sat) < __builtin_popcountll(vm)) ? (sat | (1ull << 63)) : vm;
+  }
+  std::vector<int4> chk_ranges;
+  for (int i = 0; i < n_inst; ++i) {
+    int c = h->inst_cbegin[i];
+    const int ce = h->inst_cbegin[i + 1];
+    while (c < ce) {
+      int e = c, lits_in = 0;
+      while (e < ce && (e == c || (lits_in + gk[e] <= 32 && e - c < 31))) lits_in += gk[e++];
+      chk_ranges.push_back(make_int4(c, e, i, 0));
+      c = e;
+    }
+  }
+  h->n_chk_ranges = static_cast<int>(chk_ranges.size());
   h->h_var_inst.resize(h->n);
   for (int i = 0; i < n_inst; ++i)
     for (int v = h->inst_vbegin[i]; v < h->inst_vbegin[i + 1]; ++v) h->h_var_inst[v] = i;
@@ -408,9 +436,8 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   if ((rc = upload(h->viol, violv, s))) return rc;
   if ((rc = upload(h->ranges, ranges, s))) return rc;
   if ((rc = upload(h->var_inst, var_inst_ext, s))) return rc;
-  if ((rc = upload(h->cons_vmask, b_vmask, s))) return rc;
-  if ((rc = upload(h->cons_voff, b_voff, s))) return rc;
-  if ((rc = upload(h->cons_inst, b_inst, s))) return rc;
+  if ((rc = upload(h->chk_em, chk_em, s))) return rc;
+  if ((rc = upload(h->chk_ranges, chk_ranges, s))) return rc;
   std::vector<int> zero1(1, 0);
   if ((rc = upload(h->err, zero1, s))) return rc;
   CK(cudaStreamSynchronize(s));
@@ -420,6 +447,8 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     CK(cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming));
   }
   CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  CK(cudaStreamCreateWithFlags(&h->chk, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_chk, cudaEventDisableTiming));
   if (!prepare_kernels()) return fail(AFS_E_CUDA, "kernel attribute setup: %s", cudaGetErrorString(cudaGetLastError()));
   *out = h.release();
   return AFS_OK;
@@ -429,8 +458,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
 // launch planning
 // ---------------------------------------------------------------------------
 static int launch_fe_group(afs_handle* h, const Group& g, const void* x, int xt, long long x_pitch, int b0, int nb,
-                           float* go, long long go_pitch, float* fe, long long fe_pitch, int* vflag,
-                           cudaStream_t s) {
+                           float* go, long long go_pitch, float* fe, long long fe_pitch, cudaStream_t s) {
   FeGroupArgs a{};
   a.x = x;
   a.x_pitch = x_pitch;
@@ -451,13 +479,6 @@ static int launch_fe_group(afs_handle* h, const Group& g, const void* x, int xt,
   a.fe = fe;
   a.fe_pitch = fe_pitch;
   a.err = h->err.as<int>();
-  a.cons_vmask = h->cons_vmask.as<unsigned long long>();
-  a.cons_voff = h->cons_voff.as<int>();
-  a.viol = h->viol.as<unsigned char>();
-  a.cons_inst = h->cons_inst.as<int>();
-  a.vflag = vflag;
-  a.vflag_stride = static_cast<long long>(h->n_inst) * h->B;
-  a.B = h->B;
   a.cpw = g.cpw;
   a.wait_limit = h->dbg_wait_limit;
   a.extra_tx = h->dbg_extra_tx;
@@ -480,10 +501,12 @@ static int launch_fe_group(afs_handle* h, const Group& g, const void* x, int xt,
   return AFS_OK;
 }
 
-// CSR gather and step; with `check`, the restarts whose state passed this
-// step's fused exact check are left unmoved and recorded as solved.
+// CSR gather and step. The step on the handle's own state (grad == nullptr,
+// parity p >= 0) writes its sign words, clears the check words of parity
+// 1 - p and, with `check`, leaves the restarts that passed this step's exact
+// check (words of parity p) unmoved.
 static int launch_csr(afs_handle* h, void* x, int xt, long long x_pitch, int b0, int nb, const float* go,
-                      long long go_pitch, float eta, float* grad, long long grad_pitch, bool use_sflag,
+                      long long go_pitch, float eta, float* grad, long long grad_pitch, bool check, int p,
                       cudaStream_t s) {
   CsrArgs a{};
   a.x = x;
@@ -500,8 +523,15 @@ static int launch_csr(afs_handle* h, void* x, int xt, long long x_pitch, int b0,
   a.grad_pitch = grad_pitch;
   a.var_inst = h->var_inst.as<int>();
   a.n_vars = h->n;
+  const bool own = grad == nullptr && x == h->x.p && p >= 0;
+  if (own && b0 % 32 != 0) return fail(AFS_E_STATE, "chunk start %d is not a multiple of 32", b0);
+  const size_t niw = static_cast<size_t>(h->n_inst) * h->W;
+  a.W = h->W;
   a.B = h->B;
-  a.sflag = use_sflag ? h->sflag.as<signed char>() : nullptr;
+  a.vcur = own && check ? h->vword.as<unsigned>() + p * niw : nullptr;
+  a.vnext = own ? h->vword.as<unsigned>() + (p ^ 1) * niw : nullptr;
+  a.solved = h->solved.as<int>();
+  a.sgn = own ? h->sgn.as<unsigned>() : nullptr;
   launch_csr_update(a, xt, s);
   CKL();
   return AFS_OK;
@@ -537,27 +567,56 @@ static cudaEvent_t pool_event(afs_handle* h, int idx) {
   return h->ev_pool[idx];
 }
 
+// Bit-sliced exact check of the state's sign words for every restart, into
+// the violation words of parity p (cleared by the previous step's CSR pass).
+static void launch_check_step(afs_handle* h, int p, cudaStream_t s) {
+  CheckArgs c{};
+  c.sgn = h->sgn.as<unsigned>();
+  c.W = h->W;
+  c.w0 = 0;
+  c.wc = h->W;
+  c.lit_enc = h->lit_enc.as<int>();
+  c.lit_off = h->lit_off.as<int>();
+  c.em = h->chk_em.as<unsigned long long>();
+  c.viol_off = h->viol_off.as<int>();
+  c.viol = h->viol.as<unsigned char>();
+  c.ranges = h->chk_ranges.as<int4>();
+  c.n_ranges = h->n_chk_ranges;
+  c.vword = h->vword.as<unsigned>() + static_cast<size_t>(p) * h->n_inst * h->W;
+  launch_check_bits(c, s);
+}
+
 // Enqueue nsteps of the descent loop on s (used both directly and under
-// capture). Step t reads the state x_t: its FE pass also flags x_t's violated
-// constraints (flag rows of parity p), a fold marks the restarts with no flag
-// as solved and clears the rows of parity 1-p, and the CSR pass moves only
-// the unsolved restarts. With `check`, a standalone exact check of the final
-// state ends the sequence.
+// capture). Step t reads the state x_t and has parity p = (parity0 + t) & 1.
+// With `check`, the bit-sliced exact check of x_t (violation words of parity
+// p) runs once per step on a forked stream beside the first chunk's FE
+// launches; per restart chunk the FE launches of the length buckets run
+// concurrently on forked streams, and the CSR pass moves the restarts that
+// failed the check, writes the sign words of x_{t+1}, records solved restarts
+// and clears the words of parity 1 - p. With `check`, a standalone exact
+// check of the final state ends the sequence.
 static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int parity0, cudaStream_t s,
                          long long* launches) {
   long long nl = 0;
   int ev = 0;
-  const size_t nib = static_cast<size_t>(h->n_inst) * h->B;
   for (int t = 0; t < nsteps; ++t) {
     const int p = (parity0 + t) & 1;
-    int* vcur = check ? h->vflag.as<int>() + p * VFLAG_SLOTS * nib : nullptr;
     for (int b0 = 0; b0 < h->B; b0 += h->Bc) {
       const int nb = std::min(h->Bc, h->B - b0);
       if (h->timing) CK(cudaEventRecordWithFlags(pool_event(h, ev), s, cudaEventRecordExternal));
       // the first (largest-work) bucket runs on s, the others on forked streams
       const int G = static_cast<int>(h->groups.size());
-      const bool fork = G > 1 && concurrent_enabled();
+      const bool conc = concurrent_enabled();
+      const bool chk_now = check && b0 == 0;
+      const bool fork = conc && (G > 1 || chk_now);
       if (fork) CK(cudaEventRecord(h->ev_fork, s));
+      if (chk_now) {
+        if (conc) CK(cudaStreamWaitEvent(h->chk, h->ev_fork, 0));
+        launch_check_step(h, p, conc ? h->chk : s);
+        CKL();
+        ++nl;
+        if (conc) CK(cudaEventRecord(h->ev_chk, h->chk));
+      }
       int used = 0;
       for (int gi = 0; gi < G; ++gi) {
         const Group& g = h->groups[h->order[gi]];
@@ -568,7 +627,7 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int p
           st = h->aux[a];
           used = std::max(used, a + 1);
         }
-        int rc = launch_fe_group(h, g, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, nullptr, 0, vcur, st);
+        int rc = launch_fe_group(h, g, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, nullptr, 0, st);
         if (rc) return rc;
         ++nl;
       }
@@ -576,23 +635,9 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int p
         CK(cudaEventRecord(h->ev_join[a], h->aux[a]));
         CK(cudaStreamWaitEvent(s, h->ev_join[a], 0));
       }
+      if (chk_now && conc) CK(cudaStreamWaitEvent(s, h->ev_chk, 0));
       if (h->timing) CK(cudaEventRecordWithFlags(pool_event(h, ev + 1), s, cudaEventRecordExternal));
-      if (check) {
-        FlagArgs f{};
-        f.vflag_cur = vcur;
-        f.vflag_next = h->vflag.as<int>() + (p ^ 1) * VFLAG_SLOTS * nib;
-        f.stride = static_cast<long long>(nib);
-        f.sflag = h->sflag.as<signed char>();
-        f.solved = h->solved.as<int>();
-        f.n_inst = h->n_inst;
-        f.B = h->B;
-        f.b0 = b0;
-        f.nb = nb;
-        launch_fold_flags(f, s);
-        CKL();
-        ++nl;
-      }
-      int rc = launch_csr(h, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, eta, nullptr, 0, check, s);
+      int rc = launch_csr(h, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, eta, nullptr, 0, check, p, s);
       if (rc) return rc;
       ++nl;
       if (h->timing) {
@@ -762,7 +807,6 @@ static int autotune(afs_handle* h, cudaStream_t s) {
   default_tiles(bestc);
   // 2. tile shape per short bucket at that chunk: single FE launches timed
   const int nb = std::min(h->Bc, h->B);
-  int* vcheck = h->vflag.as<int>();
   for (Group& g : h->groups) {
     if (g.is_long) continue;
     double bt = 1e30;
@@ -775,7 +819,7 @@ static int autotune(afs_handle* h, cudaStream_t s) {
         double t = 1e30;
         for (int rep = 0; rep < 3; ++rep) {
           CK(cudaEventRecord(e0, s));
-          rc = launch_fe_group(h, g, h->x.p, h->xt, h->pitch, 0, nb, h->go.as<float>(), h->Bc, nullptr, 0, vcheck, s);
+          rc = launch_fe_group(h, g, h->x.p, h->xt, h->pitch, 0, nb, h->go.as<float>(), h->Bc, nullptr, 0, s);
           if (rc) return rc;
           CK(cudaEventRecord(e1, s));
           t = std::min(t, time_ms(s, e0, e1));
@@ -838,6 +882,13 @@ int afs::graph_view(const afs_handle* h, GraphView* out) {
 
 void* afs::handle_ext(const afs_handle* h) { return h ? h->ext : nullptr; }
 
+int afs::state_written(afs_handle* h, cudaStream_t s) {
+  if (!h || h->B <= 0) return fail(AFS_E_STATE, "no restart state");
+  launch_pack_signs(h->x.p, h->xt, h->pitch, h->n, h->B, h->sgn.as<unsigned>(), h->W, s);
+  CKL();
+  return AFS_OK;
+}
+
 void afs::set_handle_ext(afs_handle* h, void* p, void (*release)(void*)) {
   if (h->ext && h->ext_release) h->ext_release(h->ext);
   h->ext = p;
@@ -858,11 +909,11 @@ int afs::eval_into_scratch(afs_handle* h, const float* x, int B, float* fe, floa
   for (int b0 = 0; b0 < B; b0 += static_cast<int>(cols)) {
     const int nb = std::min(static_cast<int>(cols), B - b0);
     for (const Group& g : h->groups) {
-      int rc = launch_fe_group(h, g, x, XT_F32, B, b0, nb, scratch, cols, fe, B, nullptr, s);
+      int rc = launch_fe_group(h, g, x, XT_F32, B, b0, nb, scratch, cols, fe, B, s);
       if (rc) return rc;
     }
     if (grad) {
-      int rc = launch_csr(h, nullptr, XT_F32, B, b0, nb, scratch, cols, 0.0f, grad, B, false, s);
+      int rc = launch_csr(h, nullptr, XT_F32, B, b0, nb, scratch, cols, 0.0f, grad, B, false, -1, s);
       if (rc) return rc;
     }
   }
@@ -913,14 +964,15 @@ int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_d
   CK(cudaMemsetAsync(h->x.p, 0, h->x.bytes, s));
   const size_t nib = static_cast<size_t>(h->n_inst) * B;
   if ((rc = h->unsat.alloc(sizeof(int) * nib))) return rc;
-  if ((rc = h->vflag.alloc(2 * VFLAG_SLOTS * sizeof(int) * nib))) return rc;
-  if ((rc = h->sflag.alloc(nib))) return rc;
+  h->W = static_cast<int>(h->pitch / 32);
+  const size_t niw = static_cast<size_t>(h->n_inst) * h->W;
+  if ((rc = h->sgn.alloc(sizeof(unsigned) * static_cast<size_t>(h->n) * h->W))) return rc;
+  if ((rc = h->vword.alloc(2 * sizeof(unsigned) * niw))) return rc;
   if ((rc = h->solved.alloc(sizeof(int) * h->n_inst))) return rc;
   if ((rc = h->col.alloc(sizeof(int) * h->n_inst))) return rc;
   if ((rc = h->assign.alloc(static_cast<size_t>(h->n)))) return rc;
   CK(cudaMemsetAsync(h->unsat.p, 0, h->unsat.bytes, s));
-  CK(cudaMemsetAsync(h->vflag.p, 0, h->vflag.bytes, s));
-  CK(cudaMemsetAsync(h->sflag.p, 0, h->sflag.bytes, s));
+  CK(cudaMemsetAsync(h->vword.p, 0, h->vword.bytes, s));
   launch_fill_int(h->solved.as<int>(), INT_MAX, h->n_inst, s);
   CKL();
   h->parity = 0;
@@ -934,6 +986,7 @@ int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_d
     launch_init_philox(h->x.p, h->xt, h->pitch, h->n, B, h->var_inst.as<int>(), seed, s);
   }
   CKL();
+  if ((rc = afs::state_written(h, s))) return rc;
   if (h->p.chunk > 0) {
     h->Bc = std::min<int>(((h->p.chunk + 31) / 32) * 32, static_cast<int>(h->pitch));
   } else {
@@ -954,8 +1007,10 @@ int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_d
   }
   // the autotuner's steps leave x unchanged but touch the check buffers and flags
   CK(cudaMemsetAsync(h->unsat.p, 0, h->unsat.bytes, s));
-  CK(cudaMemsetAsync(h->vflag.p, 0, h->vflag.bytes, s));
-  CK(cudaMemsetAsync(h->sflag.p, 0, h->sflag.bytes, s));
+  CK(cudaMemsetAsync(h->vword.p, 0, h->vword.bytes, s));
+  h->parity = 0;
+  h->step_check_valid = false;
+  // (the autotuner's eta = 0 steps rewrote the sign words of the unchanged state)
   launch_fill_int(h->solved.as<int>(), INT_MAX, h->n_inst, s);
   CKL();
   return AFS_OK;
@@ -970,6 +1025,7 @@ int afs_step(afs_handle* h, int32_t nsteps, void* stream) {
   const bool check = h->p.verify_every != 0;
   const int p0 = h->parity;
   h->parity = (h->parity + nsteps) & 1;
+  h->step_check_valid = check;
   if (!h->p.use_graph) {
     int rc = enqueue_steps(h, nsteps, h->p.eta, check, p0, s, &h->last_launches);
     if (rc) return rc;
@@ -1092,7 +1148,7 @@ int afs_set_x(afs_handle* h, const float* x_dev, void* stream) {
   if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
   launch_convert_in(x_dev, XT_F32, h->B, h->x.p, h->xt, h->pitch, h->n, h->B, static_cast<cudaStream_t>(stream));
   CKL();
-  return AFS_OK;
+  return afs::state_written(h, static_cast<cudaStream_t>(stream));
 }
 
 int afs_get_verify(afs_handle* h, int32_t* unsat_dev, int32_t* solved_dev, void* stream) {
@@ -1103,6 +1159,19 @@ int afs_get_verify(afs_handle* h, int32_t* unsat_dev, int32_t* solved_dev, void*
     CK(cudaMemcpyAsync(unsat_dev, h->unsat.p, sizeof(int) * static_cast<size_t>(h->n_inst) * h->B,
                        cudaMemcpyDeviceToDevice, s));
   if (solved_dev) CK(cudaMemcpyAsync(solved_dev, h->solved.p, sizeof(int) * h->n_inst, cudaMemcpyDeviceToDevice, s));
+  return AFS_OK;
+}
+
+int afs_get_step_check(const afs_handle* h, uint32_t* out_dev, int32_t* words_per_inst, void* stream) {
+  if (!h) return fail(AFS_E_ARG, "NULL handle");
+  if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
+  if (words_per_inst) *words_per_inst = h->W;
+  if (!out_dev) return AFS_OK;
+  if (!h->step_check_valid) return fail(AFS_E_STATE, "the last afs_step ran no exact check");
+  const size_t niw = static_cast<size_t>(h->n_inst) * h->W;
+  launch_solved_words(h->vword.as<unsigned>() + (h->parity ^ 1) * niw, h->n_inst, h->W, h->B, static_cast<unsigned*>(out_dev),
+                      static_cast<cudaStream_t>(stream));
+  CKL();
   return AFS_OK;
 }
 
@@ -1122,11 +1191,11 @@ int afs_eval_fe_grad(afs_handle* h, const void* x_dev, int32_t x_dtype, int32_t 
   for (int b0 = 0; b0 < B; b0 += cols) {
     const int nb = std::min(cols, B - b0);
     for (const Group& g : h->groups) {
-      int rc = launch_fe_group(h, g, x_dev, xt, B, b0, nb, h->eval_go.as<float>(), cols, fe_dev, B, nullptr, s);
+      int rc = launch_fe_group(h, g, x_dev, xt, B, b0, nb, h->eval_go.as<float>(), cols, fe_dev, B, s);
       if (rc) return rc;
     }
     if (grad_dev) {
-      int rc = launch_csr(h, nullptr, xt, B, b0, nb, h->eval_go.as<float>(), cols, 0.0f, grad_dev, B, false, s);
+      int rc = launch_csr(h, nullptr, xt, B, b0, nb, h->eval_go.as<float>(), cols, 0.0f, grad_dev, B, false, -1, s);
       if (rc) return rc;
     }
   }
@@ -1145,6 +1214,7 @@ int afs_step_host(afs_handle* h, const float* x_host, float* x_out_host, int32_t
   CK(cudaMemcpyAsync(h->stage.p, x_host, nb, cudaMemcpyHostToDevice, s));
   launch_convert_in(h->stage.p, XT_F32, h->B, h->x.p, h->xt, h->pitch, h->n, h->B, s);
   CKL();
+  if (int rc0 = afs::state_written(h, s)) return rc0;
   const int ve = h->p.verify_every;
   if (ve == 0) h->p.verify_every = 1;
   int rc = afs_step(h, 1, stream);

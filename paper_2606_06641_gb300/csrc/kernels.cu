@@ -3,6 +3,7 @@
 // counter-based initialisation and small data-movement helpers.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdlib>
 
@@ -145,7 +146,6 @@ struct LongLayout {
     b += 2 * static_cast<size_t>(LONG_RT) * kpad * 4;         // literal values, gradient accumulators
     b += static_cast<size_t>(LONG_RT) * nseg_max * 32 * 8;    // prefix checkpoints
     if (esp) b += static_cast<size_t>(LONG_RT) * nseg_max * 32 * 4;
-    b += static_cast<size_t>(LONG_RT) * kpad;                 // literal truth bytes
     return b;
   }
 };
@@ -172,7 +172,6 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
   float* gs = ell + LONG_RT * L.kpad;
   float2* ck = reinterpret_cast<float2*>(gs + LONG_RT * L.kpad);
   int* cke = reinterpret_cast<int*>(ck + LONG_RT * L.nseg_max * 32);
-  unsigned char* tru = reinterpret_cast<unsigned char*>(cke + (ESP ? LONG_RT * L.nseg_max * 32 : 0));
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const unsigned tab_bytes = static_cast<unsigned>(1 + 2 * nroots) * 16u;
@@ -195,8 +194,7 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
     return;
   }
 
-  // stage u[r][i] = 1 - s_i x[v_i][b] and the literal's truth at the rounded
-  // point: 8 consecutive threads read one 32-byte row
+  // stage u[r][i] = 1 - s_i x[v_i][b]: 8 consecutive threads read one 32-byte row
   const XT* x = static_cast<const XT*>(a.x);
   const int bt = tile * LONG_RT;
   for (int idx = tid; idx < k * LONG_RT; idx += blockDim.x) {
@@ -205,9 +203,7 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
     const int bl = bt + r;
     const float xv =
         bl < a.nb ? load_x<XT>(x + static_cast<long long>(li.x >> 1) * a.x_pitch + a.b0 + bl) : 0.0f;
-    const float l = (li.x & 1) ? -xv : xv;
-    ell[r * L.kpad + i] = 1.0f - l;
-    tru[r * L.kpad + i] = static_cast<unsigned char>(lit_true(l, li.x & 1));
+    ell[r * L.kpad + i] = 1.0f - ((li.x & 1) ? -xv : xv);
   }
   __syncthreads();
 
@@ -217,18 +213,6 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
   int* myce = cke + static_cast<size_t>(w) * L.nseg_max * 32;
   const int nseg = (k + 31) >> 5;
   float fe_part = 0.0f;
-
-  // exact check of the state read (Algorithm 1's unsat count): warp w, restart bt + w
-  if (a.vflag != nullptr) {
-    int t = 0;
-    const unsigned char* tr = tru + w * L.kpad;
-    for (int i = lane; i < k; i += 32) t += tr[i];
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0 && bt + w < a.nb && __ldg(a.viol + __ldg(a.cons_voff + cb) + t))
-      a.vflag[static_cast<long long>(blockIdx.x % VFLAG_SLOTS) * a.vflag_stride +
-              static_cast<long long>(__ldg(a.cons_inst + cb)) * a.B + a.b0 + bt + w] = 1;
-  }
 
   for (int rg = 0; rg < nroots; rg += 32) {
     const int j = rg + lane;
@@ -376,6 +360,33 @@ __device__ __forceinline__ float load_x_rw<__nv_bfloat16>(const __nv_bfloat16* p
   return __bfloat162float(*p);
 }
 
+// The value a state entry holds once stored (BF16 storage rounds).
+template <typename XT>
+__device__ __forceinline__ float stored_value(float v);
+template <>
+__device__ __forceinline__ float stored_value<float>(float v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ float stored_value<__nv_bfloat16>(float v) {
+  return __bfloat162float(__float2bfloat16_rn(v));
+}
+
+// Bookkeeping of the step's check, done once per (instance, word) by the
+// warps of the instance's first variable: record the lowest solved restart
+// and clear the word the next step's check will OR into.
+__device__ __forceinline__ void csr_first_var_duty(const CsrArgs& a, int inst, int word, long long wi) {
+  if (a.vcur != nullptr) {
+    const int valid = min(32, a.B - word * 32);
+    const unsigned ok = ~a.vcur[wi] & (valid >= 32 ? ~0u : ((1u << valid) - 1u));
+    if (ok) atomicMin(a.solved + inst, word * 32 + __ffs(static_cast<int>(ok)) - 1);
+  }
+  if (a.vnext != nullptr) a.vnext[wi] = 0u;
+}
+
+// One lane per restart. Evaluation mode (grad != nullptr) writes the summed
+// gradient; step mode moves the unsolved restarts and, with sgn, writes the
+// sign word of the warp's 32 restarts (the chunk start is a multiple of 32).
 template <typename XT>
 __global__ void __launch_bounds__(256) csr_update_kernel(CsrArgs a) {
   pdl_wait();
@@ -384,109 +395,170 @@ __global__ void __launch_bounds__(256) csr_update_kernel(CsrArgs a) {
   const long long warp = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int tiles = (a.nb + 31) >> 5;
   const long long vl = warp / tiles;
-  if (vl >= a.v_count) return;
+  if (vl >= a.v_count) return;  // uniform per warp
   const int tile = static_cast<int>(warp - vl * tiles);
   const int bl = tile * 32 + lane;
-  if (bl >= a.nb) return;
+  const bool act = bl < a.nb;
   const int v = a.v_begin + static_cast<int>(vl);
   const int s0 = __ldg(a.csr_off + v), s1 = __ldg(a.csr_off + v + 1);
   // eight independent loads in flight per lane; the summation order is fixed
   // by the slot order, so the result does not depend on timing
-  const float* col = a.go + bl;
+  const float* col = a.go + (act ? bl : 0);
   float acc[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u) acc[u] = 0.f;
   int s = s0;
   for (; s + 7 < s1; s += 8) {
-    float v[8];
+    float t[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = __ldg(col + static_cast<long long>(s + u) * a.go_pitch);
+    for (int u = 0; u < 8; ++u) t[u] = __ldg(col + static_cast<long long>(s + u) * a.go_pitch);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] += v[u];
+    for (int u = 0; u < 8; ++u) acc[u] += t[u];
   }
   {
-    float v[8];
+    float t[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = s + u < s1 ? __ldg(col + static_cast<long long>(s + u) * a.go_pitch) : 0.f;
+    for (int u = 0; u < 8; ++u) t[u] = s + u < s1 ? __ldg(col + static_cast<long long>(s + u) * a.go_pitch) : 0.f;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] += v[u];
+    for (int u = 0; u < 8; ++u) acc[u] += t[u];
   }
   const float g = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
   if (a.grad != nullptr) {
-    a.grad[static_cast<long long>(v) * a.grad_pitch + a.b0 + bl] = g;
+    if (act) a.grad[static_cast<long long>(v) * a.grad_pitch + a.b0 + bl] = g;
     return;
   }
-  if (a.sflag != nullptr && a.sflag[static_cast<long long>(__ldg(a.var_inst + v)) * a.B + a.b0 + bl] != 0) return;
+  const int inst = __ldg(a.var_inst + v);
+  const int word = (a.b0 + tile * 32) >> 5;
+  const long long wi = static_cast<long long>(inst) * a.W + word;
+  const unsigned viol = a.vcur != nullptr ? a.vcur[wi] : ~0u;
+  const bool solved = !((viol >> lane) & 1u);
+  if (lane == 0 && v == __ldg(a.var_inst + a.n_vars + inst)) csr_first_var_duty(a, inst, word, wi);
   XT* xp = static_cast<XT*>(a.x) + static_cast<long long>(v) * a.x_pitch + a.b0 + bl;
-  const float xn = fminf(fmaxf(fmaf(-a.eta, g, load_x_rw<XT>(xp)), -1.0f), 1.0f);
-  store_x<XT>(xp, xn);
+  float xs = 0.0f;
+  if (act) {
+    xs = load_x_rw<XT>(xp);
+    if (!solved) {
+      const float xn = fminf(fmaxf(fmaf(-a.eta, g, xs), -1.0f), 1.0f);
+      store_x<XT>(xp, xn);
+      xs = stored_value<XT>(xn);
+    }
+  }
+  const unsigned bits = __ballot_sync(0xffffffffu, act && xs < 0.0f);
+  if (a.sgn != nullptr && lane == 0) a.sgn[static_cast<long long>(v) * a.W + word] = bits;
 }
 
 // Step-path variant: each lane owns 4 consecutive restarts, so a warp reads
-// 512 contiguous bytes of every occurrence row (16-byte vector loads) and
-// updates 4 states. Needs the state's row pitch and the chunk start to be
-// multiples of 4 and the buffers 16-byte aligned (true for the library's own
-// state and occurrence buffers); lanes past nb are masked per element.
+// 512 contiguous bytes of every occurrence row (16-byte vector loads), eight
+// rows in flight, and updates 4 states. The state and the solved word are
+// read before the gather so their latency overlaps it; 8 lanes together
+// write one sign word. The grid is persistent (one wave of resident blocks)
+// and warps stride over the (variable, 128-restart tile) tasks, so no partial
+// last wave idles the machine. Needs the state's row pitch and the chunk
+// start to be multiples of 32 and the buffers 16-byte aligned (true for the
+// library's own state and occurrence buffers); lanes past nb are masked.
 template <typename XT>
-__global__ void __launch_bounds__(256) csr_update_vec4_kernel(CsrArgs a) {
-  pdl_wait();
-  pdl_trigger();
-  const int lane = threadIdx.x & 31;
-  const long long warp = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int tiles = (a.nb + 127) >> 7;
-  const long long vl = warp / tiles;
-  if (vl >= a.v_count) return;
-  const int tile = static_cast<int>(warp - vl * tiles);
+__device__ __forceinline__ void csr_vec4_task(const CsrArgs& a, int vl, int tile, int lane) {
   const int bl = tile * 128 + lane * 4;
-  if (bl >= a.nb) return;
-  const int v = a.v_begin + static_cast<int>(vl);
+  const bool act = bl < a.nb;
+  const int v = a.v_begin + vl;
   const int s0 = __ldg(a.csr_off + v), s1 = __ldg(a.csr_off + v + 1);
-  const float* col = a.go + bl;
+  const int inst = __ldg(a.var_inst + v);
+  const int word = (a.b0 + bl) >> 5;
+  const long long wi = static_cast<long long>(inst) * a.W + word;
+  unsigned sw = 0u;  // solved bits of this lane's restarts
+  if (act && a.vcur != nullptr) sw = ~(a.vcur[wi] >> (bl & 31));
+  XT* xp = static_cast<XT*>(a.x) + static_cast<long long>(v) * a.x_pitch + a.b0 + bl;
+  float xo[4] = {0.f, 0.f, 0.f, 0.f};
+  if (act) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) xo[e] = load_x_rw<XT>(xp + e);
+  }
+  const float* col = a.go + (act ? bl : 0);
   float4 acc[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-  int s = s0;
-  for (; s + 3 < s1; s += 4) {
-    float4 t[4];
+  for (int s = s0; s < s1; s += 8) {
+    float4 t[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) t[u] = __ldg(reinterpret_cast<const float4*>(col + static_cast<long long>(s + u) * a.go_pitch));
+    for (int u = 0; u < 8; ++u)
+      t[u] = s + u < s1 ? __ldg(reinterpret_cast<const float4*>(col + static_cast<long long>(s + u) * a.go_pitch))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      acc[u].x += t[u].x;
-      acc[u].y += t[u].y;
-      acc[u].z += t[u].z;
-      acc[u].w += t[u].w;
+    for (int u = 0; u < 8; ++u) {
+      acc[u & 3].x += t[u].x;
+      acc[u & 3].y += t[u].y;
+      acc[u & 3].z += t[u].z;
+      acc[u & 3].w += t[u].w;
     }
-  }
-  for (; s < s1; ++s) {
-    const float4 t = __ldg(reinterpret_cast<const float4*>(col + static_cast<long long>(s) * a.go_pitch));
-    acc[0].x += t.x;
-    acc[0].y += t.y;
-    acc[0].z += t.z;
-    acc[0].w += t.w;
   }
   const float g[4] = {(acc[0].x + acc[1].x) + (acc[2].x + acc[3].x), (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y),
                       (acc[0].z + acc[1].z) + (acc[2].z + acc[3].z), (acc[0].w + acc[1].w) + (acc[2].w + acc[3].w)};
-  const int inst = __ldg(a.var_inst + v);
-  XT* xp = static_cast<XT*>(a.x) + static_cast<long long>(v) * a.x_pitch + a.b0 + bl;
+  unsigned nib = 0u;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    if (bl + e >= a.nb) break;
-    if (a.sflag != nullptr && a.sflag[static_cast<long long>(inst) * a.B + a.b0 + bl + e] != 0) continue;
-    const float xn = fminf(fmaxf(fmaf(-a.eta, g[e], load_x_rw<XT>(xp + e)), -1.0f), 1.0f);
-    store_x<XT>(xp + e, xn);
+    if (!act || bl + e >= a.nb) continue;
+    float xs = xo[e];
+    if (!((sw >> e) & 1u)) {
+      const float xn = fminf(fmaxf(fmaf(-a.eta, g[e], xo[e]), -1.0f), 1.0f);
+      store_x<XT>(xp + e, xn);
+      xs = stored_value<XT>(xn);
+    }
+    nib |= static_cast<unsigned>(xs < 0.0f) << e;
+  }
+  // 8 lanes x 4 restarts = one word
+  unsigned wv = nib << ((lane & 7) * 4);
+  wv |= __shfl_xor_sync(0xffffffffu, wv, 1);
+  wv |= __shfl_xor_sync(0xffffffffu, wv, 2);
+  wv |= __shfl_xor_sync(0xffffffffu, wv, 4);
+  if ((lane & 7) == 0 && act) {
+    if (a.sgn != nullptr) a.sgn[static_cast<long long>(v) * a.W + word] = wv;
+    if (v == __ldg(a.var_inst + a.n_vars + inst)) csr_first_var_duty(a, inst, word, wi);
   }
 }
 
+template <typename XT>
+__global__ void __launch_bounds__(256, 5) csr_update_vec4_kernel(CsrArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  const int lane = threadIdx.x & 31;
+  const unsigned tiles = static_cast<unsigned>((a.nb + 127) >> 7);
+  const unsigned ntask = tiles * static_cast<unsigned>(a.v_count);  // < 2^32 (checked at launch)
+  const unsigned stride = gridDim.x * (blockDim.x >> 5);
+  for (unsigned task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < ntask; task += stride) {
+    const unsigned vl = task / tiles;  // uniform per warp
+    csr_vec4_task<XT>(a, static_cast<int>(vl), static_cast<int>(task - vl * tiles), lane);
+  }
+}
+
+// Resident blocks of a kernel on the whole device (cached per kernel).
+template <typename K>
+static long long resident_blocks(K kernel, int threads) {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0, sms = 1, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0) != cudaSuccess || per < 1) per = 1;
+    cached = sms * per;
+  }
+  return cached;
+}
+
 void launch_csr_update(const CsrArgs& a, int xt, cudaStream_t s) {
-  const bool vec = a.grad == nullptr && (a.go_pitch % 4) == 0 && (a.x_pitch % 4) == 0 && (a.b0 % 4) == 0 &&
+  const bool vec = a.grad == nullptr && (a.go_pitch % 32) == 0 && (a.x_pitch % 32) == 0 && (a.b0 % 32) == 0 &&
                    (reinterpret_cast<uintptr_t>(a.go) % 16) == 0;
-  if (vec) {
+  const long long tasks128 = static_cast<long long>((a.nb + 127) / 128) * a.v_count;
+  if (vec && tasks128 < (1ll << 32) - 4096LL * 1024) {
     const long long tiles = (a.nb + 127) / 128;
-    const long long blocks = (tiles * a.v_count + 7) / 8;
+    long long blocks = (tiles * a.v_count + 7) / 8;
     if (blocks == 0) return;
-    if (xt == XT_F32) launch_pdl(csr_update_vec4_kernel<float>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
-    else launch_pdl(csr_update_vec4_kernel<__nv_bfloat16>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+    if (xt == XT_F32) {
+      blocks = std::min(blocks, resident_blocks(csr_update_vec4_kernel<float>, 256));
+      launch_pdl(csr_update_vec4_kernel<float>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+    } else {
+      blocks = std::min(blocks, resident_blocks(csr_update_vec4_kernel<__nv_bfloat16>, 256));
+      launch_pdl(csr_update_vec4_kernel<__nv_bfloat16>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+    }
     return;
   }
   const long long tiles = (a.nb + 31) / 32;
@@ -495,6 +567,191 @@ void launch_csr_update(const CsrArgs& a, int xt, cudaStream_t s) {
   if (blocks == 0) return;
   if (xt == XT_F32) launch_pdl(csr_update_kernel<float>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
   else launch_pdl(csr_update_kernel<__nv_bfloat16>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+}
+
+// Sign words of a state written outside the step (initialisation, set_x):
+// one warp per (variable, word).
+template <typename XT>
+__global__ void pack_signs_kernel(const XT* x, long long pitch, int n, int B, unsigned* sgn, int W) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (warp >= static_cast<long long>(n) * W) return;  // uniform per warp
+  const int v = static_cast<int>(warp / W);
+  const int w = static_cast<int>(warp - static_cast<long long>(v) * W);
+  const int b = w * 32 + lane;
+  const bool neg = b < B && load_x<XT>(x + static_cast<long long>(v) * pitch + b) < 0.0f;
+  const unsigned bits = __ballot_sync(0xffffffffu, neg);
+  if (lane == 0) sgn[warp] = bits;
+}
+
+void launch_pack_signs(const void* x, int xt, long long x_pitch, int n, int B, unsigned* sgn, int W,
+                       cudaStream_t s) {
+  const long long warps = static_cast<long long>(n) * W;
+  if (warps == 0) return;
+  const unsigned blocks = static_cast<unsigned>((warps + 7) / 8);
+  if (xt == XT_F32) pack_signs_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(x), x_pitch, n, B, sgn, W);
+  else
+    pack_signs_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(x), x_pitch, n, B, sgn,
+                                                            W);
+}
+
+// ---------------------------------------------------------------------------
+// Bit-sliced exact check (Algorithm 1's is_sat on the sign-rounded state).
+// A thread holds 32 restarts in one word per literal: literal i is true in
+// the restarts of S_{v_i} xor (negated ? ~0 : 0), where S_v is the sign word
+// of its variable. The true count t of each restart is kept as bit planes
+// P_0..P_{np-1} (bit j of P_p is bit p of restart j's count); adding a
+// literal word is a ripple of AND/XOR through the planes. For k <= 62 the
+// violated set {t : f(t) = +1} (or its complement, when that is smaller) is
+// enumerated from a 64-bit mask and each value u becomes an equality word
+// AND_p (u_p ? P_p : ~P_p); longer constraints unpack t per restart and read
+// the violation table.
+// ---------------------------------------------------------------------------
+constexpr int CHECK_PLANES = 11;  // counts up to 2047 >= the longest constraint
+constexpr int CHECK_STAGE = 32;   // literal words a warp stages at a time
+constexpr int CHECK_WARPS = 4;
+
+template <int MAXP>
+__device__ __forceinline__ void add_words(unsigned (&P)[CHECK_PLANES], const unsigned* sw, int n, int np) {
+  for (int i = 0; i < n; ++i) {
+    unsigned carry = sw[i * 32];
+#pragma unroll
+    for (int p = 0; p < MAXP; ++p) {
+      if (p < np) {
+        const unsigned t = P[p] & carry;
+        P[p] ^= carry;
+        carry = t;
+      }
+    }
+  }
+}
+
+// Violation word of one constraint from its count planes.
+__device__ __forceinline__ unsigned violated_word(const unsigned (&P)[CHECK_PLANES], int k, int np,
+                                                  unsigned long long em, const unsigned char* vt) {
+  if (k <= 62) {
+    unsigned long long m = em & ~(1ull << 63);
+    unsigned hit = 0u;
+    while (m) {
+      const int u = __ffsll(static_cast<long long>(m)) - 1;
+      m &= m - 1;
+      unsigned e = ~0u;
+#pragma unroll
+      for (int p = 0; p < 6; ++p)
+        if (p < np) e &= ((u >> p) & 1) ? P[p] : ~P[p];
+      hit |= e;
+    }
+    return (em >> 63) ? ~hit : hit;
+  }
+  unsigned bad = 0u;
+  for (int j = 0; j < 32; ++j) {
+    int t = 0;
+#pragma unroll
+    for (int p = 0; p < CHECK_PLANES; ++p)
+      if (p < np) t |= static_cast<int>((P[p] >> j) & 1u) << p;
+    bad |= static_cast<unsigned>(__ldg(vt + t)) << j;
+  }
+  return bad;
+}
+
+// Gather the literal words of literals [base, base + cnt) (cnt <= 32) into
+// the warp's stage, all loads in flight at once: lane j of row i holds the
+// truth of literal base + i in restarts 32w + (0..31).
+__device__ __forceinline__ void check_stage(const CheckArgs& a, const unsigned* sg, unsigned* st, int base, int cnt,
+                                            int lane) {
+  const int e = lane < cnt ? __ldg(a.lit_enc + base + lane) : 0;
+  unsigned wv[CHECK_STAGE];
+#pragma unroll
+  for (int j = 0; j < CHECK_STAGE; ++j) {
+    const int enc = __shfl_sync(0xffffffffu, e, j);
+    wv[j] = j < cnt ? __ldg(sg + static_cast<long long>(enc >> 1) * a.W) ^ (0u - static_cast<unsigned>(enc & 1)) : 0u;
+  }
+#pragma unroll
+  for (int j = 0; j < CHECK_STAGE; ++j) st[j * 32] = wv[j];
+  __syncwarp();
+}
+
+// A warp handles one range (<= 32 literals, or one longer constraint) for 32
+// words: lane j owns word w0 + 32*blockIdx.y + j. The range's literal words
+// are staged in shared memory, then the constraints are counted from there;
+// the warps of a block OR their results per instance before the atomic.
+__global__ void __launch_bounds__(CHECK_WARPS * 32) check_bits_kernel(CheckArgs a) {
+  __shared__ unsigned stage[CHECK_WARPS][CHECK_STAGE][32];
+  __shared__ unsigned bad_s[CHECK_WARPS][32];
+  __shared__ int inst_s[CHECK_WARPS];
+  pdl_wait();
+  pdl_trigger();
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int rgi = blockIdx.x * CHECK_WARPS + wp;
+  const int wl = blockIdx.y * 32 + lane;
+  const bool act = wl < a.wc;
+  const int w = a.w0 + (act ? wl : 0);
+  unsigned bad = 0u;
+  int inst = -1;
+  if (rgi < a.n_ranges) {  // uniform per warp
+    const int4 rg = __ldg(a.ranges + rgi);
+    inst = rg.z;
+    const int nc = rg.y - rg.x;
+    // constraint offsets and test masks of the range, one per lane (nc < 32)
+    const int offv = __ldg(a.lit_off + rg.x + min(lane, nc));
+    const unsigned long long emv = lane < nc ? __ldg(a.em + rg.x + lane) : 0ull;
+    const int l0 = __shfl_sync(0xffffffffu, offv, 0);
+    const int l1 = __shfl_sync(0xffffffffu, offv, nc);
+    const unsigned* sg = a.sgn + w;
+    unsigned* st = &stage[wp][0][lane];
+    unsigned P[CHECK_PLANES];
+    if (l1 - l0 <= CHECK_STAGE) {
+      check_stage(a, sg, st, l0, l1 - l0, lane);
+      for (int c = 0; c < nc; ++c) {
+        const int a0 = __shfl_sync(0xffffffffu, offv, c) - l0;
+        const int a1 = __shfl_sync(0xffffffffu, offv, c + 1) - l0;
+        const unsigned long long em = __shfl_sync(0xffffffffu, emv, c);
+        const int k = a1 - a0;
+        const int np = 32 - __clz(k);
+#pragma unroll
+        for (int p = 0; p < CHECK_PLANES; ++p) P[p] = 0u;
+        add_words<6>(P, st + a0 * 32, k, np);  // k <= 32 here
+        bad |= violated_word(P, k, np, em, nullptr);
+      }
+    } else {  // one long constraint, staged 32 literals at a time
+      const int k = l1 - l0;
+      const int np = 32 - __clz(k);
+#pragma unroll
+      for (int p = 0; p < CHECK_PLANES; ++p) P[p] = 0u;
+      for (int b = 0; b < k; b += CHECK_STAGE) {
+        const int cnt = min(CHECK_STAGE, k - b);
+        check_stage(a, sg, st, l0 + b, cnt, lane);
+        add_words<CHECK_PLANES>(P, st, cnt, np);
+        __syncwarp();
+      }
+      bad = violated_word(P, k, np, __shfl_sync(0xffffffffu, emv, 0), a.viol + __ldg(a.viol_off + rg.x));
+    }
+  }
+  bad_s[wp][lane] = act ? bad : 0u;
+  if (lane == 0) inst_s[wp] = inst;
+  __syncthreads();
+  if (wp == 0 && act) {
+    unsigned acc = 0u;
+    int cur = -1;
+    for (int j = 0; j < CHECK_WARPS; ++j) {
+      const int ij = inst_s[j];
+      if (ij < 0) continue;
+      if (ij != cur) {
+        if (cur >= 0 && acc) atomicOr(a.vword + static_cast<long long>(cur) * a.W + w, acc);
+        cur = ij;
+        acc = 0u;
+      }
+      acc |= bad_s[j][lane];
+    }
+    if (cur >= 0 && acc) atomicOr(a.vword + static_cast<long long>(cur) * a.W + w, acc);
+  }
+}
+
+void launch_check_bits(const CheckArgs& a, cudaStream_t s) {
+  if (a.n_ranges == 0 || a.wc == 0) return;
+  const dim3 grid(static_cast<unsigned>((a.n_ranges + CHECK_WARPS - 1) / CHECK_WARPS),
+                  static_cast<unsigned>((a.wc + 31) / 32));
+  launch_pdl(check_bits_kernel, grid, dim3(CHECK_WARPS * 32), 0, s, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -552,31 +809,18 @@ void launch_verify(const VerifyArgs& a, int xt, cudaStream_t s) {
   else launch_pdl(verify_kernel<__nv_bfloat16>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
 }
 
-// Fold of the fused check: restart (inst, b) is solved when no warp flagged a
-// violation in any row. Records the lowest solved restart per instance and
-// clears the rows the next step's check writes.
-__global__ void fold_flags_kernel(FlagArgs a) {
-  pdl_wait();
-  pdl_trigger();
+__global__ void solved_words_kernel(const unsigned* vword, int n_inst, int W, int B, unsigned* out) {
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= static_cast<long long>(a.n_inst) * a.nb) return;
-  const int inst = static_cast<int>(i / a.nb);
-  const int b = a.b0 + static_cast<int>(i - static_cast<long long>(inst) * a.nb);
-  const long long ui = static_cast<long long>(inst) * a.B + b;
-  int any = 0;
-#pragma unroll 8
-  for (int s = 0; s < VFLAG_SLOTS; ++s) {
-    any |= a.vflag_cur[s * a.stride + ui];
-    a.vflag_next[s * a.stride + ui] = 0;
-  }
-  a.sflag[ui] = any ? 0 : 1;
-  if (!any) atomicMin(a.solved + inst, b);
+  if (i >= static_cast<long long>(n_inst) * W) return;
+  const int w = static_cast<int>(i % W);
+  const int valid = min(32, B - w * 32);
+  out[i] = ~vword[i] & (valid >= 32 ? ~0u : (valid <= 0 ? 0u : ((1u << valid) - 1u)));
 }
 
-void launch_fold_flags(const FlagArgs& a, cudaStream_t s) {
-  const long long n = static_cast<long long>(a.n_inst) * a.nb;
+void launch_solved_words(const unsigned* vword, int n_inst, int W, int B, unsigned* out, cudaStream_t s) {
+  const long long n = static_cast<long long>(n_inst) * W;
   if (n == 0) return;
-  launch_pdl(fold_flags_kernel, dim3(static_cast<unsigned>((n + 255) / 256)), dim3(256), 0, s, a);
+  solved_words_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(vword, n_inst, W, B, out);
 }
 
 __global__ void fill_int_kernel(int* p, int v, long long n) {

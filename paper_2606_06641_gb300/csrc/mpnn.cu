@@ -698,7 +698,7 @@ int afs_mpnn_init_restarts(afs_mpnn* net, afs_handle* h, int32_t B, uint64_t see
                                                                gv.n, B, B_learn, sigma_min, sigma_max, seed);
   }
   MCKL();
-  return AFS_OK;
+  return afs::state_written(h, s);
 }
 
 }  // extern "C"
