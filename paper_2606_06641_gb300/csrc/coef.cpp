@@ -190,20 +190,28 @@ void build_table(const Shape& s, int basis, int form, std::vector<float>& out) {
   const int mid = N / 2;
   if (form == FORM_SHORT) {
     if (basis == BASIS_PGF) {
-      push4(out, cr[0], 0, 0, 0);
+      // head: {c0, number of scaled complex roots, 0, 0}
+      const bool scaled = k <= KSCALED_MAX;
+      push4(out, cr[0], scaled ? k / 2 : 0, 0, 0);
       if (odd) push4(out, 0.0, cr[mid], 0, 0);
       for (int j = 1; j <= k / 2; ++j) {
-        // a_j + b_j l = b_j (l + i*gamma_j), gamma_j = cot(pi j/N); E_j = 2 ft_j b_j^k
+        // a_j + b_j l = b_j (l + i*gamma_j), gamma_j = cot(pi j/N); E_j = 2 ft_j b_j^k.
+        // For k <= KSCALED_MAX the factor is stored scaled, b_j (l + i gamma)
+        // = b_j gamma (w + i) with w = l tan(pi j/N), so that a complex
+        // multiply by it is two FMAs: {tan, 0, E'_j} with E'_j = 2 ft_j
+        // (b_j gamma_j)^k, |b_j gamma_j| = cos(pi j/N). Products of the
+        // scaled factors stay below (1 + cot^2)^(k/2) <= 2^100 and each root's
+        // contribution keeps its true size (at most 2 |ft_j|).
         double c2, s2;
         unit_root(j, 2LL * N, c2, s2);             // angle pi j / N
-        const double gamma = c2 / s2;
         double pc, ps;
         unit_root(2LL * j * k - static_cast<long long>(k) * N, 4LL * N, pc, ps);  // arg b_j^k
-        const double mag = std::pow(s2, k);        // |b_j|^k = sin(pi j/N)^k
+        const double mag = std::pow(scaled ? c2 : s2, k);  // |b_j gamma_j|^k or |b_j|^k
         const double br = mag * pc, bi = mag * ps;
         const double er = 2.0 * (cr[j] * br - ci[j] * bi);
         const double ei = 2.0 * (cr[j] * bi + ci[j] * br);
-        push4(out, 0.0, gamma, er, ei);
+        if (scaled) push4(out, s2 / c2, 0.0, er, ei);
+        else push4(out, 0.0, c2 / s2, er, ei);
       }
     } else {
       push4(out, 0.0, 0, 0, 0);

@@ -11,6 +11,9 @@ enum { FORM_SHORT = 0, FORM_LONG = 1 };
 // Constraints with k <= KSHORT use the register (short) kernels and the
 // short table layout; longer ones use the shared-memory (long) kernel.
 constexpr int KSHORT = 32;
+// Short probability-generating tables store every complex root in the
+// scaled form gamma (w + i) up to this length (see build_table).
+constexpr int KSCALED_MAX = 24;
 
 struct Shape {
   int type, k, op, param, parity;

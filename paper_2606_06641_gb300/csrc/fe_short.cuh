@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 
 #include "afsat_internal.h"
+#include "coef.h"
 
 namespace afs {
 
@@ -85,6 +86,14 @@ __device__ __forceinline__ void store_fvec<4>(float* p, const float (&v)[4]) {
 // the state's row pitch, the chunk start and the derivative pitch to be
 // multiples of 32 (the library's own state and buffers); a vector that starts
 // below nb then stays inside the padded row, and values past nb are ignored.
+// a * b, computed again where the compiler would otherwise keep the first
+// product of the same operands live (k registers) across the forward pass
+__device__ __forceinline__ float mul_recompute(float a, float b) {
+  float r;
+  asm volatile("mul.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+
 template <int K, int RPL, typename XT, bool SHIFT, bool VEC>
 __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
   pdl_wait();
@@ -173,15 +182,57 @@ __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
       }
     }
 
-    // complex roots: factor (l + alpha) + i gamma; RPI roots per iteration
-    // are independent product chains interleaved for instruction-level
-    // parallelism (they share the literal values and the accumulators)
     constexpr int NC = K / 2;
+    // complex roots stored scaled (probability-generating basis, k up to
+    // KSCALED_MAX): factor gamma (w + i) with w = l / gamma, gamma^k folded into E', so
+    // a running product times the factor is two FMAs; the gradient products
+    // have k - 1 factors and start from E' / gamma
+    constexpr bool SCALED = !SHIFT && K <= KSCALED_MAX;
+    const int ns = SCALED ? NC : 0;
+#pragma unroll 1
+    for (int j = 0; j < ns; ++j) {
+      const float4 cc = __ldg(tab + 1 + NREAL + j);
+      const float ia = cc.x;  // 1 / gamma
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        float pr[K], pi[K];
+        float Pr = cc.z * ia, Pi = cc.w * ia;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          pr[i] = Pr;
+          pi[i] = Pi;
+          if (i + 1 < K) {
+            const float w = l[r][i] * ia;
+            const float nr = fmaf(Pr, w, -Pi);
+            const float ni = fmaf(Pi, w, Pr);
+            Pr = nr;
+            Pi = ni;
+          }
+        }
+        g[r][K - 1] += pr[K - 1];
+        float Sr = l[r][K - 1] * ia, Si = 1.0f;
+#pragma unroll
+        for (int i = K - 2; i >= 0; --i) {
+          g[r][i] = fmaf(pr[i], Sr, g[r][i]);
+          g[r][i] = fmaf(-pi[i], Si, g[r][i]);
+          const float w = K > 8 ? mul_recompute(l[r][i], ia) : l[r][i] * ia;
+          const float nr = fmaf(Sr, w, -Si);
+          const float ni = fmaf(Si, w, Sr);
+          Sr = nr;
+          Si = ni;
+        }
+        fe[r] = fmaf(cc.z, Sr, fmaf(-cc.w, Si, fe[r]));
+      }
+    }
+
+    // otherwise complex roots are factors (l + alpha) + i gamma; RPI roots per
+    // iteration are independent product chains interleaved for instruction-
+    // level parallelism (they share the literal values and the accumulators)
     // (two interleaved roots measured slower at k = 20: the register growth
     // costs more occupancy than the extra chains win back)
     constexpr int RPI = 1;
 #pragma unroll 1
-    for (int j = 0; j < NC; j += RPI) {
+    for (int j = ns; j < (SCALED ? 0 : NC); j += RPI) {
       float4 cc[RPI];
       bool on[RPI];
 #pragma unroll

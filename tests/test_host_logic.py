@@ -54,7 +54,16 @@ def _eval_short(tab, k, esp, ell):
         fe += E * f.prod(axis=1)
         for i in range(k):
             grad[:, i] += E * np.delete(f, i, axis=1).prod(axis=1)
+    n_scaled = 0 if esp else int(t[0, 1])
     for j in range(k // 2):
+        if j < n_scaled:  # factor (w + i), w = l / gamma, stored as 1/gamma
+            inv_gam, _, er, ei = t[1 + nreal + j]
+            E = er + 1j * ei
+            f = ell * inv_gam + 1j
+            fe += np.real(E * f.prod(axis=1))
+            for i in range(k):
+                grad[:, i] += np.real(E * inv_gam * np.delete(f, i, axis=1).prod(axis=1))
+            continue
         alpha, gam, er, ei = t[1 + nreal + j]
         E = er + 1j * ei
         f = ell + alpha + 1j * gam
@@ -87,7 +96,7 @@ def _shapes(k):
     return out
 
 
-@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 8, 13, 20, 32])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 8, 13, 20, 24, 25, 32])
 def test_short_pgf_table_reproduces_oracle(k):
     rng = np.random.default_rng(k)
     ell = np.concatenate([rng.uniform(-1, 1, (5, k)), np.sign(rng.uniform(-1, 1, (2, k)))])
@@ -155,13 +164,20 @@ def test_esp_coefficients_exact_at_large_k():
 
 
 def test_pgf_table_has_exact_conjugate_roots():
-    """Short-form gamma_j = cot(pi j/(k+1)) and the mirrored middle root of an
-    odd length has a purely real weight."""
-    for k in (5, 9, 31):
+    """Short-form roots: gamma_j = cot(pi j/(k+1)) (stored as tan for the scaled
+    form up to k = 24, as cot beyond), and the mirrored middle root of an odd
+    length has a purely real weight."""
+    for k in (5, 9, 23, 25, 31):
         t = bd.coef_table(O.T_CARD, k, O.OP_GE, k // 2).reshape(-1, 4)
-        gam = t[2:, 1]
-        want = 1.0 / np.tan(np.pi * np.arange(1, k // 2 + 1) / (k + 1))
-        np.testing.assert_allclose(gam, want.astype(np.float32), rtol=2e-7)
+        ang = np.pi * np.arange(1, k // 2 + 1) / (k + 1)
+        if k <= 24:
+            assert t[0, 1] == k // 2
+            np.testing.assert_allclose(t[2:, 0], np.tan(ang).astype(np.float32), rtol=2e-7)
+            assert np.all(t[2:, 1] == 0.0)
+        else:
+            assert t[0, 1] == 0
+            np.testing.assert_allclose(t[2:, 1], (1.0 / np.tan(ang)).astype(np.float32), rtol=2e-7)
+            assert np.all(t[2:, 0] == 0.0)
         assert t[1, 0] == 0.0 and t[1, 2] == 0.0 and t[1, 3] == 0.0
 
 
