@@ -54,7 +54,9 @@ WORKLOADS = {
 METRIC = "FE+grad literal-evals/s"
 UNIT = "literal-evals/s"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fe_grad_traffic.json")
-KERNEL_SOURCES = ["paper_2606_06641_gb300/csrc/fe_short.cuh", "paper_2606_06641_gb300/csrc/kernels.cu"]
+KERNEL_SOURCES = ["paper_2606_06641_gb300/csrc/fe_short.cuh", "paper_2606_06641_gb300/csrc/kernels.cu",
+                  "paper_2606_06641_gb300/csrc/coef.cpp", "paper_2606_06641_gb300/csrc/coef.h",
+                  "paper_2606_06641_gb300/csrc/afsat_internal.h"]
 
 
 def kernel_source_hash() -> str:
