@@ -149,11 +149,11 @@ def gpu_id_for(dev: int) -> str:
 def make_workload(name: str):
     from paper_2606_06641_gb300 import synth
     if name == "hybrid":
-        return [synth.config2(0)]
+        return [synth.hybrid_n2000(0)]
     if name == "long":
-        return [synth.config3(0)]
+        return [synth.long_card_n10000(0)]
     if name == "batch":
-        return synth.config4(256)
+        return synth.instance_batch(256)
     raise ValueError(name)
 
 
@@ -208,7 +208,7 @@ def run_reference(args):
 
 
 def measure_time_to_solve(n_inst: int, B: int, eta: float, max_steps: int, seed: int = 17):
-    """Plain CLS vs the batched form on config-1 style random 3-SAT instances,
+    """Plain CLS vs the batched form on random 3-SAT instances (n=50, m=213),
     both from the same Philox starting points."""
     import numpy as np
     import torch
@@ -216,7 +216,7 @@ def measure_time_to_solve(n_inst: int, B: int, eta: float, max_steps: int, seed:
     from paper_2606_06641_gb300 import binding as bd
     from paper_2606_06641_gb300 import solver
     from paper_2606_06641_gb300 import synth
-    insts = [synth.config5(i, "test") for i in range(n_inst)]
+    insts = [synth.learned_split(i, "test") for i in range(n_inst)]
     hb = bd.load_batch(insts, bd.default_params(eta=eta, autotune=0))
     bd.init_restarts(hb, B, seed=seed)
     x_all = bd.get_x(hb)
@@ -262,7 +262,7 @@ def tts_summary(forms):
 
 
 def run_learned(args):
-    """Config 5: train the message-passing initialiser on assignments the
+    """Learned initialiser: train the message-passing network on assignments the
     descent finds for training instances, then solve held-out instances from
     learned and from uniform starts (and with plain CLS) at equal step budget."""
     import numpy as np
@@ -274,7 +274,7 @@ def run_learned(args):
     _b.build()
     eta, steps = 0.1, 500
     t0 = time.perf_counter()
-    train = [synth.config5(i, "train") for i in range(args.learned_train)]
+    train = [synth.learned_split(i, "train") for i in range(args.learned_train)]
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
     labels = learned.harvest(train, 64, eta, steps, seed=1)
@@ -285,7 +285,7 @@ def run_learned(args):
     hist = learned.train(net, batches, args.learned_epochs, 3e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    test = [synth.config5(i, "test") for i in range(args.learned_test)]
+    test = [synth.learned_split(i, "test") for i in range(args.learned_test)]
     B = 256
     learned.evaluate(net, test[:4], B, eta, 5, seed=2)  # warm-up
     res_u = learned.evaluate(None, test, B, eta, steps, seed=3)
@@ -299,7 +299,7 @@ def run_learned(args):
     line = {
         "metric": "median time-to-solve at equal solve rate (learned vs uniform starts vs plain CLS)",
         "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
-        "config": {"workload": "config-1 distribution random 3-SAT n=50 m=213; "
+        "config": {"workload": "random 3-SAT n=50 m=213; "
                                f"{args.learned_train} training instances, {len(test)} held-out, B={B}, "
                                f"{steps} steps, eta={eta}", "network": "3 rounds, hidden 64, BF16 GEMMs"},
         "labels": {"labelled_instances": len(labels.insts), "mean_solutions": float(labels.n_solutions.mean())

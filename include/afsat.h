@@ -77,7 +77,7 @@ enum { AFS_BASIS_PGF = 0, AFS_BASIS_ESP = 1 };
 enum { AFS_X_F32 = 0, AFS_X_BF16 = 1 };
 
 typedef struct afs_params {
-  float eta;            /* fixed step size of Algorithm 1 (line 3)          */
+  float eta;            /* fixed step size of Algorithm 1's update          */
   int32_t basis;        /* AFS_BASIS_PGF (default, stable) or AFS_BASIS_ESP  */
   int32_t x_storage;    /* AFS_X_F32 or AFS_X_BF16 storage of the state x   */
   int32_t verify_every; /* 0 = no exact check inside afs_step; otherwise

@@ -12,10 +12,9 @@ Instance format (mirrors the hybrid DIMACS records of the paper's Appendix A):
   * ``lit_off``   CSR offsets, constraint c owns ``lits[lit_off[c]:lit_off[c+1]]``
   * ``lits``      DIMACS literals: +v is variable v (1-based), -v its negation
 
-Workload recipes follow the five configurations of the method's benchmark
-plan: uniform random 3-SAT at ratio 4.26 (n=50), a hybrid mixed-type instance
+Workload recipes: uniform random 3-SAT at ratio 4.26 (n=50), a hybrid mixed-type instance
 (n=2000), a long-constraint precision stress (n=10000, k in [64,512]), an
-uneven batch of 256 instances, and the config-1 distribution for the learned
+uneven batch of 256 instances, and the n=50 random 3-SAT distribution for the learned
 initialiser. The paper's own benchmark files are not available; these
 distributions stand in for their shapes.
 """
@@ -96,9 +95,9 @@ class _Builder:
         )
 
 
-def rng_for(config: int, index: int, salt: int = 0) -> np.random.Generator:
-    """Independent PCG64 stream per (configuration, instance index, salt)."""
-    return np.random.Generator(np.random.PCG64(np.random.SeedSequence([config, index, salt])))
+def rng_for(family: int, index: int, salt: int = 0) -> np.random.Generator:
+    """Independent PCG64 stream per (workload family, instance index, salt)."""
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence([family, index, salt])))
 
 
 def _draw_lits(rng: np.random.Generator, n: int, k: int) -> np.ndarray:
@@ -135,12 +134,12 @@ def random_ksat(n: int, m: int, k: int, rng: np.random.Generator) -> Instance:
     return b.build()
 
 
-def config1(index: int = 0) -> Instance:
+def random_3sat_n50(index: int = 0) -> Instance:
     """Uniform random 3-SAT, n=50, m=213 (ratio 4.26)."""
     return random_ksat(50, 213, 3, rng_for(1, index))
 
 
-def config2(index: int = 0) -> Instance:
+def hybrid_n2000(index: int = 0) -> Instance:
     """Hybrid mixed-type instance, n=2000: 8000 3-clauses, 400 XOR(5) with a
     fair parity, 200 CARD(20) >= 10 and 100 NAE(4), in one shuffled list."""
     rng = rng_for(2, index)
@@ -162,7 +161,7 @@ def config2(index: int = 0) -> Instance:
     return b.build()
 
 
-def config3(index: int = 0, n: int = 10000, n_clauses: int = 30000, n_long: int = 500,
+def long_card_n10000(index: int = 0, n: int = 10000, n_clauses: int = 30000, n_long: int = 500,
             kmin: int = 64, kmax: int = 512) -> Instance:
     """Long-constraint stress: 3-clauses plus CARD(>= r) / EK(= r) constraints of
     length uniform in [kmin, kmax], r uniform in [ceil(k/4), floor(3k/4)],
@@ -182,7 +181,7 @@ def config3(index: int = 0, n: int = 10000, n_clauses: int = 30000, n_long: int 
     return b.build()
 
 
-def config4_instance(index: int, nmin: int = 100, nmax: int = 20000) -> Instance:
+def batch_instance(index: int, nmin: int = 100, nmax: int = 20000) -> Instance:
     """One member of the uneven batch: n log-uniform in [nmin, nmax], m = ratio*n
     with ratio uniform in [4.0, 4.3]; 90% 3-clauses, 5% XOR of length 3..8,
     5% CARD (>= r) of length 10..100 with r uniform in [k/4, 3k/4]."""
@@ -207,12 +206,12 @@ def config4_instance(index: int, nmin: int = 100, nmax: int = 20000) -> Instance
     return b.build()
 
 
-def config4(count: int = 256, nmin: int = 100, nmax: int = 20000) -> List[Instance]:
-    return [config4_instance(i, nmin, nmax) for i in range(count)]
+def instance_batch(count: int = 256, nmin: int = 100, nmax: int = 20000) -> List[Instance]:
+    return [batch_instance(i, nmin, nmax) for i in range(count)]
 
 
-def config5(index: int, split: str = "train") -> Instance:
-    """Config-1 distribution; training and held-out instances use disjoint streams."""
+def learned_split(index: int, split: str = "train") -> Instance:
+    """Random 3-SAT n=50, m=213; training and held-out instances use disjoint streams."""
     salt = 0 if split == "train" else 1
     return random_ksat(50, 213, 3, rng_for(5, index, salt))
 

@@ -33,8 +33,8 @@ def _held_out_loss(net, batches):
 
 def test_learned_starts_gain_over_uniform():
     eta, steps = 0.1, 500
-    train = [synth.config5(i, "train") for i in range(1500)]
-    test = [synth.config5(i, "test") for i in range(160)]
+    train = [synth.learned_split(i, "train") for i in range(1500)]
+    test = [synth.learned_split(i, "test") for i in range(160)]
     lab_tr = learned.harvest(train, 64, eta, steps, seed=1)
     lab_te = learned.harvest(test, 64, eta, steps, seed=2)
     assert len(lab_tr.insts) > 200 and len(lab_te.insts) > 20

@@ -28,7 +28,7 @@ def gpu_ready():
 
 
 def _graph():
-    insts = [synth.config1(i) for i in range(3)] + [synth.mixed_small(2, n=40, m=70, kmax=40)]
+    insts = [synth.random_3sat_n50(i) for i in range(3)] + [synth.mixed_small(2, n=40, m=70, kmax=40)]
     b = synth._Builder(5)  # an instance with an isolated variable
     b.add(synth.OR, [1, -2, 3])
     b.add(synth.XOR, [2, 4], parity=0)
@@ -86,7 +86,7 @@ def test_adam_step_matches_reference():
 
 
 def test_training_reduces_loss():
-    insts = [synth.config1(i) for i in range(16)]
+    insts = [synth.random_3sat_n50(i) for i in range(16)]
     union = synth.concat_instances(insts)
     h = bd.load_batch(insts)
     rng = np.random.default_rng(4)
@@ -104,7 +104,7 @@ def test_training_reduces_loss():
 
 
 def test_restarts_sampled_around_mu():
-    insts = [synth.config1(i) for i in range(4)]
+    insts = [synth.random_3sat_n50(i) for i in range(4)]
     h = bd.load_batch(insts)
     B = 64
     bd.init_restarts(h, B, seed=9)

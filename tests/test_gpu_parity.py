@@ -90,7 +90,7 @@ def test_long_lengths(k):
 
 
 def test_mixed_short_and_long_in_one_instance():
-    inst = synth.config3(0, n=2000, n_clauses=3000, n_long=12, kmin=33, kmax=300)
+    inst = synth.long_card_n10000(0, n=2000, n_clauses=3000, n_long=12, kmin=33, kmax=300)
     _check_eval(inst, synth.uniform_x0(inst.n, 41, 3))
 
 
@@ -160,7 +160,7 @@ def test_unsat_counts_bit_exact(idx):
 
 
 def test_philox_starting_points_bit_exact():
-    inst = synth.config1(3)
+    inst = synth.random_3sat_n50(3)
     h = bd.load_instance(inst)
     bd.init_restarts(h, 37, seed=0x1234_5678_9ABC)
     x = bd.get_x(h).cpu().numpy()
@@ -168,7 +168,7 @@ def test_philox_starting_points_bit_exact():
 
 
 def test_batch_starting_points_and_counts_per_instance():
-    insts = [synth.config1(i) for i in range(3)] + [synth.mixed_small(5, n=30, m=40, kmax=9)]
+    insts = [synth.random_3sat_n50(i) for i in range(3)] + [synth.mixed_small(5, n=30, m=40, kmax=9)]
     h = bd.load_batch(insts)
     B = 24
     bd.init_restarts(h, B, seed=99)
@@ -203,7 +203,7 @@ def test_few_steps_match_oracle(graph):
 
 def test_chunked_step_equals_single_chunk():
     """Restart chunks only change the launch shape, not the arithmetic."""
-    inst = synth.config2(1)
+    inst = synth.hybrid_n2000(1)
     x0 = synth.uniform_x0(inst.n, 200, 4)
     outs = []
     for chunk in (32, 96, 256):
@@ -220,7 +220,7 @@ def test_fixed_tiles_match_autotuned_and_oracle():
     """Every tile shape a caller may fix computes the same step: x after two
     steps agrees across shapes and with the oracle, and the unsat counts of
     each are the oracle's for its own state."""
-    inst = synth.config2(1)
+    inst = synth.hybrid_n2000(1)
     B = 256
     x0 = synth.uniform_x0(inst.n, B, 5)
     ks = sorted(set(int(k) for k in inst.lengths))
@@ -246,7 +246,7 @@ def test_fixed_tiles_match_autotuned_and_oracle():
 
 
 def test_set_tiles_rejects_bad_shapes():
-    inst = synth.config2(1)
+    inst = synth.hybrid_n2000(1)
     h = bd.load_instance(inst, bd.default_params(autotune=0))
     with pytest.raises(RuntimeError):
         bd.set_tiles(h, 64, {3: (1, 1)})            # before init_restarts
@@ -265,7 +265,7 @@ def test_config2_full_size_sampled():
     """The hybrid n=2000 instance at B=1024 in the launch configuration of the
     benchmark (autotuned tiles and chunk, graph replay): one step checked on
     sampled restarts against the oracle, unsat counts for every restart."""
-    inst = synth.config2(0)
+    inst = synth.hybrid_n2000(0)
     B = 1024
     eta = 0.1
     x0 = synth.uniform_x0(inst.n, B, 11)
@@ -341,14 +341,14 @@ def test_empty_constraint_set():
 
 
 def test_step_before_init_is_an_error():
-    h = bd.load_instance(synth.config1(0))
+    h = bd.load_instance(synth.random_3sat_n50(0))
     with pytest.raises(bd.AfsError) as ei:
         bd.step(h, 1)
     assert ei.value.code == -8
 
 
 def test_step_host_matches_device_step():
-    inst = synth.config1(2)
+    inst = synth.random_3sat_n50(2)
     B = 64
     x0 = synth.uniform_x0(inst.n, B, 9)
     p = bd.default_params(eta=0.1)

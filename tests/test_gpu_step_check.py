@@ -162,7 +162,7 @@ def test_planted_mixed_instances(B):
 
 
 def test_planted_hybrid_size_instance():
-    """A config-2-sized planted instance (8000+ constraints, one instance) at B=1024."""
+    """A hybrid-workload-sized planted instance (8000+ constraints, one instance) at B=1024."""
     rng = np.random.default_rng(11)
     inst, x = _planted_case(2000, 8700, 20, 1024, rng)
     _run_check([inst], [x], 1024)

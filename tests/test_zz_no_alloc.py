@@ -37,7 +37,7 @@ def _dev(a):
 
 
 def test_noalloc_matches_allocating_entry_point_on_consecutive_calls():
-    inst = synth.config2(3)  # 30400 occurrences: several column chunks of the array
+    inst = synth.hybrid_n2000(3)  # 30400 occurrences: several column chunks of the array
     h = bd.load_instance(inst)
     for call, (B, seed) in enumerate(((300, 1), (77, 2))):
         x = _dev(synth.uniform_x0(inst.n, B, seed))
@@ -52,7 +52,7 @@ def test_noalloc_matches_allocating_entry_point_on_consecutive_calls():
 
 
 def test_noalloc_mixed_long_constraints():
-    inst = synth.config3(1, n=1500, n_clauses=2000, n_long=6, kmin=40, kmax=300)
+    inst = synth.long_card_n10000(1, n=1500, n_clauses=2000, n_long=6, kmin=40, kmax=300)
     h = bd.load_instance(inst)
     x = _dev(synth.near_vertex_x0(inst.n, 45, 4))
     fe_ref, g_ref = bd.eval_fe_grad(h, x)
