@@ -61,6 +61,7 @@ struct CsrArgs {
   unsigned* vnext;
   int* solved;
   unsigned* sgn;            // nullable: sign words of the new state (layout below)
+  int discard_go;           // 1: the occurrence rows are dead after this pass (L2 lines dropped)
   int W;                    // words per variable row of sgn / per instance of vcur
   int B;                    // restarts per instance
 };

@@ -69,6 +69,16 @@ bool vec_enabled() {
   return on;
 }
 
+// Dropping consumed occurrence rows from L2 in the CSR pass (off when
+// AFS_DISCARD=0, for A/B timing).
+bool discard_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("AFS_DISCARD");
+    return !(e != nullptr && e[0] == '0');
+  }();
+  return on;
+}
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -532,6 +542,7 @@ static int launch_csr(afs_handle* h, void* x, int xt, long long x_pitch, int b0,
   a.vnext = own ? h->vword.as<unsigned>() + (p ^ 1) * niw : nullptr;
   a.solved = h->solved.as<int>();
   a.sgn = own ? h->sgn.as<unsigned>() : nullptr;
+  a.discard_go = own && discard_enabled() ? 1 : 0;
   launch_csr_update(a, xt, s);
   CKL();
   return AFS_OK;

@@ -372,6 +372,13 @@ __device__ __forceinline__ float stored_value<__nv_bfloat16>(float v) {
   return __bfloat162float(__float2bfloat16_rn(v));
 }
 
+// Invalidate the 128-byte L2 line at p (128-byte aligned) without writing it
+// back. `after` is a value loaded from that line: the operand makes the
+// discard wait for the load.
+__device__ __forceinline__ void l2_discard_line(const void* p, float after) {
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(p), "f"(after));
+}
+
 // Bookkeeping of the step's check, done once per (instance, word) by the
 // warps of the instance's first variable: record the lowest solved restart
 // and clear the word the next step's check will OR into.
@@ -477,6 +484,7 @@ __device__ __forceinline__ void csr_vec4_task(const CsrArgs& a, int vl, int tile
   float4 acc[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const bool dis = a.discard_go && act && (lane & 7) == 0;
   for (int s = s0; s < s1; s += 8) {
     float4 t[8];
 #pragma unroll
@@ -493,6 +501,11 @@ __device__ __forceinline__ void csr_vec4_task(const CsrArgs& a, int vl, int tile
   }
   const float g[4] = {(acc[0].x + acc[1].x) + (acc[2].x + acc[3].x), (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y),
                       (acc[0].z + acc[1].z) + (acc[2].z + acc[3].z), (acc[0].w + acc[1].w) + (acc[2].w + acc[3].w)};
+  // the rows are dead once read (the next FE pass rewrites them): drop their
+  // 128-byte L2 lines without a write-back, so that they make room for rows
+  // still to be read instead of costing DRAM writes (g depends on every load)
+  if (dis)
+    for (int s = s0; s < s1; ++s) l2_discard_line(col + static_cast<long long>(s) * a.go_pitch, g[0]);
   unsigned nib = 0u;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
