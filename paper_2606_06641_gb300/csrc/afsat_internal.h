@@ -39,7 +39,8 @@ struct FeGroupArgs {
 
 // Gather of per-occurrence derivatives per variable and the projected step.
 struct CsrArgs {
-  void* x;                  // x[v * x_pitch + b] (updated in place when grad == nullptr)
+  const void* x;            // x[v * x_pitch + b]: the state the step read (x_t)
+  void* x_out;              // step mode: x_{t+1}, same layout (a different buffer)
   long long x_pitch;
   int b0, nb;
   const int* csr_off;       // slots of variable v: [csr_off[v], csr_off[v+1])

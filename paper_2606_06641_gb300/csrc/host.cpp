@@ -153,8 +153,12 @@ struct afs_handle {
   // unsat: counts of the last standalone check; sgn: sign words of x (n x W);
   // vword: the per-step check's violation words, two parities of n_inst x W
   // (step t ORs into parity t & 1 and clears the other for step t + 1)
-  DevBuf x, go, unsat, sgn, vword, solved, col, assign, stage, eval_go;
+  // xb: the state, double-buffered; step t (parity p = t & 1 counted from
+  // afs_init_restarts) reads xb[p] and writes xb[1 - p], so the current state
+  // is xb[parity]
+  DevBuf xb[2], go, unsat, sgn, vword, solved, col, assign, stage, eval_go;
   int parity = 0;
+  void* xcur() const { return xb[parity].p; }
   bool step_check_valid = false;  // vword[parity ^ 1] holds the last step's check
   long long eval_go_cols = 0;
   // graphs
@@ -515,11 +519,12 @@ static int launch_fe_group(afs_handle* h, const Group& g, const void* x, int xt,
 // parity p >= 0) writes its sign words, clears the check words of parity
 // 1 - p and, with `check`, leaves the restarts that passed this step's exact
 // check (words of parity p) unmoved.
-static int launch_csr(afs_handle* h, void* x, int xt, long long x_pitch, int b0, int nb, const float* go,
-                      long long go_pitch, float eta, float* grad, long long grad_pitch, bool check, int p,
-                      cudaStream_t s) {
+static int launch_csr(afs_handle* h, const void* x, void* xout, int xt, long long x_pitch, int b0, int nb,
+                      const float* go, long long go_pitch, float eta, float* grad, long long grad_pitch, bool check,
+                      int p, cudaStream_t s) {
   CsrArgs a{};
   a.x = x;
+  a.x_out = xout;
   a.x_pitch = x_pitch;
   a.b0 = b0;
   a.nb = nb;
@@ -533,7 +538,7 @@ static int launch_csr(afs_handle* h, void* x, int xt, long long x_pitch, int b0,
   a.grad_pitch = grad_pitch;
   a.var_inst = h->var_inst.as<int>();
   a.n_vars = h->n;
-  const bool own = grad == nullptr && x == h->x.p && p >= 0;
+  const bool own = grad == nullptr && xout != nullptr && p >= 0;
   if (own && b0 % 32 != 0) return fail(AFS_E_STATE, "chunk start %d is not a multiple of 32", b0);
   const size_t niw = static_cast<size_t>(h->n_inst) * h->W;
   a.W = h->W;
@@ -549,10 +554,10 @@ static int launch_csr(afs_handle* h, void* x, int xt, long long x_pitch, int b0,
 }
 
 // Standalone exact check of the current state into h->unsat, solved flags updated.
-static int launch_check(afs_handle* h, cudaStream_t s) {
+static int launch_check(afs_handle* h, const void* x, cudaStream_t s) {
   CK(cudaMemsetAsync(h->unsat.p, 0, sizeof(int) * static_cast<size_t>(h->n_inst) * h->B, s));
   VerifyArgs v{};
-  v.x = h->x.p;
+  v.x = x;
   v.x_pitch = h->pitch;
   v.B = h->B;
   v.lit_enc = h->lit_enc.as<int>();
@@ -638,7 +643,7 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int p
           st = h->aux[a];
           used = std::max(used, a + 1);
         }
-        int rc = launch_fe_group(h, g, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, nullptr, 0, st);
+        int rc = launch_fe_group(h, g, h->xb[p].p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, nullptr, 0, st);
         if (rc) return rc;
         ++nl;
       }
@@ -648,7 +653,8 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int p
       }
       if (chk_now && conc) CK(cudaStreamWaitEvent(s, h->ev_chk, 0));
       if (h->timing) CK(cudaEventRecordWithFlags(pool_event(h, ev + 1), s, cudaEventRecordExternal));
-      int rc = launch_csr(h, h->x.p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, eta, nullptr, 0, check, p, s);
+      int rc = launch_csr(h, h->xb[p].p, h->xb[p ^ 1].p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, eta,
+                          nullptr, 0, check, p, s);
       if (rc) return rc;
       ++nl;
       if (h->timing) {
@@ -660,7 +666,7 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int p
     }
   }
   if (check && nsteps > 0) {
-    int rc = launch_check(h, s);
+    int rc = launch_check(h, h->xb[(parity0 + nsteps) & 1].p, s);
     if (rc) return rc;
     nl += 2;
   }
@@ -830,7 +836,7 @@ static int autotune(afs_handle* h, cudaStream_t s) {
         double t = 1e30;
         for (int rep = 0; rep < 3; ++rep) {
           CK(cudaEventRecord(e0, s));
-          rc = launch_fe_group(h, g, h->x.p, h->xt, h->pitch, 0, nb, h->go.as<float>(), h->Bc, nullptr, 0, s);
+          rc = launch_fe_group(h, g, h->xcur(), h->xt, h->pitch, 0, nb, h->go.as<float>(), h->Bc, nullptr, 0, s);
           if (rc) return rc;
           CK(cudaEventRecord(e1, s));
           t = std::min(t, time_ms(s, e0, e1));
@@ -884,7 +890,7 @@ int afs::graph_view(const afs_handle* h, GraphView* out) {
   out->cparity = h->h_cparity.data();
   out->inst_vbegin = h->inst_vbegin.data();
   out->var_inst_dev = h->var_inst.as<int>();
-  out->x = h->x.p;
+  out->x = h->xcur();
   out->pitch = h->pitch;
   out->B = h->B;
   out->xt = h->xt;
@@ -895,7 +901,7 @@ void* afs::handle_ext(const afs_handle* h) { return h ? h->ext : nullptr; }
 
 int afs::state_written(afs_handle* h, cudaStream_t s) {
   if (!h || h->B <= 0) return fail(AFS_E_STATE, "no restart state");
-  launch_pack_signs(h->x.p, h->xt, h->pitch, h->n, h->B, h->sgn.as<unsigned>(), h->W, s);
+  launch_pack_signs(h->xcur(), h->xt, h->pitch, h->n, h->B, h->sgn.as<unsigned>(), h->W, s);
   CKL();
   return AFS_OK;
 }
@@ -924,7 +930,7 @@ int afs::eval_into_scratch(afs_handle* h, const float* x, int B, float* fe, floa
       if (rc) return rc;
     }
     if (grad) {
-      int rc = launch_csr(h, nullptr, XT_F32, B, b0, nb, scratch, cols, 0.0f, grad, B, false, -1, s);
+      int rc = launch_csr(h, x, nullptr, XT_F32, B, b0, nb, scratch, cols, 0.0f, grad, B, false, -1, s);
       if (rc) return rc;
     }
   }
@@ -971,8 +977,11 @@ int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_d
   h->pitch = (B + 31) / 32 * 32;
   const size_t es = h->xt == XT_F32 ? 4 : 2;
   int rc;
-  if ((rc = h->x.alloc(es * h->pitch * static_cast<size_t>(h->n)))) return rc;
-  CK(cudaMemsetAsync(h->x.p, 0, h->x.bytes, s));
+  for (DevBuf& xb : h->xb) {
+    if ((rc = xb.alloc(es * h->pitch * static_cast<size_t>(h->n)))) return rc;
+    CK(cudaMemsetAsync(xb.p, 0, xb.bytes, s));
+  }
+  h->parity = 0;
   const size_t nib = static_cast<size_t>(h->n_inst) * B;
   if ((rc = h->unsat.alloc(sizeof(int) * nib))) return rc;
   h->W = static_cast<int>(h->pitch / 32);
@@ -992,9 +1001,9 @@ int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_d
     g.cpw = 1;
   }
   if (x0_dev) {
-    launch_convert_in(x0_dev, XT_F32, B, h->x.p, h->xt, h->pitch, h->n, B, s);
+    launch_convert_in(x0_dev, XT_F32, B, h->xcur(), h->xt, h->pitch, h->n, B, s);
   } else {
-    launch_init_philox(h->x.p, h->xt, h->pitch, h->n, B, h->var_inst.as<int>(), seed, s);
+    launch_init_philox(h->xcur(), h->xt, h->pitch, h->n, B, h->var_inst.as<int>(), seed, s);
   }
   CKL();
   if ((rc = afs::state_written(h, s))) return rc;
@@ -1108,7 +1117,7 @@ int afs_round_and_verify(afs_handle* h, int32_t* unsat_host, int32_t* best_host,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   launch_fill_int(h->solved.as<int>(), INT_MAX, h->n_inst, s);
   CKL();
-  int rc = launch_check(h, s);
+  int rc = launch_check(h, h->xcur(), s);
   if (rc) return rc;
   const size_t nib = static_cast<size_t>(h->n_inst) * h->B;
   std::vector<int> un(nib);
@@ -1125,7 +1134,7 @@ int afs_round_and_verify(afs_handle* h, int32_t* unsat_host, int32_t* best_host,
     best[i] = bi;
   }
   CK(cudaMemcpyAsync(h->col.p, best.data(), sizeof(int) * h->n_inst, cudaMemcpyHostToDevice, s));
-  launch_gather_column(h->x.p, h->xt, h->pitch, h->var_inst.as<int>(), h->n, h->col.as<int>(),
+  launch_gather_column(h->xcur(), h->xt, h->pitch, h->var_inst.as<int>(), h->n, h->col.as<int>(),
                        h->assign.as<signed char>(), s);
   CKL();
   std::vector<int8_t> asg(h->n);
@@ -1149,7 +1158,7 @@ int afs_round_and_verify(afs_handle* h, int32_t* unsat_host, int32_t* best_host,
 int afs_get_x(afs_handle* h, float* x_dev, void* stream) {
   if (!h || !x_dev) return fail(AFS_E_ARG, "NULL argument");
   if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
-  launch_convert_in(h->x.p, h->xt, h->pitch, x_dev, XT_F32, h->B, h->n, h->B, static_cast<cudaStream_t>(stream));
+  launch_convert_in(h->xcur(), h->xt, h->pitch, x_dev, XT_F32, h->B, h->n, h->B, static_cast<cudaStream_t>(stream));
   CKL();
   return AFS_OK;
 }
@@ -1157,7 +1166,7 @@ int afs_get_x(afs_handle* h, float* x_dev, void* stream) {
 int afs_set_x(afs_handle* h, const float* x_dev, void* stream) {
   if (!h || !x_dev) return fail(AFS_E_ARG, "NULL argument");
   if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
-  launch_convert_in(x_dev, XT_F32, h->B, h->x.p, h->xt, h->pitch, h->n, h->B, static_cast<cudaStream_t>(stream));
+  launch_convert_in(x_dev, XT_F32, h->B, h->xcur(), h->xt, h->pitch, h->n, h->B, static_cast<cudaStream_t>(stream));
   CKL();
   return afs::state_written(h, static_cast<cudaStream_t>(stream));
 }
@@ -1206,7 +1215,7 @@ int afs_eval_fe_grad(afs_handle* h, const void* x_dev, int32_t x_dtype, int32_t 
       if (rc) return rc;
     }
     if (grad_dev) {
-      int rc = launch_csr(h, nullptr, xt, B, b0, nb, h->eval_go.as<float>(), cols, 0.0f, grad_dev, B, false, -1, s);
+      int rc = launch_csr(h, x_dev, nullptr, xt, B, b0, nb, h->eval_go.as<float>(), cols, 0.0f, grad_dev, B, false, -1, s);
       if (rc) return rc;
     }
   }
@@ -1223,7 +1232,7 @@ int afs_step_host(afs_handle* h, const float* x_host, float* x_out_host, int32_t
     if (rc) return rc;
   }
   CK(cudaMemcpyAsync(h->stage.p, x_host, nb, cudaMemcpyHostToDevice, s));
-  launch_convert_in(h->stage.p, XT_F32, h->B, h->x.p, h->xt, h->pitch, h->n, h->B, s);
+  launch_convert_in(h->stage.p, XT_F32, h->B, h->xcur(), h->xt, h->pitch, h->n, h->B, s);
   CKL();
   if (int rc0 = afs::state_written(h, s)) return rc0;
   const int ve = h->p.verify_every;
@@ -1234,7 +1243,7 @@ int afs_step_host(afs_handle* h, const float* x_host, float* x_out_host, int32_t
   CK(cudaMemcpyAsync(unsat_host, h->unsat.p, sizeof(int) * static_cast<size_t>(h->n_inst) * h->B,
                      cudaMemcpyDeviceToHost, s));
   if (x_out_host) {
-    launch_convert_in(h->x.p, h->xt, h->pitch, h->stage.p, XT_F32, h->B, h->n, h->B, s);
+    launch_convert_in(h->xcur(), h->xt, h->pitch, h->stage.p, XT_F32, h->B, h->n, h->B, s);
     CKL();
     CK(cudaMemcpyAsync(x_out_host, h->stage.p, nb, cudaMemcpyDeviceToHost, s));
   }

@@ -391,6 +391,30 @@ __device__ __forceinline__ void csr_first_var_duty(const CsrArgs& a, int inst, i
   if (a.vnext != nullptr) a.vnext[wi] = 0u;
 }
 
+// Store n <= 4 consecutive state values (one vector store when n == 4).
+template <typename XT>
+__device__ __forceinline__ void store_xvec(XT* p, const float (&v)[4], int n);
+template <>
+__device__ __forceinline__ void store_xvec<float>(float* p, const float (&v)[4], int n) {
+  if (n == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    for (int e = 0; e < n; ++e) p[e] = v[e];
+  }
+}
+template <>
+__device__ __forceinline__ void store_xvec<__nv_bfloat16>(__nv_bfloat16* p, const float (&v)[4], int n) {
+  if (n == 4) {
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]), hi = __floats2bfloat162_rn(v[2], v[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<const unsigned*>(&lo);
+    u.y = *reinterpret_cast<const unsigned*>(&hi);
+    *reinterpret_cast<uint2*>(p) = u;
+  } else {
+    for (int e = 0; e < n; ++e) p[e] = __float2bfloat16_rn(v[e]);
+  }
+}
+
 // One lane per restart. Evaluation mode (grad != nullptr) writes the summed
 // gradient; step mode moves the unsolved restarts and, with sgn, writes the
 // sign word of the warp's 32 restarts (the chunk start is a multiple of 32).
@@ -440,15 +464,12 @@ __global__ void __launch_bounds__(256) csr_update_kernel(CsrArgs a) {
   const unsigned viol = a.vcur != nullptr ? a.vcur[wi] : ~0u;
   const bool solved = !((viol >> lane) & 1u);
   if (lane == 0 && v == __ldg(a.var_inst + a.n_vars + inst)) csr_first_var_duty(a, inst, word, wi);
-  XT* xp = static_cast<XT*>(a.x) + static_cast<long long>(v) * a.x_pitch + a.b0 + bl;
+  const long long xi = static_cast<long long>(v) * a.x_pitch + a.b0 + bl;
   float xs = 0.0f;
   if (act) {
-    xs = load_x_rw<XT>(xp);
-    if (!solved) {
-      const float xn = fminf(fmaxf(fmaf(-a.eta, g, xs), -1.0f), 1.0f);
-      store_x<XT>(xp, xn);
-      xs = stored_value<XT>(xn);
-    }
+    xs = load_x<XT>(static_cast<const XT*>(a.x) + xi);
+    if (!solved) xs = stored_value<XT>(fminf(fmaxf(fmaf(-a.eta, g, xs), -1.0f), 1.0f));
+    store_x<XT>(static_cast<XT*>(a.x_out) + xi, xs);  // a solved restart keeps x_t
   }
   const unsigned bits = __ballot_sync(0xffffffffu, act && xs < 0.0f);
   if (a.sgn != nullptr && lane == 0) a.sgn[static_cast<long long>(v) * a.W + word] = bits;
@@ -474,12 +495,9 @@ __device__ __forceinline__ void csr_vec4_task(const CsrArgs& a, int vl, int tile
   const long long wi = static_cast<long long>(inst) * a.W + word;
   unsigned sw = 0u;  // solved bits of this lane's restarts
   if (act && a.vcur != nullptr) sw = ~(a.vcur[wi] >> (bl & 31));
-  XT* xp = static_cast<XT*>(a.x) + static_cast<long long>(v) * a.x_pitch + a.b0 + bl;
+  const long long xi = static_cast<long long>(v) * a.x_pitch + a.b0 + bl;
   float xo[4] = {0.f, 0.f, 0.f, 0.f};
-  if (act) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) xo[e] = load_x_rw<XT>(xp + e);
-  }
+  if (act) load_xvec<XT, 4>(static_cast<const XT*>(a.x) + xi, xo);
   const float* col = a.go + (act ? bl : 0);
   float4 acc[4];
 #pragma unroll
@@ -507,17 +525,14 @@ __device__ __forceinline__ void csr_vec4_task(const CsrArgs& a, int vl, int tile
   if (dis)
     for (int s = s0; s < s1; ++s) l2_discard_line(col + static_cast<long long>(s) * a.go_pitch, g[0]);
   unsigned nib = 0u;
+  float xn[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    if (!act || bl + e >= a.nb) continue;
-    float xs = xo[e];
-    if (!((sw >> e) & 1u)) {
-      const float xn = fminf(fmaxf(fmaf(-a.eta, g[e], xo[e]), -1.0f), 1.0f);
-      store_x<XT>(xp + e, xn);
-      xs = stored_value<XT>(xn);
-    }
-    nib |= static_cast<unsigned>(xs < 0.0f) << e;
+    // a solved restart keeps x_t; restarts past nb only fill the vector
+    xn[e] = ((sw >> e) & 1u) ? xo[e] : stored_value<XT>(fminf(fmaxf(fmaf(-a.eta, g[e], xo[e]), -1.0f), 1.0f));
+    if (act && bl + e < a.nb) nib |= static_cast<unsigned>(xn[e] < 0.0f) << e;
   }
+  if (act) store_xvec<XT>(static_cast<XT*>(a.x_out) + xi, xn, min(4, a.nb - bl));
   // 8 lanes x 4 restarts = one word
   unsigned wv = nib << ((lane & 7) * 4);
   wv |= __shfl_xor_sync(0xffffffffu, wv, 1);
