@@ -193,8 +193,10 @@ int afs_eval_fe_grad(afs_handle* h, const void* x_dev, int32_t x_dtype, int32_t 
  * fixed 16 MiB file-scope device array inside the library, which every GPU
  * that loads the library holds until the process exits. Restarts are
  * processed in chunks of 32..256 columns sized to that array; an instance
- * whose literal occurrences x 32 restarts x 4 bytes exceed 16 MiB (more than
- * 131072 occurrences) is rejected with AFS_E_ARG. The first call on each
+ * whose occurrences with derivative rows x 32 restarts x 4 bytes exceed
+ * 16 MiB (more than 131072 of them) is rejected with AFS_E_ARG. Occurrences
+ * in constraints of length <= 3 (probability-generating basis) need no row:
+ * their derivatives are recomputed in the gather. The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture. All calls share the one array
  * and its contents carry over from the last call, so calls whose work

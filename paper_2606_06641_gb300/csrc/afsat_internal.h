@@ -8,6 +8,11 @@ namespace afs {
 
 enum XType { XT_F32 = 0, XT_BF16 = 1 };
 
+// Constraints of length KFUSE (probability-generating basis) have no
+// occurrence-derivative rows: the derivative of each of their occurrences is
+// recomputed from the other two literals' state by a gather-side pass.
+constexpr int KFUSE = 3;
+
 // One FE+gradient launch over a group of constraints that share a length k
 // and are stored contiguously in bucket order: constraint c of the group owns
 // literals [lit_base + c*k, lit_base + (c+1)*k).
@@ -44,6 +49,9 @@ struct CsrArgs {
   long long x_pitch;
   int b0, nb;
   const int* csr_off;       // slots of variable v: [csr_off[v], csr_off[v+1])
+  const int* fus_off;       // fused occurrences of v: fus[fus_off[v] .. fus_off[v+1])
+  const int4* fus;          // {other literal, other literal, table offset, negated}
+  const float4* coef;       // coefficient tables (short form)
   int v_begin, v_count;
   const float* go;
   long long go_pitch;
@@ -63,6 +71,8 @@ struct CsrArgs {
   int* solved;
   unsigned* sgn;            // nullable: sign words of the new state (layout below)
   int discard_go;           // 1: the occurrence rows are dead after this pass (L2 lines dropped)
+  float* gf;                // step mode: gf[v * gf_pitch + (b - b0)] = summed derivatives of the fused
+  long long gf_pitch;       // occurrences of v (written by the fused pass, read by the CSR pass)
   int W;                    // words per variable row of sgn / per instance of vcur
   int B;                    // restarts per instance
 };
@@ -124,6 +134,9 @@ size_t long_smem_bytes(int kmax, bool esp);
 bool prepare_kernels();
 void launch_fe_long(const FeGroupArgs& a, int xt, int basis, int rt, cudaStream_t s);
 void launch_csr_update(const CsrArgs& a, int xt, cudaStream_t s);
+// The fused occurrences' summed derivatives of every variable for the chunk
+// (reads x_t only, so it runs beside the FE launches) into a.gf.
+void launch_fused_grad(const CsrArgs& a, int xt, cudaStream_t s);
 void launch_verify(const VerifyArgs& a, int xt, cudaStream_t s);
 void launch_solved(const int* unsat, int n_inst, int B, int* solved, cudaStream_t s);
 void launch_init_philox(void* x, int xt, long long x_pitch, int n, int B, const int* var_inst,

@@ -292,7 +292,9 @@ __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       const float sg = ((negm >> i) & 1u) ? -1.0f : 1.0f;
-      float* row = a.go + static_cast<long long>(__ldg(&ls[i].y)) * a.go_pitch;
+      const int slot = __ldg(&ls[i].y);
+      if (K == KFUSE && slot < 0) continue;  // fused constraint: no derivative row
+      float* row = a.go + static_cast<long long>(slot) * a.go_pitch;
       if constexpr (V) {
         if (act[0]) {
           float gv[RPL];

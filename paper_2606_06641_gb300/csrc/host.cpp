@@ -69,6 +69,13 @@ bool vec_enabled() {
   return on;
 }
 
+// Recomputing the derivatives of constraints with k == KFUSE in a gather-side
+// pass (off when AFS_FUSE=0, for A/B timing; read when an instance is loaded).
+bool fuse_enabled() {
+  const char* e = std::getenv("AFS_FUSE");
+  return !(e != nullptr && e[0] == '0');
+}
+
 // Dropping consumed occurrence rows from L2 in the CSR pass (off when
 // AFS_DISCARD=0, for A/B timing).
 bool discard_enabled() {
@@ -118,6 +125,7 @@ struct Group {
   long long lit_base;
   int rpl;          // restarts per lane (short kernel tile)
   int cpw;          // constraints per warp (short kernel tile)
+  bool fused = false;  // k == KFUSE: derivatives recomputed in the fused pass
 };
 
 }  // namespace
@@ -125,7 +133,9 @@ struct Group {
 struct afs_handle {
   afs_params p{};
   int n_inst = 0, n = 0, m = 0;
-  long long L = 0;  // literal occurrences (= CSR slots)
+  long long L = 0;  // literal occurrences
+  long long Lgo = 0;  // occurrences with a derivative row (not in fused constraints)
+  long long n_fused = 0;  // occurrences in fused constraints
   std::vector<int> inst_vbegin, inst_cbegin;
   // host copies for the independent re-check
   std::vector<int> h_lit_enc, h_lit_off, h_viol_off, h_cons_inst, h_var_inst;
@@ -137,13 +147,14 @@ struct afs_handle {
   // test hook for the bounded-wait path of the long kernel (0 = normal)
   long long dbg_wait_limit = 0;
   unsigned dbg_extra_tx = 0;
-  // buckets, and their launch order (largest work first)
+  // buckets, and their launch order (largest work first); step_order leaves
+  // out the fused buckets, whose derivatives the CSR pass recomputes
   std::vector<Group> groups;
-  std::vector<int> order;
+  std::vector<int> order, step_order;
   double work_per_restart = 0.0;
   // device instance data
   DevBuf litslot, cons_tab, cons_orig, cons_k, cons_lit, coef, csr_off, lit_enc, lit_off, viol_off, viol,
-      ranges, var_inst, err, chk_em, chk_ranges;
+      ranges, var_inst, err, chk_em, chk_ranges, fus_off, fus;
   int n_ranges = 0, n_chk_ranges = 0;
   // restart state
   int B = 0, xt = XT_F32;
@@ -156,7 +167,8 @@ struct afs_handle {
   // xb: the state, double-buffered; step t (parity p = t & 1 counted from
   // afs_init_restarts) reads xb[p] and writes xb[1 - p], so the current state
   // is xb[parity]
-  DevBuf xb[2], go, unsat, sgn, vword, solved, col, assign, stage, eval_go;
+  // gf: the fused occurrences' summed derivatives per variable (n x chunk)
+  DevBuf xb[2], go, gf, unsat, sgn, vword, solved, col, assign, stage, eval_go;
   int parity = 0;
   void* xcur() const { return xb[parity].p; }
   bool step_check_valid = false;  // vword[parity ^ 1] holds the last step's check
@@ -169,9 +181,10 @@ struct afs_handle {
   cudaStream_t aux[NAUX] = {};
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[NAUX] = {};
-  // the per-step exact check runs on its own forked stream beside the FE launches
-  cudaStream_t chk = nullptr;
-  cudaEvent_t ev_chk = nullptr;
+  // the per-step exact check and the fused pass run on their own forked
+  // streams beside the FE launches
+  cudaStream_t chk = nullptr, fus_s = nullptr;
+  cudaEvent_t ev_chk = nullptr, ev_fus = nullptr;
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs, timed_graphs;  // (nsteps, start parity)
   std::map<std::pair<int, int>, std::pair<std::vector<std::pair<int, int>>, std::vector<std::pair<int, int>>>>
       timed_pairs;
@@ -195,6 +208,8 @@ struct afs_handle {
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (chk) cudaStreamDestroy(chk);
     if (ev_chk) cudaEventDestroy(ev_chk);
+    if (fus_s) cudaStreamDestroy(fus_s);
+    if (ev_fus) cudaEventDestroy(ev_fus);
     if (ext && ext_release) ext_release(ext);
   }
   void drop_graphs() {
@@ -324,6 +339,11 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   std::vector<int2> litslot;
   litslot.reserve(L + m);
   h->work_per_restart = 0.0;
+  // constraints of length KFUSE (probability-generating basis) get no
+  // occurrence rows: the CSR pass recomputes their derivatives from the
+  // other literals' state
+  const bool can_fuse = h->p.basis == AFS_BASIS_PGF && fuse_enabled();
+  auto fused_k = [&](int k) { return can_fuse && k == KFUSE; };
   for (int pos = 0; pos < m; ++pos) {
     const int g = order[pos];
     const int k = gk[g];
@@ -341,7 +361,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
       last->c_count++;
     } else {
       // long constraints form one group sorted by decreasing length: its k is the longest
-      h->groups.push_back(Group{is_long, k, pos, 1, static_cast<long long>(b_lit[pos]), 1, 1});
+      h->groups.push_back(Group{is_long, k, pos, 1, static_cast<long long>(b_lit[pos]), 1, 1, fused_k(k)});
     }
   }
   {
@@ -352,21 +372,40 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     h->order.resize(h->groups.size());
     for (size_t gi = 0; gi < h->groups.size(); ++gi) h->order[gi] = static_cast<int>(gi);
     std::stable_sort(h->order.begin(), h->order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    for (int gi : h->order)
+      if (!h->groups[gi].fused) h->step_order.push_back(gi);
   }
-  // ---- CSR: slots in variable-major order, occurrences of a variable in bucket order ----
-  std::vector<int> csr(h->n + 1, 0);
-  for (const int2& ls : litslot)
-    if (ls.y == -1) csr[(ls.x >> 1) + 1]++;
-  for (int v = 0; v < h->n; ++v) csr[v + 1] += csr[v];
+  // ---- CSR: slots in variable-major order, occurrences of a variable in
+  // bucket order; occurrences in fused constraints get an entry
+  // {other literal, other literal, table, negated} instead of a slot ----
+  std::vector<int> csr(h->n + 1, 0), fcsr(h->n + 1, 0);
+  for (int pos = 0; pos < m; ++pos)
+    for (int t = 0; t < b_k[pos]; ++t) (fused_k(b_k[pos]) ? fcsr : csr)[(litslot[b_lit[pos] + t].x >> 1) + 1]++;
+  for (int v = 0; v < h->n; ++v) {
+    csr[v + 1] += csr[v];
+    fcsr[v + 1] += fcsr[v];
+  }
+  std::vector<int4> fus(static_cast<size_t>(fcsr[h->n]));
   {
-    std::vector<int> fill(csr.begin(), csr.end() - 1);
+    std::vector<int> fill(csr.begin(), csr.end() - 1), ffill(fcsr.begin(), fcsr.end() - 1);
     for (int pos = 0; pos < m; ++pos) {
-      for (int t = 0; t < b_k[pos]; ++t) {
+      const int k = b_k[pos];
+      for (int t = 0; t < k; ++t) {
         int2& ls = litslot[b_lit[pos] + t];
-        ls.y = fill[ls.x >> 1]++;
+        if (!fused_k(k)) {
+          ls.y = fill[ls.x >> 1]++;
+          continue;
+        }
+        int other[2] = {0, 0}, no = 0;
+        for (int u = 0; u < k; ++u)
+          if (u != t) other[no++] = litslot[b_lit[pos] + u].x;
+        fus[ffill[ls.x >> 1]++] = make_int4(other[0], other[1], b_tab[pos], ls.x & 1);
+        ls.y = -1;
       }
     }
   }
+  h->Lgo = csr[h->n];
+  h->n_fused = fcsr[h->n];
   // ---- exact-check structures (load order) ----
   h->h_lit_enc.resize(L);
   h->h_lit_off.assign(m + 1, 0);
@@ -444,6 +483,8 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   if ((rc = upload(h->cons_lit, b_lit, s))) return rc;
   if ((rc = upload(h->coef, coef, s))) return rc;
   if ((rc = upload(h->csr_off, csr, s))) return rc;
+  if ((rc = upload(h->fus_off, fcsr, s))) return rc;
+  if ((rc = upload(h->fus, fus, s))) return rc;
   if ((rc = upload(h->lit_enc, h->h_lit_enc, s))) return rc;
   if ((rc = upload(h->lit_off, h->h_lit_off, s))) return rc;
   if ((rc = upload(h->viol_off, viol_off, s))) return rc;
@@ -463,6 +504,8 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   CK(cudaStreamCreateWithFlags(&h->chk, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&h->ev_chk, cudaEventDisableTiming));
+  CK(cudaStreamCreateWithFlags(&h->fus_s, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_fus, cudaEventDisableTiming));
   if (!prepare_kernels()) return fail(AFS_E_CUDA, "kernel attribute setup: %s", cudaGetErrorString(cudaGetLastError()));
   *out = h.release();
   return AFS_OK;
@@ -473,6 +516,8 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
 // ---------------------------------------------------------------------------
 static int launch_fe_group(afs_handle* h, const Group& g, const void* x, int xt, long long x_pitch, int b0, int nb,
                            float* go, long long go_pitch, float* fe, long long fe_pitch, cudaStream_t s) {
+  // a fused bucket writes no derivative rows: it is launched only for its FE values
+  if (g.fused && fe == nullptr) return AFS_OK;
   FeGroupArgs a{};
   a.x = x;
   a.x_pitch = x_pitch;
@@ -529,6 +574,9 @@ static int launch_csr(afs_handle* h, const void* x, void* xout, int xt, long lon
   a.b0 = b0;
   a.nb = nb;
   a.csr_off = h->csr_off.as<int>();
+  a.fus_off = h->fus_off.as<int>();
+  a.fus = h->fus.as<int4>();
+  a.coef = h->coef.as<float4>();
   a.v_begin = 0;
   a.v_count = h->n;
   a.go = go;
@@ -548,7 +596,29 @@ static int launch_csr(afs_handle* h, const void* x, void* xout, int xt, long lon
   a.solved = h->solved.as<int>();
   a.sgn = own ? h->sgn.as<unsigned>() : nullptr;
   a.discard_go = own && discard_enabled() ? 1 : 0;
+  a.gf = own && h->n_fused > 0 ? h->gf.as<float>() : nullptr;
+  a.gf_pitch = go_pitch;
   launch_csr_update(a, xt, s);
+  CKL();
+  return AFS_OK;
+}
+
+// The fused pass of a chunk: summed derivatives of the fused occurrences of
+// every variable at the state x (x_t) into gf (pitch = chunk).
+static int launch_fused(afs_handle* h, const void* x, int b0, int nb, cudaStream_t s) {
+  CsrArgs a{};
+  a.x = x;
+  a.x_pitch = h->pitch;
+  a.b0 = b0;
+  a.nb = nb;
+  a.v_begin = 0;
+  a.v_count = h->n;
+  a.fus_off = h->fus_off.as<int>();
+  a.fus = h->fus.as<int4>();
+  a.coef = h->coef.as<float4>();
+  a.gf = h->gf.as<float>();
+  a.gf_pitch = h->Bc;
+  launch_fused_grad(a, h->xt, s);
   CKL();
   return AFS_OK;
 }
@@ -621,11 +691,19 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int p
       const int nb = std::min(h->Bc, h->B - b0);
       if (h->timing) CK(cudaEventRecordWithFlags(pool_event(h, ev), s, cudaEventRecordExternal));
       // the first (largest-work) bucket runs on s, the others on forked streams
-      const int G = static_cast<int>(h->groups.size());
+      const int G = static_cast<int>(h->step_order.size());
       const bool conc = concurrent_enabled();
       const bool chk_now = check && b0 == 0;
-      const bool fork = conc && (G > 1 || chk_now);
+      const bool fus_now = h->n_fused > 0;
+      const bool fork = conc && (G > 1 || chk_now || fus_now);
       if (fork) CK(cudaEventRecord(h->ev_fork, s));
+      if (fus_now) {
+        if (conc) CK(cudaStreamWaitEvent(h->fus_s, h->ev_fork, 0));
+        int rc = launch_fused(h, h->xb[p].p, b0, nb, conc ? h->fus_s : s);
+        if (rc) return rc;
+        ++nl;
+        if (conc) CK(cudaEventRecord(h->ev_fus, h->fus_s));
+      }
       if (chk_now) {
         if (conc) CK(cudaStreamWaitEvent(h->chk, h->ev_fork, 0));
         launch_check_step(h, p, conc ? h->chk : s);
@@ -635,7 +713,7 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int p
       }
       int used = 0;
       for (int gi = 0; gi < G; ++gi) {
-        const Group& g = h->groups[h->order[gi]];
+        const Group& g = h->groups[h->step_order[gi]];
         cudaStream_t st = s;
         if (fork && gi > 0) {
           const int a = (gi - 1) % afs_handle::NAUX;
@@ -652,6 +730,7 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int p
         CK(cudaStreamWaitEvent(s, h->ev_join[a], 0));
       }
       if (chk_now && conc) CK(cudaStreamWaitEvent(s, h->ev_chk, 0));
+      if (fus_now && conc) CK(cudaStreamWaitEvent(s, h->ev_fus, 0));
       if (h->timing) CK(cudaEventRecordWithFlags(pool_event(h, ev + 1), s, cudaEventRecordExternal));
       int rc = launch_csr(h, h->xb[p].p, h->xb[p ^ 1].p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, eta,
                           nullptr, 0, check, p, s);
@@ -699,7 +778,12 @@ static void collect_timing(afs_handle* h) {
 }
 
 static int alloc_go(afs_handle* h, int cols) {
-  const size_t need = sizeof(float) * static_cast<size_t>(std::max<long long>(h->L, 1)) * cols;
+  const size_t need = sizeof(float) * static_cast<size_t>(std::max<long long>(h->Lgo, 1)) * cols;
+  const size_t need_f = h->n_fused > 0 ? sizeof(float) * static_cast<size_t>(h->n) * cols : 0;
+  if (h->gf.bytes < need_f) {
+    int rc = h->gf.alloc(need_f);
+    if (rc) return rc;
+  }
   if (h->go.bytes >= need) return AFS_OK;
   return h->go.alloc(need);
 }
@@ -710,7 +794,7 @@ static int alloc_go(afs_handle* h, int cols) {
 static int default_chunk(const afs_handle* h) {
   const long long Bp = (h->B + 31) / 32 * 32;
   const double budget = 40.0e6;
-  long long c = static_cast<long long>(budget / (4.0 * std::max<long long>(h->L, 1)));
+  long long c = static_cast<long long>(budget / (4.0 * std::max<long long>(h->Lgo, 1)));
   c = std::max<long long>(32, c / 32 * 32);
   return static_cast<int>(std::min(c, Bp));
 }
@@ -825,7 +909,7 @@ static int autotune(afs_handle* h, cudaStream_t s) {
   // 2. tile shape per short bucket at that chunk: single FE launches timed
   const int nb = std::min(h->Bc, h->B);
   for (Group& g : h->groups) {
-    if (g.is_long) continue;
+    if (g.is_long || g.fused) continue;
     double bt = 1e30;
     int best_rpl = g.rpl, best_cpw = g.cpw;
     for (int rpl = 1; rpl <= (pgf ? max_rpl_for_k(g.k) : 1); rpl *= 2) {
@@ -916,13 +1000,14 @@ int afs::eval_into_scratch(afs_handle* h, const float* x, int B, float* fe, floa
                            long long cap_floats, cudaStream_t s) {
   if (!h || !x || !scratch) return fail(AFS_E_ARG, "NULL argument");
   if (B <= 0) return fail(AFS_E_ARG, "B must be positive");
-  const long long L = std::max<long long>(h->L, 1);
+  const long long L = std::max<long long>(h->Lgo, 1);
   long long cols = std::min<long long>((B + 31) / 32 * 32, 256);
   while (cols > 32 && L * cols > cap_floats) cols -= 32;
   if (L * cols > cap_floats)
     return fail(AFS_E_ARG,
-                "instance has %lld literal occurrences: 32 restarts need %lld bytes of scratch, the buffer holds %lld",
-                h->L, L * 32 * 4, cap_floats * 4);
+                "instance has %lld literal occurrences with derivative rows: 32 restarts need %lld bytes of "
+                "scratch, the buffer holds %lld",
+                h->Lgo, L * 32 * 4, cap_floats * 4);
   for (int b0 = 0; b0 < B; b0 += static_cast<int>(cols)) {
     const int nb = std::min(static_cast<int>(cols), B - b0);
     for (const Group& g : h->groups) {
@@ -1203,7 +1288,7 @@ int afs_eval_fe_grad(afs_handle* h, const void* x_dev, int32_t x_dtype, int32_t 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int xt = x_dtype == AFS_X_BF16 ? XT_BF16 : XT_F32;
   const int cols = std::min<int>((B + 31) / 32 * 32, 256);
-  const size_t need = sizeof(float) * static_cast<size_t>(std::max<long long>(h->L, 1)) * cols;
+  const size_t need = sizeof(float) * static_cast<size_t>(std::max<long long>(h->Lgo, 1)) * cols;
   if (h->eval_go.bytes < need) {
     int rc = h->eval_go.alloc(need);
     if (rc) return rc;

@@ -309,19 +309,6 @@ bool pdl_enabled() {
   return on;
 }
 
-bool prepare_kernels() {
-  int dev = 0, optin = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return false;
-  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
-  if (LongLayout(1024).bytes(true) + 64 > static_cast<size_t>(optin)) return false;
-  bool ok = true;
-  ok &= raise_smem_cap(fe_grad_long_kernel<float, false>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<float, true>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, false>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, true>, optin);
-  return ok;
-}
-
 // a.k carries the group's longest constraint for the long kernel
 void launch_fe_long(const FeGroupArgs& a, int xt, int basis, int /*rt*/, cudaStream_t s) {
   if (xt == XT_F32) {
@@ -370,6 +357,62 @@ __device__ __forceinline__ float stored_value<float>(float v) {
 template <>
 __device__ __forceinline__ float stored_value<__nv_bfloat16>(float v) {
   return __bfloat162float(__float2bfloat16_rn(v));
+}
+
+// Fused constraints (k = KFUSE = 3, probability-generating tables): the
+// derivative of occurrence `self` is s_self * dFE/dl_self, recomputed from the
+// two other literals' values with the constraint's table: the real root
+// w = -1 contributes E l1 l2, the complex pair (scaled form) Re(E' tan (l1 tan
+// + i)(l2 tan + i)) -- the same products at the roots as the FE kernel's
+// gradient, without the self factor. The entries {other, other, table,
+// negated} of variable v are read with uniform loads (the warp's lanes share
+// them); the gathers of FB occurrences are in flight at a time, R consecutive
+// restarts per lane starting at column col.
+template <typename XT, int R, int FB>
+__device__ __forceinline__ void fused_sum(const CsrArgs& a, int v, long long col, bool act, float (&acc)[R]) {
+  const int f0 = __ldg(a.fus_off + v), f1 = __ldg(a.fus_off + v + 1);
+  const XT* x = static_cast<const XT*>(a.x);
+  for (int f = f0; f < f1; f += FB) {  // uniform per warp
+    int4 e[FB];
+    float x1[FB][R], x2[FB][R];
+#pragma unroll
+    for (int u = 0; u < FB; ++u) {
+      e[u] = f + u < f1 ? __ldg(a.fus + f + u) : make_int4(0, 0, -1, 0);
+      const bool ld = act && e[u].z >= 0;
+      const XT* p1 = x + static_cast<long long>(e[u].x >> 1) * a.x_pitch + col;
+      const XT* p2 = x + static_cast<long long>(e[u].y >> 1) * a.x_pitch + col;
+      if constexpr (R == 4) {
+        if (ld) {
+          load_xvec<XT, 4>(p1, x1[u]);
+          load_xvec<XT, 4>(p2, x2[u]);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          x1[u][r] = ld ? load_x<XT>(p1 + r) : 0.0f;
+          x2[u][r] = ld ? load_x<XT>(p2 + r) : 0.0f;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < FB; ++u) {
+      if (e[u].z < 0) continue;  // uniform
+      const float4* tab = a.coef + e[u].z;
+      const float s1 = (e[u].x & 1) ? -1.0f : 1.0f, s2 = (e[u].y & 1) ? -1.0f : 1.0f;
+      const float ss = (e[u].w & 1) ? -1.0f : 1.0f;
+      const float Es = __ldg(&tab[1].y) * (s1 * s2);  // real root, the other signs folded
+      const float4 cc = __ldg(tab + 2);                // complex pair {tan, 0, E'}
+      const float ia1 = cc.x * s1, ia2 = cc.x * s2;
+      const float p0r = cc.z * cc.x, p0i = cc.w * cc.x;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float w1 = x1[u][r] * ia1, w2 = x2[u][r] * ia2;
+        const float pr = fmaf(p0r, w1, -p0i), pi = fmaf(p0i, w1, p0r);
+        const float d = fmaf(Es * x1[u][r], x2[u][r], fmaf(pr, w2, -pi));
+        acc[r] = fmaf(ss, d, acc[r]);
+      }
+    }
+  }
 }
 
 // Invalidate the 128-byte L2 line at p (128-byte aligned) without writing it
@@ -432,6 +475,8 @@ __global__ void __launch_bounds__(256) csr_update_kernel(CsrArgs a) {
   const bool act = bl < a.nb;
   const int v = a.v_begin + static_cast<int>(vl);
   const int s0 = __ldg(a.csr_off + v), s1 = __ldg(a.csr_off + v + 1);
+  float accf[1] = {0.0f};
+  fused_sum<XT, 1, 4>(a, v, a.b0 + (act ? bl : 0), act, accf);
   // eight independent loads in flight per lane; the summation order is fixed
   // by the slot order, so the result does not depend on timing
   const float* col = a.go + (act ? bl : 0);
@@ -453,7 +498,7 @@ __global__ void __launch_bounds__(256) csr_update_kernel(CsrArgs a) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) acc[u] += t[u];
   }
-  const float g = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  const float g = accf[0] + (((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7])));
   if (a.grad != nullptr) {
     if (act) a.grad[static_cast<long long>(v) * a.grad_pitch + a.b0 + bl] = g;
     return;
@@ -502,6 +547,9 @@ __device__ __forceinline__ void csr_vec4_task(const CsrArgs& a, int vl, int tile
   float4 acc[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+  // fused occurrences: summed by the fused pass beside the FE launches (the
+  // step path always provides gf when the instance has fused occurrences)
+  const float* gfp = a.gf != nullptr && act ? a.gf + static_cast<long long>(v) * a.gf_pitch + bl : nullptr;
   const bool dis = a.discard_go && act && (lane & 7) == 0;
   for (int s = s0; s < s1; s += 8) {
     float4 t[8];
@@ -517,8 +565,11 @@ __device__ __forceinline__ void csr_vec4_task(const CsrArgs& a, int vl, int tile
       acc[u & 3].w += t[u].w;
     }
   }
-  const float g[4] = {(acc[0].x + acc[1].x) + (acc[2].x + acc[3].x), (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y),
-                      (acc[0].z + acc[1].z) + (acc[2].z + acc[3].z), (acc[0].w + acc[1].w) + (acc[2].w + acc[3].w)};
+  const float4 gf = gfp != nullptr ? __ldg(reinterpret_cast<const float4*>(gfp)) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float g[4] = {gf.x + ((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x)),
+                      gf.y + ((acc[0].y + acc[1].y) + (acc[2].y + acc[3].y)),
+                      gf.z + ((acc[0].z + acc[1].z) + (acc[2].z + acc[3].z)),
+                      gf.w + ((acc[0].w + acc[1].w) + (acc[2].w + acc[3].w))};
   // the rows are dead once read (the next FE pass rewrites them): drop their
   // 128-byte L2 lines without a write-back, so that they make room for rows
   // still to be read instead of costing DRAM writes (g depends on every load)
@@ -558,18 +609,60 @@ __global__ void __launch_bounds__(256, 5) csr_update_vec4_kernel(CsrArgs a) {
   }
 }
 
+// The fused pass: warps stride over the (variable, 128-restart tile) tasks and
+// store the summed derivatives of each variable's fused occurrences (4
+// restarts per lane) into gf. The gathers are plain vector loads, FUSED_FB
+// occurrences (2 rows each) in flight per warp.
+template <typename XT>
+constexpr int FUSED_FB = sizeof(XT) == 4 ? 4 : 2;
+
+template <typename XT>
+__global__ void __launch_bounds__(256) fused_grad_kernel(CsrArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  const int lane = threadIdx.x & 31;
+  const unsigned tiles = static_cast<unsigned>((a.nb + 127) >> 7);
+  const unsigned ntask = tiles * static_cast<unsigned>(a.v_count);  // < 2^32 (checked at launch)
+  const unsigned stride = gridDim.x * (blockDim.x >> 5);
+  for (unsigned task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < ntask; task += stride) {
+    const unsigned vl = task / tiles;  // uniform per warp
+    const int v = a.v_begin + static_cast<int>(vl);
+    const int bl = static_cast<int>(task - vl * tiles) * 128 + lane * 4;
+    const bool act = bl < a.nb;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    fused_sum<XT, 4, FUSED_FB<XT>>(a, v, a.b0 + (act ? bl : 0), act, acc);
+    if (act)
+      *reinterpret_cast<float4*>(a.gf + static_cast<long long>(v) * a.gf_pitch + bl) =
+          make_float4(acc[0], acc[1], acc[2], acc[3]);
+  }
+}
+
 // Resident blocks of a kernel on the whole device (cached per kernel).
 template <typename K>
-static long long resident_blocks(K kernel, int threads) {
+static long long resident_blocks(K kernel, int threads, size_t smem = 0) {
   static int cached = 0;
   if (cached == 0) {
     int dev = 0, sms = 1, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0) != cudaSuccess || per < 1) per = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) per = 1;
     cached = sms * per;
   }
   return cached;
+}
+
+void launch_fused_grad(const CsrArgs& a, int xt, cudaStream_t s) {
+  const long long tasks = static_cast<long long>((a.nb + 127) / 128) * a.v_count;
+  if (tasks == 0) return;
+  if (tasks >= (1ll << 32) - 4096LL * 1024) return;  // (never for instances that load)
+  long long blocks = (tasks + 7) / 8;
+  if (xt == XT_F32) {
+    blocks = std::min(blocks, resident_blocks(fused_grad_kernel<float>, 256));
+    launch_pdl(fused_grad_kernel<float>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+  } else {
+    blocks = std::min(blocks, resident_blocks(fused_grad_kernel<__nv_bfloat16>, 256));
+    launch_pdl(fused_grad_kernel<__nv_bfloat16>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+  }
 }
 
 void launch_csr_update(const CsrArgs& a, int xt, cudaStream_t s) {
@@ -985,6 +1078,19 @@ void launch_gather_column(const void* x, int xt, long long x_pitch, const int* v
   else
     gather_column_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(x), x_pitch, var_inst,
                                                                n, col_of, out);
+}
+
+bool prepare_kernels() {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+  if (LongLayout(1024).bytes(true) + 64 > static_cast<size_t>(optin)) return false;
+  bool ok = true;
+  ok &= raise_smem_cap(fe_grad_long_kernel<float, false>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<float, true>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, false>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, true>, optin);
+  return ok;
 }
 
 }  // namespace afs

@@ -364,3 +364,55 @@ def test_step_host_matches_device_step():
     un = bd.step_host(h2, xh, xo)
     np.testing.assert_array_equal(xo.numpy(), x_dev)
     np.testing.assert_array_equal(un.numpy(), un_dev.cpu().numpy())
+
+
+# ---- constraints with k <= 3: derivatives recomputed in the CSR pass ----------
+def test_fused_gradient_without_fe_values():
+    """Gradient-only evaluation (no FE kernel for the k <= 3 buckets) equals the
+    oracle and the gradient of the full evaluation."""
+    inst = synth.mixed_small(2, n=30, m=80, kmax=5)
+    x = synth.uniform_x0(inst.n, 70, 21)
+    h = bd.load_instance(inst)
+    _, g_only = bd.eval_fe_grad(h, _dev(x), want_fe=False)
+    fe, g_full = bd.eval_fe_grad(h, _dev(x))
+    fe_ref, go_ref, g_ref = O.evaluate(inst, x.astype(np.float64))
+    assert torch.equal(g_only, g_full)
+    assert (np.abs(g_only.cpu().numpy() - g_ref) / _grad_scale(inst, go_ref)).max() <= TOL
+    assert np.abs(fe.cpu().numpy() - fe_ref).max() <= TOL
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_fused_lengths_with_repeated_variables(k):
+    """Every fused length, with a variable repeated inside a constraint and
+    complementary literals, through the step path and the evaluation path."""
+    b = synth._Builder(6)
+    rng = np.random.default_rng(k)
+    for _ in range(40):
+        lits = rng.integers(1, 7, size=k) * np.where(rng.random(k) < 0.5, -1, 1)
+        b.add(int(rng.integers(0, 7)) if k > 1 else synth.OR, lits, synth.GE, int(rng.integers(0, k + 1)),
+              int(rng.integers(0, 2)))
+    inst = b.build()
+    x0 = synth.uniform_x0(inst.n, 40, 30 + k)
+    _check_eval(inst, x0)
+    h = bd.load_instance(inst, bd.default_params(eta=0.1, verify_every=0, autotune=0))
+    bd.init_restarts(h, 40, x0=_dev(x0))
+    bd.step(h, 1)
+    ref = O.pgd_step(inst, x0.astype(np.float64), 0.1)
+    assert np.abs(bd.get_x(h).cpu().numpy() - ref).max() <= 0.1 * 2 * TOL
+
+
+def test_fused_and_unfused_steps_agree(monkeypatch):
+    """The same steps with the k <= 3 derivatives recomputed in the CSR pass and
+    with them written as occurrence rows by the FE kernel."""
+    inst = synth.hybrid_n2000(1)
+    B = 256
+    x0 = synth.uniform_x0(inst.n, B, 17)
+    outs = []
+    for fuse in ("1", "0"):
+        monkeypatch.setenv("AFS_FUSE", fuse)
+        h = bd.load_instance(inst, bd.default_params(eta=0.1, autotune=0))
+        bd.init_restarts(h, B, x0=_dev(x0))
+        bd.step(h, 3)
+        outs.append(bd.get_x(h).cpu().numpy())
+        h.free()
+    assert np.abs(outs[0] - outs[1]).max() <= 1e-5

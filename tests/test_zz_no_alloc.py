@@ -66,8 +66,9 @@ def test_noalloc_mixed_long_constraints():
 
 
 def test_noalloc_rejects_instances_beyond_the_array():
-    # 160000 occurrences x 32 restarts x 4 bytes > 16 MiB
-    inst = synth.random_ksat(20000, 53334, 3, synth.rng_for(400, 0))
+    # 160000 occurrences of 4-clauses (each with a derivative row) x 32
+    # restarts x 4 bytes > 16 MiB
+    inst = synth.random_ksat(20000, 40000, 4, synth.rng_for(400, 0))
     assert inst.n_lits > 131072
     h = bd.load_instance(inst)
     x = _dev(synth.uniform_x0(inst.n, 32, 0))
@@ -75,3 +76,19 @@ def test_noalloc_rejects_instances_beyond_the_array():
     with pytest.raises(bd.AfsError) as ei:
         bd.eval_fe_grad_noalloc(h, x, None, g)
     assert ei.value.code == -1 and "scratch" in str(ei.value)
+
+
+def test_noalloc_takes_large_instances_of_short_constraints():
+    """160000 occurrences of 3-clauses need no derivative rows (the gather
+    recomputes them), so the fixed array is not a limit for them; results
+    equal the allocating entry point's."""
+    inst = synth.random_ksat(20000, 53334, 3, synth.rng_for(400, 1))
+    assert inst.n_lits > 131072
+    h = bd.load_instance(inst)
+    x = _dev(synth.uniform_x0(inst.n, 64, 3))
+    fe_ref, g_ref = bd.eval_fe_grad(h, x)
+    fe = torch.empty_like(fe_ref)
+    g = torch.empty_like(g_ref)
+    bd.eval_fe_grad_noalloc(h, x, fe, g)
+    torch.cuda.synchronize()
+    assert torch.equal(fe, fe_ref) and torch.equal(g, g_ref)
