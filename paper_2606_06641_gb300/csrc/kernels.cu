@@ -612,12 +612,17 @@ __global__ void __launch_bounds__(256, 5) csr_update_vec4_kernel(CsrArgs a) {
 // The fused pass: warps stride over the (variable, 128-restart tile) tasks and
 // store the summed derivatives of each variable's fused occurrences (4
 // restarts per lane) into gf. The gathers are plain vector loads, FUSED_FB
-// occurrences (2 rows each) in flight per warp.
+// occurrences (2 rows each) in flight per warp. A staged variant (per-warp
+// cp.async.bulk copies of the 512-byte row segments into shared memory,
+// double-buffered on mbarriers) measured slower than these loads.
+// (two occurrences in flight and 128-thread blocks measured best: more
+// resident warps beat deeper per-warp batches for these L2 gathers)
 template <typename XT>
-constexpr int FUSED_FB = sizeof(XT) == 4 ? 4 : 2;
+constexpr int FUSED_FB = 2;
+constexpr int FUSED_THREADS = 128;
 
 template <typename XT>
-__global__ void __launch_bounds__(256) fused_grad_kernel(CsrArgs a) {
+__global__ void __launch_bounds__(FUSED_THREADS) fused_grad_kernel(CsrArgs a) {
   pdl_wait();
   pdl_trigger();
   const int lane = threadIdx.x & 31;
@@ -655,13 +660,14 @@ void launch_fused_grad(const CsrArgs& a, int xt, cudaStream_t s) {
   const long long tasks = static_cast<long long>((a.nb + 127) / 128) * a.v_count;
   if (tasks == 0) return;
   if (tasks >= (1ll << 32) - 4096LL * 1024) return;  // (never for instances that load)
-  long long blocks = (tasks + 7) / 8;
+  constexpr int W = FUSED_THREADS / 32;
+  long long blocks = (tasks + W - 1) / W;
   if (xt == XT_F32) {
-    blocks = std::min(blocks, resident_blocks(fused_grad_kernel<float>, 256));
-    launch_pdl(fused_grad_kernel<float>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+    blocks = std::min(blocks, resident_blocks(fused_grad_kernel<float>, FUSED_THREADS));
+    launch_pdl(fused_grad_kernel<float>, dim3(static_cast<unsigned>(blocks)), dim3(FUSED_THREADS), 0, s, a);
   } else {
-    blocks = std::min(blocks, resident_blocks(fused_grad_kernel<__nv_bfloat16>, 256));
-    launch_pdl(fused_grad_kernel<__nv_bfloat16>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+    blocks = std::min(blocks, resident_blocks(fused_grad_kernel<__nv_bfloat16>, FUSED_THREADS));
+    launch_pdl(fused_grad_kernel<__nv_bfloat16>, dim3(static_cast<unsigned>(blocks)), dim3(FUSED_THREADS), 0, s, a);
   }
 }
 
