@@ -100,6 +100,8 @@ struct CheckArgs {
   const int4* ranges;       // {c_begin, c_end, instance, 0}
   int n_ranges;
   unsigned* vword;
+  int* unsat;               // non-null: count mode, unsat[inst * B + b] += violated constraints
+  int B;                    // restarts per instance (count mode)
 };
 void launch_check_bits(const CheckArgs& a, cudaStream_t s);
 
@@ -109,19 +111,6 @@ void launch_solved_words(const unsigned* vword, int n_inst, int W, int B, unsign
 // p[0..n) = v
 void launch_fill_int(int* p, int v, long long n, cudaStream_t s);
 
-// Exact check of the sign-rounded state.
-struct VerifyArgs {
-  const void* x;
-  long long x_pitch;
-  int B;                    // restarts
-  const int* lit_enc;       // load order literals, var << 1 | negated
-  const int* lit_off;       // load order constraint offsets
-  const int* viol_off;      // per constraint offset into viol
-  const unsigned char* viol;  // viol[viol_off[c] + t] = 1 where f(t) = +1
-  const int4* ranges;       // {c_begin, c_end, instance, 0}
-  int n_ranges;
-  int* unsat;               // unsat[inst * B + b]
-};
 
 // Launch wrappers (kernels.cu / short_*.cu).
 // Return false if no kernel exists for (k, rpl).
@@ -137,7 +126,6 @@ void launch_csr_update(const CsrArgs& a, int xt, cudaStream_t s);
 // The fused occurrences' summed derivatives of every variable for the chunk
 // (reads x_t only, so it runs beside the FE launches) into a.gf.
 void launch_fused_grad(const CsrArgs& a, int xt, cudaStream_t s);
-void launch_verify(const VerifyArgs& a, int xt, cudaStream_t s);
 void launch_solved(const int* unsat, int n_inst, int B, int* solved, cudaStream_t s);
 void launch_init_philox(void* x, int xt, long long x_pitch, int n, int B, const int* var_inst,
                         unsigned long long seed, cudaStream_t s);

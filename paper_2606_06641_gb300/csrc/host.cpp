@@ -154,8 +154,8 @@ struct afs_handle {
   double work_per_restart = 0.0;
   // device instance data
   DevBuf litslot, cons_tab, cons_orig, cons_k, cons_lit, coef, csr_off, lit_enc, lit_off, viol_off, viol,
-      ranges, var_inst, err, chk_em, chk_ranges, fus_off, fus;
-  int n_ranges = 0, n_chk_ranges = 0;
+      var_inst, err, chk_em, chk_ranges, fus_off, fus;
+  int n_chk_ranges = 0;
   // restart state
   int B = 0, xt = XT_F32;
   long long pitch = 0;
@@ -430,18 +430,6 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     h->h_cparity[g] = shape[g].parity;
   }
   h->h_viol = violv;
-  std::vector<int4> ranges;
-  for (int i = 0; i < n_inst; ++i) {
-    int c = h->inst_cbegin[i];
-    const int ce = h->inst_cbegin[i + 1];
-    while (c < ce) {
-      int e = c, lits_in = 0;
-      while (e < ce && (e == c || (lits_in + gk[e] <= 48 && e - c < 8))) lits_in += gk[e++];
-      ranges.push_back(make_int4(c, e, i, 0));
-      c = e;
-    }
-  }
-  h->n_ranges = static_cast<int>(ranges.size());
   // bit-sliced check: counts to test per constraint (the violated ones, or
   // the satisfied ones with bit 63 set when fewer); ranges of <= 32 literals
   // and < 32 constraints, a longer constraint alone
@@ -489,7 +477,6 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   if ((rc = upload(h->lit_off, h->h_lit_off, s))) return rc;
   if ((rc = upload(h->viol_off, viol_off, s))) return rc;
   if ((rc = upload(h->viol, violv, s))) return rc;
-  if ((rc = upload(h->ranges, ranges, s))) return rc;
   if ((rc = upload(h->var_inst, var_inst_ext, s))) return rc;
   if ((rc = upload(h->chk_em, chk_em, s))) return rc;
   if ((rc = upload(h->chk_ranges, chk_ranges, s))) return rc;
@@ -623,21 +610,26 @@ static int launch_fused(afs_handle* h, const void* x, int b0, int nb, cudaStream
   return AFS_OK;
 }
 
-// Standalone exact check of the current state into h->unsat, solved flags updated.
+// Standalone exact check of the state x (whose sign words are current) into
+// h->unsat: the bit-sliced check in count mode, then the solved fold.
 static int launch_check(afs_handle* h, const void* x, cudaStream_t s) {
+  (void)x;
   CK(cudaMemsetAsync(h->unsat.p, 0, sizeof(int) * static_cast<size_t>(h->n_inst) * h->B, s));
-  VerifyArgs v{};
-  v.x = x;
-  v.x_pitch = h->pitch;
-  v.B = h->B;
-  v.lit_enc = h->lit_enc.as<int>();
-  v.lit_off = h->lit_off.as<int>();
-  v.viol_off = h->viol_off.as<int>();
-  v.viol = h->viol.as<unsigned char>();
-  v.ranges = h->ranges.as<int4>();
-  v.n_ranges = h->n_ranges;
-  v.unsat = h->unsat.as<int>();
-  launch_verify(v, h->xt, s);
+  CheckArgs c{};
+  c.sgn = h->sgn.as<unsigned>();
+  c.W = h->W;
+  c.w0 = 0;
+  c.wc = h->W;
+  c.lit_enc = h->lit_enc.as<int>();
+  c.lit_off = h->lit_off.as<int>();
+  c.em = h->chk_em.as<unsigned long long>();
+  c.viol_off = h->viol_off.as<int>();
+  c.viol = h->viol.as<unsigned char>();
+  c.ranges = h->chk_ranges.as<int4>();
+  c.n_ranges = h->n_chk_ranges;
+  c.unsat = h->unsat.as<int>();
+  c.B = h->B;
+  launch_check_bits(c, s);
   CKL();
   launch_solved(h->unsat.as<int>(), h->n_inst, h->B, h->solved.as<int>(), s);
   CKL();

@@ -800,11 +800,16 @@ __device__ __forceinline__ void check_stage(const CheckArgs& a, const unsigned* 
 
 // A warp handles one range (<= 32 literals, or one longer constraint) for 32
 // words: lane j owns word w0 + 32*blockIdx.y + j. The range's literal words
-// are staged in shared memory, then the constraints are counted from there;
-// the warps of a block OR their results per instance before the atomic.
+// are staged in shared memory, then the constraints are counted from there.
+// COUNT = false: the violation words of the range are ORed, and the warps of
+// a block merge them per instance before the atomic OR into vword. COUNT =
+// true (the exact unsat count of the final state): the violation words are
+// added into 5 bit planes (a range has < 32 constraints), and the block adds
+// the per-restart counts of its warps per instance into unsat.
+template <bool COUNT>
 __global__ void __launch_bounds__(CHECK_WARPS * 32) check_bits_kernel(CheckArgs a) {
   __shared__ unsigned stage[CHECK_WARPS][CHECK_STAGE][32];
-  __shared__ unsigned bad_s[CHECK_WARPS][32];
+  __shared__ unsigned bad_s[CHECK_WARPS][COUNT ? 5 : 1][32];
   __shared__ int inst_s[CHECK_WARPS];
   pdl_wait();
   pdl_trigger();
@@ -814,6 +819,7 @@ __global__ void __launch_bounds__(CHECK_WARPS * 32) check_bits_kernel(CheckArgs 
   const bool act = wl < a.wc;
   const int w = a.w0 + (act ? wl : 0);
   unsigned bad = 0u;
+  unsigned C[5] = {0u, 0u, 0u, 0u, 0u};  // COUNT: violated constraints per restart, bit planes
   int inst = -1;
   if (rgi < a.n_ranges) {  // uniform per warp
     const int4 rg = __ldg(a.ranges + rgi);
@@ -838,7 +844,18 @@ __global__ void __launch_bounds__(CHECK_WARPS * 32) check_bits_kernel(CheckArgs 
 #pragma unroll
         for (int p = 0; p < CHECK_PLANES; ++p) P[p] = 0u;
         add_words<6>(P, st + a0 * 32, k, np);  // k <= 32 here
-        bad |= violated_word(P, k, np, em, nullptr);
+        const unsigned vb = violated_word(P, k, np, em, nullptr);
+        if constexpr (COUNT) {
+          unsigned carry = vb;
+#pragma unroll
+          for (int p = 0; p < 5; ++p) {
+            const unsigned t = C[p] & carry;
+            C[p] ^= carry;
+            carry = t;
+          }
+        } else {
+          bad |= vb;
+        }
       }
     } else {  // one long constraint, staged 32 literals at a time
       const int k = l1 - l0;
@@ -852,11 +869,41 @@ __global__ void __launch_bounds__(CHECK_WARPS * 32) check_bits_kernel(CheckArgs 
         __syncwarp();
       }
       bad = violated_word(P, k, np, __shfl_sync(0xffffffffu, emv, 0), a.viol + __ldg(a.viol_off + rg.x));
+      C[0] = bad;
     }
   }
-  bad_s[wp][lane] = act ? bad : 0u;
+  if constexpr (COUNT) {
+#pragma unroll
+    for (int p = 0; p < 5; ++p) bad_s[wp][p][lane] = act ? C[p] : 0u;
+  } else {
+    bad_s[wp][0][lane] = act ? bad : 0u;
+  }
   if (lane == 0) inst_s[wp] = inst;
   __syncthreads();
+  if constexpr (COUNT) {
+    // thread t: word lane t & 31, restarts j = t >> 5, + CHECK_WARPS, ...
+    const int wl2 = threadIdx.x & 31;
+    const int ww = a.w0 + blockIdx.y * 32 + wl2;
+    if (blockIdx.y * 32 + wl2 >= a.wc) return;
+    for (int j = threadIdx.x >> 5; j < 32; j += CHECK_WARPS) {
+      const int b = ww * 32 + j;
+      if (b >= a.B) break;
+      int cnt = 0, cur = -1;
+      for (int q = 0; q < CHECK_WARPS; ++q) {
+        const int iq = inst_s[q];
+        if (iq < 0) continue;
+        if (iq != cur) {
+          if (cur >= 0 && cnt) atomicAdd(a.unsat + static_cast<long long>(cur) * a.B + b, cnt);
+          cur = iq;
+          cnt = 0;
+        }
+#pragma unroll
+        for (int p = 0; p < 5; ++p) cnt += static_cast<int>((bad_s[q][p][wl2] >> j) & 1u) << p;
+      }
+      if (cur >= 0 && cnt) atomicAdd(a.unsat + static_cast<long long>(cur) * a.B + b, cnt);
+    }
+    return;
+  }
   if (wp == 0 && act) {
     unsigned acc = 0u;
     int cur = -1;
@@ -868,7 +915,7 @@ __global__ void __launch_bounds__(CHECK_WARPS * 32) check_bits_kernel(CheckArgs 
         cur = ij;
         acc = 0u;
       }
-      acc |= bad_s[j][lane];
+      acc |= bad_s[j][0][lane];
     }
     if (cur >= 0 && acc) atomicOr(a.vword + static_cast<long long>(cur) * a.W + w, acc);
   }
@@ -878,63 +925,10 @@ void launch_check_bits(const CheckArgs& a, cudaStream_t s) {
   if (a.n_ranges == 0 || a.wc == 0) return;
   const dim3 grid(static_cast<unsigned>((a.n_ranges + CHECK_WARPS - 1) / CHECK_WARPS),
                   static_cast<unsigned>((a.wc + 31) / 32));
-  launch_pdl(check_bits_kernel, grid, dim3(CHECK_WARPS * 32), 0, s, a);
+  if (a.unsat != nullptr) launch_pdl(check_bits_kernel<true>, grid, dim3(CHECK_WARPS * 32), 0, s, a);
+  else launch_pdl(check_bits_kernel<false>, grid, dim3(CHECK_WARPS * 32), 0, s, a);
 }
 
-// ---------------------------------------------------------------------------
-// Exact check (Algorithm 1's unsat count at the sign-rounded point):
-// literal true iff (x_v < 0) xor negated; constraint violated iff
-// viol[t] = 1 for its true count t. One warp per (range of constraints of
-// one instance, 32 restarts); one atomic add per lane per range.
-// ---------------------------------------------------------------------------
-template <typename XT>
-__global__ void __launch_bounds__(256) verify_kernel(VerifyArgs a) {
-  pdl_wait();
-  pdl_trigger();
-  const int lane = threadIdx.x & 31;
-  const long long warp = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int tiles = (a.B + 31) >> 5;
-  const long long rgi = warp / tiles;
-  if (rgi >= a.n_ranges) return;
-  const int tile = static_cast<int>(warp - rgi * tiles);
-  const int b = tile * 32 + lane;
-  const bool act = b < a.B;
-  const int4 rg = __ldg(a.ranges + rgi);
-  const XT* x = static_cast<const XT*>(a.x);
-  int count = 0;
-  const XT* xb = x + (act ? b : 0);
-  for (int c = rg.x; c < rg.y; ++c) {
-    const int l0 = __ldg(a.lit_off + c), l1 = __ldg(a.lit_off + c + 1);
-    int t = 0;
-    int l = l0;
-    for (; l + 3 < l1; l += 4) {  // four independent gathers in flight
-      const int e0 = __ldg(a.lit_enc + l), e1 = __ldg(a.lit_enc + l + 1);
-      const int e2 = __ldg(a.lit_enc + l + 2), e3 = __ldg(a.lit_enc + l + 3);
-      const float x0 = load_x<XT>(xb + static_cast<long long>(e0 >> 1) * a.x_pitch);
-      const float x1 = load_x<XT>(xb + static_cast<long long>(e1 >> 1) * a.x_pitch);
-      const float x2 = load_x<XT>(xb + static_cast<long long>(e2 >> 1) * a.x_pitch);
-      const float x3 = load_x<XT>(xb + static_cast<long long>(e3 >> 1) * a.x_pitch);
-      t += (static_cast<int>(x0 < 0.0f) ^ (e0 & 1)) + (static_cast<int>(x1 < 0.0f) ^ (e1 & 1)) +
-           (static_cast<int>(x2 < 0.0f) ^ (e2 & 1)) + (static_cast<int>(x3 < 0.0f) ^ (e3 & 1));
-    }
-    for (; l < l1; ++l) {
-      const int enc = __ldg(a.lit_enc + l);
-      const float xv = load_x<XT>(xb + static_cast<long long>(enc >> 1) * a.x_pitch);
-      t += static_cast<int>(xv < 0.0f) ^ (enc & 1);
-    }
-    count += __ldg(a.viol + __ldg(a.viol_off + c) + t);
-  }
-  if (act && count > 0) atomicAdd(a.unsat + static_cast<long long>(rg.z) * a.B + b, count);
-}
-
-void launch_verify(const VerifyArgs& a, int xt, cudaStream_t s) {
-  const long long tiles = (a.B + 31) / 32;
-  const long long nwarps = tiles * a.n_ranges;
-  const long long blocks = (nwarps + 7) / 8;
-  if (blocks == 0) return;
-  if (xt == XT_F32) launch_pdl(verify_kernel<float>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
-  else launch_pdl(verify_kernel<__nv_bfloat16>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
-}
 
 __global__ void solved_words_kernel(const unsigned* vword, int n_inst, int W, int B, unsigned* out) {
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
