@@ -429,9 +429,9 @@ def run_ours(args):
     peaks, peak_src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tinst = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
-    # the FE+gradient work is done by the FE launches of the length buckets and,
-    # for constraints with k <= 3, inside the CSR pass (their derivatives are
-    # recomputed there): time both phases
+    # the FE+gradient work is done by the FE launches of the length buckets,
+    # the fused pass (the derivatives of 3-literal constraints, recomputed
+    # per variable beside them) and the CSR pass: time both phases
     grad_ms_step = fe_ms_step + csr_ms / K
     achieved = work / (grad_ms_step * 1e-3) / 1e12 if grad_ms_step > 0 else 0.0
     traffic = None
@@ -487,7 +487,7 @@ def run_ours(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
                          "frac": achieved / peak_tinst if peak_tinst else None, "traffic": traffic,
                          "kernel": "FE+gradient work of a step: the FE launches of the length buckets plus the "
-                                   "CSR pass (gather, step, and the recomputed derivatives of constraints with k <= 3)",
+                                   "fused pass (recomputed derivatives of 3-literal constraints) and the CSR pass",
                          "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
                                        f"(max SM clock, {peak_src})",
                          "fe_ms_per_step": fe_ms_step, "csr_ms_per_step": csr_ms / K,

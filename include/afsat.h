@@ -136,12 +136,14 @@ int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_d
 
 /* afs_step: nsteps iterations of Algorithm 1 with the fixed step eta for all
  * restarts: FE and gradient (Sec. 2.1.2), x <- clamp(x - eta * grad, -1, 1).
- * With verify_every != 0 each iteration also counts, in the same pass, the
- * violated constraints of the sign-rounded state it reads; a restart with
- * none is solved and is not moved again (Algorithm 1 returns on is_sat), and
- * the call ends with an exact check of the final state (afs_get_verify).
- * Replayed as a captured CUDA graph when use_graph is set (the first call for
- * a given nsteps and step parity captures). */
+ * With verify_every != 0 each iteration also checks exactly, beside its FE
+ * launches, the sign-rounded state it reads (Algorithm 1's is_sat, computed
+ * on packed sign words 32 restarts at a time); a restart that violates
+ * nothing is solved and is not moved again (Algorithm 1 returns on is_sat),
+ * and the call ends with an exact count of the final state's violated
+ * constraints (afs_get_verify). Replayed as a captured CUDA graph when
+ * use_graph is set (the first call for a given nsteps and step parity
+ * captures). */
 int afs_step(afs_handle* h, int32_t nsteps, void* stream);
 
 /* afs_round_and_verify: sign-round every restart (x < 0 -> True), count the
@@ -195,7 +197,7 @@ int afs_eval_fe_grad(afs_handle* h, const void* x_dev, int32_t x_dtype, int32_t 
  * processed in chunks of 32..256 columns sized to that array; an instance
  * whose occurrences with derivative rows x 32 restarts x 4 bytes exceed
  * 16 MiB (more than 131072 of them) is rejected with AFS_E_ARG. Occurrences
- * in constraints of length <= 3 (probability-generating basis) need no row:
+ * in constraints of length 3 (probability-generating basis) need no row:
  * their derivatives are recomputed in the gather. The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture. All calls share the one array

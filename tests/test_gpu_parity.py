@@ -366,9 +366,9 @@ def test_step_host_matches_device_step():
     np.testing.assert_array_equal(un.numpy(), un_dev.cpu().numpy())
 
 
-# ---- constraints with k <= 3: derivatives recomputed in the CSR pass ----------
+# ---- 3-literal constraints: derivatives recomputed in the gather --------------
 def test_fused_gradient_without_fe_values():
-    """Gradient-only evaluation (no FE kernel for the k <= 3 buckets) equals the
+    """Gradient-only evaluation (no FE kernel for the k = 3 bucket) equals the
     oracle and the gradient of the full evaluation."""
     inst = synth.mixed_small(2, n=30, m=80, kmax=5)
     x = synth.uniform_x0(inst.n, 70, 21)
@@ -383,8 +383,8 @@ def test_fused_gradient_without_fe_values():
 
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_fused_lengths_with_repeated_variables(k):
-    """Every fused length, with a variable repeated inside a constraint and
-    complementary literals, through the step path and the evaluation path."""
+    """Short lengths around the fused one (k = 1, 2 through the FE kernels, k = 3
+    fused), with repeated and complementary literals, through the step and evaluation paths."""
     b = synth._Builder(6)
     rng = np.random.default_rng(k)
     for _ in range(40):
@@ -402,7 +402,7 @@ def test_fused_lengths_with_repeated_variables(k):
 
 
 def test_fused_and_unfused_steps_agree(monkeypatch):
-    """The same steps with the k <= 3 derivatives recomputed in the CSR pass and
+    """The same steps with the k = 3 derivatives recomputed in the fused pass and
     with them written as occurrence rows by the FE kernel."""
     inst = synth.hybrid_n2000(1)
     B = 256
