@@ -664,6 +664,10 @@ static void launch_check_step(afs_handle* h, int p, cudaStream_t s) {
   launch_check_bits(c, s);
 }
 
+// The fused pass is enqueued before the FE launches of a chunk (true) or after
+// them (false); the order decides which kernel the block scheduler serves first.
+constexpr bool FUSED_FIRST = true;
+
 // Enqueue nsteps of the descent loop on s (used both directly and under
 // capture). Step t reads the state x_t and has parity p = (parity0 + t) & 1.
 // With `check`, the bit-sliced exact check of x_t (violation words of parity
@@ -689,12 +693,18 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int p
       const bool fus_now = h->n_fused > 0;
       const bool fork = conc && (G > 1 || chk_now || fus_now);
       if (fork) CK(cudaEventRecord(h->ev_fork, s));
-      if (fus_now) {
+      auto fused_now = [&]() -> int {
+        if (!fus_now) return AFS_OK;
         if (conc) CK(cudaStreamWaitEvent(h->fus_s, h->ev_fork, 0));
         int rc = launch_fused(h, h->xb[p].p, b0, nb, conc ? h->fus_s : s);
         if (rc) return rc;
         ++nl;
         if (conc) CK(cudaEventRecord(h->ev_fus, h->fus_s));
+        return AFS_OK;
+      };
+      if (FUSED_FIRST) {
+        int rc = fused_now();
+        if (rc) return rc;
       }
       if (chk_now) {
         if (conc) CK(cudaStreamWaitEvent(h->chk, h->ev_fork, 0));
@@ -716,6 +726,10 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int p
         int rc = launch_fe_group(h, g, h->xb[p].p, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, nullptr, 0, st);
         if (rc) return rc;
         ++nl;
+      }
+      if (!FUSED_FIRST) {
+        int rc = fused_now();
+        if (rc) return rc;
       }
       for (int a = 0; a < used; ++a) {
         CK(cudaEventRecord(h->ev_join[a], h->aux[a]));

@@ -621,7 +621,8 @@ template <typename XT>
 constexpr int FUSED_FB = 2;
 constexpr int FUSED_THREADS = 128;
 // the persistent grid takes 1/FUSED_GRID_DIV of the resident-block slots, so
-// that the FE launches running beside it find SMs free
+// that the FE launches running beside it find SMs free (0: one block per 4
+// tasks, no persistent grid)
 constexpr int FUSED_GRID_DIV = 1;
 
 template <typename XT>
@@ -666,11 +667,13 @@ void launch_fused_grad(const CsrArgs& a, int xt, cudaStream_t s) {
   constexpr int W = FUSED_THREADS / 32;
   long long blocks = (tasks + W - 1) / W;
   if (xt == XT_F32) {
-    blocks = std::min(blocks, std::max(1LL, resident_blocks(fused_grad_kernel<float>, FUSED_THREADS) / FUSED_GRID_DIV));
+    if (FUSED_GRID_DIV > 0)
+      blocks = std::min(blocks, std::max(1LL, resident_blocks(fused_grad_kernel<float>, FUSED_THREADS) / FUSED_GRID_DIV));
     launch_pdl(fused_grad_kernel<float>, dim3(static_cast<unsigned>(blocks)), dim3(FUSED_THREADS), 0, s, a);
   } else {
-    blocks = std::min(blocks,
-                      std::max(1LL, resident_blocks(fused_grad_kernel<__nv_bfloat16>, FUSED_THREADS) / FUSED_GRID_DIV));
+    if (FUSED_GRID_DIV > 0)
+      blocks = std::min(blocks,
+                        std::max(1LL, resident_blocks(fused_grad_kernel<__nv_bfloat16>, FUSED_THREADS) / FUSED_GRID_DIV));
     launch_pdl(fused_grad_kernel<__nv_bfloat16>, dim3(static_cast<unsigned>(blocks)), dim3(FUSED_THREADS), 0, s, a);
   }
 }
