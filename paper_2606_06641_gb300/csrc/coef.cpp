@@ -190,11 +190,21 @@ void build_table(const Shape& s, int basis, int form, std::vector<float>& out) {
   const int mid = N / 2;
   if (form == FORM_SHORT) {
     if (basis == BASIS_PGF) {
-      // head: {c0, number of scaled complex roots, 0, 0}
+      // head: {c0, number of scaled complex roots stored, 0, 0}. A scaled
+      // table keeps only the roots whose coefficient is not zero: a truth
+      // table with a sparse spectrum (parity: the single root w = -1) costs
+      // only its nonzero roots. The exact zeros of such spectra come out of
+      // the FP64 DFT as rounding residue (|ft_j| ~ 1e-16); anything at or
+      // below ZERO_ROOT (each root contributes at most 2 |ft_j|) is dropped.
+      constexpr double ZERO_ROOT = 1e-13;
       const bool scaled = k <= KSCALED_MAX;
-      push4(out, cr[0], scaled ? k / 2 : 0, 0, 0);
+      int kept = 0;
+      for (int j = 1; j <= k / 2; ++j)
+        if (!scaled || std::hypot(cr[j], ci[j]) > ZERO_ROOT) ++kept;
+      push4(out, cr[0], scaled ? kept : 0, 0, 0);
       if (odd) push4(out, 0.0, cr[mid], 0, 0);
       for (int j = 1; j <= k / 2; ++j) {
+        if (scaled && std::hypot(cr[j], ci[j]) <= ZERO_ROOT) continue;
         // a_j + b_j l = b_j (l + i*gamma_j), gamma_j = cot(pi j/N); E_j = 2 ft_j b_j^k.
         // For k <= KSCALED_MAX the factor is stored scaled, b_j (l + i gamma)
         // = b_j gamma (w + i) with w = l tan(pi j/N), so that a complex
@@ -268,11 +278,13 @@ void build_table(const Shape& s, int basis, int form, std::vector<float>& out) {
   }
 }
 
-double work_instr(int k) {
+double work_instr(int k, int complex_roots) {
   // per complex root: prefix (4) and suffix (4) complex products and the
   // gradient combine (2) per literal, plus 2 for the value; per real root:
   // 3 per literal plus 1.
-  return static_cast<double>(k / 2) * (10.0 * k + 2.0) + static_cast<double>(k & 1) * (3.0 * k + 1.0);
+  return static_cast<double>(complex_roots) * (10.0 * k + 2.0) + static_cast<double>(k & 1) * (3.0 * k + 1.0);
 }
+
+double work_instr(int k) { return work_instr(k, k / 2); }
 
 }  // namespace afs

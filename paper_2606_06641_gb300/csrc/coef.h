@@ -54,5 +54,7 @@ void build_table(const Shape& s, int basis, int form, std::vector<float>& out);
 // Algorithmic FP32 lane instructions of one FE+gradient evaluation of a
 // constraint of length k for one restart (see the kernels' cost model).
 double work_instr(int k);
+// The same with the number of complex roots a table actually keeps.
+double work_instr(int k, int complex_roots);
 
 }  // namespace afs

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
     // a running product times the factor is two FMAs; the gradient products
     // have k - 1 factors and start from E' / gamma
     constexpr bool SCALED = !SHIFT && K <= KSCALED_MAX;
-    const int ns = SCALED ? NC : 0;
+    const int ns = SCALED ? static_cast<int>(head.y) : 0;  // roots stored (zero ones dropped)
 #pragma unroll 1
     for (int j = 0; j < ns; ++j) {
       const float4 cc = __ldg(tab + 1 + NREAL + j);

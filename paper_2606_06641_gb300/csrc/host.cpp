@@ -336,6 +336,12 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     return gk[a] > gk[b];
   });
   std::vector<int> b_tab(m), b_orig(m), b_k(m), b_lit(m);
+  // the work model counts the complex roots a short scaled table keeps
+  auto cons_work = [&](int g) {
+    const int k = gk[g];
+    const bool scaled = h->p.basis == AFS_BASIS_PGF && k <= KSHORT && k <= KSCALED_MAX;
+    return work_instr(k, scaled ? static_cast<int>(coef[4 * static_cast<size_t>(cons_tab_load[g]) + 1]) : k / 2);
+  };
   std::vector<int2> litslot;
   litslot.reserve(L + m);
   h->work_per_restart = 0.0;
@@ -354,7 +360,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     b_lit[pos] = static_cast<int>(litslot.size());
     for (int t = 0; t < k; ++t) litslot.push_back(make_int2(enc_of(ginst[g], lits[goff[g] + t]), -1));
     if (k > KSHORT && (k & 1)) litslot.push_back(make_int2(0, 0));
-    h->work_per_restart += work_instr(k);
+    h->work_per_restart += cons_work(g);
     const bool is_long = k > KSHORT;
     Group* last = h->groups.empty() ? nullptr : &h->groups.back();
     if (last && last->is_long == is_long && (is_long || last->k == k)) {
@@ -368,7 +374,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     std::vector<double> work(h->groups.size(), 0.0);
     for (size_t gi = 0; gi < h->groups.size(); ++gi)
       for (int c = h->groups[gi].c_begin; c < h->groups[gi].c_begin + h->groups[gi].c_count; ++c)
-        work[gi] += work_instr(b_k[c]);
+        work[gi] += cons_work(b_orig[c]);
     h->order.resize(h->groups.size());
     for (size_t gi = 0; gi < h->groups.size(); ++gi) h->order[gi] = static_cast<int>(gi);
     std::stable_sort(h->order.begin(), h->order.end(), [&](int a, int b) { return work[a] > work[b]; });

@@ -401,7 +401,8 @@ __device__ __forceinline__ void fused_sum(const CsrArgs& a, int v, long long col
       const float s1 = (e[u].x & 1) ? -1.0f : 1.0f, s2 = (e[u].y & 1) ? -1.0f : 1.0f;
       const float ss = (e[u].w & 1) ? -1.0f : 1.0f;
       const float Es = __ldg(&tab[1].y) * (s1 * s2);  // real root, the other signs folded
-      const float4 cc = __ldg(tab + 2);                // complex pair {tan, 0, E'}
+      // the complex pair {tan, 0, E'}, absent when its coefficient is zero
+      const float4 cc = __ldg(&tab[0].y) > 0.5f ? __ldg(tab + 2) : make_float4(0.f, 0.f, 0.f, 0.f);
       const float ia1 = cc.x * s1, ia2 = cc.x * s2;
       const float p0r = cc.z * cc.x, p0i = cc.w * cc.x;
 #pragma unroll

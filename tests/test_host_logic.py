@@ -55,7 +55,9 @@ def _eval_short(tab, k, esp, ell):
         for i in range(k):
             grad[:, i] += E * np.delete(f, i, axis=1).prod(axis=1)
     n_scaled = 0 if esp else int(t[0, 1])
-    for j in range(k // 2):
+    # scaled tables (PGF, k <= 24) store only their nonzero complex roots
+    n_complex = n_scaled if (not esp and k <= 24) else k // 2
+    for j in range(n_complex):
         if j < n_scaled:  # factor (w + i), w = l / gamma, stored as 1/gamma
             inv_gam, _, er, ei = t[1 + nreal + j]
             E = er + 1j * ei
@@ -171,8 +173,12 @@ def test_pgf_table_has_exact_conjugate_roots():
         t = bd.coef_table(O.T_CARD, k, O.OP_GE, k // 2).reshape(-1, 4)
         ang = np.pi * np.arange(1, k // 2 + 1) / (k + 1)
         if k <= 24:
-            assert t[0, 1] == k // 2
-            np.testing.assert_allclose(t[2:, 0], np.tan(ang).astype(np.float32), rtol=2e-7)
+            # the stored roots are a subsequence of j = 1..k/2 (zero ones dropped)
+            assert 1 <= t[0, 1] <= k // 2 and t.shape[0] == 2 + int(t[0, 1])
+            tans = np.tan(ang).astype(np.float32)
+            idx = [int(np.argmin(np.abs(tans - v))) for v in t[2:, 0]]
+            assert idx == sorted(set(idx))
+            np.testing.assert_allclose(t[2:, 0], tans[idx], rtol=2e-7)
             assert np.all(t[2:, 1] == 0.0)
         else:
             assert t[0, 1] == 0
@@ -208,6 +214,23 @@ def test_overlong_constraint_rejected():
     with pytest.raises(bd.AfsError) as ei:
         bd.load_instance(b.build(), stream=0)
     assert ei.value.code == -3
+
+
+def test_parity_tables_keep_only_the_nonzero_root():
+    """The spectrum of an odd-length parity constraint is the single root
+    w = -1: a scaled table stores no complex root whose coefficient is zero,
+    and it still reproduces the oracle."""
+    rng = np.random.default_rng(7)
+    for k in (3, 5, 7, 9):
+        for par in (0, 1):
+            tab = bd.coef_table(O.T_XOR, k, 0, 0, par, basis=bd.BASIS_PGF, form=0)
+            t = tab.reshape(-1, 4)
+            assert t[0, 1] == 0 and t.shape[0] == 2   # head and the real root only
+            ell = rng.uniform(-1, 1, (4, k))
+            fe, g = _eval_short(tab, k, False, ell)
+            ref_fe, ref_g = O.fe_and_dfe(O.truth_table(O.T_XOR, k, 0, 0, par), ell)
+            np.testing.assert_allclose(fe, ref_fe, atol=2e-6, rtol=0)
+            np.testing.assert_allclose(g, ref_g, atol=2e-6, rtol=0)
 
 
 def test_tile_spec_round_trip():
