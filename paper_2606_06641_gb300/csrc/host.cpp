@@ -673,6 +673,9 @@ static void launch_check_step(afs_handle* h, int p, cudaStream_t s) {
 // The fused pass is enqueued before the FE launches of a chunk (true) or after
 // them (false); the order decides which kernel the block scheduler serves first.
 constexpr bool FUSED_FIRST = true;
+// The FE buckets after the first (largest-work) one run on forked streams
+// (true) or follow it on the step's stream (false).
+constexpr bool BUCKETS_ON_AUX = true;
 
 // Enqueue nsteps of the descent loop on s (used both directly and under
 // capture). Step t reads the state x_t and has parity p = (parity0 + t) & 1.
@@ -723,7 +726,7 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int p
       for (int gi = 0; gi < G; ++gi) {
         const Group& g = h->groups[h->step_order[gi]];
         cudaStream_t st = s;
-        if (fork && gi > 0) {
+        if (fork && gi > 0 && BUCKETS_ON_AUX) {
           const int a = (gi - 1) % afs_handle::NAUX;
           if (gi - 1 < afs_handle::NAUX) CK(cudaStreamWaitEvent(h->aux[a], h->ev_fork, 0));
           st = h->aux[a];
