@@ -416,3 +416,22 @@ def test_fused_and_unfused_steps_agree(monkeypatch):
         outs.append(bd.get_x(h).cpu().numpy())
         h.free()
     assert np.abs(outs[0] - outs[1]).max() <= 1e-5
+
+
+def test_parsed_hybrid_file_end_to_end():
+    """An instance read from the hybrid format runs through the library: FE,
+    gradient and the exact check agree with the oracle."""
+    from paper_2606_06641_gb300 import dimacs
+    text = "\n".join([
+        "p cnf 12 9",
+        "h 1 -2 3 0", "x 2 4 -5 6 0", "nae 1 7 8 0", "amo -3 9 10 0", "e 4 11 12 0",
+        "ek 2 1 5 9 12 0", "card >=3 2 3 6 7 8 0", "card <=1 10 11 -12 0", "d -2 1 4 8 0",
+    ])
+    inst = dimacs.parse(text).inst
+    x = synth.uniform_x0(inst.n, 64, 77)
+    _check_eval(inst, x)
+    h = bd.load_instance(inst, bd.default_params(eta=0.1, autotune=0))
+    bd.init_restarts(h, 64, x0=_dev(x))
+    bd.step(h, 20)
+    un, best, asg, sol = bd.round_and_verify(h)
+    np.testing.assert_array_equal(un[0], O.unsat_count(inst, bd.get_x(h).cpu().numpy()))
