@@ -363,10 +363,17 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     h->work_per_restart += cons_work(g);
     const bool is_long = k > KSHORT;
     Group* last = h->groups.empty() ? nullptr : &h->groups.back();
-    if (last && last->is_long == is_long && (is_long || last->k == k)) {
+    // long constraints (sorted by decreasing length) are grouped by the power
+    // of two above their length, so each launch sizes its shared memory to
+    // the group's longest constraint (its k)
+    auto pow2_class = [](int kk) {
+      int c = 1;
+      while (c < kk) c <<= 1;
+      return c;
+    };
+    if (last && last->is_long == is_long && (is_long ? pow2_class(last->k) == pow2_class(k) : last->k == k)) {
       last->c_count++;
     } else {
-      // long constraints form one group sorted by decreasing length: its k is the longest
       h->groups.push_back(Group{is_long, k, pos, 1, static_cast<long long>(b_lit[pos]), 1, 1, fused_k(k)});
     }
   }

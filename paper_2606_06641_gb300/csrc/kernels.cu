@@ -63,10 +63,13 @@ constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 // a_j + b_j l_i (|a_j + b_j l| <= 1 for the probability-generating basis).
 // Warp w owns restart w of the tile and its lanes own 32 roots at a time.
 // The forward pass keeps one prefix checkpoint per 32-literal segment in
-// shared memory; the backward pass rebuilds a segment's prefixes in registers,
-// multiplies them by the running suffix (which starts at the gradient weight
-// D_j), and a 31-shuffle reduce-scatter sums the 32 roots so lane t ends with
-// literal t of the segment. With the paper's basis (ESP) the factors grow up
+// shared memory; the backward pass takes a segment as two halves of
+// LONG_HALF literals (the upper half's starting prefix is recomputed from the
+// checkpoint), rebuilds a half's prefixes in registers, multiplies them by
+// the running suffix (which starts at the gradient weight D_j) and stores
+// each lane's (root's) contributions as a row of a per-warp shared-memory
+// tile, whose columns the lanes then sum, so lane t ends with literal t of
+// the half summed over the 32 roots. With the paper's basis (ESP) the factors grow up
 // to 2 in modulus, so running products are renormalised at segment boundaries
 // into a mantissa and an integer power of two (exponent field of the IEEE
 // encoding) and the contributions are rescaled before the root sum.
@@ -86,30 +89,23 @@ __device__ __forceinline__ void renorm(float& r, float& i, int& e) {
   e += sh;
 }
 
-__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int t = 0; t < o; ++t) {
-      const float send = up ? v[t] : v[t + o];
-      const float keep = up ? v[t + o] : v[t];
-      v[t] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
-  }
-  return v[0];
-}
+constexpr int LONG_SEG = 32;   // literals per prefix checkpoint
+constexpr int LONG_HALF = 16;  // literals whose prefixes are held in registers at a time
+constexpr int LONG_TP = 17;    // row pitch of the transpose tile (conflict-free columns)
 
 // el[t] = u_t = 1 - l_t; the factor is A - b u, passed as (ar, ai) = A and
-// (br, bi) = -b so that each component is one FMA.
-template <bool FULL>
+// (br, bi) = -b so that each component is one FMA. The prefixes of the
+// segment are rebuilt from the checkpoint Q, then walked backwards with the
+// running suffix S; the contribution Re(prefix * S) of literal t is written
+// to row `lane`, column t of the warp's tile (scaled by 2^escale).
+template <bool FULL, bool ESP>
 __device__ __forceinline__ void long_segment(const float* el, int n, float ar, float ai, float br, float bi,
-                                             float Qr, float Qi, float& Sr, float& Si, float (&v)[32]) {
-  float pr[32], pi[32];
+                                             float Qr, float Qi, float& Sr, float& Si, int escale, float* trow) {
+  float pr[LONG_HALF], pi[LONG_HALF];
   pr[0] = Qr;
   pi[0] = Qi;
 #pragma unroll
-  for (int t = 0; t < 31; ++t) {
+  for (int t = 0; t < LONG_HALF - 1; ++t) {
     if (FULL || t + 1 < n) {
       const float ll = el[t];
       const float Fr = fmaf(br, ll, ar), Fi = fmaf(bi, ll, ai);
@@ -118,19 +114,29 @@ __device__ __forceinline__ void long_segment(const float* el, int n, float ar, f
     }
   }
 #pragma unroll
-  for (int t = 31; t >= 0; --t) {
+  for (int t = LONG_HALF - 1; t >= 0; --t) {
+    float v = 0.0f;
     if (FULL || t < n) {
-      v[t] = fmaf(pr[t], Sr, -pi[t] * Si);
+      v = fmaf(pr[t], Sr, -pi[t] * Si);
       const float ll = el[t];
       const float Fr = fmaf(br, ll, ar), Fi = fmaf(bi, ll, ai);
       const float nr = fmaf(Sr, Fr, -Si * Fi);
       const float ni = fmaf(Sr, Fi, Si * Fr);
       Sr = nr;
       Si = ni;
-    } else {
-      v[t] = 0.0f;
     }
+    trow[t] = ESP ? ldexpf(v, escale) : v;
   }
+}
+
+// Column sums of the warp's 32 x LONG_HALF tile: lane L adds rows
+// 16*(L>>4) .. +15 of column L & 15, the two halves meet by one shuffle.
+__device__ __forceinline__ float long_column_sum(const float* tile, int lane) {
+  const int c = lane & (LONG_HALF - 1), h = lane >> 4;
+  float s = 0.0f;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) s += tile[(h * 16 + r) * LONG_TP + c];
+  return s + __shfl_xor_sync(0xffffffffu, s, 16);
 }
 
 struct LongLayout {
@@ -138,7 +144,7 @@ struct LongLayout {
   __host__ __device__ LongLayout(int kmax) {
     kpad = (kmax + 3) & ~3;
     tab_cap = 1 + 2 * (kmax / 2 + 2);
-    nseg_max = (kmax + 31) / 32;
+    nseg_max = (kmax + LONG_SEG - 1) / LONG_SEG;
   }
   __host__ __device__ size_t bytes(bool esp) const {
     size_t b = static_cast<size_t>(tab_cap) * 16;            // coefficient table
@@ -146,6 +152,7 @@ struct LongLayout {
     b += 2 * static_cast<size_t>(LONG_RT) * kpad * 4;         // literal values, gradient accumulators
     b += static_cast<size_t>(LONG_RT) * nseg_max * 32 * 8;    // prefix checkpoints
     if (esp) b += static_cast<size_t>(LONG_RT) * nseg_max * 32 * 4;
+    b += static_cast<size_t>(LONG_RT) * 32 * LONG_TP * 4;     // transpose tiles
     return b;
   }
 };
@@ -172,6 +179,7 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
   float* gs = ell + LONG_RT * L.kpad;
   float2* ck = reinterpret_cast<float2*>(gs + LONG_RT * L.kpad);
   int* cke = reinterpret_cast<int*>(ck + LONG_RT * L.nseg_max * 32);
+  float* tps = reinterpret_cast<float*>(cke + (ESP ? LONG_RT * L.nseg_max * 32 : 0));
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const unsigned tab_bytes = static_cast<unsigned>(1 + 2 * nroots) * 16u;
@@ -211,7 +219,8 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
   float* gr = gs + w * L.kpad;
   float2* myck = ck + static_cast<size_t>(w) * L.nseg_max * 32;
   int* myce = cke + static_cast<size_t>(w) * L.nseg_max * 32;
-  const int nseg = (k + 31) >> 5;
+  float* tpw = tps + static_cast<size_t>(w) * 32 * LONG_TP;  // this warp's transpose tile
+  const int nseg = (k + LONG_SEG - 1) / LONG_SEG;
   float fe_part = 0.0f;
 
   for (int rg = 0; rg < nroots; rg += 32) {
@@ -228,8 +237,8 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
     for (int seg = 0; seg < nseg; ++seg) {
       myck[seg * 32 + lane] = make_float2(Pr, Pi);
       if (ESP) myce[seg * 32 + lane] = Pe;
-      const int i0 = seg * 32;
-      const int n = min(32, k - i0);
+      const int i0 = seg * LONG_SEG;
+      const int n = min(LONG_SEG, k - i0);
 #pragma unroll 4
       for (int t = 0; t < n; ++t) {
         const float ll = el[i0 + t];
@@ -249,22 +258,33 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
     float Sr = dr, Si = di;
     int Se = 0;
     for (int seg = nseg - 1; seg >= 0; --seg) {
-      const int i0 = seg * 32;
-      const int n = min(32, k - i0);
+      const int i0 = seg * LONG_SEG;
+      const int n = min(LONG_SEG, k - i0);
       const float2 Q = myck[seg * 32 + lane];
-      float v[32];
       const int escale = ESP ? myce[seg * 32 + lane] + Se : 0;
-      if (n == 32)
-        long_segment<true>(el + i0, n, ar, ai, br, bi, Q.x, Q.y, Sr, Si, v);
-      else
-        long_segment<false>(el + i0, n, ar, ai, br, bi, Q.x, Q.y, Sr, Si, v);
-      if (ESP) {
-#pragma unroll
-        for (int t = 0; t < 32; ++t) v[t] = ldexpf(v[t], escale);
-        renorm(Sr, Si, Se);
+      float* trow = tpw + lane * LONG_TP;
+      for (int hf = (n - 1) / LONG_HALF; hf >= 0; --hf) {  // upper half first
+        const int h0 = hf * LONG_HALF;
+        const int nh = min(LONG_HALF, n - h0);
+        float Qr = Q.x, Qi = Q.y;
+        for (int t = 0; t < h0; ++t) {  // the prefix at the half's start
+          const float ll = el[i0 + t];
+          const float Fr = fmaf(br, ll, ar), Fi = fmaf(bi, ll, ai);
+          const float nr = fmaf(Qr, Fr, -Qi * Fi);
+          const float ni = fmaf(Qr, Fi, Qi * Fr);
+          Qr = nr;
+          Qi = ni;
+        }
+        if (nh == LONG_HALF)
+          long_segment<true, ESP>(el + i0 + h0, nh, ar, ai, br, bi, Qr, Qi, Sr, Si, escale, trow);
+        else
+          long_segment<false, ESP>(el + i0 + h0, nh, ar, ai, br, bi, Qr, Qi, Sr, Si, escale, trow);
+        __syncwarp();
+        const float s = long_column_sum(tpw, lane);
+        if (lane < nh) gr[i0 + h0 + lane] += s;
+        __syncwarp();  // the tile is read before the next half's rows
       }
-      const float s = reduce_scatter32(v, lane);
-      if (lane < n) gr[i0 + lane] += s;
+      if (ESP) renorm(Sr, Si, Se);
     }
   }
   // value: sum of the lanes' root terms
