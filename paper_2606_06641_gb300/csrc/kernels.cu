@@ -62,20 +62,18 @@ constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 // Same expansion as the short kernel, in the direct factor form
 // a_j + b_j l_i (|a_j + b_j l| <= 1 for the probability-generating basis).
 // Warp w owns restart w of the tile and its lanes own 32 roots at a time.
-// The forward pass keeps one prefix checkpoint per 32-literal segment in
-// shared memory; the backward pass takes a segment as two halves of
-// LONG_HALF literals (the upper half's starting prefix is recomputed from the
-// checkpoint), rebuilds a half's prefixes in registers, multiplies them by
-// the running suffix (which starts at the gradient weight D_j) and stores
-// each lane's (root's) contributions as a row of a per-warp shared-memory
-// tile, whose columns the lanes then sum, so lane t ends with literal t of
-// the half summed over the 32 roots. With the paper's basis (ESP) the factors grow up
+// The forward pass keeps one prefix checkpoint per LONG_SEG-literal segment
+// in shared memory; the backward pass rebuilds a segment's prefixes (and its
+// factors) in registers, multiplies them by the running suffix (which starts
+// at the gradient weight D_j) and stores each lane's (root's) contributions
+// as a row of a per-warp shared-memory tile, whose columns the lanes then
+// sum, so lane t ends with literal t of the segment summed over the 32 roots. With the paper's basis (ESP) the factors grow up
 // to 2 in modulus, so running products are renormalised at segment boundaries
 // into a mantissa and an integer power of two (exponent field of the IEEE
 // encoding) and the contributions are rescaled before the root sum.
 // The coefficient table and literal list are staged with cp.async.bulk.
 // ---------------------------------------------------------------------------
-constexpr int LONG_RT = 8;
+constexpr int LONG_RT = 8;  // restarts (warps) per CTA; 4 for the longest groups (shared memory)
 
 __device__ __forceinline__ void renorm(float& r, float& i, int& e) {
   const float m = fmaxf(fabsf(r), fabsf(i));
@@ -89,37 +87,51 @@ __device__ __forceinline__ void renorm(float& r, float& i, int& e) {
   e += sh;
 }
 
-constexpr int LONG_SEG = 32;   // literals per prefix checkpoint
-constexpr int LONG_HALF = 16;  // literals whose prefixes are held in registers at a time
+constexpr int LONG_SEG = 16;   // literals per prefix checkpoint (prefixes and factors held in registers)
 constexpr int LONG_TP = 17;    // row pitch of the transpose tile (conflict-free columns)
 
 // el[t] = u_t = 1 - l_t; the factor is A - b u, passed as (ar, ai) = A and
 // (br, bi) = -b so that each component is one FMA. The prefixes of the
-// segment are rebuilt from the checkpoint Q, then walked backwards with the
-// running suffix S; the contribution Re(prefix * S) of literal t is written
-// to row `lane`, column t of the warp's tile (scaled by 2^escale).
-template <bool FULL, bool ESP>
+// segment are rebuilt from the checkpoint Q (with CF the factors are kept in
+// registers for the backward walk, else rebuilt there), then walked
+// backwards with the running suffix S; the contribution Re(prefix * S) of
+// literal t is written to row `lane`, column t of the warp's tile (scaled by
+// 2^escale).
+template <bool FULL, bool ESP, bool CF>
 __device__ __forceinline__ void long_segment(const float* el, int n, float ar, float ai, float br, float bi,
                                              float Qr, float Qi, float& Sr, float& Si, int escale, float* trow) {
-  float pr[LONG_HALF], pi[LONG_HALF];
+  float pr[LONG_SEG], pi[LONG_SEG], fr[CF ? LONG_SEG : 1], fi[CF ? LONG_SEG : 1];
   pr[0] = Qr;
   pi[0] = Qi;
 #pragma unroll
-  for (int t = 0; t < LONG_HALF - 1; ++t) {
-    if (FULL || t + 1 < n) {
+  for (int t = 0; t < LONG_SEG; ++t) {
+    if (FULL || t < n) {
       const float ll = el[t];
       const float Fr = fmaf(br, ll, ar), Fi = fmaf(bi, ll, ai);
-      pr[t + 1] = fmaf(pr[t], Fr, -pi[t] * Fi);
-      pi[t + 1] = fmaf(pr[t], Fi, pi[t] * Fr);
+      if constexpr (CF) {
+        fr[t] = Fr;
+        fi[t] = Fi;
+      }
+      if (t + 1 < LONG_SEG) {
+        pr[t + 1] = fmaf(pr[t], Fr, -pi[t] * Fi);
+        pi[t + 1] = fmaf(pr[t], Fi, pi[t] * Fr);
+      }
     }
   }
 #pragma unroll
-  for (int t = LONG_HALF - 1; t >= 0; --t) {
+  for (int t = LONG_SEG - 1; t >= 0; --t) {
     float v = 0.0f;
     if (FULL || t < n) {
       v = fmaf(pr[t], Sr, -pi[t] * Si);
-      const float ll = el[t];
-      const float Fr = fmaf(br, ll, ar), Fi = fmaf(bi, ll, ai);
+      float Fr, Fi;
+      if constexpr (CF) {
+        Fr = fr[t];
+        Fi = fi[t];
+      } else {
+        const float ll = el[t];
+        Fr = fmaf(br, ll, ar);
+        Fi = fmaf(bi, ll, ai);
+      }
       const float nr = fmaf(Sr, Fr, -Si * Fi);
       const float ni = fmaf(Sr, Fi, Si * Fr);
       Sr = nr;
@@ -129,10 +141,10 @@ __device__ __forceinline__ void long_segment(const float* el, int n, float ar, f
   }
 }
 
-// Column sums of the warp's 32 x LONG_HALF tile: lane L adds rows
+// Column sums of the warp's 32 x LONG_SEG tile: lane L adds rows
 // 16*(L>>4) .. +15 of column L & 15, the two halves meet by one shuffle.
 __device__ __forceinline__ float long_column_sum(const float* tile, int lane) {
-  const int c = lane & (LONG_HALF - 1), h = lane >> 4;
+  const int c = lane & (LONG_SEG - 1), h = lane >> 4;
   float s = 0.0f;
 #pragma unroll
   for (int r = 0; r < 16; ++r) s += tile[(h * 16 + r) * LONG_TP + c];
@@ -140,8 +152,8 @@ __device__ __forceinline__ float long_column_sum(const float* tile, int lane) {
 }
 
 struct LongLayout {
-  int kpad, tab_cap, nseg_max;
-  __host__ __device__ LongLayout(int kmax) {
+  int kpad, tab_cap, nseg_max, rt;
+  __host__ __device__ LongLayout(int kmax, int rt_ = LONG_RT) : rt(rt_) {
     kpad = (kmax + 3) & ~3;
     tab_cap = 1 + 2 * (kmax / 2 + 2);
     nseg_max = (kmax + LONG_SEG - 1) / LONG_SEG;
@@ -149,22 +161,25 @@ struct LongLayout {
   __host__ __device__ size_t bytes(bool esp) const {
     size_t b = static_cast<size_t>(tab_cap) * 16;            // coefficient table
     b += static_cast<size_t>(kpad) * 8;                       // literal list
-    b += 2 * static_cast<size_t>(LONG_RT) * kpad * 4;         // literal values, gradient accumulators
-    b += static_cast<size_t>(LONG_RT) * nseg_max * 32 * 8;    // prefix checkpoints
-    if (esp) b += static_cast<size_t>(LONG_RT) * nseg_max * 32 * 4;
-    b += static_cast<size_t>(LONG_RT) * 32 * LONG_TP * 4;     // transpose tiles
+    b += 2 * static_cast<size_t>(rt) * kpad * 4;              // literal values, gradient accumulators
+    b += static_cast<size_t>(rt) * nseg_max * 32 * 8;         // prefix checkpoints
+    if (esp) b += static_cast<size_t>(rt) * nseg_max * 32 * 4;
+    b += static_cast<size_t>(rt) * 32 * LONG_TP * 4;          // transpose tiles
     return b;
   }
 };
 
-template <typename XT, bool ESP>
-__global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int kmax) {
+template <typename XT, bool ESP, int RT>
+__global__ void __launch_bounds__(RT * 32) fe_grad_long_kernel(FeGroupArgs a, int kmax) {
+  // the groups that run 4 restarts per CTA (the longest) keep a segment's
+  // factors in registers: fewer instructions, more registers per thread
+  constexpr bool CF = RT == 4;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) unsigned long long bar;
   pdl_wait();
   pdl_trigger();
-  const LongLayout L(kmax);
-  const int tiles = (a.nb + LONG_RT - 1) / LONG_RT;
+  const LongLayout L(kmax, RT);
+  const int tiles = (a.nb + RT - 1) / RT;
   const int cl = blockIdx.x / tiles;
   const int tile = blockIdx.x - cl * tiles;
   const int cb = a.c_begin + cl;
@@ -176,10 +191,10 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
   float4* tab = reinterpret_cast<float4*>(smem);
   int2* lits = reinterpret_cast<int2*>(tab + L.tab_cap);
   float* ell = reinterpret_cast<float*>(lits + L.kpad);
-  float* gs = ell + LONG_RT * L.kpad;
-  float2* ck = reinterpret_cast<float2*>(gs + LONG_RT * L.kpad);
-  int* cke = reinterpret_cast<int*>(ck + LONG_RT * L.nseg_max * 32);
-  float* tps = reinterpret_cast<float*>(cke + (ESP ? LONG_RT * L.nseg_max * 32 : 0));
+  float* gs = ell + RT * L.kpad;
+  float2* ck = reinterpret_cast<float2*>(gs + RT * L.kpad);
+  int* cke = reinterpret_cast<int*>(ck + RT * L.nseg_max * 32);
+  float* tps = reinterpret_cast<float*>(cke + (ESP ? RT * L.nseg_max * 32 : 0));
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const unsigned tab_bytes = static_cast<unsigned>(1 + 2 * nroots) * 16u;
@@ -194,7 +209,7 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
     bulk_g2s(tab, a.coef + tab_off, tab_bytes, &bar);
     bulk_g2s(lits, a.litslot + litoff, lit_bytes, &bar);
   }
-  for (int i = tid; i < LONG_RT * L.kpad; i += blockDim.x) gs[i] = 0.0f;
+  for (int i = tid; i < RT * L.kpad; i += blockDim.x) gs[i] = 0.0f;
   const long long limit = a.wait_limit > 0 ? a.wait_limit : WAIT_LIMIT_CYCLES;
   if (!mbar_wait_bounded(&bar, 0, limit)) {
     if (tid == 0) atomicExch(a.err, DEV_ERR_TIMEOUT);
@@ -202,11 +217,11 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
     return;
   }
 
-  // stage u[r][i] = 1 - s_i x[v_i][b]: 8 consecutive threads read one 32-byte row
+  // stage u[r][i] = 1 - s_i x[v_i][b]: RT consecutive threads read one row segment
   const XT* x = static_cast<const XT*>(a.x);
-  const int bt = tile * LONG_RT;
-  for (int idx = tid; idx < k * LONG_RT; idx += blockDim.x) {
-    const int i = idx >> 3, r = idx & 7;
+  const int bt = tile * RT;
+  for (int idx = tid; idx < k * RT; idx += blockDim.x) {
+    const int i = idx / RT, r = idx % RT;
     const int2 li = lits[i];
     const int bl = bt + r;
     const float xv =
@@ -263,28 +278,15 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
       const float2 Q = myck[seg * 32 + lane];
       const int escale = ESP ? myce[seg * 32 + lane] + Se : 0;
       float* trow = tpw + lane * LONG_TP;
-      for (int hf = (n - 1) / LONG_HALF; hf >= 0; --hf) {  // upper half first
-        const int h0 = hf * LONG_HALF;
-        const int nh = min(LONG_HALF, n - h0);
-        float Qr = Q.x, Qi = Q.y;
-        for (int t = 0; t < h0; ++t) {  // the prefix at the half's start
-          const float ll = el[i0 + t];
-          const float Fr = fmaf(br, ll, ar), Fi = fmaf(bi, ll, ai);
-          const float nr = fmaf(Qr, Fr, -Qi * Fi);
-          const float ni = fmaf(Qr, Fi, Qi * Fr);
-          Qr = nr;
-          Qi = ni;
-        }
-        if (nh == LONG_HALF)
-          long_segment<true, ESP>(el + i0 + h0, nh, ar, ai, br, bi, Qr, Qi, Sr, Si, escale, trow);
-        else
-          long_segment<false, ESP>(el + i0 + h0, nh, ar, ai, br, bi, Qr, Qi, Sr, Si, escale, trow);
-        __syncwarp();
-        const float s = long_column_sum(tpw, lane);
-        if (lane < nh) gr[i0 + h0 + lane] += s;
-        __syncwarp();  // the tile is read before the next half's rows
-      }
+      if (n == LONG_SEG)
+        long_segment<true, ESP, CF>(el + i0, n, ar, ai, br, bi, Q.x, Q.y, Sr, Si, escale, trow);
+      else
+        long_segment<false, ESP, CF>(el + i0, n, ar, ai, br, bi, Q.x, Q.y, Sr, Si, escale, trow);
       if (ESP) renorm(Sr, Si, Se);
+      __syncwarp();
+      const float s = long_column_sum(tpw, lane);
+      if (lane < n) gr[i0 + lane] += s;
+      __syncwarp();  // the tile is read before the next segment's rows
     }
   }
   // value: sum of the lanes' root terms
@@ -293,8 +295,8 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
   if (a.fe != nullptr && lane == 0 && bt + w < a.nb)
     a.fe[static_cast<long long>(__ldg(a.cons_orig + cb)) * a.fe_pitch + a.b0 + bt + w] = tab[0].x + fe_part;
   __syncthreads();
-  for (int idx = tid; idx < k * LONG_RT; idx += blockDim.x) {
-    const int i = idx >> 3, r = idx & 7;
+  for (int idx = tid; idx < k * RT; idx += blockDim.x) {
+    const int i = idx / RT, r = idx % RT;
     if (bt + r < a.nb) {
       const int2 li = lits[i];
       const float gv = gs[r * L.kpad + i];
@@ -303,14 +305,28 @@ __global__ void __launch_bounds__(256) fe_grad_long_kernel(FeGroupArgs a, int km
   }
 }
 
-size_t long_smem_bytes(int kmax, bool esp) { return LongLayout(kmax).bytes(esp); }
+// Long groups whose shared memory at 8 restarts per CTA exceeds LONG_RT4_BYTES
+// run 4 restarts per CTA, so that more CTAs fit on an SM (and the longest
+// constraints fit at all).
+constexpr size_t LONG_RT4_BYTES = 64 * 1024;
+
+size_t long_smem_bytes(int kmax, bool esp) {
+  const size_t b8 = LongLayout(kmax, 8).bytes(esp);
+  return b8 > LONG_RT4_BYTES ? LongLayout(kmax, 4).bytes(esp) : b8;
+}
+
 
 template <typename XT, bool ESP>
 static void launch_long_t(const FeGroupArgs& a, cudaStream_t s) {
-  const size_t smem = LongLayout(a.k).bytes(ESP);
-  const int tiles = (a.nb + LONG_RT - 1) / LONG_RT;
+  const bool rt4 = LongLayout(a.k, 8).bytes(ESP) > LONG_RT4_BYTES;
+  const int rt = rt4 ? 4 : 8;
+  const size_t smem = LongLayout(a.k, rt).bytes(ESP);
+  const int tiles = (a.nb + rt - 1) / rt;
   const long long blocks = static_cast<long long>(tiles) * a.c_count;
-  launch_pdl(fe_grad_long_kernel<XT, ESP>, dim3(static_cast<unsigned>(blocks)), dim3(256), smem, s, a, a.k);
+  if (rt4)
+    launch_pdl(fe_grad_long_kernel<XT, ESP, 4>, dim3(static_cast<unsigned>(blocks)), dim3(128), smem, s, a, a.k);
+  else
+    launch_pdl(fe_grad_long_kernel<XT, ESP, 8>, dim3(static_cast<unsigned>(blocks)), dim3(256), smem, s, a, a.k);
 }
 
 template <typename K>
@@ -1112,12 +1128,16 @@ bool prepare_kernels() {
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
-  if (LongLayout(1024).bytes(true) + 64 > static_cast<size_t>(optin)) return false;
+  if (LongLayout(1024, 4).bytes(true) + 64 > static_cast<size_t>(optin)) return false;
   bool ok = true;
-  ok &= raise_smem_cap(fe_grad_long_kernel<float, false>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<float, true>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, false>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, true>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<float, false, 8>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<float, true, 8>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, false, 8>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, true, 8>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<float, false, 4>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<float, true, 4>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, false, 4>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, true, 4>, optin);
   return ok;
 }
 
