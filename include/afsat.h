@@ -151,8 +151,9 @@ int afs_step(afs_handle* h, int32_t nsteps, void* stream);
  *   unsat_host[B * n_inst] (nullable)  per instance and restart
  *   best_host[n_inst]      (nullable)  restart with the fewest violations
  *                                      (lowest index on ties)
- *   assign_host[n_total]   (nullable)  +1/-1 values of the best restart of
- *                                      each instance, variables in load order
+ *   assign_host[n_total]   (nullable)  the sign of x in the best restart of
+ *                                      each instance (-1 = True, +1 = False),
+ *                                      variables in load order
  *   solved_host[n_inst]    (nullable)  1 if some restart satisfies everything
  * The best assignments are re-checked on the host with independent integer
  * code; a disagreement returns AFS_E_VERIFY. Synchronises `stream`. */
@@ -169,6 +170,18 @@ int afs_set_x(afs_handle* h, const float* x_dev, void* stream);
  * seen solved per instance since afs_init_restarts (INT32_MAX if none) into
  * solved_dev[n_inst]; either may be NULL. */
 int afs_get_verify(afs_handle* h, int32_t* unsat_dev, int32_t* solved_dev, void* stream);
+/* afs_set_fixed: partial assignments (the paper's prefix assignments). values
+ * holds n_groups rows of n_total int8 (variables of the handle in load order):
+ * +1 = the variable is fixed True, -1 = fixed False, 0 = free. The restarts
+ * are split into n_groups equal contiguous ranges (restart b uses row
+ * b * n_groups / B). A fixed variable's state is set to -1 (True) or +1
+ * (False) now and after every later write of the state (afs_init_restarts,
+ * afs_set_x, afs_step_host, the learned initialiser), and the step never
+ * moves it (its gradient is not applied). values == NULL or n_groups == 0
+ * clears the assignments. Requires afs_init_restarts; host memory; n_groups
+ * must not exceed B. */
+int afs_set_fixed(afs_handle* h, const int8_t* values_host, int32_t n_groups, void* stream);
+
 /* afs_get_step_check: the outcome of the exact check inside the last step
  * that ran one (verify_every != 0), per instance and word of 32 restarts:
  * bit j of out_dev[inst * W + w] is 1 when restart 32w + j satisfied every

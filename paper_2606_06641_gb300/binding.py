@@ -66,6 +66,7 @@ SIGNATURES = {
     "afs_tuning": (_I32, [_P, _P, _P, _I32]),
     "afs_tiles": (_I32, [_P, _P, _P, _P, _I32]),
     "afs_get_step_check": (_I32, [_P, _P, _P, _P]),
+    "afs_set_fixed": (_I32, [_P, _P, _I32, _P]),
     "afs_set_tiles": (_I32, [_P, _I32, _P, _P, _I32]),
     "afs_coef_table": (_I32, [_I32, _I32, _I32, _I32, _I32, _I32, _I32, _P, _I32, _P]),
     "afs_esp_coefficients": (_I32, [_I32, _I32, _I32, _I32, _I32, _P]),
@@ -237,6 +238,25 @@ def get_verify(h: Handle, stream=None):
     sol = torch.empty(h.n_inst, dtype=torch.int32, device="cuda")
     _check(lib().afs_get_verify(h.ptr, _ptr(un), _ptr(sol), _stream(stream)))
     return un, sol
+
+
+def set_fixed(h: Handle, values=None, stream=None) -> None:
+    """Partial assignments: values [n] or [groups, n] int8 (+1 True, -1 False,
+    0 free; restart b uses row b * groups // B), or a {variable (1-based): bool}
+    dict such as a reader's units; None clears them."""
+    if values is None:
+        _check(lib().afs_set_fixed(h.ptr, None, 0, _stream(stream)))
+        return
+    if isinstance(values, dict):
+        arr = np.zeros(h.n, np.int8)
+        for v, val in values.items():
+            arr[int(v) - 1] = 1 if val else -1
+        values = arr
+    arr = np.ascontiguousarray(np.asarray(values, dtype=np.int8))
+    if arr.ndim == 1:
+        arr = arr[None, :]
+    assert arr.shape[1] == h.n
+    _check(lib().afs_set_fixed(h.ptr, arr.ctypes.data, arr.shape[0], _stream(stream)))
 
 
 def get_step_check(h: Handle, stream=None):

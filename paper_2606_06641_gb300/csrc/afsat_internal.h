@@ -71,6 +71,8 @@ struct CsrArgs {
   int* solved;
   unsigned* sgn;            // nullable: sign words of the new state (layout below)
   int discard_go;           // 1: the occurrence rows are dead after this pass (L2 lines dropped)
+  const signed char* fixv;  // nullable: fixv[g * n_vars + v] != 0 = v fixed in restart group g
+  int n_fix_groups;         // restart b belongs to group b * n_fix_groups / B
   float* gf;                // step mode: gf[v * gf_pitch + (b - b0)] = summed derivatives of the fused
   long long gf_pitch;       // occurrences of v (written by the fused pass, read by the CSR pass)
   int W;                    // words per variable row of sgn / per instance of vcur
@@ -83,6 +85,10 @@ struct CsrArgs {
 // 32 restarts per integer operation from them.
 void launch_pack_signs(const void* x, int xt, long long x_pitch, int n, int B, unsigned* sgn, int W,
                        cudaStream_t s);
+// Set the state of fixed variables: x[v][b] = -1 where fixv[g(b) * n + v] > 0
+// (True), +1 where it is < 0, g(b) = b * groups / B.
+void launch_apply_fixed(void* x, int xt, long long x_pitch, int n, int B, const signed char* fixv, int groups,
+                        cudaStream_t s);
 
 // Bit-sliced exact check of the state in sign words (Algorithm 1's is_sat):
 // one thread per (range of constraints of one instance, word of 32 restarts)

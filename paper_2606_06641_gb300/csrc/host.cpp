@@ -169,6 +169,9 @@ struct afs_handle {
   // is xb[parity]
   // gf: the fused occurrences' summed derivatives per variable (n x chunk)
   DevBuf xb[2], go, gf, unsat, sgn, vword, solved, col, assign, stage, eval_go;
+  // partial assignments: fix_groups rows of n int8 (0 = free, +1 True, -1 False)
+  DevBuf fixv;
+  int fix_groups = 0;
   int parity = 0;
   void* xcur() const { return xb[parity].p; }
   bool step_check_valid = false;  // vword[parity ^ 1] holds the last step's check
@@ -596,6 +599,8 @@ static int launch_csr(afs_handle* h, const void* x, void* xout, int xt, long lon
   a.solved = h->solved.as<int>();
   a.sgn = own ? h->sgn.as<unsigned>() : nullptr;
   a.discard_go = own && discard_enabled() ? 1 : 0;
+  a.fixv = own && h->fix_groups > 0 ? h->fixv.as<signed char>() : nullptr;
+  a.n_fix_groups = h->fix_groups;
   a.gf = own && h->n_fused > 0 ? h->gf.as<float>() : nullptr;
   a.gf_pitch = go_pitch;
   launch_csr_update(a, xt, s);
@@ -1007,6 +1012,10 @@ void* afs::handle_ext(const afs_handle* h) { return h ? h->ext : nullptr; }
 
 int afs::state_written(afs_handle* h, cudaStream_t s) {
   if (!h || h->B <= 0) return fail(AFS_E_STATE, "no restart state");
+  if (h->fix_groups > 0) {
+    launch_apply_fixed(h->xcur(), h->xt, h->pitch, h->n, h->B, h->fixv.as<signed char>(), h->fix_groups, s);
+    CKL();
+  }
   launch_pack_signs(h->xcur(), h->xt, h->pitch, h->n, h->B, h->sgn.as<unsigned>(), h->W, s);
   CKL();
   return AFS_OK;
@@ -1287,6 +1296,28 @@ int afs_get_verify(afs_handle* h, int32_t* unsat_dev, int32_t* solved_dev, void*
                        cudaMemcpyDeviceToDevice, s));
   if (solved_dev) CK(cudaMemcpyAsync(solved_dev, h->solved.p, sizeof(int) * h->n_inst, cudaMemcpyDeviceToDevice, s));
   return AFS_OK;
+}
+
+int afs_set_fixed(afs_handle* h, const int8_t* values_host, int32_t n_groups, void* stream) {
+  if (!h) return fail(AFS_E_ARG, "NULL handle");
+  if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (values_host == nullptr || n_groups == 0) {
+    h->fix_groups = 0;
+    h->drop_graphs();
+    return AFS_OK;
+  }
+  if (n_groups < 0 || n_groups > h->B) return fail(AFS_E_ARG, "n_groups must be in 1..B");
+  const size_t cnt = static_cast<size_t>(n_groups) * h->n;
+  for (size_t i = 0; i < cnt; ++i)
+    if (values_host[i] < -1 || values_host[i] > 1) return fail(AFS_E_ARG, "fixed values must be -1, 0 or +1");
+  int rc = h->fixv.alloc(cnt);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(h->fixv.p, values_host, cnt, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // the host buffer may go away after the call
+  h->fix_groups = n_groups;
+  h->drop_graphs();  // the CSR launches carry the mask
+  return afs::state_written(h, s);
 }
 
 int afs_get_step_check(const afs_handle* h, uint32_t* out_dev, int32_t* words_per_inst, void* stream) {

@@ -544,7 +544,10 @@ __global__ void __launch_bounds__(256) csr_update_kernel(CsrArgs a) {
   const int word = (a.b0 + tile * 32) >> 5;
   const long long wi = static_cast<long long>(inst) * a.W + word;
   const unsigned viol = a.vcur != nullptr ? a.vcur[wi] : ~0u;
-  const bool solved = !((viol >> lane) & 1u);
+  const bool solved = !((viol >> lane) & 1u) ||
+                      (a.fixv != nullptr && act &&
+                       a.fixv[static_cast<long long>((a.b0 + bl) * static_cast<long long>(a.n_fix_groups) / a.B) *
+                                  a.n_vars + v] != 0);
   if (lane == 0 && v == __ldg(a.var_inst + a.n_vars + inst)) csr_first_var_duty(a, inst, word, wi);
   const long long xi = static_cast<long long>(v) * a.x_pitch + a.b0 + bl;
   float xs = 0.0f;
@@ -575,8 +578,15 @@ __device__ __forceinline__ void csr_vec4_task(const CsrArgs& a, int vl, int tile
   const int inst = __ldg(a.var_inst + v);
   const int word = (a.b0 + bl) >> 5;
   const long long wi = static_cast<long long>(inst) * a.W + word;
-  unsigned sw = 0u;  // solved bits of this lane's restarts
+  unsigned sw = 0u;  // solved (or fixed) bits of this lane's restarts
   if (act && a.vcur != nullptr) sw = ~(a.vcur[wi] >> (bl & 31));
+  if (act && a.fixv != nullptr) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const long long g = static_cast<long long>(a.b0 + bl + e) * a.n_fix_groups / a.B;
+      if (bl + e < a.nb && a.fixv[g * a.n_vars + v] != 0) sw |= 1u << e;
+    }
+  }
   const long long xi = static_cast<long long>(v) * a.x_pitch + a.b0 + bl;
   float xo[4] = {0.f, 0.f, 0.f, 0.f};
   if (act) load_xvec<XT, 4>(static_cast<const XT*>(a.x) + xi, xo);
@@ -742,6 +752,27 @@ void launch_csr_update(const CsrArgs& a, int xt, cudaStream_t s) {
 
 // Sign words of a state written outside the step (initialisation, set_x):
 // one warp per (variable, word).
+template <typename XT>
+__global__ void apply_fixed_kernel(XT* x, long long pitch, int n, int B, const signed char* fixv, int groups) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= static_cast<long long>(n) * B) return;
+  const int v = static_cast<int>(i / B), b = static_cast<int>(i - static_cast<long long>(v) * B);
+  const signed char f = fixv[static_cast<long long>(b) * groups / B * n + v];
+  if (f != 0) store_x<XT>(x + static_cast<long long>(v) * pitch + b, f > 0 ? -1.0f : 1.0f);
+}
+
+void launch_apply_fixed(void* x, int xt, long long x_pitch, int n, int B, const signed char* fixv, int groups,
+                        cudaStream_t s) {
+  const long long total = static_cast<long long>(n) * B;
+  if (total == 0 || fixv == nullptr || groups <= 0) return;
+  const unsigned blocks = static_cast<unsigned>((total + 255) / 256);
+  if (xt == XT_F32)
+    apply_fixed_kernel<float><<<blocks, 256, 0, s>>>(static_cast<float*>(x), x_pitch, n, B, fixv, groups);
+  else
+    apply_fixed_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(static_cast<__nv_bfloat16*>(x), x_pitch, n, B, fixv,
+                                                            groups);
+}
+
 template <typename XT>
 __global__ void pack_signs_kernel(const XT* x, long long pitch, int n, int B, unsigned* sgn, int W) {
   const int lane = threadIdx.x & 31;

@@ -435,3 +435,68 @@ def test_parsed_hybrid_file_end_to_end():
     bd.step(h, 20)
     un, best, asg, sol = bd.round_and_verify(h)
     np.testing.assert_array_equal(un[0], O.unsat_count(inst, bd.get_x(h).cpu().numpy()))
+
+
+# ---- partial assignments ------------------------------------------------------
+def test_fixed_variables_hold_and_the_rest_follow_the_oracle():
+    """A fixed variable sits at -1 (True) / +1 (False) from the moment it is
+    fixed and is never moved; the free variables take the oracle's projected
+    step of the state with the fixed values in place."""
+    inst = synth.hybrid_n2000(3)
+    B = 96
+    rng = np.random.default_rng(4)
+    fix = np.zeros(inst.n, np.int8)
+    idx = rng.choice(inst.n, size=300, replace=False)
+    fix[idx] = np.where(rng.random(300) < 0.5, 1, -1)
+    x0 = synth.uniform_x0(inst.n, B, 8)
+    h = bd.load_instance(inst, bd.default_params(eta=0.1, verify_every=0, autotune=0))
+    bd.init_restarts(h, B, x0=_dev(x0))
+    bd.set_fixed(h, fix)
+    xf = bd.get_x(h).cpu().numpy()
+    want = x0.copy()
+    want[fix != 0] = np.where(fix[fix != 0] > 0, -1.0, 1.0)[:, None]
+    np.testing.assert_array_equal(xf, want)
+    bd.step(h, 1)
+    x1 = bd.get_x(h).cpu().numpy()
+    ref = O.pgd_step(inst, want.astype(np.float64), 0.1)
+    free = fix == 0
+    assert np.abs(x1[free] - ref[free]).max() <= 0.1 * 2 * TOL
+    np.testing.assert_array_equal(x1[~free], want[~free])
+    bd.step(h, 5)
+    np.testing.assert_array_equal(bd.get_x(h).cpu().numpy()[~free], want[~free])
+
+
+def test_fixed_assignments_per_restart_group_and_clearing():
+    inst = synth.mixed_small(5)
+    B = 64
+    fix = np.zeros((2, inst.n), np.int8)
+    fix[0, :5] = 1
+    fix[1, 5:10] = -1
+    h = bd.load_instance(inst, bd.default_params(eta=0.1, autotune=0))
+    bd.init_restarts(h, B, seed=9)
+    bd.set_fixed(h, fix)
+    bd.step(h, 3)
+    x = bd.get_x(h).cpu().numpy()
+    assert np.all(x[:5, :32] == -1.0) and np.all(x[5:10, 32:] == 1.0)
+    bd.init_restarts(h, B, seed=10)      # the assignments survive a re-initialisation
+    x = bd.get_x(h).cpu().numpy()
+    assert np.all(x[:5, :32] == -1.0) and np.all(x[5:10, 32:] == 1.0)
+    bd.set_fixed(h, None)
+    bd.step(h, 1)
+    assert np.any(bd.get_x(h).cpu().numpy()[:5, :32] != -1.0)
+
+
+def test_reader_units_as_partial_assignment():
+    from paper_2606_06641_gb300 import dimacs
+    text = "\n".join(["p cnf 8 6", "1 0", "e -2 0", "ek 3 3 4 5 0", "h 6 7 8 0", "x 1 6 8 0",
+                      "card <=1 2 6 7 0"])
+    p = dimacs.parse(text)
+    assert p.units == {1: True, 2: False, 3: True, 4: True, 5: True}
+    h = bd.load_instance(p.inst, bd.default_params(eta=0.1, autotune=0))
+    bd.init_restarts(h, 32, seed=2)
+    bd.set_fixed(h, p.units)
+    bd.step(h, 50)
+    un, best, asg, sol = bd.round_and_verify(h)
+    assert sol[0] == 1
+    for v, val in p.units.items():
+        assert asg[v - 1] == (-1 if val else 1)   # the sign of x: -1 = True
