@@ -527,6 +527,48 @@ def run_ours(args):
     return 0
 
 
+def run_batch_sweep(args):
+    """Throughput against the restart count B for one workload (SURVEY NEXT 4:
+    where the autotuned chunk and the L2 make the rate peak). One line per run:
+    B, chunk, tiles, literal-evals/s, ms per step; same timing rules as the
+    main measurement (graph replays of 10 steps, L2 flushed between)."""
+    import torch
+    from paper_2606_06641_gb300 import binding as bd
+    from paper_2606_06641_gb300 import build as _b
+    _b.build()
+    insts = make_workload(args.workload)
+    L = sum(i.n_lits for i in insts)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    rows = []
+    for B in [int(b) for b in args.sweep_b.split(",")]:
+        params = bd.default_params(eta=0.1, verify_every=1)
+        h = bd.load_instance(insts[0], params) if len(insts) == 1 else bd.load_batch(insts, params)
+        bd.init_restarts(h, B, seed=1000)
+        S, R = 10, max(1, args.steps // 10)
+        for _ in range(3):
+            bd.step(h, 1)
+        bd.step(h, S)
+        torch.cuda.synchronize()
+        ms = 0.0
+        for r in range(R):
+            flush.fill_(float(r))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bd.step(h, S)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        chunk, tiles = bd.tiles(h)
+        rows.append({"B": B, "value": L * B * R * S / (ms * 1e-3), "ms_per_step": ms / (R * S), "chunk": chunk,
+                     "tiles": bd.format_tiles(chunk, tiles)})
+        h.free()
+        print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": WORKLOADS[args.workload][0],
+                      "batch_sweep": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -542,6 +584,7 @@ def main():
     ap.add_argument("--steps-per-graph", type=int, default=10)
     ap.add_argument("--chunk", type=int, default=0, help="restarts per chunk (0 = autotuned)")
     ap.add_argument("--tiles", default="", help="fixed chunk and tiles, 'chunk:k=RPLxCPW,...' (no autotuning)")
+    ap.add_argument("--sweep-b", default="", help="comma-separated restart counts: throughput against B")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--tts-instances", type=int, default=128)
     ap.add_argument("--tts-eta", type=float, default=0.1)
@@ -555,6 +598,8 @@ def main():
         return run_reference(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.sweep_b:
+        return run_batch_sweep(args)
     return run_ours(args)
 
 
