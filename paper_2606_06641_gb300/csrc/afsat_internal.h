@@ -50,7 +50,7 @@ struct CsrArgs {
   int b0, nb;
   const int* csr_off;       // slots of variable v: [csr_off[v], csr_off[v+1])
   const int* fus_off;       // fused occurrences of v: fus[fus_off[v] .. fus_off[v+1])
-  const int4* fus;          // {other literal, other literal, table offset, negated}
+  const float4* fus;        // 2 per entry: {E s1 s2, tan s1, tan s2, E'r tan}, {E'i tan, s_self, v1, v2 (int bits)}
   const float4* coef;       // coefficient tables (short form)
   int v_begin, v_count;
   const float* go;

@@ -401,7 +401,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     csr[v + 1] += csr[v];
     fcsr[v + 1] += fcsr[v];
   }
-  std::vector<int4> fus(static_cast<size_t>(fcsr[h->n]));
+  std::vector<float4> fus(2 * static_cast<size_t>(fcsr[h->n]));
   {
     std::vector<int> fill(csr.begin(), csr.end() - 1), ffill(fcsr.begin(), fcsr.end() - 1);
     for (int pos = 0; pos < m; ++pos) {
@@ -415,7 +415,21 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
         int other[2] = {0, 0}, no = 0;
         for (int u = 0; u < k; ++u)
           if (u != t) other[no++] = litslot[b_lit[pos] + u].x;
-        fus[ffill[ls.x >> 1]++] = make_int4(other[0], other[1], b_tab[pos], ls.x & 1);
+        // the products at the roots without the self factor, with the
+        // other literals' signs and the root scale folded into the entry:
+        // {E s1 s2, tan s1, tan s2, E'r tan}, {E'i tan, s_self, v1, v2}
+        const float* tb = &coef[4 * static_cast<size_t>(b_tab[pos])];
+        const float s1 = (other[0] & 1) ? -1.0f : 1.0f, s2 = (other[1] & 1) ? -1.0f : 1.0f;
+        const float Er = tb[5];  // the real root w = -1: {0, E, 0, 0}
+        const bool cpx = tb[1] > 0.5f;  // the complex pair {tan, 0, E'} when its coefficient is not zero
+        const float tn = cpx ? tb[8] : 0.0f, epr = cpx ? tb[10] : 0.0f, epi = cpx ? tb[11] : 0.0f;
+        const size_t fe = 2 * static_cast<size_t>(ffill[ls.x >> 1]++);
+        fus[fe] = make_float4(Er * (s1 * s2), tn * s1, tn * s2, epr * tn);
+        int v1 = other[0] >> 1, v2 = other[1] >> 1;
+        float fv1, fv2;
+        std::memcpy(&fv1, &v1, 4);
+        std::memcpy(&fv2, &v2, 4);
+        fus[fe + 1] = make_float4(epi * tn, (ls.x & 1) ? -1.0f : 1.0f, fv1, fv2);
         ls.y = -1;
       }
     }
@@ -578,7 +592,7 @@ static int launch_csr(afs_handle* h, const void* x, void* xout, int xt, long lon
   a.nb = nb;
   a.csr_off = h->csr_off.as<int>();
   a.fus_off = h->fus_off.as<int>();
-  a.fus = h->fus.as<int4>();
+  a.fus = h->fus.as<float4>();
   a.coef = h->coef.as<float4>();
   a.v_begin = 0;
   a.v_count = h->n;
@@ -619,7 +633,7 @@ static int launch_fused(afs_handle* h, const void* x, int b0, int nb, cudaStream
   a.v_begin = 0;
   a.v_count = h->n;
   a.fus_off = h->fus_off.as<int>();
-  a.fus = h->fus.as<int4>();
+  a.fus = h->fus.as<float4>();
   a.coef = h->coef.as<float4>();
   a.gf = h->gf.as<float>();
   a.gf_pitch = h->Bc;

@@ -397,30 +397,36 @@ __device__ __forceinline__ float stored_value<__nv_bfloat16>(float v) {
 
 // Fused constraints (k = KFUSE = 3, probability-generating tables): the
 // derivative of occurrence `self` is s_self * dFE/dl_self, recomputed from the
-// two other literals' values with the constraint's table: the real root
-// w = -1 contributes E l1 l2, the complex pair (scaled form) Re(E' tan (l1 tan
-// + i)(l2 tan + i)) -- the same products at the roots as the FE kernel's
-// gradient, without the self factor. The entries {other, other, table,
-// negated} of variable v are read with uniform loads (the warp's lanes share
-// them); the gathers of FB occurrences are in flight at a time, R consecutive
-// restarts per lane starting at column col.
+// two other literals' state: the real root w = -1 contributes E l1 l2, the
+// complex pair (scaled form) Re(E' tan (l1 tan + i)(l2 tan + i)) -- the same
+// products at the roots as the FE kernel's gradient, without the self factor.
+// Each entry carries the root constants with the other literals' signs
+// folded in ({E s1 s2, tan s1, tan s2, E'r tan}, {E'i tan, s_self, v1, v2}),
+// read with uniform loads (the warp's lanes share them); the gathers of FB
+// occurrences are in flight at a time, R consecutive restarts per lane
+// starting at column col.
 template <typename XT, int R, int FB>
 __device__ __forceinline__ void fused_sum(const CsrArgs& a, int v, long long col, bool act, float (&acc)[R]) {
   const int f0 = __ldg(a.fus_off + v), f1 = __ldg(a.fus_off + v + 1);
   const XT* x = static_cast<const XT*>(a.x);
   for (int f = f0; f < f1; f += FB) {  // uniform per warp
-    int4 e[FB];
+    float4 c0[FB], c1[FB];
     float x1[FB][R], x2[FB][R];
 #pragma unroll
     for (int u = 0; u < FB; ++u) {
-      e[u] = f + u < f1 ? __ldg(a.fus + f + u) : make_int4(0, 0, -1, 0);
-      const bool ld = act && e[u].z >= 0;
-      const XT* p1 = x + static_cast<long long>(e[u].x >> 1) * a.x_pitch + col;
-      const XT* p2 = x + static_cast<long long>(e[u].y >> 1) * a.x_pitch + col;
+      const bool ok = f + u < f1;
+      c0[u] = ok ? __ldg(a.fus + 2 * (f + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      c1[u] = ok ? __ldg(a.fus + 2 * (f + u) + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const bool ld = act && ok;
+      const XT* p1 = x + static_cast<long long>(__float_as_int(c1[u].z)) * a.x_pitch + col;
+      const XT* p2 = x + static_cast<long long>(__float_as_int(c1[u].w)) * a.x_pitch + col;
       if constexpr (R == 4) {
         if (ld) {
           load_xvec<XT, 4>(p1, x1[u]);
           load_xvec<XT, 4>(p2, x2[u]);
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) x1[u][r] = x2[u][r] = 0.0f;
         }
       } else {
 #pragma unroll
@@ -432,21 +438,13 @@ __device__ __forceinline__ void fused_sum(const CsrArgs& a, int v, long long col
     }
 #pragma unroll
     for (int u = 0; u < FB; ++u) {
-      if (e[u].z < 0) continue;  // uniform
-      const float4* tab = a.coef + e[u].z;
-      const float s1 = (e[u].x & 1) ? -1.0f : 1.0f, s2 = (e[u].y & 1) ? -1.0f : 1.0f;
-      const float ss = (e[u].w & 1) ? -1.0f : 1.0f;
-      const float Es = __ldg(&tab[1].y) * (s1 * s2);  // real root, the other signs folded
-      // the complex pair {tan, 0, E'}, absent when its coefficient is zero
-      const float4 cc = __ldg(&tab[0].y) > 0.5f ? __ldg(tab + 2) : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float ia1 = cc.x * s1, ia2 = cc.x * s2;
-      const float p0r = cc.z * cc.x, p0i = cc.w * cc.x;
+      // an absent occurrence has all constants 0 and adds 0
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const float w1 = x1[u][r] * ia1, w2 = x2[u][r] * ia2;
-        const float pr = fmaf(p0r, w1, -p0i), pi = fmaf(p0i, w1, p0r);
-        const float d = fmaf(Es * x1[u][r], x2[u][r], fmaf(pr, w2, -pi));
-        acc[r] = fmaf(ss, d, acc[r]);
+        const float w1 = x1[u][r] * c0[u].y, w2 = x2[u][r] * c0[u].z;
+        const float pr = fmaf(c0[u].w, w1, -c1[u].x), pi = fmaf(c1[u].x, w1, c0[u].w);
+        const float d = fmaf(c0[u].x * x1[u][r], x2[u][r], fmaf(pr, w2, -pi));
+        acc[r] = fmaf(c1[u].y, d, acc[r]);
       }
     }
   }
