@@ -226,6 +226,32 @@ def pgd_step(inst, x: np.ndarray, eta: float) -> np.ndarray:
     return np.clip(x.astype(np.float64) - eta * g, -1.0, 1.0)
 
 
+def armijo_step(inst, x: np.ndarray, s: float, beta: float, c: float, trials: int):
+    """One projected-gradient step with Armijo backtracking per restart (the
+    line search Algorithm 1 leaves unspecified, read as): g = grad F(x); trial
+    i = 0, 1, .. tries eta_i = s * beta**i and x_i = proj_[-1,1](x - eta_i g),
+    and the first trial with F(x_i) <= F(x) + c * sum_v g_v (x_i,v - x_v) is
+    taken; a restart that accepts none takes the last trial. Returns the new
+    state and the chosen trial per restart (-1 where none was accepted)."""
+    x = np.asarray(x, dtype=np.float64)
+    fe0, _, g = evaluate(inst, x, want_grad=True)
+    f0 = fe0.sum(axis=0)
+    out = np.empty_like(x)
+    chosen = np.full(x.shape[1], -1, dtype=np.int64)
+    done = np.zeros(x.shape[1], dtype=bool)
+    for i in range(trials):
+        xi = np.clip(x - (s * beta ** i) * g, -1.0, 1.0)
+        fi = objective(inst, xi)
+        dec = (g * (xi - x)).sum(axis=0)
+        ok = (fi <= f0 + c * dec) & ~done
+        out[:, ok] = xi[:, ok]
+        chosen[ok] = i
+        done |= ok
+        if i == trials - 1:
+            out[:, ~done] = xi[:, ~done]
+    return out, chosen
+
+
 def round_signs(x: np.ndarray) -> np.ndarray:
     """Sign rounding: True (-1) where x < 0, False (+1) otherwise."""
     return np.where(np.asarray(x) < 0, -1, 1).astype(np.int8)

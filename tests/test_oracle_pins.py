@@ -281,3 +281,36 @@ def test_philox_uniform_x0_properties():
     # different seeds and streams give different points
     assert not np.array_equal(x, O.philox_uniform_x0(12346, 64, 40))
     assert not np.array_equal(x, O.philox_uniform_x0(12345, 64, 40, stream=1))
+
+
+# ---- the line-search step -------------------------------------------------------
+def test_armijo_single_trial_is_the_fixed_step():
+    inst = synth.mixed_small(1)
+    x = synth.uniform_x0(inst.n, 12, 3).astype(np.float64)
+    got, chosen = O.armijo_step(inst, x, 0.07, 0.5, 1e-4, 1)
+    np.testing.assert_allclose(got, O.pgd_step(inst, x, 0.07), rtol=0, atol=1e-15)
+    assert np.all(chosen <= 0)
+
+
+def test_armijo_choice_satisfies_and_previous_violates_the_condition():
+    """The accepted trial meets the sufficient-decrease inequality, every larger
+    trial breaks it, and accepted steps never increase the objective."""
+    inst = synth.mixed_small(4)
+    x = synth.uniform_x0(inst.n, 40, 4).astype(np.float64)
+    s, beta, c, T = 30.0, 0.5, 1e-4, 8   # large first steps, so that some restarts backtrack
+    got, chosen = O.armijo_step(inst, x, s, beta, c, T)
+    _, _, g = O.evaluate(inst, x)
+    f0 = O.objective(inst, x)
+
+    def cond(i):
+        xi = np.clip(x - s * beta ** i * g, -1, 1)
+        return O.objective(inst, xi) <= f0 + c * (g * (xi - x)).sum(axis=0)
+
+    conds = np.stack([cond(i) for i in range(T)])
+    for b in range(x.shape[1]):
+        if chosen[b] >= 0:
+            assert conds[chosen[b], b] and not conds[:chosen[b], b].any()
+            assert O.objective(inst, got[:, [b]])[0] <= f0[b] + 1e-12
+        else:
+            assert not conds[:, b].any()
+    assert np.any(chosen > 0) and np.any(chosen == 0)
