@@ -52,6 +52,7 @@ WORKLOADS = {
               "5% CARD(10..100); B=64 restarts each, one handle", 64),
 }
 METRIC = "FE+grad literal-evals/s"
+LINE_SEARCH = (1.0, 0.5, 1e-4, 6)   # first step, backtracking factor, sufficient-decrease constant, trials
 UNIT = "literal-evals/s"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fe_grad_traffic.json")
 KERNEL_SOURCES = ["paper_2606_06641_gb300/csrc/fe_short.cuh", "paper_2606_06641_gb300/csrc/kernels.cu",
@@ -229,10 +230,16 @@ def measure_time_to_solve(n_inst: int, B: int, eta: float, max_steps: int, seed:
     solver.solve_batched(insts[:2], B, eta, 5, seed=seed)       # warm the library and allocator
     plain = solver.solve_plain(insts, B, eta, max_steps, x0s=x0s)
     batched = solver.solve_batched(insts, B, eta, max_steps, x0=x_all, steps_per_poll=10)
+    ls = LINE_SEARCH
+    batched_ls = solver.solve_batched(insts, B, eta, max_steps, x0=x_all, line_search=ls)
     forms = {"plain": (plain.solved, plain.seconds, plain.steps, plain.total_seconds),
-             "batched": (batched.solved, batched.seconds, batched.steps, batched.total_seconds)}
+             "batched": (batched.solved, batched.seconds, batched.steps, batched.total_seconds),
+             "batched_line_search": (batched_ls.solved, batched_ls.seconds, batched_ls.steps,
+                                     batched_ls.total_seconds)}
     out = tts_summary(forms)
     out.update({"instances": n_inst, "n": 50, "m": 213, "restarts": B, "eta": eta, "max_steps": max_steps,
+                "line_search": {"s": ls[0], "beta": ls[1], "c": ls[2], "trials": ls[3],
+                                "note": "Armijo backtracking per restart, checked every iteration"},
                 "same_solved_set": bool(np.array_equal(plain.solved, batched.solved)),
                 "start_points": "identical (Philox, batch convention) for both forms"})
     return out

@@ -146,6 +146,20 @@ int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_d
  * captures). */
 int afs_step(afs_handle* h, int32_t nsteps, void* stream);
 
+/* afs_step_ls: nsteps iterations of Algorithm 1 with a backtracking line
+ * search instead of the fixed step (the paper leaves its line search
+ * unspecified; this is projected Armijo backtracking per restart): with
+ * g = grad F(x), trial i = 0 .. trials-1 tries eta_i = s * beta^i and
+ * x_i = clamp(x - eta_i g, -1, 1), and the first trial with
+ * F(x_i) <= F(x) + c * sum_v g_v (x_i,v - x_v) is taken (a restart that
+ * accepts none takes the last trial). F is evaluated with the same kernels as
+ * afs_eval_fe_grad. Fixed variables (afs_set_fixed) are not moved. The call
+ * ends with an exact count of the final state (afs_get_verify). chosen_dev
+ * (nullable, device, n_inst * B) receives the trial each restart took in the
+ * last iteration, -1 where it accepted none. Not captured in a graph. */
+int afs_step_ls(afs_handle* h, int32_t nsteps, float s, float beta, float c, int32_t trials, int32_t* chosen_dev,
+                void* stream);
+
 /* afs_round_and_verify: sign-round every restart (x < 0 -> True), count the
  * violated constraints exactly (Algorithm 1's unsat count), and report:
  *   unsat_host[B * n_inst] (nullable)  per instance and restart

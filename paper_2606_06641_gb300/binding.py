@@ -67,6 +67,7 @@ SIGNATURES = {
     "afs_tiles": (_I32, [_P, _P, _P, _P, _I32]),
     "afs_get_step_check": (_I32, [_P, _P, _P, _P]),
     "afs_set_fixed": (_I32, [_P, _P, _I32, _P]),
+    "afs_step_ls": (_I32, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I32, _P, _P]),
     "afs_set_tiles": (_I32, [_P, _I32, _P, _P, _I32]),
     "afs_coef_table": (_I32, [_I32, _I32, _I32, _I32, _I32, _I32, _I32, _P, _I32, _P]),
     "afs_esp_coefficients": (_I32, [_I32, _I32, _I32, _I32, _I32, _P]),
@@ -238,6 +239,17 @@ def get_verify(h: Handle, stream=None):
     sol = torch.empty(h.n_inst, dtype=torch.int32, device="cuda")
     _check(lib().afs_get_verify(h.ptr, _ptr(un), _ptr(sol), _stream(stream)))
     return un, sol
+
+
+def step_ls(h: Handle, nsteps: int, s: float = 1.0, beta: float = 0.5, c: float = 1e-4, trials: int = 6,
+            stream=None):
+    """nsteps iterations with Armijo backtracking per restart; returns the trial
+    each restart took in the last iteration (-1 = none accepted) [n_inst, B]."""
+    import torch
+    chosen = torch.empty((h.n_inst, h.B), dtype=torch.int32, device="cuda")
+    _check(lib().afs_step_ls(h.ptr, int(nsteps), float(s), float(beta), float(c), int(trials), _ptr(chosen),
+                             _stream(stream)))
+    return chosen
 
 
 def set_fixed(h: Handle, values=None, stream=None) -> None:

@@ -111,6 +111,31 @@ struct CheckArgs {
 };
 void launch_check_bits(const CheckArgs& a, cudaStream_t s);
 
+// Line search (afs_step_ls). Per-restart objective: out[inst * B + b] =
+// sum of fe[c * pitch + b] over the constraints c of each instance (cinst[c]
+// = instance of load-order constraint c).
+void launch_objective(const float* fe, long long pitch, int m, const int* cinst, int B, float* out, cudaStream_t s);
+// Candidate of one trial: for the restarts with done == 0, xc = proj(x - eta g)
+// (fixed variables keep x) and dec[inst * B + b] += sum_v g (xc - x).
+struct LsCandArgs {
+  const void* x;
+  void* xc;
+  const float* g;
+  long long pitch;          // of x, xc and g
+  int n, B, xt;
+  float eta;
+  const int* done;          // [n_inst * B]
+  const int* var_inst;      // instance of each variable
+  const signed char* fixv;  // nullable partial assignments
+  int n_fix_groups;
+  float* dec;               // [n_inst * B]
+};
+void launch_ls_candidate(const LsCandArgs& a, cudaStream_t s);
+// Acceptance: done, chosen = trial where the restart was not done and
+// f_trial <= f0 + c * dec.
+void launch_ls_accept(const float* f_trial, const float* f0, const float* dec, float c, int trial, int* done,
+                      int* chosen, long long count, cudaStream_t s);
+
 // Solved bits (1 = no violated constraint) of the violation words of a check,
 // restarts >= B cleared: out[inst * W + w].
 void launch_solved_words(const unsigned* vword, int n_inst, int W, int B, unsigned* out, cudaStream_t s);

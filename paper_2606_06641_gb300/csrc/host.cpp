@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -154,7 +155,7 @@ struct afs_handle {
   double work_per_restart = 0.0;
   // device instance data
   DevBuf litslot, cons_tab, cons_orig, cons_k, cons_lit, coef, csr_off, lit_enc, lit_off, viol_off, viol,
-      var_inst, err, chk_em, chk_ranges, fus_off, fus;
+      var_inst, err, chk_em, chk_ranges, fus_off, fus, cinst;
   int n_chk_ranges = 0;
   // restart state
   int B = 0, xt = XT_F32;
@@ -172,6 +173,8 @@ struct afs_handle {
   // partial assignments: fix_groups rows of n int8 (0 = free, +1 True, -1 False)
   DevBuf fixv;
   int fix_groups = 0;
+  // line search: FE rows, gradient, per-restart objective / decrease / state
+  DevBuf ls_fe, ls_g, ls_f0, ls_fi, ls_dec, ls_done, ls_chosen;
   int parity = 0;
   void* xcur() const { return xb[parity].p; }
   bool step_check_valid = false;  // vword[parity ^ 1] holds the last step's check
@@ -502,6 +505,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   if ((rc = upload(h->coef, coef, s))) return rc;
   if ((rc = upload(h->csr_off, csr, s))) return rc;
   if ((rc = upload(h->fus_off, fcsr, s))) return rc;
+  if ((rc = upload(h->cinst, ginst, s))) return rc;
   if ((rc = upload(h->fus, fus, s))) return rc;
   if ((rc = upload(h->lit_enc, h->h_lit_enc, s))) return rc;
   if ((rc = upload(h->lit_off, h->h_lit_off, s))) return rc;
@@ -1371,6 +1375,90 @@ int afs_eval_fe_grad(afs_handle* h, const void* x_dev, int32_t x_dtype, int32_t 
       if (rc) return rc;
     }
   }
+  return AFS_OK;
+}
+
+// FE of every constraint (load order, rows of pitch floats) and, with g, the
+// gradient of the state x (the handle's layout), chunk by chunk.
+static int eval_state(afs_handle* h, const void* x, float* fe, float* g, cudaStream_t s) {
+  for (int b0 = 0; b0 < h->B; b0 += h->Bc) {
+    const int nb = std::min(h->Bc, h->B - b0);
+    for (const Group& gr : h->groups) {
+      int rc = launch_fe_group(h, gr, x, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, fe, h->pitch, s);
+      if (rc) return rc;
+    }
+    if (g) {
+      int rc = launch_csr(h, x, nullptr, h->xt, h->pitch, b0, nb, h->go.as<float>(), h->Bc, 0.0f, g, h->pitch, false,
+                          -1, s);
+      if (rc) return rc;
+    }
+  }
+  return AFS_OK;
+}
+
+int afs_step_ls(afs_handle* h, int32_t nsteps, float step0, float beta, float c, int32_t trials, int32_t* chosen_dev,
+                void* stream) {
+  if (!h) return fail(AFS_E_ARG, "NULL handle");
+  if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
+  if (nsteps < 0 || trials < 1 || !(step0 > 0.0f) || !(beta > 0.0f && beta < 1.0f) || !(c >= 0.0f))
+    return fail(AFS_E_ARG, "need nsteps >= 0, trials >= 1, s > 0, 0 < beta < 1, c >= 0");
+  if (nsteps == 0) return AFS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t nib = static_cast<size_t>(h->n_inst) * h->B;
+  int rc;
+  if ((rc = h->ls_fe.alloc(sizeof(float) * static_cast<size_t>(std::max(h->m, 1)) * h->pitch))) return rc;
+  if ((rc = h->ls_g.alloc(sizeof(float) * static_cast<size_t>(h->n) * h->pitch))) return rc;
+  if ((rc = h->ls_f0.alloc(sizeof(float) * nib))) return rc;
+  if ((rc = h->ls_fi.alloc(sizeof(float) * nib))) return rc;
+  if ((rc = h->ls_dec.alloc(sizeof(float) * nib))) return rc;
+  if ((rc = h->ls_done.alloc(sizeof(int) * nib))) return rc;
+  if ((rc = h->ls_chosen.alloc(sizeof(int) * nib))) return rc;
+  float* fe = h->ls_fe.as<float>();
+  for (int t = 0; t < nsteps; ++t) {
+    const int p = h->parity;
+    void* xin = h->xb[p].p;
+    void* xout = h->xb[p ^ 1].p;
+    if ((rc = eval_state(h, xin, fe, h->ls_g.as<float>(), s))) return rc;
+    CK(cudaMemsetAsync(h->ls_f0.p, 0, sizeof(float) * nib, s));
+    launch_objective(fe, h->pitch, h->m, h->cinst.as<int>(), h->B, h->ls_f0.as<float>(), s);
+    CKL();
+    CK(cudaMemsetAsync(h->ls_done.p, 0, sizeof(int) * nib, s));
+    launch_fill_int(h->ls_chosen.as<int>(), -1, static_cast<long long>(nib), s);
+    for (int i = 0; i < trials; ++i) {
+      CK(cudaMemsetAsync(h->ls_dec.p, 0, sizeof(float) * nib, s));
+      LsCandArgs a{};
+      a.x = xin;
+      a.xc = xout;
+      a.g = h->ls_g.as<float>();
+      a.pitch = h->pitch;
+      a.n = h->n;
+      a.B = h->B;
+      a.xt = h->xt;
+      a.eta = static_cast<float>(step0 * std::pow(static_cast<double>(beta), i));
+      a.done = h->ls_done.as<int>();
+      a.var_inst = h->var_inst.as<int>();
+      a.fixv = h->fix_groups > 0 ? h->fixv.as<signed char>() : nullptr;
+      a.n_fix_groups = h->fix_groups;
+      a.dec = h->ls_dec.as<float>();
+      launch_ls_candidate(a, s);
+      CKL();
+      if ((rc = eval_state(h, xout, fe, nullptr, s))) return rc;
+      CK(cudaMemsetAsync(h->ls_fi.p, 0, sizeof(float) * nib, s));
+      launch_objective(fe, h->pitch, h->m, h->cinst.as<int>(), h->B, h->ls_fi.as<float>(), s);
+      CKL();
+      launch_ls_accept(h->ls_fi.as<float>(), h->ls_f0.as<float>(), h->ls_dec.as<float>(), c, i,
+                       h->ls_done.as<int>(), h->ls_chosen.as<int>(), static_cast<long long>(nib), s);
+      CKL();
+    }
+    // restarts that accepted no trial keep the last candidate, already in xout
+    h->parity ^= 1;
+    if ((rc = afs::state_written(h, s))) return rc;
+  }
+  // the next checked step ORs into the words of its parity: start both clean
+  CK(cudaMemsetAsync(h->vword.p, 0, h->vword.bytes, s));
+  h->step_check_valid = false;
+  if ((rc = launch_check(h, h->xcur(), s))) return rc;
+  if (chosen_dev) CK(cudaMemcpyAsync(chosen_dev, h->ls_chosen.p, sizeof(int) * nib, cudaMemcpyDeviceToDevice, s));
   return AFS_OK;
 }
 

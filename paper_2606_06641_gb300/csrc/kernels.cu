@@ -1017,6 +1017,87 @@ void launch_solved_words(const unsigned* vword, int n_inst, int W, int B, unsign
   solved_words_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(vword, n_inst, W, B, out);
 }
 
+// ---------------------------------------------------------------------------
+// Line search (Armijo backtracking per restart)
+// ---------------------------------------------------------------------------
+// Thread per restart column of a chunk of 64 constraint rows; the sum runs
+// over the rows of one instance at a time and is added with an atomic.
+__global__ void objective_kernel(const float* fe, long long pitch, int m, const int* cinst, int B, float* out) {
+  const int b = blockIdx.y * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const int r0 = blockIdx.x * 64, r1 = min(m, r0 + 64);
+  float acc = 0.0f;
+  int cur = __ldg(cinst + r0);
+  for (int r = r0; r < r1; ++r) {
+    const int ir = __ldg(cinst + r);
+    if (ir != cur) {
+      atomicAdd(out + static_cast<long long>(cur) * B + b, acc);
+      acc = 0.0f;
+      cur = ir;
+    }
+    acc += fe[static_cast<long long>(r) * pitch + b];
+  }
+  atomicAdd(out + static_cast<long long>(cur) * B + b, acc);
+}
+
+void launch_objective(const float* fe, long long pitch, int m, const int* cinst, int B, float* out, cudaStream_t s) {
+  if (m <= 0 || B <= 0) return;
+  const dim3 grid(static_cast<unsigned>((m + 63) / 64), static_cast<unsigned>((B + 127) / 128));
+  objective_kernel<<<grid, 128, 0, s>>>(fe, pitch, m, cinst, B, out);
+}
+
+template <typename XT>
+__global__ void ls_candidate_kernel(LsCandArgs a) {
+  const int b = blockIdx.y * blockDim.x + threadIdx.x;
+  if (b >= a.B) return;
+  const int v0 = blockIdx.x * 64, v1 = min(a.n, v0 + 64);
+  const XT* x = static_cast<const XT*>(a.x);
+  XT* xc = static_cast<XT*>(a.xc);
+  int cur = __ldg(a.var_inst + v0);
+  float acc = 0.0f;
+  for (int v = v0; v < v1; ++v) {
+    const int iv = __ldg(a.var_inst + v);
+    if (iv != cur) {
+      if (!a.done[static_cast<long long>(cur) * a.B + b]) atomicAdd(a.dec + static_cast<long long>(cur) * a.B + b, acc);
+      acc = 0.0f;
+      cur = iv;
+    }
+    if (a.done[static_cast<long long>(iv) * a.B + b]) continue;
+    const long long i = static_cast<long long>(v) * a.pitch + b;
+    const float xv = load_x<XT>(x + i), gv = a.g[i];
+    const bool fixed = a.fixv != nullptr &&
+                       a.fixv[static_cast<long long>(b) * a.n_fix_groups / a.B * a.n + v] != 0;
+    const float xn = fixed ? xv : stored_value<XT>(fminf(fmaxf(fmaf(-a.eta, gv, xv), -1.0f), 1.0f));
+    store_x<XT>(xc + i, xn);
+    acc = fmaf(gv, xn - xv, acc);
+  }
+  if (!a.done[static_cast<long long>(cur) * a.B + b]) atomicAdd(a.dec + static_cast<long long>(cur) * a.B + b, acc);
+}
+
+void launch_ls_candidate(const LsCandArgs& a, cudaStream_t s) {
+  if (a.n <= 0 || a.B <= 0) return;
+  const dim3 grid(static_cast<unsigned>((a.n + 63) / 64), static_cast<unsigned>((a.B + 127) / 128));
+  if (a.xt == XT_F32) ls_candidate_kernel<float><<<grid, 128, 0, s>>>(a);
+  else ls_candidate_kernel<__nv_bfloat16><<<grid, 128, 0, s>>>(a);
+}
+
+__global__ void ls_accept_kernel(const float* f_trial, const float* f0, const float* dec, float c, int trial,
+                                 int* done, int* chosen, long long count) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= count || done[i]) return;
+  if (f_trial[i] <= fmaf(c, dec[i], f0[i])) {
+    done[i] = 1;
+    chosen[i] = trial;
+  }
+}
+
+void launch_ls_accept(const float* f_trial, const float* f0, const float* dec, float c, int trial, int* done,
+                      int* chosen, long long count, cudaStream_t s) {
+  if (count <= 0) return;
+  ls_accept_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, s>>>(f_trial, f0, dec, c, trial, done, chosen,
+                                                                            count);
+}
+
 __global__ void fill_int_kernel(int* p, int v, long long n) {
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;

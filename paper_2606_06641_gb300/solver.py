@@ -100,8 +100,10 @@ def solve_plain(insts: Sequence[Instance], B: int, eta: float, max_steps: int, s
 
 
 def solve_batched(insts: Sequence[Instance], B: int, eta: float, max_steps: int, seed: int = 0,
-                  steps_per_poll: int = 10, x0=None) -> SolveResult:
-    """All instances in one handle; S-step graph replays, solved flags polled between them."""
+                  steps_per_poll: int = 10, x0=None, line_search=None) -> SolveResult:
+    """All instances in one handle; S-step graph replays, solved flags polled
+    between them. line_search = (s, beta, c, trials) replaces the fixed step by
+    Armijo backtracking (afs_step_ls, one iteration per poll)."""
     import torch
     n = len(insts)
     solved = np.zeros(n, bool)
@@ -116,7 +118,11 @@ def solve_batched(insts: Sequence[Instance], B: int, eta: float, max_steps: int,
     S = max(1, steps_per_poll)
     while done_steps < max_steps:
         s = min(S, max_steps - done_steps)
-        bd.step(h, s)
+        if line_search is None:
+            bd.step(h, s)
+        else:
+            s = 1
+            bd.step_ls(h, 1, *line_search)
         done_steps += s
         _, sol = bd.get_verify(h)
         sol_host.copy_(sol)

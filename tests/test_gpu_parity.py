@@ -500,3 +500,54 @@ def test_reader_units_as_partial_assignment():
     assert sol[0] == 1
     for v, val in p.units.items():
         assert asg[v - 1] == (-1 if val else 1)   # the sign of x: -1 = True
+
+
+# ---- line search ---------------------------------------------------------------
+def test_line_search_step_matches_the_oracle():
+    """One Armijo step: the trial each restart takes is the oracle's (except
+    where the sufficient-decrease test is within FP32 noise of its bound), and
+    the new state equals the oracle's for those restarts."""
+    inst = synth.mixed_small(4)
+    B = 40
+    x0 = synth.uniform_x0(inst.n, B, 4)
+    s, beta, c, T = 30.0, 0.5, 1e-4, 8
+    ref, ref_chosen = O.armijo_step(inst, x0.astype(np.float64), s, beta, c, T)
+    h = bd.load_instance(inst, bd.default_params(autotune=0))
+    bd.init_restarts(h, B, x0=_dev(x0))
+    chosen = bd.step_ls(h, 1, s, beta, c, T).cpu().numpy()[0]
+    x1 = bd.get_x(h).cpu().numpy()
+    # the margin of each trial's test, from the oracle
+    _, _, g = O.evaluate(inst, x0.astype(np.float64))
+    f0 = O.objective(inst, x0.astype(np.float64))
+    close = np.zeros(B, bool)
+    for i in range(T):
+        xi = np.clip(x0 - s * beta ** i * g, -1, 1)
+        margin = O.objective(inst, xi) - (f0 + c * (g * (xi - x0)).sum(axis=0))
+        close |= np.abs(margin) < 1e-4 * np.maximum(1.0, np.abs(f0))
+    same = chosen == ref_chosen
+    assert np.all(same | close)
+    assert same.sum() >= B - 2
+    assert np.abs(x1[:, same] - ref[:, same]).max() <= 1e-4
+    assert np.any(ref_chosen > 0)
+    un, _ = bd.get_verify(h)
+    np.testing.assert_array_equal(un.cpu().numpy()[0], O.unsat_count(inst, x1))
+
+
+def test_line_search_then_fixed_steps_with_partial_assignment():
+    inst = synth.hybrid_n2000(2)
+    B = 64
+    fix = np.zeros(inst.n, np.int8)
+    fix[:50] = 1
+    h = bd.load_instance(inst, bd.default_params(eta=0.1, autotune=0))
+    bd.init_restarts(h, B, seed=5)
+    bd.set_fixed(h, fix)
+    f_before = O.objective(inst, bd.get_x(h).cpu().numpy().astype(np.float64))
+    chosen = bd.step_ls(h, 3, 1.0, 0.5, 1e-4, 6).cpu().numpy()
+    x = bd.get_x(h).cpu().numpy()
+    assert np.all(x[:50] == -1.0)
+    assert np.all(O.objective(inst, x.astype(np.float64))[chosen[0] >= 0] <= f_before[chosen[0] >= 0] + 1e-3)
+    bd.step(h, 2)   # the checked fixed-step path runs on after the line-search steps
+    x2 = bd.get_x(h).cpu().numpy()
+    un, _ = bd.get_verify(h)
+    np.testing.assert_array_equal(un.cpu().numpy()[0], O.unsat_count(inst, x2))
+    assert np.all(x2[:50] == -1.0)
