@@ -413,8 +413,11 @@ def run_ours(args):
         flush.fill_(float(r))
         e0[r].record(stream)
         bd.step(h, S)
+        # each replay ends, as a solver's poll does, with the exact count of
+        # the state it left (two kernels: the counting check and the fold)
+        bd.get_verify(h)
         e1[r].record(stream)
-        launches += bd.last_launch_count(h)
+        launches += bd.last_launch_count(h) + 2
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -563,6 +566,7 @@ def run_batch_sweep(args):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             bd.step(h, S)
+            bd.get_verify(h)
             e1.record(stream)
             torch.cuda.synchronize()
             ms += e0.elapsed_time(e1)

@@ -139,9 +139,9 @@ int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_d
  * With verify_every != 0 each iteration also checks exactly, beside its FE
  * launches, the sign-rounded state it reads (Algorithm 1's is_sat, computed
  * on packed sign words 32 restarts at a time); a restart that violates
- * nothing is solved and is not moved again (Algorithm 1 returns on is_sat),
- * and the call ends with an exact count of the final state's violated
- * constraints (afs_get_verify). Replayed as a captured CUDA graph when
+ * nothing is solved and is not moved again (Algorithm 1 returns on is_sat).
+ * The exact count of the final state's violated constraints is computed when
+ * afs_get_verify first asks for it. Replayed as a captured CUDA graph when
  * use_graph is set (the first call for a given nsteps and step parity
  * captures). */
 int afs_step(afs_handle* h, int32_t nsteps, void* stream);
@@ -179,10 +179,11 @@ int afs_round_and_verify(afs_handle* h, int32_t* unsat_host, int32_t* best_host,
 int afs_get_x(afs_handle* h, float* x_dev, void* stream);
 /* Overwrite the state from FP32 x_dev[v * B + b] (rounded for BF16 storage). */
 int afs_set_x(afs_handle* h, const float* x_dev, void* stream);
-/* Read the per-restart unsat counts of the check that ended the last afs_step
- * call (the state it left) into unsat_dev[n_inst * B] and the lowest restart
- * seen solved per instance since afs_init_restarts (INT32_MAX if none) into
- * solved_dev[n_inst]; either may be NULL. */
+/* Read the per-restart unsat counts of the current state into
+ * unsat_dev[n_inst * B] and the lowest restart seen solved per instance since
+ * afs_init_restarts (INT32_MAX if none) into solved_dev[n_inst]; either may be
+ * NULL. The exact count runs on `stream` (the bit-sliced check in count mode)
+ * on the first call after the state changed; later calls copy it. */
 int afs_get_verify(afs_handle* h, int32_t* unsat_dev, int32_t* solved_dev, void* stream);
 /* afs_set_fixed: partial assignments (the paper's prefix assignments). values
  * holds n_groups rows of n_total int8 (variables of the handle in load order):

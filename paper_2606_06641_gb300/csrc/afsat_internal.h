@@ -12,6 +12,10 @@ enum XType { XT_F32 = 0, XT_BF16 = 1 };
 // occurrence-derivative rows: the derivative of each of their occurrences is
 // recomputed from the other two literals' state by a gather-side pass.
 constexpr int KFUSE = 3;
+// Each variable's list of such entries is padded with zero entries (all
+// constants 0, both other literals the variable itself) to a multiple of
+// FUS_PAD, so that the pass reads them in pairs without bounds selects.
+constexpr int FUS_PAD = 2;
 
 // One FE+gradient launch over a group of constraints that share a length k
 // and are stored contiguously in bucket order: constraint c of the group owns

@@ -178,6 +178,7 @@ struct afs_handle {
   int parity = 0;
   void* xcur() const { return xb[parity].p; }
   bool step_check_valid = false;  // vword[parity ^ 1] holds the last step's check
+  bool count_valid = false;       // unsat holds the exact count of the current state
   long long eval_go_cols = 0;
   // graphs
   cudaStream_t cap = nullptr;
@@ -400,11 +401,19 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   std::vector<int> csr(h->n + 1, 0), fcsr(h->n + 1, 0);
   for (int pos = 0; pos < m; ++pos)
     for (int t = 0; t < b_k[pos]; ++t) (fused_k(b_k[pos]) ? fcsr : csr)[(litslot[b_lit[pos] + t].x >> 1) + 1]++;
+  long long n_fused = 0;
   for (int v = 0; v < h->n; ++v) {
     csr[v + 1] += csr[v];
-    fcsr[v + 1] += fcsr[v];
+    n_fused += fcsr[v + 1];
+    fcsr[v + 1] = fcsr[v] + (fcsr[v + 1] + FUS_PAD - 1) / FUS_PAD * FUS_PAD;
   }
-  std::vector<float4> fus(2 * static_cast<size_t>(fcsr[h->n]));
+  // padding entries: zero constants, both other literals the variable itself
+  std::vector<float4> fus(2 * static_cast<size_t>(fcsr[h->n]), make_float4(0.f, 0.f, 0.f, 0.f));
+  for (int v = 0; v < h->n; ++v) {
+    float fv;
+    std::memcpy(&fv, &v, 4);
+    for (int f = fcsr[v]; f < fcsr[v + 1]; ++f) fus[2 * static_cast<size_t>(f) + 1] = make_float4(0.f, 0.f, fv, fv);
+  }
   {
     std::vector<int> fill(csr.begin(), csr.end() - 1), ffill(fcsr.begin(), fcsr.end() - 1);
     for (int pos = 0; pos < m; ++pos) {
@@ -438,7 +447,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     }
   }
   h->Lgo = csr[h->n];
-  h->n_fused = fcsr[h->n];
+  h->n_fused = n_fused;
   // ---- exact-check structures (load order) ----
   h->h_lit_enc.resize(L);
   h->h_lit_off.assign(m + 1, 0);
@@ -789,11 +798,6 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int p
       }
     }
   }
-  if (check && nsteps > 0) {
-    int rc = launch_check(h, h->xb[(parity0 + nsteps) & 1].p, s);
-    if (rc) return rc;
-    nl += 2;
-  }
   if (launches) *launches = nl;
   return AFS_OK;
 }
@@ -1030,6 +1034,7 @@ void* afs::handle_ext(const afs_handle* h) { return h ? h->ext : nullptr; }
 
 int afs::state_written(afs_handle* h, cudaStream_t s) {
   if (!h || h->B <= 0) return fail(AFS_E_STATE, "no restart state");
+  h->count_valid = false;
   if (h->fix_groups > 0) {
     launch_apply_fixed(h->xcur(), h->xt, h->pitch, h->n, h->B, h->fixv.as<signed char>(), h->fix_groups, s);
     CKL();
@@ -1180,6 +1185,7 @@ int afs_step(afs_handle* h, int32_t nsteps, void* stream) {
   const int p0 = h->parity;
   h->parity = (h->parity + nsteps) & 1;
   h->step_check_valid = check;
+  h->count_valid = false;
   if (!h->p.use_graph) {
     int rc = enqueue_steps(h, nsteps, h->p.eta, check, p0, s, &h->last_launches);
     if (rc) return rc;
@@ -1253,6 +1259,7 @@ int afs_round_and_verify(afs_handle* h, int32_t* unsat_host, int32_t* best_host,
   CKL();
   int rc = launch_check(h, h->xcur(), s);
   if (rc) return rc;
+  h->count_valid = true;
   const size_t nib = static_cast<size_t>(h->n_inst) * h->B;
   std::vector<int> un(nib);
   CK(cudaMemcpyAsync(un.data(), h->unsat.p, nib * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1309,6 +1316,11 @@ int afs_get_verify(afs_handle* h, int32_t* unsat_dev, int32_t* solved_dev, void*
   if (!h) return fail(AFS_E_ARG, "NULL handle");
   if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!h->count_valid) {  // the exact count of the current state, computed when first asked for
+    int rc = launch_check(h, h->xcur(), s);
+    if (rc) return rc;
+    h->count_valid = true;
+  }
   if (unsat_dev)
     CK(cudaMemcpyAsync(unsat_dev, h->unsat.p, sizeof(int) * static_cast<size_t>(h->n_inst) * h->B,
                        cudaMemcpyDeviceToDevice, s));
@@ -1458,6 +1470,7 @@ int afs_step_ls(afs_handle* h, int32_t nsteps, float step0, float beta, float c,
   CK(cudaMemsetAsync(h->vword.p, 0, h->vword.bytes, s));
   h->step_check_valid = false;
   if ((rc = launch_check(h, h->xcur(), s))) return rc;
+  h->count_valid = true;
   if (chosen_dev) CK(cudaMemcpyAsync(chosen_dev, h->ls_chosen.p, sizeof(int) * nib, cudaMemcpyDeviceToDevice, s));
   return AFS_OK;
 }
@@ -1480,6 +1493,8 @@ int afs_step_host(afs_handle* h, const float* x_host, float* x_out_host, int32_t
   int rc = afs_step(h, 1, stream);
   h->p.verify_every = ve;
   if (rc) return rc;
+  if ((rc = launch_check(h, h->xcur(), s))) return rc;
+  h->count_valid = true;
   CK(cudaMemcpyAsync(unsat_host, h->unsat.p, sizeof(int) * static_cast<size_t>(h->n_inst) * h->B,
                      cudaMemcpyDeviceToHost, s));
   if (x_out_host) {

@@ -409,15 +409,19 @@ template <typename XT, int R, int FB>
 __device__ __forceinline__ void fused_sum(const CsrArgs& a, int v, long long col, bool act, float (&acc)[R]) {
   const int f0 = __ldg(a.fus_off + v), f1 = __ldg(a.fus_off + v + 1);
   const XT* x = static_cast<const XT*>(a.x);
+  // lists are padded to pairs: with FB == FUS_PAD every entry of a batch
+  // exists, and col (clamped to the launch's first restart on idle lanes) is
+  // a valid column, so the loads need no guard
+  constexpr bool PAIRS = FB == FUS_PAD;
   for (int f = f0; f < f1; f += FB) {  // uniform per warp
     float4 c0[FB], c1[FB];
     float x1[FB][R], x2[FB][R];
 #pragma unroll
     for (int u = 0; u < FB; ++u) {
-      const bool ok = f + u < f1;
+      const bool ok = PAIRS || f + u < f1;
       c0[u] = ok ? __ldg(a.fus + 2 * (f + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
       c1[u] = ok ? __ldg(a.fus + 2 * (f + u) + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-      const bool ld = act && ok;
+      const bool ld = PAIRS || (act && ok);
       const XT* p1 = x + static_cast<long long>(__float_as_int(c1[u].z)) * a.x_pitch + col;
       const XT* p2 = x + static_cast<long long>(__float_as_int(c1[u].w)) * a.x_pitch + col;
       if constexpr (R == 4) {

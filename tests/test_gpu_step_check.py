@@ -210,3 +210,34 @@ def test_step_check_unavailable_after_unchecked_step():
     bd.step(h, 1)
     with pytest.raises(RuntimeError):
         bd.get_step_check(h)
+
+
+def test_count_follows_every_state_write():
+    """get_verify counts the current state: right after init_restarts, after
+    steps, after set_x and after set_fixed, and a repeated call agrees."""
+    rng = np.random.default_rng(13)
+    B = 64
+    inst, x = _planted_case(70, 180, 9, B, rng)
+    h = bd.load_instance(inst, bd.default_params(eta=0.07, verify_every=1, autotune=0))
+    bd.init_restarts(h, B, x0=torch.from_numpy(x).cuda())
+
+    def agree():
+        un, _ = bd.get_verify(h)
+        un2, _ = bd.get_verify(h)
+        ref = O.unsat_count(inst, bd.get_x(h).cpu().numpy())
+        np.testing.assert_array_equal(un.cpu().numpy()[0], ref)
+        np.testing.assert_array_equal(un2.cpu().numpy()[0], ref)
+
+    agree()
+    bd.step(h, 3)
+    agree()
+    x2 = np.where(rng.random(x.shape) < 0.5, -x, x).astype(np.float32)
+    bd.set_x(h, torch.from_numpy(x2).cuda())
+    agree()
+    fix = np.zeros((1, inst.n), np.int8)
+    fix[0, :10] = 1
+    bd.set_fixed(h, fix)
+    agree()
+    bd.step(h, 2)
+    agree()
+    h.free()
