@@ -12,6 +12,9 @@ enum XType { XT_F32 = 0, XT_BF16 = 1 };
 // occurrence-derivative rows: the derivative of each of their occurrences is
 // recomputed from the other two literals' state by a gather-side pass.
 constexpr int KFUSE = 3;
+// The derivative of a length-3 constraint in one of its variables is the
+// level (Walsh) expansion s (c1 + c2 (l1 + l2) + c3 l1 l2) of the other two
+// literals l = s x, folded into four constants per occurrence.
 // Each variable's list of such entries is padded with zero entries (all
 // constants 0, both other literals the variable itself) to a multiple of
 // FUS_PAD, so that the pass reads them in pairs without bounds selects.
@@ -54,7 +57,8 @@ struct CsrArgs {
   int b0, nb;
   const int* csr_off;       // slots of variable v: [csr_off[v], csr_off[v+1])
   const int* fus_off;       // fused occurrences of v: fus[fus_off[v] .. fus_off[v+1])
-  const float4* fus;        // 2 per entry: {E s1 s2, tan s1, tan s2, E'r tan}, {E'i tan, s_self, v1, v2 (int bits)}
+  const float4* fus;        // 2 per entry: {A, B1, B2, C}, {v1, v2 (int bits), 0, 0}: the derivative
+                            // in v of the entry's constraint is x1 (A x2 + B1) + B2 x2 + C
   const float4* coef;       // coefficient tables (short form)
   int v_begin, v_count;
   const float* go;

@@ -412,8 +412,19 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   for (int v = 0; v < h->n; ++v) {
     float fv;
     std::memcpy(&fv, &v, 4);
-    for (int f = fcsr[v]; f < fcsr[v + 1]; ++f) fus[2 * static_cast<size_t>(f) + 1] = make_float4(0.f, 0.f, fv, fv);
+    for (int f = fcsr[v]; f < fcsr[v + 1]; ++f) fus[2 * static_cast<size_t>(f) + 1] = make_float4(fv, fv, 0.f, 0.f);
   }
+  // Walsh coefficients by level, c_d = f_hat(|S| = d), of each fused shape
+  std::map<Shape, std::vector<double>> level_cache;
+  auto levels_of = [&](const Shape& sh) -> const std::vector<double>& {
+    auto it = level_cache.find(sh);
+    if (it == level_cache.end()) {
+      std::vector<double> c;
+      esp_coefficients(sh, c);
+      it = level_cache.emplace(sh, std::move(c)).first;
+    }
+    return it->second;
+  };
   {
     std::vector<int> fill(csr.begin(), csr.end() - 1), ffill(fcsr.begin(), fcsr.end() - 1);
     for (int pos = 0; pos < m; ++pos) {
@@ -427,21 +438,21 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
         int other[2] = {0, 0}, no = 0;
         for (int u = 0; u < k; ++u)
           if (u != t) other[no++] = litslot[b_lit[pos] + u].x;
-        // the products at the roots without the self factor, with the
-        // other literals' signs and the root scale folded into the entry:
-        // {E s1 s2, tan s1, tan s2, E'r tan}, {E'i tan, s_self, v1, v2}
-        const float* tb = &coef[4 * static_cast<size_t>(b_tab[pos])];
-        const float s1 = (other[0] & 1) ? -1.0f : 1.0f, s2 = (other[1] & 1) ? -1.0f : 1.0f;
-        const float Er = tb[5];  // the real root w = -1: {0, E, 0, 0}
-        const bool cpx = tb[1] > 0.5f;  // the complex pair {tan, 0, E'} when its coefficient is not zero
-        const float tn = cpx ? tb[8] : 0.0f, epr = cpx ? tb[10] : 0.0f, epi = cpx ? tb[11] : 0.0f;
+        // the derivative in the self literal's variable from the level
+        // expansion FE = sum_S c_|S| prod_{i in S} l_i with l = s x:
+        //   s_self (c1 + c2 (s1 x1 + s2 x2) + c3 s1 s2 x1 x2)
+        //   = x1 (A x2 + B1) + B2 x2 + C,   entry {A, B1, B2, C}, {v1, v2}
+        const std::vector<double>& cl = levels_of(shape[b_orig[pos]]);
+        const double s1 = (other[0] & 1) ? -1.0 : 1.0, s2 = (other[1] & 1) ? -1.0 : 1.0;
+        const double ss = (ls.x & 1) ? -1.0 : 1.0;
         const size_t fe = 2 * static_cast<size_t>(ffill[ls.x >> 1]++);
-        fus[fe] = make_float4(Er * (s1 * s2), tn * s1, tn * s2, epr * tn);
+        fus[fe] = make_float4(static_cast<float>(ss * cl[3] * s1 * s2), static_cast<float>(ss * cl[2] * s1),
+                              static_cast<float>(ss * cl[2] * s2), static_cast<float>(ss * cl[1]));
         int v1 = other[0] >> 1, v2 = other[1] >> 1;
         float fv1, fv2;
         std::memcpy(&fv1, &v1, 4);
         std::memcpy(&fv2, &v2, 4);
-        fus[fe + 1] = make_float4(epi * tn, (ls.x & 1) ? -1.0f : 1.0f, fv1, fv2);
+        fus[fe + 1] = make_float4(fv1, fv2, 0.0f, 0.0f);
         ls.y = -1;
       }
     }

@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 
 #include "afsat_internal.h"
 #include "fe_short.cuh"
@@ -405,25 +407,29 @@ __device__ __forceinline__ float stored_value<__nv_bfloat16>(float v) {
 // read with uniform loads (the warp's lanes share them); the gathers of FB
 // occurrences are in flight at a time, R consecutive restarts per lane
 // starting at column col.
-template <typename XT, int R, int FB>
+template <typename XT, int R, int FB, bool OFF32 = false>
 __device__ __forceinline__ void fused_sum(const CsrArgs& a, int v, long long col, bool act, float (&acc)[R]) {
   const int f0 = __ldg(a.fus_off + v), f1 = __ldg(a.fus_off + v + 1);
-  const XT* x = static_cast<const XT*>(a.x);
+  const XT* xc = static_cast<const XT*>(a.x) + col;
   // lists are padded to pairs: with FB == FUS_PAD every entry of a batch
   // exists, and col (clamped to the launch's first restart on idle lanes) is
   // a valid column, so the loads need no guard
   constexpr bool PAIRS = FB == FUS_PAD;
+  float cs = 0.0f;  // sum of the entries' constant terms (the same for every restart)
   for (int f = f0; f < f1; f += FB) {  // uniform per warp
-    float4 c0[FB], c1[FB];
+    float4 c[FB];
     float x1[FB][R], x2[FB][R];
 #pragma unroll
     for (int u = 0; u < FB; ++u) {
       const bool ok = PAIRS || f + u < f1;
-      c0[u] = ok ? __ldg(a.fus + 2 * (f + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
-      c1[u] = ok ? __ldg(a.fus + 2 * (f + u) + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+      c[u] = ok ? __ldg(a.fus + 2 * (f + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int2 vv = ok ? __ldg(reinterpret_cast<const int2*>(a.fus + 2 * (f + u) + 1)) : make_int2(0, 0);
       const bool ld = PAIRS || (act && ok);
-      const XT* p1 = x + static_cast<long long>(__float_as_int(c1[u].z)) * a.x_pitch + col;
-      const XT* p2 = x + static_cast<long long>(__float_as_int(c1[u].w)) * a.x_pitch + col;
+      // OFF32: the launch checked that every row offset v * x_pitch fits 32 bits
+      const XT* p1 = OFF32 ? xc + static_cast<unsigned>(vv.x) * static_cast<unsigned>(a.x_pitch)
+                           : xc + static_cast<long long>(vv.x) * a.x_pitch;
+      const XT* p2 = OFF32 ? xc + static_cast<unsigned>(vv.y) * static_cast<unsigned>(a.x_pitch)
+                           : xc + static_cast<long long>(vv.y) * a.x_pitch;
       if constexpr (R == 4) {
         if (ld) {
           load_xvec<XT, 4>(p1, x1[u]);
@@ -442,16 +448,19 @@ __device__ __forceinline__ void fused_sum(const CsrArgs& a, int v, long long col
     }
 #pragma unroll
     for (int u = 0; u < FB; ++u) {
-      // an absent occurrence has all constants 0 and adds 0
+      // the level expansion of the entry's derivative, x1 (A x2 + B1) + B2 x2
+      // (+ C, summed once); an absent occurrence has all constants 0
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const float w1 = x1[u][r] * c0[u].y, w2 = x2[u][r] * c0[u].z;
-        const float pr = fmaf(c0[u].w, w1, -c1[u].x), pi = fmaf(c1[u].x, w1, c0[u].w);
-        const float d = fmaf(c0[u].x * x1[u][r], x2[u][r], fmaf(pr, w2, -pi));
-        acc[r] = fmaf(c1[u].y, d, acc[r]);
+        const float t1 = fmaf(c[u].x, x2[u][r], c[u].y);
+        acc[r] = fmaf(x1[u][r], t1, acc[r]);
+        acc[r] = fmaf(c[u].z, x2[u][r], acc[r]);
       }
+      cs += c[u].w;
     }
   }
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] += cs;
 }
 
 // Invalidate the 128-byte L2 line at p (128-byte aligned) without writing it
@@ -674,7 +683,7 @@ constexpr int FUSED_THREADS = 128;
 // tasks, no persistent grid)
 constexpr int FUSED_GRID_DIV = 1;
 
-template <typename XT>
+template <typename XT, bool OFF32>
 __global__ void __launch_bounds__(FUSED_THREADS) fused_grad_kernel(CsrArgs a) {
   pdl_wait();
   pdl_trigger();
@@ -688,7 +697,7 @@ __global__ void __launch_bounds__(FUSED_THREADS) fused_grad_kernel(CsrArgs a) {
     const int bl = static_cast<int>(task - vl * tiles) * 128 + lane * 4;
     const bool act = bl < a.nb;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    fused_sum<XT, 4, FUSED_FB<XT>>(a, v, a.b0 + (act ? bl : 0), act, acc);
+    fused_sum<XT, 4, FUSED_FB<XT>, OFF32>(a, v, a.b0 + (act ? bl : 0), act, acc);
     if (act)
       *reinterpret_cast<float4*>(a.gf + static_cast<long long>(v) * a.gf_pitch + bl) =
           make_float4(acc[0], acc[1], acc[2], acc[3]);
@@ -698,15 +707,27 @@ __global__ void __launch_bounds__(FUSED_THREADS) fused_grad_kernel(CsrArgs a) {
 // Resident blocks of a kernel on the whole device (cached per kernel).
 template <typename K>
 static long long resident_blocks(K kernel, int threads, size_t smem = 0) {
-  static int cached = 0;
-  if (cached == 0) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, long long> cached;  // (kernel, threads) -> blocks
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), threads);
+  auto it = cached.find(key);
+  if (it == cached.end()) {
     int dev = 0, sms = 1, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) per = 1;
-    cached = sms * per;
+    it = cached.emplace(key, static_cast<long long>(sms) * per).first;
   }
-  return cached;
+  return it->second;
+}
+
+template <typename XT, bool OFF32>
+static void launch_fused_t(const CsrArgs& a, long long blocks, cudaStream_t s) {
+  auto kern = fused_grad_kernel<XT, OFF32>;
+  if (FUSED_GRID_DIV > 0)
+    blocks = std::min(blocks, std::max(1LL, resident_blocks(kern, FUSED_THREADS) / FUSED_GRID_DIV));
+  launch_pdl(kern, dim3(static_cast<unsigned>(blocks)), dim3(FUSED_THREADS), 0, s, a);
 }
 
 void launch_fused_grad(const CsrArgs& a, int xt, cudaStream_t s) {
@@ -714,16 +735,20 @@ void launch_fused_grad(const CsrArgs& a, int xt, cudaStream_t s) {
   if (tasks == 0) return;
   if (tasks >= (1ll << 32) - 4096LL * 1024) return;  // (never for instances that load)
   constexpr int W = FUSED_THREADS / 32;
-  long long blocks = (tasks + W - 1) / W;
+  const long long blocks = (tasks + W - 1) / W;
+  // row offsets v * x_pitch in 32 bits when the whole state fits
+  const bool off32 = static_cast<unsigned long long>(a.n_vars) * static_cast<unsigned long long>(a.x_pitch) <
+                     (1ull << 32);
   if (xt == XT_F32) {
-    if (FUSED_GRID_DIV > 0)
-      blocks = std::min(blocks, std::max(1LL, resident_blocks(fused_grad_kernel<float>, FUSED_THREADS) / FUSED_GRID_DIV));
-    launch_pdl(fused_grad_kernel<float>, dim3(static_cast<unsigned>(blocks)), dim3(FUSED_THREADS), 0, s, a);
+    if (off32)
+      launch_fused_t<float, true>(a, blocks, s);
+    else
+      launch_fused_t<float, false>(a, blocks, s);
   } else {
-    if (FUSED_GRID_DIV > 0)
-      blocks = std::min(blocks,
-                        std::max(1LL, resident_blocks(fused_grad_kernel<__nv_bfloat16>, FUSED_THREADS) / FUSED_GRID_DIV));
-    launch_pdl(fused_grad_kernel<__nv_bfloat16>, dim3(static_cast<unsigned>(blocks)), dim3(FUSED_THREADS), 0, s, a);
+    if (off32)
+      launch_fused_t<__nv_bfloat16, true>(a, blocks, s);
+    else
+      launch_fused_t<__nv_bfloat16, false>(a, blocks, s);
   }
 }
 

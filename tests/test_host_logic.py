@@ -239,3 +239,22 @@ def test_tile_spec_round_trip():
     assert chunk == 1024 and tiles == {3: (4, 2), 4: (2, 1), 5: (4, 1), 20: (1, 1)}
     assert bd.format_tiles(chunk, tiles) == spec
     assert bd.parse_tiles("0:") == (0, {})
+
+
+def test_length3_level_expansion_derivative():
+    """The fused pass's derivative of a length-3 constraint in its first
+    variable, x1 (A x2 + B1) + B2 x2 + C with A = s c3 s1 s2, B1 = s c2 s1,
+    B2 = s c2 s2, C = s c1 (c_d the library's level coefficients, l = s x),
+    equals the oracle's s * dFE/dl for every shape and sign pattern."""
+    rng = np.random.default_rng(33)
+    x = rng.uniform(-1, 1, (6, 3))
+    for (ct, op, r, par) in _shapes(3):
+        f = O.truth_table(ct, 3, op, r, par)
+        c = bd.esp_coefficients(ct, 3, op, r, par)
+        for signs in ((1, 1, 1), (-1, 1, -1), (1, -1, -1), (-1, -1, 1)):
+            s = np.array(signs, dtype=np.float64)
+            _, g = O.fe_and_dfe(f, x * s)
+            want = s[0] * g[:, 0]
+            A, B1, B2, C = s[0] * c[3] * s[1] * s[2], s[0] * c[2] * s[1], s[0] * c[2] * s[2], s[0] * c[1]
+            got = x[:, 1] * (A * x[:, 2] + B1) + B2 * x[:, 2] + C
+            np.testing.assert_allclose(got, want, atol=1e-14, rtol=0)
