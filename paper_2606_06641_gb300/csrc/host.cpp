@@ -722,7 +722,9 @@ static void launch_check_step(afs_handle* h, int p, cudaStream_t s) {
 
 // The fused pass is enqueued before the FE launches of a chunk (true) or after
 // them (false); the order decides which kernel the block scheduler serves first.
-constexpr bool FUSED_FIRST = true;
+// After measured best: the compute-bound buckets take their blocks first and
+// the fused pass's gathers fill the slots around them.
+constexpr bool FUSED_FIRST = false;
 // The FE buckets after the first (largest-work) one run on forked streams
 // (true) or follow it on the step's stream (false).
 constexpr bool BUCKETS_ON_AUX = true;

@@ -678,10 +678,10 @@ __global__ void __launch_bounds__(256, 5) csr_update_vec4_kernel(CsrArgs a) {
 template <typename XT>
 constexpr int FUSED_FB = 2;
 constexpr int FUSED_THREADS = 128;
-// the persistent grid takes 1/FUSED_GRID_DIV of the resident-block slots, so
-// that the FE launches running beside it find SMs free (0: one block per 4
-// tasks, no persistent grid)
-constexpr int FUSED_GRID_DIV = 1;
+// the persistent grid takes 1/FUSED_GRID_DIV of the resident-block slots (0:
+// one block per 4 tasks, no persistent grid, which measured best: the FE
+// launches beside it then share the SMs block by block)
+constexpr int FUSED_GRID_DIV = 0;
 
 template <typename XT, bool OFF32>
 __global__ void __launch_bounds__(FUSED_THREADS) fused_grad_kernel(CsrArgs a) {
