@@ -63,6 +63,7 @@ struct CsrArgs {
   int v_begin, v_count;
   const float* go;
   long long go_pitch;
+  long long go_rows;        // occurrence rows in go (offset range check)
   float eta;
   float* grad;              // optional: grad[v * grad_pitch + b] (evaluation mode)
   long long grad_pitch;

@@ -87,6 +87,17 @@ bool discard_enabled() {
   return on;
 }
 
+// L2 size of the current device (cached per process).
+static double l2_bytes() {
+  static const double v = [] {
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || l2 <= 0) l2 = 64 << 20;
+    return static_cast<double>(l2);
+  }();
+  return v;
+}
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -622,6 +633,7 @@ static int launch_csr(afs_handle* h, const void* x, void* xout, int xt, long lon
   a.v_count = h->n;
   a.go = go;
   a.go_pitch = go_pitch;
+  a.go_rows = h->Lgo;
   a.eta = eta;
   a.grad = grad;
   a.grad_pitch = grad_pitch;
@@ -636,7 +648,12 @@ static int launch_csr(afs_handle* h, const void* x, void* xout, int xt, long lon
   a.vnext = own ? h->vword.as<unsigned>() + (p ^ 1) * niw : nullptr;
   a.solved = h->solved.as<int>();
   a.sgn = own ? h->sgn.as<unsigned>() : nullptr;
-  a.discard_go = own && discard_enabled() ? 1 : 0;
+  // dropping the read rows from L2 pays when the derivative buffer does not
+  // stay resident anyway (more than half of L2); smaller buffers skip it
+  a.discard_go = own && discard_enabled() &&
+                         static_cast<double>(h->Lgo) * static_cast<double>(go_pitch) * sizeof(float) > 0.5 * l2_bytes()
+                     ? 1
+                     : 0;
   a.fixv = own && h->fix_groups > 0 ? h->fixv.as<signed char>() : nullptr;
   a.n_fix_groups = h->fix_groups;
   a.gf = own && h->n_fused > 0 ? h->gf.as<float>() : nullptr;

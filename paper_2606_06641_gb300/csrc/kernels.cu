@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(256) csr_update_kernel(CsrArgs a) {
 }
 
 // Step-path variant: each lane owns 4 consecutive restarts, so a warp reads
-// 512 contiguous bytes of every occurrence row (16-byte vector loads), eight
+// 512 contiguous bytes of every occurrence row (16-byte vector loads), four
 // rows in flight, and updates 4 states. The state and the solved word are
 // read before the gather so their latency overlaps it; 8 lanes together
 // write one sign word. The grid is persistent (one wave of resident blocks)
@@ -580,7 +580,8 @@ __global__ void __launch_bounds__(256) csr_update_kernel(CsrArgs a) {
 // last wave idles the machine. Needs the state's row pitch and the chunk
 // start to be multiples of 32 and the buffers 16-byte aligned (true for the
 // library's own state and occurrence buffers); lanes past nb are masked.
-template <typename XT>
+// OFF32: the launch checked that every state and row offset fits 32 bits.
+template <typename XT, bool OFF32>
 __device__ __forceinline__ void csr_vec4_task(const CsrArgs& a, int vl, int tile, int lane) {
   const int bl = tile * 128 + lane * 4;
   const bool act = bl < a.nb;
@@ -598,7 +599,9 @@ __device__ __forceinline__ void csr_vec4_task(const CsrArgs& a, int vl, int tile
       if (bl + e < a.nb && a.fixv[g * a.n_vars + v] != 0) sw |= 1u << e;
     }
   }
-  const long long xi = static_cast<long long>(v) * a.x_pitch + a.b0 + bl;
+  const long long xi = OFF32 ? static_cast<long long>(static_cast<unsigned>(v) * static_cast<unsigned>(a.x_pitch) +
+                                                     static_cast<unsigned>(a.b0 + bl))
+                            : static_cast<long long>(v) * a.x_pitch + a.b0 + bl;
   float xo[4] = {0.f, 0.f, 0.f, 0.f};
   if (act) load_xvec<XT, 4>(static_cast<const XT*>(a.x) + xi, xo);
   const float* col = a.go + (act ? bl : 0);
@@ -609,14 +612,18 @@ __device__ __forceinline__ void csr_vec4_task(const CsrArgs& a, int vl, int tile
   // step path always provides gf when the instance has fused occurrences)
   const float* gfp = a.gf != nullptr && act ? a.gf + static_cast<long long>(v) * a.gf_pitch + bl : nullptr;
   const bool dis = a.discard_go && act && (lane & 7) == 0;
-  for (int s = s0; s < s1; s += 8) {
-    float4 t[8];
+  // most variables have few rows: batches of four, the summation order
+  // (row j into acc[j mod 4]) fixed by the slot order
+  for (int s = s0; s < s1; s += 4) {
+    float4 t[4];
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-      t[u] = s + u < s1 ? __ldg(reinterpret_cast<const float4*>(col + static_cast<long long>(s + u) * a.go_pitch))
-                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int u = 0; u < 4; ++u) {
+      const float* rp = OFF32 ? col + static_cast<unsigned>(s + u) * static_cast<unsigned>(a.go_pitch)
+                              : col + static_cast<long long>(s + u) * a.go_pitch;
+      t[u] = s + u < s1 ? __ldg(reinterpret_cast<const float4*>(rp)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 4; ++u) {
       acc[u & 3].x += t[u].x;
       acc[u & 3].y += t[u].y;
       acc[u & 3].z += t[u].z;
@@ -653,7 +660,7 @@ __device__ __forceinline__ void csr_vec4_task(const CsrArgs& a, int vl, int tile
   }
 }
 
-template <typename XT>
+template <typename XT, bool OFF32>
 __global__ void __launch_bounds__(256, 5) csr_update_vec4_kernel(CsrArgs a) {
   pdl_wait();
   pdl_trigger();
@@ -663,7 +670,7 @@ __global__ void __launch_bounds__(256, 5) csr_update_vec4_kernel(CsrArgs a) {
   const unsigned stride = gridDim.x * (blockDim.x >> 5);
   for (unsigned task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < ntask; task += stride) {
     const unsigned vl = task / tiles;  // uniform per warp
-    csr_vec4_task<XT>(a, static_cast<int>(vl), static_cast<int>(task - vl * tiles), lane);
+    csr_vec4_task<XT, OFF32>(a, static_cast<int>(vl), static_cast<int>(task - vl * tiles), lane);
   }
 }
 
@@ -760,12 +767,25 @@ void launch_csr_update(const CsrArgs& a, int xt, cudaStream_t s) {
     const long long tiles = (a.nb + 127) / 128;
     long long blocks = (tiles * a.v_count + 7) / 8;
     if (blocks == 0) return;
+    // state offsets v * x_pitch + b and row offsets slot * go_pitch in 32 bits
+    // when both buffers are that small
+    const bool off32 =
+        static_cast<unsigned long long>(a.n_vars) * static_cast<unsigned long long>(a.x_pitch) < (1ull << 32) &&
+        static_cast<unsigned long long>(a.go_rows) * static_cast<unsigned long long>(a.go_pitch) < (1ull << 32);
+    auto go = [&](auto kern) {
+      blocks = std::min(blocks, resident_blocks(kern, 256));
+      launch_pdl(kern, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+    };
     if (xt == XT_F32) {
-      blocks = std::min(blocks, resident_blocks(csr_update_vec4_kernel<float>, 256));
-      launch_pdl(csr_update_vec4_kernel<float>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+      if (off32)
+        go(csr_update_vec4_kernel<float, true>);
+      else
+        go(csr_update_vec4_kernel<float, false>);
     } else {
-      blocks = std::min(blocks, resident_blocks(csr_update_vec4_kernel<__nv_bfloat16>, 256));
-      launch_pdl(csr_update_vec4_kernel<__nv_bfloat16>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, s, a);
+      if (off32)
+        go(csr_update_vec4_kernel<__nv_bfloat16, true>);
+      else
+        go(csr_update_vec4_kernel<__nv_bfloat16, false>);
     }
     return;
   }
