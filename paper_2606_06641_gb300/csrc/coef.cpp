@@ -7,6 +7,7 @@
 // division deferred, and mirrored terms are copied rather than recomputed.
 #include "coef.h"
 
+#include <algorithm>
 #include <cmath>
 #include <stdexcept>
 
@@ -181,6 +182,72 @@ static void push4(std::vector<float>& o, double a, double b, double c, double d)
   o.push_back(static_cast<float>(d));
 }
 
+// Long probability-generating table (see coef.h): the roots whose
+// coefficient is not zero, complex roots by increasing angle theta_j = pi j/N
+// and the real root (odd k, theta = pi/2) last; per root the factor
+// a_j + b_j l = s_j g_j(l) with, for the form of its 32-root pass,
+//   A: g = l tan(theta) + i,  s = b cot(theta),  g' = tan(theta)
+//   B: g = l + i cot(theta),  s = b,              g' = 1
+// (b_j = sin(theta) e^{i(theta - pi/2)}, so |s_A| = cos, |s_B| = sin and
+// arg s = theta - pi/2 for both). E' = E s^k and D' = E s^k g' are stored
+// as a shared power of two 2^eb and mantissas. A pass takes form A when
+// every factor of its roots is bounded by LONG_FACTOR_BOUND (1/cos(theta)),
+// else form B (bound 1/sin(theta); the real root's factor is l itself).
+static void build_long_scaled(int k, const std::vector<double>& cr, const std::vector<double>& ci,
+                              std::vector<float>& out) {
+  const int N = k + 1;
+  constexpr double ZERO_ROOT = 1e-13;
+  struct Root {
+    int j;          // root index (N/2 for the real root)
+    double er, ei;  // E_j (complex pair: 2 ft_j; real root: ft_mid)
+  };
+  std::vector<Root> roots;
+  for (int j = 1; j <= k / 2; ++j)
+    if (std::hypot(cr[j], ci[j]) > ZERO_ROOT) roots.push_back({j, 2.0 * cr[j], 2.0 * ci[j]});
+  const int n_complex = static_cast<int>(roots.size());
+  if ((k & 1) && std::fabs(cr[N / 2]) > ZERO_ROOT) roots.push_back({N / 2, cr[N / 2], 0.0});
+  const int n = static_cast<int>(roots.size());
+  out.clear();
+  push4(out, cr[0], n, n_complex, 0);
+  for (int p0 = 0; p0 < n; p0 += 32) {
+    const int p1 = std::min(n, p0 + 32);
+    bool form_a = true;
+    for (int r = p0; r < p1; ++r) {
+      double c, sn;
+      unit_root(roots[r].j, 2LL * N, c, sn);  // angle pi j / N
+      if (2 * roots[r].j == N || 1.0 / c >= LONG_FACTOR_BOUND) form_a = false;
+    }
+    for (int r = p0; r < p1; ++r) {
+      const Root& rt = roots[r];
+      double c, sn;
+      unit_root(rt.j, 2LL * N, c, sn);
+      const bool real_root = 2 * rt.j == N;
+      if (!form_a && !real_root && 1.0 / sn >= LONG_FACTOR_BOUND)
+        throw std::invalid_argument("long table: no scaled factor form fits a root pass");
+      double pf, qf, gp, mag_log2;
+      if (form_a) {
+        pf = sn / c;   // tan
+        qf = 1.0;
+        gp = pf;
+        mag_log2 = k * std::log2(c);
+      } else {
+        pf = 1.0;
+        qf = real_root ? 0.0 : c / sn;  // cot
+        gp = 1.0;
+        mag_log2 = real_root ? 0.0 : k * std::log2(sn);
+      }
+      double pc = 1.0, ps = 0.0;  // e^{i k (theta - pi/2)}
+      if (!real_root) unit_root(2LL * rt.j * k - static_cast<long long>(k) * N, 4LL * N, pc, ps);
+      const double eb = std::floor(mag_log2);
+      const double m = std::exp2(mag_log2 - eb);
+      const double sr = m * pc, si = m * ps;
+      const double er = rt.er * sr - rt.ei * si, ei = rt.er * si + rt.ei * sr;
+      push4(out, pf, qf, eb, form_a ? 1.0 : 0.0);
+      push4(out, er * gp, ei * gp, er, ei);
+    }
+  }
+}
+
 void build_table(const Shape& s, int basis, int form, std::vector<float>& out) {
   const int k = s.k, N = k + 1;
   std::vector<double> cr, ci;
@@ -245,7 +312,9 @@ void build_table(const Shape& s, int basis, int form, std::vector<float>& out) {
     // perturbs a factor by eps*|b| (small at the dominant low roots) instead of
     // eps; with a and b rounded separately that error would add up coherently
     // over the k factors.
-    if (basis == BASIS_PGF) {
+    if (basis == BASIS_PGF && k >= LONG_SCALED_MIN_K) {
+      build_long_scaled(k, cr, ci, out);
+    } else if (basis == BASIS_PGF) {
       push4(out, cr[0], 0, 0, 0);
       if (odd) {
         push4(out, 1.0, 0.0, 1.0, 0.0);
@@ -283,6 +352,10 @@ double work_instr(int k, int complex_roots) {
   // gradient combine (2) per literal, plus 2 for the value; per real root:
   // 3 per literal plus 1.
   return static_cast<double>(complex_roots) * (10.0 * k + 2.0) + static_cast<double>(k & 1) * (3.0 * k + 1.0);
+}
+
+double work_instr(int k, int complex_roots, int real_roots) {
+  return static_cast<double>(complex_roots) * (10.0 * k + 2.0) + static_cast<double>(real_roots) * (3.0 * k + 1.0);
 }
 
 double work_instr(int k) { return work_instr(k, k / 2); }

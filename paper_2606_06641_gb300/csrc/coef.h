@@ -8,6 +8,14 @@ namespace afs {
 enum { BASIS_PGF = 0, BASIS_ESP = 1 };
 enum { FORM_SHORT = 0, FORM_LONG = 1 };
 
+// Long probability-generating tables use the scaled factor form from this
+// length on (below it the direct form, whose products need no exponent
+// tracking, costs less per pass).
+constexpr int LONG_SCALED_MIN_K = 129;
+// Largest factor modulus a scaled long-table root may reach for |l| <= 1:
+// 16 such factors (one checkpoint segment) stay below 2^126.
+constexpr double LONG_FACTOR_BOUND = 234.0;
+
 // Constraints with k <= KSHORT use the register (short) kernels and the
 // short table layout; longer ones use the shared-memory (long) kernel.
 constexpr int KSHORT = 32;
@@ -45,10 +53,18 @@ void esp_coefficients(const Shape& s, std::vector<double>& c);
 //     the kernel evaluates  FE   = c0 + sum_r E_r prod_i (l_i + alpha_r)
 //                                     + sum_j Re(E_j prod_i (l_i + alpha_j + i gamma_j))
 //                          dFE/dl_i = sum_r E_r prod_{i'!=i} (...) + sum_j Re(E_j prod_{i'!=i} (...))
-//  long form:  {c0,0,0,0}, per root (real roots first, imaginary parts 0)
-//              {A.re, A.im, b.re, b.im}, {D.re, D.im, E.re, E.im}
+//  long form, paper basis and probability-generating basis below
+//              LONG_SCALED_MIN_K: {c0,0,0,0}, per root (real roots first,
+//              imaginary parts 0) {A.re, A.im, b.re, b.im}, {D.re, D.im, E.re, E.im}
 //     with the factor a + b l = A - b (1 - l), A = a + b:
 //     FE = c0 + sum Re(E prod_i F_i),  dFE/dl_i = sum Re(D prod_{i'!=i} F_i')
+//  long form, probability-generating basis from LONG_SCALED_MIN_K on:
+//     {c0, n stored, n complex, 0},
+//     per stored root {p, q, eb, form}, {D'.re, D'.im, E'.re, E'.im} with the
+//     scaled factor g(l) = p l + i q (form 1: p = tan, q = 1; form 0: p = 1,
+//     q = cot, 0 for the real root), the form the same for each run of 32
+//     roots:  FE = c0 + sum 2^eb Re(E' prod_i g_i),
+//             dFE/dl_i = sum 2^eb Re(D' prod_{i'!=i} g_i')
 void build_table(const Shape& s, int basis, int form, std::vector<float>& out);
 
 // Algorithmic FP32 lane instructions of one FE+gradient evaluation of a
@@ -56,5 +72,7 @@ void build_table(const Shape& s, int basis, int form, std::vector<float>& out);
 double work_instr(int k);
 // The same with the number of complex roots a table actually keeps.
 double work_instr(int k, int complex_roots);
+// The same with the complex and real roots a table actually keeps.
+double work_instr(int k, int complex_roots, int real_roots);
 
 }  // namespace afs

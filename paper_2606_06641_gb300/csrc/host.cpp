@@ -355,10 +355,16 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   });
   std::vector<int> b_tab(m), b_orig(m), b_k(m), b_lit(m);
   // the work model counts the complex roots a short scaled table keeps
+  // (and the roots a long probability-generating table keeps)
   auto cons_work = [&](int g) {
     const int k = gk[g];
-    const bool scaled = h->p.basis == AFS_BASIS_PGF && k <= KSHORT && k <= KSCALED_MAX;
-    return work_instr(k, scaled ? static_cast<int>(coef[4 * static_cast<size_t>(cons_tab_load[g]) + 1]) : k / 2);
+    const float* head = &coef[4 * static_cast<size_t>(cons_tab_load[g])];
+    if (h->p.basis == AFS_BASIS_PGF && k >= LONG_SCALED_MIN_K) {
+      const int stored = static_cast<int>(head[1]), cplx = static_cast<int>(head[2]);
+      return work_instr(k, cplx, stored - cplx);
+    }
+    const bool scaled = h->p.basis == AFS_BASIS_PGF && k <= KSCALED_MAX;
+    return work_instr(k, scaled ? static_cast<int>(head[1]) : k / 2);
   };
   std::vector<int2> litslot;
   litslot.reserve(L + m);

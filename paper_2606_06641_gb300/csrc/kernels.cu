@@ -61,19 +61,24 @@ constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 // ---------------------------------------------------------------------------
 // Long constraints (k > 32): one CTA per (constraint, 8 restarts).
 //
-// Same expansion as the short kernel, in the direct factor form
-// a_j + b_j l_i (|a_j + b_j l| <= 1 for the probability-generating basis).
+// Same expansion as the short kernel. The probability-generating tables give
+// each root's factor in a scaled form p l + i q (a complex multiply is three
+// or four FP32 instructions; zero-coefficient roots are not stored); the
+// paper's basis keeps the direct form a_j + b_j l_i.
 // Warp w owns restart w of the tile and its lanes own 32 roots at a time.
 // The forward pass keeps one prefix checkpoint per LONG_SEG-literal segment
 // in shared memory; the backward pass rebuilds a segment's prefixes (and its
 // factors) in registers, multiplies them by the running suffix (which starts
 // at the gradient weight D_j) and stores each lane's (root's) contributions
 // as a row of a per-warp shared-memory tile, whose columns the lanes then
-// sum, so lane t ends with literal t of the segment summed over the 32 roots. With the paper's basis (ESP) the factors grow up
-// to 2 in modulus, so running products are renormalised at segment boundaries
-// into a mantissa and an integer power of two (exponent field of the IEEE
-// encoding) and the contributions are rescaled before the root sum.
-// The coefficient table and literal list are staged with cp.async.bulk.
+// sum, so lane t ends with literal t of the segment summed over the 32 roots.
+// Scaled factors (up to 234 in modulus) and the paper's basis (up to 2) make
+// running products leave the FP32 range, so they are renormalised at segment
+// boundaries into a mantissa and an integer power of two (exponent field of
+// the IEEE encoding) and the contributions are rescaled before the root sum.
+// The literal list is staged with cp.async.bulk; the coefficient table is
+// read through L1. Exponents are 16-bit (at most 8 bits of growth per
+// literal, k <= 1024).
 // ---------------------------------------------------------------------------
 constexpr int LONG_RT = 8;  // restarts (warps) per CTA; 4 for the longest groups (shared memory)
 
@@ -143,6 +148,75 @@ __device__ __forceinline__ void long_segment(const float* el, int n, float ar, f
   }
 }
 
+// The probability-generating tables' scaled factor g = p l + i q (form A: q
+// = 1, three FP32 instructions per complex multiply; form B: p = 1, four).
+// Same walk as long_segment; the checkpoint Q arrives pre-scaled by its share
+// of the power of two, and sc (the rest) scales each contribution.
+template <bool FULL, bool FA, bool CF>
+__device__ __forceinline__ void long_segment_scaled(const float* el, int n, float p, float q, float Qr, float Qi,
+                                                    float& Sr, float& Si, float sc, float* trow) {
+  float pr[LONG_SEG], pi[LONG_SEG], wv[CF ? LONG_SEG : 1];
+  pr[0] = Qr;
+  pi[0] = Qi;
+#pragma unroll
+  for (int t = 0; t < LONG_SEG; ++t) {
+    if (FULL || t < n) {
+      const float w = FA ? el[t] * p : el[t];
+      if constexpr (CF) wv[t] = w;
+      if (t + 1 < LONG_SEG) {
+        if constexpr (FA) {
+          pr[t + 1] = fmaf(pr[t], w, -pi[t]);
+          pi[t + 1] = fmaf(pi[t], w, pr[t]);
+        } else {
+          pr[t + 1] = fmaf(pr[t], w, -pi[t] * q);
+          pi[t + 1] = fmaf(pi[t], w, pr[t] * q);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int t = LONG_SEG - 1; t >= 0; --t) {
+    float v = 0.0f;
+    if (FULL || t < n) {
+      v = fmaf(pr[t], Sr, -pi[t] * Si) * sc;
+      const float w = CF ? wv[t] : (FA ? el[t] * p : el[t]);
+      float nr, ni;
+      if constexpr (FA) {
+        nr = fmaf(Sr, w, -Si);
+        ni = fmaf(Si, w, Sr);
+      } else {
+        nr = fmaf(Sr, w, -Si * q);
+        ni = fmaf(Si, w, Sr * q);
+      }
+      Sr = nr;
+      Si = ni;
+    }
+    trow[t] = v;
+  }
+}
+
+// Forward walk of one segment in the scaled form (prefix only).
+template <bool FA>
+__device__ __forceinline__ void long_forward_scaled(const float* el, int n, float p, float q, float& Pr, float& Pi) {
+#pragma unroll 4
+  for (int t = 0; t < n; ++t) {
+    const float w = FA ? el[t] * p : el[t];
+    float nr, ni;
+    if constexpr (FA) {
+      nr = fmaf(Pr, w, -Pi);
+      ni = fmaf(Pi, w, Pr);
+    } else {
+      nr = fmaf(Pr, w, -Pi * q);
+      ni = fmaf(Pi, w, Pr * q);
+    }
+    Pr = nr;
+    Pi = ni;
+  }
+}
+
+// 2^e as a float for -126 <= e <= 127.
+__device__ __forceinline__ float exp2_int(int e) { return __int_as_float((e + 127) << 23); }
+
 // Column sums of the warp's 32 x LONG_SEG tile: lane L adds rows
 // 16*(L>>4) .. +15 of column L & 15, the two halves meet by one shuffle.
 __device__ __forceinline__ float long_column_sum(const float* tile, int lane) {
@@ -153,26 +227,35 @@ __device__ __forceinline__ float long_column_sum(const float* tile, int lane) {
   return s + __shfl_xor_sync(0xffffffffu, s, 16);
 }
 
+// Shared memory of one CTA (the coefficient table is read through L1: each
+// lane loads its root's two granules once per 32-root pass).
 struct LongLayout {
-  int kpad, tab_cap, nseg_max, rt;
+  int kpad, nseg_max, rt;
   __host__ __device__ LongLayout(int kmax, int rt_ = LONG_RT) : rt(rt_) {
-    kpad = (kmax + 3) & ~3;
-    tab_cap = 1 + 2 * (kmax / 2 + 2);
+    kpad = (kmax + 7) & ~7;
     nseg_max = (kmax + LONG_SEG - 1) / LONG_SEG;
   }
   __host__ __device__ size_t bytes(bool esp) const {
-    size_t b = static_cast<size_t>(tab_cap) * 16;            // coefficient table
-    b += static_cast<size_t>(kpad) * 8;                       // literal list
+    (void)esp;
+    size_t b = static_cast<size_t>(kpad) * 8;                 // literal list
     b += 2 * static_cast<size_t>(rt) * kpad * 4;              // literal values, gradient accumulators
     b += static_cast<size_t>(rt) * nseg_max * 32 * 8;         // prefix checkpoints
-    if (esp) b += static_cast<size_t>(rt) * nseg_max * 32 * 4;
+    b += static_cast<size_t>(rt) * nseg_max * 32 * 2;         // their power-of-two exponents (16 bits)
+    b = (b + 15) & ~static_cast<size_t>(15);
     b += static_cast<size_t>(rt) * 32 * LONG_TP * 4;          // transpose tiles
     return b;
   }
 };
 
-template <typename XT, bool ESP, int RT>
+// MODE: LONG_PGF (direct factors), LONG_ESP (paper basis, renormalised) or
+// LONG_PGF_SCALED (scaled factors, renormalised; lengths from
+// LONG_SCALED_MIN_K on, which is a length-class boundary, so a group never
+// mixes the two probability-generating layouts).
+enum { LONG_PGF = 0, LONG_ESP = 1, LONG_PGF_SCALED = 2 };
+
+template <typename XT, int MODE, int RT>
 __global__ void __launch_bounds__(RT * 32) fe_grad_long_kernel(FeGroupArgs a, int kmax) {
+  constexpr bool ESP = MODE == LONG_ESP, SCALED = MODE == LONG_PGF_SCALED;
   // the groups that run 4 restarts per CTA (the longest) keep a segment's
   // factors in registers: fewer instructions, more registers per thread
   constexpr bool CF = RT == 4;
@@ -188,18 +271,19 @@ __global__ void __launch_bounds__(RT * 32) fe_grad_long_kernel(FeGroupArgs a, in
   const int k = __ldg(a.cons_k + cb);
   const int litoff = __ldg(a.cons_lit + cb);
   const int tab_off = __ldg(a.cons_tab + cb);
-  const int nroots = k / 2 + (k & 1) + (ESP ? 1 : 0);
+  // a probability-generating table stores its root count (zero roots dropped)
+  const int nroots = SCALED ? static_cast<int>(__ldg(a.coef + tab_off).y) : k / 2 + (k & 1) + (ESP ? 1 : 0);
 
-  float4* tab = reinterpret_cast<float4*>(smem);
-  int2* lits = reinterpret_cast<int2*>(tab + L.tab_cap);
+  const float4* tab = a.coef + tab_off;  // read through L1
+  int2* lits = reinterpret_cast<int2*>(smem);
   float* ell = reinterpret_cast<float*>(lits + L.kpad);
   float* gs = ell + RT * L.kpad;
   float2* ck = reinterpret_cast<float2*>(gs + RT * L.kpad);
-  int* cke = reinterpret_cast<int*>(ck + RT * L.nseg_max * 32);
-  float* tps = reinterpret_cast<float*>(cke + (ESP ? RT * L.nseg_max * 32 : 0));
+  short* cke = reinterpret_cast<short*>(ck + RT * L.nseg_max * 32);
+  float* tps = reinterpret_cast<float*>(
+      smem + ((reinterpret_cast<unsigned char*>(cke + RT * L.nseg_max * 32) - smem + 15) & ~static_cast<size_t>(15)));
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const unsigned tab_bytes = static_cast<unsigned>(1 + 2 * nroots) * 16u;
   const unsigned lit_bytes = static_cast<unsigned>((k + 1) & ~1) * 8u;
   if (tid == 0) {
     mbar_init(&bar, 1);
@@ -207,8 +291,7 @@ __global__ void __launch_bounds__(RT * 32) fe_grad_long_kernel(FeGroupArgs a, in
   }
   __syncthreads();
   if (tid == 0) {
-    mbar_expect_tx(&bar, tab_bytes + lit_bytes + a.extra_tx);
-    bulk_g2s(tab, a.coef + tab_off, tab_bytes, &bar);
+    mbar_expect_tx(&bar, lit_bytes + a.extra_tx);
     bulk_g2s(lits, a.litslot + litoff, lit_bytes, &bar);
   }
   for (int i = tid; i < RT * L.kpad; i += blockDim.x) gs[i] = 0.0f;
@@ -219,7 +302,8 @@ __global__ void __launch_bounds__(RT * 32) fe_grad_long_kernel(FeGroupArgs a, in
     return;
   }
 
-  // stage u[r][i] = 1 - s_i x[v_i][b]: RT consecutive threads read one row segment
+  // stage u[r][i] = 1 - s_i x[v_i][b] (direct factors) or l[r][i] = s_i x[v_i][b]
+  // (scaled factors): RT consecutive threads read one row segment
   const XT* x = static_cast<const XT*>(a.x);
   const int bt = tile * RT;
   for (int idx = tid; idx < k * RT; idx += blockDim.x) {
@@ -228,74 +312,141 @@ __global__ void __launch_bounds__(RT * 32) fe_grad_long_kernel(FeGroupArgs a, in
     const int bl = bt + r;
     const float xv =
         bl < a.nb ? load_x<XT>(x + static_cast<long long>(li.x >> 1) * a.x_pitch + a.b0 + bl) : 0.0f;
-    ell[r * L.kpad + i] = 1.0f - ((li.x & 1) ? -xv : xv);
+    const float lv = (li.x & 1) ? -xv : xv;
+    ell[r * L.kpad + i] = SCALED ? lv : 1.0f - lv;
   }
   __syncthreads();
 
   const float* el = ell + w * L.kpad;
   float* gr = gs + w * L.kpad;
   float2* myck = ck + static_cast<size_t>(w) * L.nseg_max * 32;
-  int* myce = cke + static_cast<size_t>(w) * L.nseg_max * 32;
+  short* myce = cke + static_cast<size_t>(w) * L.nseg_max * 32;
   float* tpw = tps + static_cast<size_t>(w) * 32 * LONG_TP;  // this warp's transpose tile
   const int nseg = (k + LONG_SEG - 1) / LONG_SEG;
   float fe_part = 0.0f;
 
-  for (int rg = 0; rg < nroots; rg += 32) {
-    const int j = rg + lane;
-    float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f, dr = 0.f, di = 0.f, er = 0.f, ei = 0.f;
-    if (j < nroots) {  // factor A - b u: keep (A, -b)
-      const float4 t0 = tab[1 + 2 * j], t1 = tab[2 + 2 * j];
-      ar = t0.x; ai = t0.y; br = -t0.z; bi = -t0.w;
-      dr = t1.x; di = t1.y; er = t1.z; ei = t1.w;
-    }
-    // forward: prefix checkpoints at segment starts
-    float Pr = 1.0f, Pi = 0.0f;
-    int Pe = 0;
-    for (int seg = 0; seg < nseg; ++seg) {
-      myck[seg * 32 + lane] = make_float2(Pr, Pi);
-      if (ESP) myce[seg * 32 + lane] = Pe;
-      const int i0 = seg * LONG_SEG;
-      const int n = min(LONG_SEG, k - i0);
-#pragma unroll 4
-      for (int t = 0; t < n; ++t) {
-        const float ll = el[i0 + t];
-        const float Fr = fmaf(br, ll, ar), Fi = fmaf(bi, ll, ai);
-        const float nr = fmaf(Pr, Fr, -Pi * Fi);
-        const float ni = fmaf(Pr, Fi, Pi * Fr);
-        Pr = nr;
-        Pi = ni;
+  if constexpr (SCALED) {
+    for (int rg = 0; rg < nroots; rg += 32) {
+      const int j = rg + lane;
+      float p = 0.f, q = 0.f, dr = 0.f, di = 0.f, er = 0.f, ei = 0.f, fa = 0.f;
+      int eb = 0;
+      if (j < nroots) {
+        const float4 t0 = __ldg(tab + 1 + 2 * j), t1 = __ldg(tab + 2 + 2 * j);
+        p = t0.x; q = t0.y; eb = static_cast<int>(t0.z); fa = t0.w;
+        dr = t1.x; di = t1.y; er = t1.z; ei = t1.w;
       }
-      if (ESP) renorm(Pr, Pi, Pe);
-    }
-    float val = fmaf(er, Pr, -ei * Pi);
-    if (ESP) val = ldexpf(val, Pe);
-    fe_part += val;
+      // the table gives every root of a 32-root pass the same form
+      const bool form_a = __shfl_sync(0xffffffffu, fa, 0) > 0.5f;
+      // forward: prefix checkpoints (mantissa, power of two) at segment starts
+      float Pr = 1.0f, Pi = 0.0f;
+      int Pe = 0;
+      for (int seg = 0; seg < nseg; ++seg) {
+        myck[seg * 32 + lane] = make_float2(Pr, Pi);
+        myce[seg * 32 + lane] = static_cast<short>(Pe);
+        const int i0 = seg * LONG_SEG;
+        const int n = min(LONG_SEG, k - i0);
+        if (form_a)
+          long_forward_scaled<true>(el + i0, n, p, q, Pr, Pi);
+        else
+          long_forward_scaled<false>(el + i0, n, p, q, Pr, Pi);
+        renorm(Pr, Pi, Pe);
+      }
+      // this pass's value, summed over its roots (every lane gets the sum)
+      float fe_pass = ldexpf(fmaf(er, Pr, -ei * Pi), Pe + eb);
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) fe_pass += __shfl_xor_sync(0xffffffffu, fe_pass, o);
+      fe_part += fe_pass;
 
-    // backward: suffix from the gradient weight, segment by segment
-    float Sr = dr, Si = di;
-    int Se = 0;
-    for (int seg = nseg - 1; seg >= 0; --seg) {
-      const int i0 = seg * LONG_SEG;
-      const int n = min(LONG_SEG, k - i0);
-      const float2 Q = myck[seg * 32 + lane];
-      const int escale = ESP ? myce[seg * 32 + lane] + Se : 0;
-      float* trow = tpw + lane * LONG_TP;
-      if (n == LONG_SEG)
-        long_segment<true, ESP, CF>(el + i0, n, ar, ai, br, bi, Q.x, Q.y, Sr, Si, escale, trow);
-      else
-        long_segment<false, ESP, CF>(el + i0, n, ar, ai, br, bi, Q.x, Q.y, Sr, Si, escale, trow);
-      if (ESP) renorm(Sr, Si, Se);
-      __syncwarp();
-      const float s = long_column_sum(tpw, lane);
-      if (lane < n) gr[i0 + lane] += s;
-      __syncwarp();  // the tile is read before the next segment's rows
+      // backward: suffix from D', segment by segment; a contribution's power of
+      // two (checkpoint + suffix + table) is split between the checkpoint
+      // (down to 2^-126) and a per-contribution factor
+      float Sr = dr, Si = di;
+      int Se = 0;
+      renorm(Sr, Si, Se);
+      for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int i0 = seg * LONG_SEG;
+        const int n = min(LONG_SEG, k - i0);
+        const float2 Q = myck[seg * 32 + lane];
+        const int escale = myce[seg * 32 + lane] + Se + eb;
+        const int e1 = min(max(escale, -126), 127), e2 = escale - e1;
+        const float s1 = exp2_int(e1), s2 = e2 >= -126 ? exp2_int(min(e2, 127)) : 0.0f;
+        float* trow = tpw + lane * LONG_TP;
+        if (form_a) {
+          if (n == LONG_SEG)
+            long_segment_scaled<true, true, CF>(el + i0, n, p, q, Q.x * s1, Q.y * s1, Sr, Si, s2, trow);
+          else
+            long_segment_scaled<false, true, CF>(el + i0, n, p, q, Q.x * s1, Q.y * s1, Sr, Si, s2, trow);
+        } else {
+          if (n == LONG_SEG)
+            long_segment_scaled<true, false, CF>(el + i0, n, p, q, Q.x * s1, Q.y * s1, Sr, Si, s2, trow);
+          else
+            long_segment_scaled<false, false, CF>(el + i0, n, p, q, Q.x * s1, Q.y * s1, Sr, Si, s2, trow);
+        }
+        renorm(Sr, Si, Se);
+        __syncwarp();
+        const float sum = long_column_sum(tpw, lane);
+        if (lane < n) gr[i0 + lane] += sum;
+        __syncwarp();  // the tile is read before the next segment's rows
+      }
+    }
+  } else {
+    for (int rg = 0; rg < nroots; rg += 32) {
+      const int j = rg + lane;
+      float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f, dr = 0.f, di = 0.f, er = 0.f, ei = 0.f;
+      if (j < nroots) {  // factor A - b u: keep (A, -b)
+        const float4 t0 = __ldg(tab + 1 + 2 * j), t1 = __ldg(tab + 2 + 2 * j);
+        ar = t0.x; ai = t0.y; br = -t0.z; bi = -t0.w;
+        dr = t1.x; di = t1.y; er = t1.z; ei = t1.w;
+      }
+      // forward: prefix checkpoints at segment starts
+      float Pr = 1.0f, Pi = 0.0f;
+      int Pe = 0;
+      for (int seg = 0; seg < nseg; ++seg) {
+        myck[seg * 32 + lane] = make_float2(Pr, Pi);
+        if (ESP) myce[seg * 32 + lane] = static_cast<short>(Pe);
+        const int i0 = seg * LONG_SEG;
+        const int n = min(LONG_SEG, k - i0);
+#pragma unroll 4
+        for (int t = 0; t < n; ++t) {
+          const float ll = el[i0 + t];
+          const float Fr = fmaf(br, ll, ar), Fi = fmaf(bi, ll, ai);
+          const float nr = fmaf(Pr, Fr, -Pi * Fi);
+          const float ni = fmaf(Pr, Fi, Pi * Fr);
+          Pr = nr;
+          Pi = ni;
+        }
+        if (ESP) renorm(Pr, Pi, Pe);
+      }
+      float val = fmaf(er, Pr, -ei * Pi);
+      if (ESP) val = ldexpf(val, Pe);
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+      fe_part += val;
+
+      // backward: suffix from the gradient weight, segment by segment
+      float Sr = dr, Si = di;
+      int Se = 0;
+      for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int i0 = seg * LONG_SEG;
+        const int n = min(LONG_SEG, k - i0);
+        const float2 Q = myck[seg * 32 + lane];
+        const int escale = ESP ? myce[seg * 32 + lane] + Se : 0;
+        float* trow = tpw + lane * LONG_TP;
+        if (n == LONG_SEG)
+          long_segment<true, ESP, CF>(el + i0, n, ar, ai, br, bi, Q.x, Q.y, Sr, Si, escale, trow);
+        else
+          long_segment<false, ESP, CF>(el + i0, n, ar, ai, br, bi, Q.x, Q.y, Sr, Si, escale, trow);
+        if (ESP) renorm(Sr, Si, Se);
+        __syncwarp();
+        const float s = long_column_sum(tpw, lane);
+        if (lane < n) gr[i0 + lane] += s;
+        __syncwarp();  // the tile is read before the next segment's rows
+      }
     }
   }
-  // value: sum of the lanes' root terms
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) fe_part += __shfl_xor_sync(0xffffffffu, fe_part, o);
+  // value: fe_part holds the sum over all roots in every lane
   if (a.fe != nullptr && lane == 0 && bt + w < a.nb)
-    a.fe[static_cast<long long>(__ldg(a.cons_orig + cb)) * a.fe_pitch + a.b0 + bt + w] = tab[0].x + fe_part;
+    a.fe[static_cast<long long>(__ldg(a.cons_orig + cb)) * a.fe_pitch + a.b0 + bt + w] = __ldg(tab).x + fe_part;
   __syncthreads();
   for (int idx = tid; idx < k * RT; idx += blockDim.x) {
     const int i = idx / RT, r = idx % RT;
@@ -318,17 +469,23 @@ size_t long_smem_bytes(int kmax, bool esp) {
 }
 
 
-template <typename XT, bool ESP>
+template <typename XT, int MODE>
 static void launch_long_t(const FeGroupArgs& a, cudaStream_t s) {
-  const bool rt4 = LongLayout(a.k, 8).bytes(ESP) > LONG_RT4_BYTES;
+  const bool rt4 = LongLayout(a.k, 8).bytes(MODE == LONG_ESP) > LONG_RT4_BYTES;
   const int rt = rt4 ? 4 : 8;
-  const size_t smem = LongLayout(a.k, rt).bytes(ESP);
+  const size_t smem = LongLayout(a.k, rt).bytes(MODE == LONG_ESP);
   const int tiles = (a.nb + rt - 1) / rt;
   const long long blocks = static_cast<long long>(tiles) * a.c_count;
-  if (rt4)
-    launch_pdl(fe_grad_long_kernel<XT, ESP, 4>, dim3(static_cast<unsigned>(blocks)), dim3(128), smem, s, a, a.k);
-  else
-    launch_pdl(fe_grad_long_kernel<XT, ESP, 8>, dim3(static_cast<unsigned>(blocks)), dim3(256), smem, s, a, a.k);
+  if constexpr (MODE == LONG_PGF) {
+    // direct probability-generating groups are at most LONG_SCALED_MIN_K - 1
+    // long, which always fits 8 restarts per CTA
+    launch_pdl(fe_grad_long_kernel<XT, MODE, 8>, dim3(static_cast<unsigned>(blocks)), dim3(256), smem, s, a, a.k);
+  } else {
+    if (rt4)
+      launch_pdl(fe_grad_long_kernel<XT, MODE, 4>, dim3(static_cast<unsigned>(blocks)), dim3(128), smem, s, a, a.k);
+    else
+      launch_pdl(fe_grad_long_kernel<XT, MODE, 8>, dim3(static_cast<unsigned>(blocks)), dim3(256), smem, s, a, a.k);
+  }
 }
 
 template <typename K>
@@ -349,12 +506,15 @@ bool pdl_enabled() {
 
 // a.k carries the group's longest constraint for the long kernel
 void launch_fe_long(const FeGroupArgs& a, int xt, int basis, int /*rt*/, cudaStream_t s) {
+  const int mode = basis != 0 ? LONG_ESP : (a.k >= LONG_SCALED_MIN_K ? LONG_PGF_SCALED : LONG_PGF);
   if (xt == XT_F32) {
-    if (basis == 0) launch_long_t<float, false>(a, s);
-    else launch_long_t<float, true>(a, s);
+    if (mode == LONG_PGF) launch_long_t<float, LONG_PGF>(a, s);
+    else if (mode == LONG_ESP) launch_long_t<float, LONG_ESP>(a, s);
+    else launch_long_t<float, LONG_PGF_SCALED>(a, s);
   } else {
-    if (basis == 0) launch_long_t<__nv_bfloat16, false>(a, s);
-    else launch_long_t<__nv_bfloat16, true>(a, s);
+    if (mode == LONG_PGF) launch_long_t<__nv_bfloat16, LONG_PGF>(a, s);
+    else if (mode == LONG_ESP) launch_long_t<__nv_bfloat16, LONG_ESP>(a, s);
+    else launch_long_t<__nv_bfloat16, LONG_PGF_SCALED>(a, s);
   }
 }
 
@@ -1289,14 +1449,16 @@ bool prepare_kernels() {
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
   if (LongLayout(1024, 4).bytes(true) + 64 > static_cast<size_t>(optin)) return false;
   bool ok = true;
-  ok &= raise_smem_cap(fe_grad_long_kernel<float, false, 8>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<float, true, 8>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, false, 8>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, true, 8>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<float, false, 4>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<float, true, 4>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, false, 4>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, true, 4>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<float, LONG_PGF, 8>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<float, LONG_ESP, 8>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<float, LONG_ESP, 4>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<float, LONG_PGF_SCALED, 8>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<float, LONG_PGF_SCALED, 4>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, LONG_PGF, 8>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, LONG_ESP, 8>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, LONG_ESP, 4>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, LONG_PGF_SCALED, 8>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, LONG_PGF_SCALED, 4>, optin);
   return ok;
 }
 

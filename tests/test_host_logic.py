@@ -75,7 +75,30 @@ def _eval_short(tab, k, esp, ell):
     return fe, grad
 
 
+LONG_SCALED_MIN_K = 129
+
+
+def _eval_long_pgf_scaled(tab, k, ell):
+    """The scaled long probability-generating form: per stored root
+    {p, q, eb, form}, {D'}, {E'}; factor g = p l + i q. The products are
+    formed in log space (they leave the FP64 range at large k)."""
+    t = tab.astype(np.float64).reshape(-1, 4)
+    fe = np.full(ell.shape[0], t[0, 0])
+    grad = np.zeros_like(ell)
+    for r in range(int(t[0, 1])):
+        p, q, eb, _ = t[1 + 2 * r]
+        dr, di, er, ei = t[2 + 2 * r]
+        lg = np.log((p * ell + 1j * q).astype(np.complex128))
+        tot = lg.sum(axis=1) + eb * np.log(2.0)
+        fe += np.real((er + 1j * ei) * np.exp(tot))
+        for i in range(k):
+            grad[:, i] += np.real((dr + 1j * di) * np.exp(tot - lg[:, i]))
+    return fe, grad
+
+
 def _eval_long(tab, k, esp, ell):
+    if not esp and k >= LONG_SCALED_MIN_K:
+        return _eval_long_pgf_scaled(tab, k, ell)
     t = tab.astype(np.float64).reshape(-1, 4)
     fe = np.full(ell.shape[0], t[0, 0])
     grad = np.zeros_like(ell)
@@ -111,7 +134,7 @@ def test_short_pgf_table_reproduces_oracle(k):
         np.testing.assert_allclose(g, ref_g, atol=2e-6, rtol=0)
 
 
-@pytest.mark.parametrize("k", [1, 3, 33, 64, 101])
+@pytest.mark.parametrize("k", [1, 3, 33, 64, 101, 128, 129, 130, 160])
 def test_long_pgf_table_reproduces_oracle(k):
     rng = np.random.default_rng(50 + k)
     ell = rng.uniform(-1, 1, (3, k))
@@ -258,3 +281,27 @@ def test_length3_level_expansion_derivative():
             A, B1, B2, C = s[0] * c[3] * s[1] * s[2], s[0] * c[2] * s[1], s[0] * c[2] * s[2], s[0] * c[1]
             got = x[:, 1] * (A * x[:, 2] + B1) + B2 * x[:, 2] + C
             np.testing.assert_allclose(got, want, atol=1e-14, rtol=0)
+
+
+@pytest.mark.parametrize("k", list(range(129, 1025, 37)) + [130, 391, 392, 393, 784, 785, 1023, 1024])
+def test_long_pgf_scaled_forms_stay_bounded(k):
+    """Every 32-root pass of a long probability-generating table has one
+    factor form, and over |l| <= 1 each factor's modulus stays below the bound
+    that keeps 16 of them inside FP32 (form A: |l tan + i| <= 1/cos; form B:
+    |l + i cot| <= 1/sin, the real root's factor l at most 1). The stored
+    roots are exactly those with a nonzero coefficient."""
+    for (ct, op, r, par) in [(O.T_CARD, O.OP_GE, k // 2, 1), (O.T_EK, 0, k // 3, 1), (O.T_XOR, 0, 0, 1)]:
+        t = bd.coef_table(ct, k, op, r, par, basis=bd.BASIS_PGF, form=1).astype(np.float64).reshape(-1, 4)
+        n, nc = int(t[0, 1]), int(t[0, 2])
+        assert t.shape[0] == 1 + 2 * n and 0 <= nc <= n <= nc + (k & 1)
+        if ct == O.T_XOR and k % 2 == 1:
+            assert nc == 0 and n == 1   # odd-length parity: only the real root w = -1
+        for p0 in range(0, n, 32):
+            rows = t[1 + 2 * p0:1 + 2 * min(n, p0 + 32):2]
+            assert len(set(rows[:, 3])) == 1
+            bound = np.sqrt(rows[:, 0] ** 2 + rows[:, 1] ** 2)
+            assert np.all(bound < 234.0), (k, p0, bound.max())
+            if rows[0, 3] == 1.0:
+                assert np.all(rows[:, 1] == 1.0)
+            else:
+                assert np.all(rows[:, 0] == 1.0)
