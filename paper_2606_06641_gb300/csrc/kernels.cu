@@ -733,9 +733,11 @@ __global__ void __launch_bounds__(256) csr_update_kernel(CsrArgs a) {
 
 // Step-path variant: each lane owns 4 consecutive restarts, so a warp reads
 // 512 contiguous bytes of every occurrence row (16-byte vector loads), four
-// rows in flight, and updates 4 states. The state and the solved word are
-// read before the gather so their latency overlaps it; 8 lanes together
-// write one sign word. The grid is persistent (one wave of resident blocks)
+// rows in flight, and updates 4 states. The state, the solved word and the
+// instance's first variable are read before the gather so their latency
+// overlaps it; 8 lanes together write one sign word. 64 registers (four
+// 256-thread blocks per SM) measured faster than squeezing to five blocks.
+// The grid is persistent (one wave of resident blocks)
 // and warps stride over the (variable, 128-restart tile) tasks, so no partial
 // last wave idles the machine. Needs the state's row pitch and the chunk
 // start to be multiples of 32 and the buffers 16-byte aligned (true for the
@@ -748,6 +750,7 @@ __device__ __forceinline__ void csr_vec4_task(const CsrArgs& a, int vl, int tile
   const int v = a.v_begin + vl;
   const int s0 = __ldg(a.csr_off + v), s1 = __ldg(a.csr_off + v + 1);
   const int inst = __ldg(a.var_inst + v);
+  const int first_var = __ldg(a.var_inst + a.n_vars + inst);
   const int word = (a.b0 + bl) >> 5;
   const long long wi = static_cast<long long>(inst) * a.W + word;
   unsigned sw = 0u;  // solved (or fixed) bits of this lane's restarts
@@ -816,12 +819,12 @@ __device__ __forceinline__ void csr_vec4_task(const CsrArgs& a, int vl, int tile
   wv |= __shfl_xor_sync(0xffffffffu, wv, 4);
   if ((lane & 7) == 0 && act) {
     if (a.sgn != nullptr) a.sgn[static_cast<long long>(v) * a.W + word] = wv;
-    if (v == __ldg(a.var_inst + a.n_vars + inst)) csr_first_var_duty(a, inst, word, wi);
+    if (v == first_var) csr_first_var_duty(a, inst, word, wi);
   }
 }
 
 template <typename XT, bool OFF32>
-__global__ void __launch_bounds__(256, 5) csr_update_vec4_kernel(CsrArgs a) {
+__global__ void __launch_bounds__(256, 4) csr_update_vec4_kernel(CsrArgs a) {
   pdl_wait();
   pdl_trigger();
   const int lane = threadIdx.x & 31;
