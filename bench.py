@@ -35,6 +35,7 @@ import argparse
 import hashlib
 import json
 import os
+import tempfile
 import statistics
 import subprocess
 import sys
@@ -93,7 +94,7 @@ class ClockSampler:
     def __init__(self, gpu_id: str):
         self.gpu_id = gpu_id
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"afsat_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -538,8 +539,8 @@ def run_ours(args):
 
 
 def run_batch_sweep(args):
-    """Throughput against the restart count B for one workload (SURVEY NEXT 4:
-    where the autotuned chunk and the L2 make the rate peak). One line per run:
+    """Throughput against the restart count B for one workload (where the
+    autotuned chunk and the L2 make the rate peak). One line per run:
     B, chunk, tiles, literal-evals/s, ms per step; same timing rules as the
     main measurement (graph replays of 10 steps, L2 flushed between)."""
     import torch

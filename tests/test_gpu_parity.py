@@ -89,6 +89,31 @@ def test_long_lengths(k):
         _check_eval(inst, synth.near_vertex_x0(inst.n, 11, k, spread=0.02), tol=tol)
 
 
+@pytest.mark.parametrize("k", [129, 130, 391, 392, 393, 785])
+def test_long_scaled_form_boundaries(k):
+    """Lengths where the long probability-generating tables switch to the
+    scaled factor form (129) and where a 32-root pass switches form (k near
+    392: the last pass of roots close to pi/2; odd k: the real root), for
+    parity (odd k keeps the real root only, even k every complex root), NAE,
+    EO and a threshold, at uniform and near-vertex points."""
+    tol = TOL * max(1.0, (k / 512) ** 2)
+    for t, op, r, par in ((synth.XOR, 0, 0, 1), (synth.XOR, 0, 0, 0), (synth.NAE, 0, 0, 1), (synth.EO, 0, 0, 1),
+                          (synth.CARD, synth.GE, k // 2, 1)):
+        inst = synth.single_type(t, k, 2, k + 5, index=k + t, op=op, param=r, parity=par)
+        _check_eval(inst, synth.uniform_x0(inst.n, 13, k), tol=tol)
+        _check_eval(inst, synth.near_vertex_x0(inst.n, 7, k, spread=0.02), tol=tol)
+
+
+def test_bf16_storage_long_scaled():
+    """BF16 state with long constraints in both long layouts (k = 100 direct,
+    k = 300 scaled): arithmetic at the dequantised point within 1e-5."""
+    for k in (100, 300):
+        inst = synth.single_type(synth.CARD, k, 2, k + 9, index=k, op=synth.GE, param=k // 2)
+        x = synth.uniform_x0(inst.n, 24, k)
+        x_deq = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+        _check_eval(inst, x_deq, x_dtype=torch.bfloat16, x_ref=x_deq)
+
+
 def test_mixed_short_and_long_in_one_instance():
     inst = synth.long_card_n10000(0, n=2000, n_clauses=3000, n_long=12, kmin=33, kmax=300)
     _check_eval(inst, synth.uniform_x0(inst.n, 41, 3))
