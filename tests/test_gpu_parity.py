@@ -528,14 +528,21 @@ def test_reader_units_as_partial_assignment():
 
 
 # ---- line search ---------------------------------------------------------------
-def test_line_search_step_matches_the_oracle():
+@pytest.mark.parametrize("which", ["mixed", "long"])
+def test_line_search_step_matches_the_oracle(which):
     """One Armijo step: the trial each restart takes is the oracle's (except
     where the sufficient-decrease test is within FP32 noise of its bound), and
-    the new state equals the oracle's for those restarts."""
-    inst = synth.mixed_small(4)
+    the new state equals the oracle's for those restarts. "long" adds
+    constraints of length 100..300 (both long-table layouts), whose FE values
+    enter the objective the trials are judged by."""
+    if which == "mixed":
+        inst = synth.mixed_small(4)
+    else:
+        inst = synth.long_card_n10000(0, n=400, n_clauses=600, n_long=6, kmin=100, kmax=300)
     B = 40
     x0 = synth.uniform_x0(inst.n, B, 4)
-    s, beta, c, T = 30.0, 0.5, 1e-4, 8
+    # (a stricter decrease constant makes the long instance backtrack too)
+    s, beta, c, T = 30.0, 0.5, (1e-4 if which == "mixed" else 0.5), 8
     ref, ref_chosen = O.armijo_step(inst, x0.astype(np.float64), s, beta, c, T)
     h = bd.load_instance(inst, bd.default_params(autotune=0))
     bd.init_restarts(h, B, x0=_dev(x0))
