@@ -156,7 +156,9 @@ int afs_step(afs_handle* h, int32_t nsteps, void* stream);
  * afs_eval_fe_grad. Fixed variables (afs_set_fixed) are not moved. The call
  * ends with an exact count of the final state (afs_get_verify). chosen_dev
  * (nullable, device, n_inst * B) receives the trial each restart took in the
- * last iteration, -1 where it accepted none. Not captured in a graph. */
+ * last iteration, -1 where it accepted none. With use_graph set, the second
+ * call with the same nsteps, step parity, trials, s, beta and c captures a
+ * CUDA graph that later such calls replay (the first launches directly). */
 int afs_step_ls(afs_handle* h, int32_t nsteps, float s, float beta, float c, int32_t trials, int32_t* chosen_dev,
                 void* stream);
 

@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cmath>
 #include <cstring>
+#include <array>
 #include <map>
 #include <memory>
 #include <string>
@@ -204,6 +205,10 @@ struct afs_handle {
   cudaStream_t chk = nullptr, fus_s = nullptr;
   cudaEvent_t ev_chk = nullptr, ev_fus = nullptr;
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs, timed_graphs;  // (nsteps, start parity)
+  std::map<std::pair<int, int>, long long> graph_launches;                 // kernels per cached graph
+  // line-search iterations: (nsteps, start parity, trials, s, beta, c bits)
+  std::map<std::array<uint32_t, 6>, cudaGraphExec_t> ls_graphs;
+  std::map<std::array<uint32_t, 6>, int> ls_uses;  // calls seen per key (captured from the second on)
   std::map<std::pair<int, int>, std::pair<std::vector<std::pair<int, int>>, std::vector<std::pair<int, int>>>>
       timed_pairs;
   // timing
@@ -217,6 +222,7 @@ struct afs_handle {
   ~afs_handle() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.second);
     for (auto& g : timed_graphs) cudaGraphExecDestroy(g.second);
+    for (auto& g : ls_graphs) cudaGraphExecDestroy(g.second);
     for (auto e : ev_pool) cudaEventDestroy(e);
     if (cap) cudaStreamDestroy(cap);
     for (int i = 0; i < NAUX; ++i) {
@@ -233,9 +239,13 @@ struct afs_handle {
   void drop_graphs() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.second);
     for (auto& g : timed_graphs) cudaGraphExecDestroy(g.second);
+    for (auto& g : ls_graphs) cudaGraphExecDestroy(g.second);
     graphs.clear();
     timed_graphs.clear();
     timed_pairs.clear();
+    graph_launches.clear();
+    ls_graphs.clear();
+    ls_uses.clear();
   }
 };
 
@@ -1253,10 +1263,9 @@ int afs_step(afs_handle* h, int32_t nsteps, void* stream) {
       h->csr_pairs.resize(cs0);
     }
     it = cache.emplace(key, exec).first;
+    h->graph_launches[key] = nl;
   } else {
-    const int chunks = (h->B + h->Bc - 1) / h->Bc;
-    nl = static_cast<long long>(nsteps) * chunks * (static_cast<long long>(h->groups.size()) + (check ? 2 : 1));
-    if (check) nl += 2;
+    nl = h->graph_launches[key];
   }
   h->last_launches = nl;
   CK(cudaGraphLaunch(it->second, s));
@@ -1444,26 +1453,18 @@ static int eval_state(afs_handle* h, const void* x, float* fe, float* g, cudaStr
   return AFS_OK;
 }
 
-int afs_step_ls(afs_handle* h, int32_t nsteps, float step0, float beta, float c, int32_t trials, int32_t* chosen_dev,
-                void* stream) {
-  if (!h) return fail(AFS_E_ARG, "NULL handle");
-  if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
-  if (nsteps < 0 || trials < 1 || !(step0 > 0.0f) || !(beta > 0.0f && beta < 1.0f) || !(c >= 0.0f))
-    return fail(AFS_E_ARG, "need nsteps >= 0, trials >= 1, s > 0, 0 < beta < 1, c >= 0");
-  if (nsteps == 0) return AFS_OK;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+// nsteps line-search iterations from parity p0 onto s (no host state
+// changes; captured as a graph by afs_step_ls): per iteration the FE and
+// gradient at x, the objective, then per trial the candidate, its FE, its
+// objective and the acceptance; the accepted state (or the last trial) is in
+// the other buffer. Ends with the exact count of the final state.
+static int enqueue_ls(afs_handle* h, int nsteps, float step0, float beta, float c, int trials, int p0,
+                      cudaStream_t s) {
   const size_t nib = static_cast<size_t>(h->n_inst) * h->B;
-  int rc;
-  if ((rc = h->ls_fe.alloc(sizeof(float) * static_cast<size_t>(std::max(h->m, 1)) * h->pitch))) return rc;
-  if ((rc = h->ls_g.alloc(sizeof(float) * static_cast<size_t>(h->n) * h->pitch))) return rc;
-  if ((rc = h->ls_f0.alloc(sizeof(float) * nib))) return rc;
-  if ((rc = h->ls_fi.alloc(sizeof(float) * nib))) return rc;
-  if ((rc = h->ls_dec.alloc(sizeof(float) * nib))) return rc;
-  if ((rc = h->ls_done.alloc(sizeof(int) * nib))) return rc;
-  if ((rc = h->ls_chosen.alloc(sizeof(int) * nib))) return rc;
   float* fe = h->ls_fe.as<float>();
+  int rc;
   for (int t = 0; t < nsteps; ++t) {
-    const int p = h->parity;
+    const int p = (p0 + t) & 1;
     void* xin = h->xb[p].p;
     void* xout = h->xb[p ^ 1].p;
     if ((rc = eval_state(h, xin, fe, h->ls_g.as<float>(), s))) return rc;
@@ -1498,14 +1499,70 @@ int afs_step_ls(afs_handle* h, int32_t nsteps, float step0, float beta, float c,
                        h->ls_done.as<int>(), h->ls_chosen.as<int>(), static_cast<long long>(nib), s);
       CKL();
     }
-    // restarts that accepted no trial keep the last candidate, already in xout
-    h->parity ^= 1;
-    if ((rc = afs::state_written(h, s))) return rc;
+    // restarts that accepted no trial keep the last candidate, already in
+    // xout; fixed variables and the sign words of the new state
+    if (h->fix_groups > 0) {
+      launch_apply_fixed(xout, h->xt, h->pitch, h->n, h->B, h->fixv.as<signed char>(), h->fix_groups, s);
+      CKL();
+    }
+    launch_pack_signs(xout, h->xt, h->pitch, h->n, h->B, h->sgn.as<unsigned>(), h->W, s);
+    CKL();
   }
   // the next checked step ORs into the words of its parity: start both clean
   CK(cudaMemsetAsync(h->vword.p, 0, h->vword.bytes, s));
+  return launch_check(h, h->xb[(p0 + nsteps) & 1].p, s);
+}
+
+int afs_step_ls(afs_handle* h, int32_t nsteps, float step0, float beta, float c, int32_t trials, int32_t* chosen_dev,
+                void* stream) {
+  if (!h) return fail(AFS_E_ARG, "NULL handle");
+  if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
+  if (nsteps < 0 || trials < 1 || !(step0 > 0.0f) || !(beta > 0.0f && beta < 1.0f) || !(c >= 0.0f))
+    return fail(AFS_E_ARG, "need nsteps >= 0, trials >= 1, s > 0, 0 < beta < 1, c >= 0");
+  if (nsteps == 0) return AFS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t nib = static_cast<size_t>(h->n_inst) * h->B;
+  int rc;
+  if ((rc = h->ls_fe.alloc(sizeof(float) * static_cast<size_t>(std::max(h->m, 1)) * h->pitch))) return rc;
+  if ((rc = h->ls_g.alloc(sizeof(float) * static_cast<size_t>(h->n) * h->pitch))) return rc;
+  if ((rc = h->ls_f0.alloc(sizeof(float) * nib))) return rc;
+  if ((rc = h->ls_fi.alloc(sizeof(float) * nib))) return rc;
+  if ((rc = h->ls_dec.alloc(sizeof(float) * nib))) return rc;
+  if ((rc = h->ls_done.alloc(sizeof(int) * nib))) return rc;
+  if ((rc = h->ls_chosen.alloc(sizeof(int) * nib))) return rc;
+  const int p0 = h->parity;
+  if (!h->p.use_graph) {
+    if ((rc = enqueue_ls(h, nsteps, step0, beta, c, trials, p0, s))) return rc;
+  } else {
+    std::array<uint32_t, 6> key{static_cast<uint32_t>(nsteps), static_cast<uint32_t>(p0),
+                                static_cast<uint32_t>(trials), 0u, 0u, 0u};
+    std::memcpy(&key[3], &step0, 4);
+    std::memcpy(&key[4], &beta, 4);
+    std::memcpy(&key[5], &c, 4);
+    auto it = h->ls_graphs.find(key);
+    // a key's first call launches directly (a short solve need not pay the
+    // capture); a repeated call captures and replays from then on
+    if (it == h->ls_graphs.end() && h->ls_uses[key]++ == 0) {
+      if ((rc = enqueue_ls(h, nsteps, step0, beta, c, trials, p0, s))) return rc;
+    } else if (it == h->ls_graphs.end()) {
+      cudaGraph_t graph;
+      CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+      rc = enqueue_ls(h, nsteps, step0, beta, c, trials, p0, h->cap);
+      cudaError_t ce = cudaStreamEndCapture(h->cap, &graph);
+      if (rc) return rc;
+      if (ce != cudaSuccess) return fail(AFS_E_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+      cudaGraphExec_t exec;
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) return fail(AFS_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+      it = h->ls_graphs.emplace(key, exec).first;
+      CK(cudaGraphLaunch(it->second, s));
+    } else {
+      CK(cudaGraphLaunch(it->second, s));
+    }
+  }
+  h->parity = (p0 + nsteps) & 1;
   h->step_check_valid = false;
-  if ((rc = launch_check(h, h->xcur(), s))) return rc;
   h->count_valid = true;
   if (chosen_dev) CK(cudaMemcpyAsync(chosen_dev, h->ls_chosen.p, sizeof(int) * nib, cudaMemcpyDeviceToDevice, s));
   return AFS_OK;

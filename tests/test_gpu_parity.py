@@ -583,3 +583,28 @@ def test_line_search_then_fixed_steps_with_partial_assignment():
     un, _ = bd.get_verify(h)
     np.testing.assert_array_equal(un.cpu().numpy()[0], O.unsat_count(inst, x2))
     assert np.all(x2[:50] == -1.0)
+
+
+def test_line_search_graph_replay_equals_direct_launches():
+    """The captured line-search graph (replayed across calls and parities)
+    gives bit-identical states, trial choices and counts to direct launches."""
+    inst = synth.hybrid_n2000(3)
+    B = 96
+    x0 = synth.uniform_x0(inst.n, B, 8)
+    out = {}
+    for use_graph in (0, 1):
+        h = bd.load_instance(inst, bd.default_params(eta=0.1, autotune=0, use_graph=use_graph))
+        bd.init_restarts(h, B, x0=_dev(x0))
+        ch = []
+        # per (nsteps, start parity): direct launches, then capture, then replays
+        for _ in range(6):
+            ch.append(bd.step_ls(h, 1, 2.0, 0.5, 1e-3, 5).cpu().numpy())
+        for _ in range(3):
+            ch.append(bd.step_ls(h, 2, 2.0, 0.5, 1e-3, 5).cpu().numpy())
+        un, _ = bd.get_verify(h)
+        out[use_graph] = (bd.get_x(h).cpu().numpy(), np.stack(ch), un.cpu().numpy())
+        h.free()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+    np.testing.assert_array_equal(out[1][2][0], O.unsat_count(inst, out[1][0]))
