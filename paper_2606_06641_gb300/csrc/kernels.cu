@@ -158,10 +158,23 @@ __device__ __forceinline__ void long_segment_scaled(const float* el, int n, floa
   float pr[LONG_SEG], pi[LONG_SEG], wv[CF ? LONG_SEG : 1];
   pr[0] = Qr;
   pi[0] = Qi;
+  // the segment's literal values as four 16-byte broadcast reads (a segment
+  // starts 16-byte aligned; a partial one reads past n inside the CTA's
+  // shared memory and ignores those values)
+  const float4* e4 = reinterpret_cast<const float4*>(el);
+  float ev[LONG_SEG];
+#pragma unroll
+  for (int u = 0; u < LONG_SEG / 4; ++u) {
+    const float4 v = e4[u];
+    ev[4 * u] = v.x;
+    ev[4 * u + 1] = v.y;
+    ev[4 * u + 2] = v.z;
+    ev[4 * u + 3] = v.w;
+  }
 #pragma unroll
   for (int t = 0; t < LONG_SEG; ++t) {
     if (FULL || t < n) {
-      const float w = FA ? el[t] * p : el[t];
+      const float w = FA ? ev[t] * p : ev[t];
       if constexpr (CF) wv[t] = w;
       if (t + 1 < LONG_SEG) {
         if constexpr (FA) {
@@ -179,7 +192,7 @@ __device__ __forceinline__ void long_segment_scaled(const float* el, int n, floa
     float v = 0.0f;
     if (FULL || t < n) {
       v = fmaf(pr[t], Sr, -pi[t] * Si) * sc;
-      const float w = CF ? wv[t] : (FA ? el[t] * p : el[t]);
+      const float w = CF ? wv[t] : (FA ? ev[t] * p : ev[t]);
       float nr, ni;
       if constexpr (FA) {
         nr = fmaf(Sr, w, -Si);
@@ -197,21 +210,31 @@ __device__ __forceinline__ void long_segment_scaled(const float* el, int n, floa
 
 // Forward walk of one segment in the scaled form (prefix only).
 template <bool FA>
-__device__ __forceinline__ void long_forward_scaled(const float* el, int n, float p, float q, float& Pr, float& Pi) {
-#pragma unroll 4
-  for (int t = 0; t < n; ++t) {
-    const float w = FA ? el[t] * p : el[t];
-    float nr, ni;
-    if constexpr (FA) {
-      nr = fmaf(Pr, w, -Pi);
-      ni = fmaf(Pi, w, Pr);
-    } else {
-      nr = fmaf(Pr, w, -Pi * q);
-      ni = fmaf(Pi, w, Pr * q);
-    }
-    Pr = nr;
-    Pi = ni;
+__device__ __forceinline__ void long_forward_step(float l, float p, float q, float& Pr, float& Pi) {
+  const float w = FA ? l * p : l;
+  float nr, ni;
+  if constexpr (FA) {
+    nr = fmaf(Pr, w, -Pi);
+    ni = fmaf(Pi, w, Pr);
+  } else {
+    nr = fmaf(Pr, w, -Pi * q);
+    ni = fmaf(Pi, w, Pr * q);
   }
+  Pr = nr;
+  Pi = ni;
+}
+template <bool FA>
+__device__ __forceinline__ void long_forward_scaled(const float* el, int n, float p, float q, float& Pr, float& Pi) {
+  // four literals per 16-byte broadcast read (el is 16-byte aligned)
+  int t = 0;
+  for (; t + 4 <= n; t += 4) {
+    const float4 v = *reinterpret_cast<const float4*>(el + t);
+    long_forward_step<FA>(v.x, p, q, Pr, Pi);
+    long_forward_step<FA>(v.y, p, q, Pr, Pi);
+    long_forward_step<FA>(v.z, p, q, Pr, Pi);
+    long_forward_step<FA>(v.w, p, q, Pr, Pi);
+  }
+  for (; t < n; ++t) long_forward_step<FA>(el[t], p, q, Pr, Pi);
 }
 
 // 2^e as a float for -126 <= e <= 127.
@@ -406,15 +429,23 @@ __global__ void __launch_bounds__(RT * 32) fe_grad_long_kernel(FeGroupArgs a, in
         if (ESP) myce[seg * 32 + lane] = static_cast<short>(Pe);
         const int i0 = seg * LONG_SEG;
         const int n = min(LONG_SEG, k - i0);
-#pragma unroll 4
-        for (int t = 0; t < n; ++t) {
-          const float ll = el[i0 + t];
+        // four literals per 16-byte broadcast read (segments start aligned)
+        auto fstep = [&](float ll) {
           const float Fr = fmaf(br, ll, ar), Fi = fmaf(bi, ll, ai);
           const float nr = fmaf(Pr, Fr, -Pi * Fi);
           const float ni = fmaf(Pr, Fi, Pi * Fr);
           Pr = nr;
           Pi = ni;
+        };
+        int t = 0;
+        for (; t + 4 <= n; t += 4) {
+          const float4 v = *reinterpret_cast<const float4*>(el + i0 + t);
+          fstep(v.x);
+          fstep(v.y);
+          fstep(v.z);
+          fstep(v.w);
         }
+        for (; t < n; ++t) fstep(el[i0 + t]);
         if (ESP) renorm(Pr, Pi, Pe);
       }
       float val = fmaf(er, Pr, -ei * Pi);
