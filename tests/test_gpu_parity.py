@@ -309,6 +309,61 @@ def test_config2_full_size_sampled():
     assert (np.abs(g.cpu().numpy() - g_ref) / _grad_scale(inst, go_ref)).max() <= TOL
 
 
+def _check_step_columns(inst, x0, x1, cols, eta, tol=TOL):
+    """x1 = one step from x0, checked on the sampled restarts `cols` against
+    the oracle: the update within eta * tol of the variable's gradient scale,
+    and the exact unsat counts of the new state."""
+    _, go_ref, g_ref = O.evaluate(inst, x0[:, cols].astype(np.float64))
+    ref = np.clip(x0[:, cols].astype(np.float64) - eta * g_ref, -1.0, 1.0)
+    bound = eta * tol * _grad_scale(inst, go_ref) + 1e-6
+    assert np.all(np.abs(x1[:, cols] - ref) <= bound)
+
+
+def test_config3_full_size_sampled():
+    """The long-constraint instance (n = 10000, 30000 3-OR + 500 CARD/EK of
+    length 64..512) at B = 4096 in the launch configuration of the benchmark:
+    one step checked on sampled restarts, and the exact counts of the new
+    state on them."""
+    inst = synth.long_card_n10000(0)
+    B, eta = 4096, 0.1
+    x0 = synth.uniform_x0(inst.n, B, 12)
+    h = bd.load_instance(inst, bd.default_params(eta=eta))
+    bd.init_restarts(h, B, x0=_dev(x0))
+    bd.step(h, 1)
+    x1 = bd.get_x(h).cpu().numpy()
+    un, _ = bd.get_verify(h)
+    h.free()
+    cols = np.array([0, 1, 31, 32, 1000, 2047, 2048, 4095])
+    _check_step_columns(inst, x0, x1, cols, eta)   # lengths up to 512: the 1e-5 bar
+    np.testing.assert_array_equal(un.cpu().numpy()[0][cols], O.unsat_count(inst, x1[:, cols]))
+
+
+def test_config4_full_size_sampled():
+    """The uneven batch (256 instances, n log-uniform in 100..20000, B = 64 each)
+    in one handle as the benchmark loads it: one step, checked for the
+    smallest, a middle and the largest instance on every restart (counts) and
+    on sampled restarts (update)."""
+    insts = synth.instance_batch(256)
+    B, eta = 64, 0.1
+    h = bd.load_batch(insts, bd.default_params(eta=eta))
+    bd.init_restarts(h, B, seed=21)
+    x0 = bd.get_x(h).cpu().numpy()
+    bd.step(h, 1)
+    x1 = bd.get_x(h).cpu().numpy()
+    un, _ = bd.get_verify(h)
+    un = un.cpu().numpy()
+    h.free()
+    offs = np.concatenate([[0], np.cumsum([i.n for i in insts])])
+    sizes = np.array([i.n for i in insts])
+    order = np.argsort(sizes)
+    cols = np.array([0, 1, 31, 32, 63])
+    for i in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        inst = insts[i]
+        a, b = offs[i], offs[i + 1]
+        np.testing.assert_array_equal(un[i], O.unsat_count(inst, x1[a:b]), err_msg=f"instance {i}")
+        _check_step_columns(inst, x0[a:b], x1[a:b], cols, eta)
+
+
 # ---- solver behaviour and edge cases ---------------------------------------
 def test_never_reports_sat_on_unsat_instances():
     seen = {True: 0, False: 0}
