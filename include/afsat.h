@@ -82,11 +82,12 @@ typedef struct afs_params {
   int32_t x_storage;    /* AFS_X_F32 or AFS_X_BF16 storage of the state x   */
   int32_t verify_every; /* 0 = no exact check inside afs_step; otherwise
                            every step checks the state it reads and leaves
-                           solved restarts unmoved, and each afs_step call
-                           ends with a check of its final state             */
+                           solved restarts unmoved (the exact count of the
+                           final state is computed by afs_get_verify)       */
   int32_t chunk;        /* restarts per chunk of the step (0 = autotuned)    */
   int32_t autotune;     /* 1 = time tile shapes per bucket at init           */
-  int32_t use_graph;    /* 1 = replay afs_step as a captured CUDA graph      */
+  int32_t use_graph;    /* 1 = replay afs_step (and repeated afs_step_ls
+                           calls) as captured CUDA graphs                   */
   int32_t reserved;
 } afs_params;
 
@@ -328,8 +329,10 @@ int afs_set_tiles(afs_handle* h, int32_t chunk, const int32_t* rpl_by_k, const i
 
 /* afs_coef_table: the FP32 coefficient table the kernels use for one
  * constraint shape (for host-side inspection and tests). form 0 = short
- * (k <= 32) layout, form 1 = long layout. Writes up to cap floats into out
- * and the table length into *len. No device work. */
+ * (k <= 32) layout, form 1 = long layout (in the probability-generating basis
+ * the direct-factor layout below k = 129 and the scaled-factor layout from
+ * 129 on). Writes up to cap floats into out and the table length into *len.
+ * No device work. */
 int afs_coef_table(int32_t type, int32_t k, int32_t op, int32_t param, int32_t parity,
                    int32_t basis, int32_t form, float* out, int32_t cap, int32_t* len);
 /* afs_esp_coefficients: f_hat(|S| = d) for d = 0..k in FP64 (Eq. 1's
