@@ -48,7 +48,7 @@ extern "C" {
 #define AFS_E_VERIFY (-7)    /* host re-check of a device result disagreed     */
 #define AFS_E_STATE (-8)     /* call out of order (e.g. step before init)      */
 
-#define AFS_MAX_LEN 1024     /* longest constraint accepted                   */
+#define AFS_MAX_LEN 512      /* longest constraint accepted                   */
 
 /* ---- constraint records (Table 1; Appendix A type table) ----------------
  * A literal is True when its value is -1 (Sec. 2.1: True -> -1, False -> +1).
@@ -327,12 +327,28 @@ int afs_tiles(const afs_handle* h, int32_t* chunk, int32_t* rpl_by_k, int32_t* c
  * changes and AFS_E_ARG is returned. Cached step graphs are dropped. */
 int afs_set_tiles(afs_handle* h, int32_t chunk, const int32_t* rpl_by_k, const int32_t* cpw_by_k, int32_t kcap);
 
+/* afs_long_tiles: the kernel tile of each long-constraint group (k > 32) in
+ * bucket order (longest first): lanes per restart (8, 16 or 32; a pass of the
+ * probability-generating kernel evaluates that many roots of one restart)
+ * and warps per CTA, plus the group's longest constraint. Writes min(cap,
+ * groups) entries to the non-NULL arrays and the number of long groups to *n.
+ * Tiles are chosen at load (fewest idle lanes, then most resident warps) and
+ * timed by the autotuner at afs_init_restarts. No device work. */
+int afs_long_tiles(const afs_handle* h, int32_t* lanes, int32_t* warps, int32_t* kmax, int32_t cap, int32_t* n);
+/* afs_set_long_tiles: fix the tiles of the long groups of a
+ * probability-generating handle, n entries in afs_long_tiles order; an entry
+ * with lanes = warps = 0 keeps that group's tile. Each pair must be one of
+ * the kernel's tiles, (32,4), (32,8), (16,2), (16,4) or (8,2), and fit the
+ * group's shared memory; otherwise nothing changes and AFS_E_ARG is returned.
+ * Cached step graphs are dropped. No device work. */
+int afs_set_long_tiles(afs_handle* h, const int32_t* lanes, const int32_t* warps, int32_t n);
+
 /* afs_coef_table: the FP32 coefficient table the kernels use for one
  * constraint shape (for host-side inspection and tests). form 0 = short
  * (k <= 32) layout, form 1 = long layout (in the probability-generating basis
- * the direct-factor layout below k = 129 and the scaled-factor layout from
- * 129 on). Writes up to cap floats into out and the table length into *len.
- * No device work. */
+ * the factor-form layout with per-segment scale powers; in the paper's basis
+ * the direct-factor layout). Writes up to cap floats into out and the table
+ * length into *len. No device work. */
 int afs_coef_table(int32_t type, int32_t k, int32_t op, int32_t param, int32_t parity,
                    int32_t basis, int32_t form, float* out, int32_t cap, int32_t* len);
 /* afs_esp_coefficients: f_hat(|S| = d) for d = 0..k in FP64 (Eq. 1's

@@ -23,7 +23,7 @@ ERRORS = {-1: "AFS_E_ARG", -2: "AFS_E_VAR_RANGE", -3: "AFS_E_LEN", -4: "AFS_E_TY
           -6: "AFS_E_TIMEOUT", -7: "AFS_E_VERIFY", -8: "AFS_E_STATE"}
 BASIS_PGF, BASIS_ESP = 0, 1
 X_F32, X_BF16 = 0, 1
-MAX_LEN = 1024
+MAX_LEN = 512
 
 CONS_DTYPE = np.dtype([("type", "u1"), ("op", "u1"), ("parity", "u1"), ("reserved", "u1"),
                        ("param", "<i4"), ("lit_offset", "<i4"), ("len", "<i4")])
@@ -69,6 +69,8 @@ SIGNATURES = {
     "afs_set_fixed": (_I32, [_P, _P, _I32, _P]),
     "afs_step_ls": (_I32, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I32, _P, _P]),
     "afs_set_tiles": (_I32, [_P, _I32, _P, _P, _I32]),
+    "afs_long_tiles": (_I32, [_P, _P, _P, _P, _I32, _P]),
+    "afs_set_long_tiles": (_I32, [_P, _P, _P, _I32]),
     "afs_coef_table": (_I32, [_I32, _I32, _I32, _I32, _I32, _I32, _I32, _P, _I32, _P]),
     "afs_esp_coefficients": (_I32, [_I32, _I32, _I32, _I32, _I32, _P]),
     "afs_last_error": (ctypes.c_char_p, []),
@@ -441,6 +443,25 @@ def set_tiles(h: Handle, chunk: int = 0, tiles=None):
         rpl[int(k)] = int(r)
         cpw[int(k)] = int(c)
     _check(lib().afs_set_tiles(h.ptr, int(chunk), rpl, cpw, 33))
+
+
+def long_tiles(h: Handle):
+    """[(lanes per restart, warps per CTA, longest k)] of the long groups, longest first."""
+    n = ctypes.c_int32()
+    _check(lib().afs_long_tiles(h.ptr, None, None, None, 0, ctypes.byref(n)))
+    lw = (ctypes.c_int32 * max(1, n.value))()
+    nw = (ctypes.c_int32 * max(1, n.value))()
+    km = (ctypes.c_int32 * max(1, n.value))()
+    _check(lib().afs_long_tiles(h.ptr, lw, nw, km, n.value, ctypes.byref(n)))
+    return [(lw[i], nw[i], km[i]) for i in range(n.value)]
+
+
+def set_long_tiles(h: Handle, tiles):
+    """Fix the long groups' (lanes, warps) tiles, in long_tiles order; (0, 0) keeps one."""
+    n = len(tiles)
+    lw = (ctypes.c_int32 * max(1, n))(*[int(t[0]) for t in tiles])
+    nw = (ctypes.c_int32 * max(1, n))(*[int(t[1]) for t in tiles])
+    _check(lib().afs_set_long_tiles(h.ptr, lw, nw, n))
 
 
 def parse_tiles(spec: str):

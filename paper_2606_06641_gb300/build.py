@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(LIB_DIR, "libafsat.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-O2", f"-I{INCLUDE}", f"-I{CSRC}"]
-SOURCES = ["host.cpp", "coef.cpp", "kernels.cu", "short_pgf_f32.cu", "short_pgf_bf16.cu",
+SOURCES = ["host.cpp", "coef.cpp", "kernels.cu", "long_pgf.cu", "short_pgf_f32.cu", "short_pgf_bf16.cu",
            "short_esp_f32.cu", "short_esp_bf16.cu", "noalloc.cu", "mpnn.cu"]
 
 

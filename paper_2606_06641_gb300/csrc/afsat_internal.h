@@ -158,10 +158,20 @@ bool launch_short_pgf_f32(const FeGroupArgs& a, int rpl, int warps, cudaStream_t
 bool launch_short_pgf_bf16(const FeGroupArgs& a, int rpl, int warps, cudaStream_t s);
 bool launch_short_esp_f32(const FeGroupArgs& a, int rpl, int warps, cudaStream_t s);
 bool launch_short_esp_bf16(const FeGroupArgs& a, int rpl, int warps, cudaStream_t s);
-size_t long_smem_bytes(int kmax, bool esp);
-// One-time kernel attribute setup (raises the long kernel's shared-memory cap).
+// One-time kernel attribute setup (raises the long kernels' shared-memory cap).
 bool prepare_kernels();
-void launch_fe_long(const FeGroupArgs& a, int xt, int basis, int rt, cudaStream_t s);
+// Long group (a.k = its longest constraint). The probability-generating
+// kernel runs tile (wl lanes per restart, nw warps per CTA), one of
+// LONG_PGF_SHAPES; false if no kernel exists for that tile.
+bool launch_fe_long(const FeGroupArgs& a, int xt, int basis, int wl, int nw, cudaStream_t s);
+constexpr int LONG_PGF_NSHAPES = 5;
+extern const int LONG_PGF_SHAPES[LONG_PGF_NSHAPES][2];  // {wl, nw}
+bool launch_fe_long_pgf(const FeGroupArgs& a, int xt, int wl, int nw, cudaStream_t s);
+bool prepare_long_pgf(int optin_smem);
+size_t long_pgf_smem_bytes(int kmax, int wl, int nw);
+// Warps of the probability-generating long kernel resident per SM for a
+// group of longest constraint kmax (0 if the tile does not fit).
+int long_pgf_resident_warps(int xt, int kmax, int wl, int nw);
 void launch_csr_update(const CsrArgs& a, int xt, cudaStream_t s);
 // The fused occurrences' summed derivatives of every variable for the chunk
 // (reads x_t only, so it runs beside the FE launches) into a.gf.

@@ -8,6 +8,7 @@
 #include "coef.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <stdexcept>
 
@@ -182,73 +183,186 @@ static void push4(std::vector<float>& o, double a, double b, double c, double d)
   o.push_back(static_cast<float>(d));
 }
 
-// Long probability-generating table (see coef.h): the roots whose
-// coefficient is not zero, complex roots by increasing angle theta_j = pi j/N
-// and the real root (odd k, theta = pi/2) last; per root the factor
-// a_j + b_j l = s_j g_j(l) with, for the form of its 32-root pass,
-//   A: g = l tan(theta) + i,  s = b cot(theta),  g' = tan(theta)
-//   B: g = l + i cot(theta),  s = b,              g' = 1
-// (b_j = sin(theta) e^{i(theta - pi/2)}, so |s_A| = cos, |s_B| = sin and
-// arg s = theta - pi/2 for both). E' = E s^k and D' = E s^k g' are stored
-// as a shared power of two 2^eb and mantissas. A pass takes form A when
-// every factor of its roots is bounded by LONG_FACTOR_BOUND (1/cos(theta)),
-// else form B (bound 1/sin(theta); the real root's factor is l itself).
-static void build_long_scaled(int k, const std::vector<double>& cr, const std::vector<double>& ci,
-                              std::vector<float>& out) {
-  const int N = k + 1;
-  constexpr double ZERO_ROOT = 1e-13;
-  struct Root {
-    int j;          // root index (N/2 for the real root)
-    double er, ei;  // E_j (complex pair: 2 ft_j; real root: ft_mid)
-  };
-  std::vector<Root> roots;
-  for (int j = 1; j <= k / 2; ++j)
-    if (std::hypot(cr[j], ci[j]) > ZERO_ROOT) roots.push_back({j, 2.0 * cr[j], 2.0 * ci[j]});
-  const int n_complex = static_cast<int>(roots.size());
-  if ((k & 1) && std::fabs(cr[N / 2]) > ZERO_ROOT) roots.push_back({N / 2, cr[N / 2], 0.0});
-  const int n = static_cast<int>(roots.size());
-  out.clear();
-  push4(out, cr[0], n, n_complex, 0);
-  for (int p0 = 0; p0 < n; p0 += 32) {
-    const int p1 = std::min(n, p0 + 32);
-    bool form_a = true;
-    for (int r = p0; r < p1; ++r) {
-      double c, sn;
-      unit_root(roots[r].j, 2LL * N, c, sn);  // angle pi j / N
-      if (2 * roots[r].j == N || 1.0 / c >= LONG_FACTOR_BOUND) form_a = false;
-    }
-    for (int r = p0; r < p1; ++r) {
-      const Root& rt = roots[r];
-      double c, sn;
-      unit_root(rt.j, 2LL * N, c, sn);
-      const bool real_root = 2 * rt.j == N;
-      if (!form_a && !real_root && 1.0 / sn >= LONG_FACTOR_BOUND)
-        throw std::invalid_argument("long table: no scaled factor form fits a root pass");
-      double pf, qf, gp, mag_log2;
-      if (form_a) {
-        pf = sn / c;   // tan
-        qf = 1.0;
-        gp = pf;
-        mag_log2 = k * std::log2(c);
-      } else {
-        pf = 1.0;
-        qf = real_root ? 0.0 : c / sn;  // cot
-        gp = 1.0;
-        mag_log2 = real_root ? 0.0 : k * std::log2(sn);
+// Long probability-generating table (see coef.h).
+//
+// Roots. A complex root pair j, -j (theta_j = pi j / N < pi/2) whose exact
+// coefficient is not zero is evaluated in one of two factor forms,
+//   A: g(l) = p l + i,  p = tan(theta_j) rounded to FP32,
+//   B: g(l) = l + i p,  p = cot(theta_j) rounded to FP32,
+// and the node the kernel actually uses is z'_j = e^{2 i theta'_j} with
+// tan(theta'_j) = p (A) or cot(theta'_j) = p (B) exactly. Rounding tan(theta)
+// to FP32 would otherwise perturb every one of the k factors of a product the
+// same way (a relative error up to k eps in each product). Instead the
+// coefficients are solved in FP64 for the nodes the kernel uses:
+// sum_j c'_j z'_j^t = f(t) for t = 0..k, by iterative refinement started
+// from the DFT of f at the exact roots (the nodes differ from the roots of
+// unity by an angle of about 1e-7, so a few correction steps reach FP64
+// accuracy). The identity
+//   sum_j c'_j prod_i (q_i + p_i z'_j) = sum_t P(T = t) sum_j c'_j z'_j^t
+// then gives the expansion exactly for any nodes, so only per-operation
+// rounding remains. Node 0 (z = 1), the real root z = -1 (odd k) and the
+// roots not evaluated (zero exact coefficient) stay exact.
+//
+// Factor. At node z' the literal factor is a' + b' l with a' = (1 + z')/2,
+// b' = (1 - z')/2 and a'/b' = i cot(theta'), so a' + b' l = s g(l) with
+// s = b'/p (form A, |s| = cos theta') or s = b' (form B, |s| = sin theta').
+// The kernel walks the literals in segments of LONG_SEG = 16 (the last
+// segment n_last long) and keeps running products at their true size at
+// segment boundaries with powers of s: forward, P <- P prod_seg g then
+// P <- P s^16 (full segments); backward, a segment of n literals starts from
+// the checkpoint times s^a and the suffix carried as S s^b (a + b = n - 1:
+// a = 7, b = 8 for a full segment), so Re(prefix * suffix) is the true
+// contribution; after the walk the suffix is multiplied by s^16 (full) or by
+// s^(8 - b + n) (the last segment, walked first). Within a segment
+// |g| <= 1/|s| and the split keeps both running products within 2^126.
+// Roots take form A (one FP32 instruction fewer per complex multiply) up to
+// the first block of 32 kept roots that holds a root with cos(theta) below
+// LONG_FORM_B_COS (there s^16 would leave FP32's normal range), form B from
+// that block on; kernel passes of 8, 16 or 32 roots never straddle it.
+//
+// FP32 rounding of the powers. A stored power s^e is rounded once, but the
+// kernel applies s^16 once per segment, so its rounding would add up over
+// the segments. It is the same factor for every point, so it is compensated
+// in the values that close each chain: E' makes the value exact with the
+// rounded s^16 applied nseg - 1 times, D' makes every full segment's
+// contributions exact with the rounded s^7, s^c and nseg - 2 rounded s^16,
+// and s^a makes the last segment's exact with D' and nseg - 1 rounded s^16.
+// Per kept root (by increasing angle) four granules
+//   {p, s^7}, {s^16, s^a}, {s^c, D'}, {E', 0, 0}
+// with E = 2 c'_j, D = E b'. Head: {c'_0, kept complex roots, c'_mid (the
+// real root's coefficient, odd k), 1 if the real root is present},
+// {first form-B root (a multiple of 32; = kept roots if none), 0, 0, 0}.
+// The real root's factor is l itself (a = 0, b = 1).
+namespace {
+struct Cx {
+  double r, i;
+};
+Cx cmul(Cx a, Cx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+Cx cdiv(Cx a, Cx b) {
+  const double d = b.r * b.r + b.i * b.i;
+  return {(a.r * b.r + a.i * b.i) / d, (a.i * b.r - a.r * b.i) / d};
+}
+Cx cpow(Cx z, int e) {
+  Cx r{1.0, 0.0};
+  while (e > 0) {
+    if (e & 1) r = cmul(r, z);
+    z = cmul(z, z);
+    e >>= 1;
+  }
+  return r;
+}
+Cx f32(Cx z) { return {static_cast<double>(static_cast<float>(z.r)), static_cast<double>(static_cast<float>(z.i))}; }
+}  // namespace
+
+static void build_long_pgf(const Shape& s, std::vector<float>& out) {
+  const int k = s.k, N = k + 1, J = k / 2;  // complex pairs j = 1..J
+  const bool odd = (k & 1) != 0;
+  std::vector<int8_t> f;
+  truth_table(s, f);
+  // exact roots of unity w^m, m = 0..N-1 (for the DFT steps)
+  std::vector<double> wr(N), wi(N);
+  for (int m = 0; m < N; ++m) unit_root(m, N, wr[m], wi[m]);
+  std::vector<double> cr(J + 1, 0.0), ci(J + 1, 0.0);
+  double cmid = 0.0;
+  auto dft_add = [&](const std::vector<double>& src) {  // c_j += (1/N) sum_t src[t] w^{-jt}
+    for (int j = 0; j <= J; ++j) {
+      double sr = 0.0, si = 0.0;
+      for (int t = 0; t <= k; ++t) {
+        const int m = static_cast<int>((static_cast<long long>(j) * t) % N);
+        sr += src[t] * wr[m];
+        si -= src[t] * wi[m];
       }
-      double pc = 1.0, ps = 0.0;  // e^{i k (theta - pi/2)}
-      if (!real_root) unit_root(2LL * rt.j * k - static_cast<long long>(k) * N, 4LL * N, pc, ps);
-      const double eb = std::floor(mag_log2);
-      const double m = std::exp2(mag_log2 - eb);
-      const double sr = m * pc, si = m * ps;
-      const double er = rt.er * sr - rt.ei * si, ei = rt.er * si + rt.ei * sr;
-      push4(out, pf, qf, eb, form_a ? 1.0 : 0.0);
-      push4(out, er * gp, ei * gp, er, ei);
+      cr[j] += sr / N;
+      ci[j] += j == 0 ? 0.0 : si / N;
     }
+    if (odd) {
+      double sm = 0.0;
+      for (int t = 0; t <= k; ++t) sm += (t & 1) ? -src[t] : src[t];
+      cmid += sm / N;
+    }
+  };
+  std::vector<double> res(N);
+  for (int t = 0; t <= k; ++t) res[t] = f[t];
+  dft_add(res);  // exact-root coefficients
+  constexpr double ZERO_ROOT = 1e-13;
+  const bool has_real = odd && std::fabs(cmid) > ZERO_ROOT;
+  // kept roots, their forms and nodes
+  std::vector<int> kept;
+  int first_b = -1;
+  std::vector<double> cosj(J + 1, 1.0), sinj(J + 1, 0.0);
+  for (int j = 1; j <= J; ++j) {
+    unit_root(j, 2LL * N, cosj[j], sinj[j]);  // angle pi j / N
+    if (std::hypot(cr[j], ci[j]) <= ZERO_ROOT) continue;
+    if (first_b < 0 && cosj[j] < LONG_FORM_B_COS) first_b = static_cast<int>(kept.size());
+    kept.push_back(j);
+  }
+  const int nk = static_cast<int>(kept.size());
+  const int form_b_from = first_b < 0 ? nk : first_b / 32 * 32;
+  std::vector<Cx> z(J + 1);
+  std::vector<double> pv(J + 1, 0.0);
+  std::vector<int> formb(J + 1, 0);
+  for (int j = 1; j <= J; ++j) {
+    double c, sn;
+    unit_root(2LL * j, 2LL * N, c, sn);  // exact node w^j
+    z[j] = Cx{c, sn};
+  }
+  for (int r = 0; r < nk; ++r) {
+    const int j = kept[r];
+    const bool fb = r >= form_b_from;
+    const double p = static_cast<float>(fb ? cosj[j] / sinj[j] : sinj[j] / cosj[j]);
+    const double t = fb ? 1.0 / p : p, d = 1.0 + t * t;  // tan(theta') = t
+    pv[j] = p;
+    formb[j] = fb ? 1 : 0;
+    z[j] = Cx{(1.0 - t * t) / d, 2.0 * t / d};
+  }
+  // refine c'_j (j = 0..J) and c'_mid against the nodes
+  for (int it = 0; it < 3; ++it) {
+    // residual f(t) - [c0 + 2 Re sum_j c_j z_j^t + cmid (-1)^t]
+    for (int t = 0; t <= k; ++t) res[t] = f[t] - cr[0] - (odd ? ((t & 1) ? -cmid : cmid) : 0.0);
+    for (int j = 1; j <= J; ++j) {
+      Cx pw{1.0, 0.0};  // z_j^t by repeated multiplication
+      for (int t = 0; t <= k; ++t) {
+        res[t] -= 2.0 * (cr[j] * pw.r - ci[j] * pw.i);
+        pw = cmul(pw, z[j]);
+      }
+    }
+    dft_add(res);
+  }
+  const int nseg = (k + LONG_SEG - 1) / LONG_SEG;
+  const int n_last = k - LONG_SEG * (nseg - 1);
+  const int a_last = (n_last - 1) / 2, b_last = n_last - 1 - a_last, c_last = 8 - b_last + n_last;
+  out.clear();
+  push4(out, cr[0], nk, has_real ? cmid : 0.0, has_real ? 1.0 : 0.0);
+  push4(out, form_b_from, 0, 0, 0);
+  for (int r = 0; r < nk; ++r) {
+    const int j = kept[r];
+    const double p = pv[j];
+    const Cx b{0.5 * (1.0 - z[j].r), -0.5 * z[j].i};  // b' = (1 - z')/2
+    const Cx E{2.0 * cr[j], 2.0 * ci[j]};
+    const Cx D = cmul(E, b);
+    const Cx sc = formb[j] ? b : Cx{b.r / p, b.i / p};
+    if (1.0 / std::hypot(sc.r, sc.i) >= 32768.0) throw std::invalid_argument("long table: root factor bound exceeded");
+    const Cx s7 = f32(cpow(sc, 7)), s16 = f32(cpow(sc, 16)), scl = f32(cpow(sc, c_last));
+    const Cx r16 = cdiv(cpow(sc, 16), s16);  // exact / rounded s^16
+    // E' = E s^n_last (s^16 / fl(s^16))^(nseg-1)
+    const Cx Ep = cmul(cmul(E, cpow(sc, n_last)), cpow(r16, nseg - 1));
+    // D' = D s^b (s^7/fl(s^7)) (s^c/fl(s^c)) (s^16/fl(s^16))^(nseg-2)
+    const Cx Dp = f32(cmul(cmul(cmul(D, cpow(sc, b_last)), cmul(cdiv(cpow(sc, 7), s7), cdiv(cpow(sc, c_last), scl))),
+                           cpow(r16, nseg - 2)));
+    // s^a = D s^(b+a) (s^16/fl(s^16))^(nseg-1) / D'
+    const Cx Sa = cdiv(cmul(cmul(D, cpow(sc, b_last + a_last)), cpow(r16, nseg - 1)), Dp);
+    push4(out, p, s7.r, s7.i, 0.0);
+    push4(out, s16.r, s16.i, Sa.r, Sa.i);
+    push4(out, scl.r, scl.i, Dp.r, Dp.i);
+    push4(out, Ep.r, Ep.i, 0.0, 0.0);
   }
 }
 
 void build_table(const Shape& s, int basis, int form, std::vector<float>& out) {
+  if (form == FORM_LONG && basis == BASIS_PGF) {
+    build_long_pgf(s, out);
+    return;
+  }
   const int k = s.k, N = k + 1;
   std::vector<double> cr, ci;
   dft_coefficients(s, basis, cr, ci);
@@ -306,43 +420,21 @@ void build_table(const Shape& s, int basis, int form, std::vector<float>& out) {
       }
     }
   } else {
-    // every root, real or complex, is two granules {A, b}, {D, E} with the
-    // factor written a + b l = A - b (1 - l), A = a + b. In the
-    // probability-generating basis A = 1 exactly, so the FP32 rounding of b
-    // perturbs a factor by eps*|b| (small at the dominant low roots) instead of
-    // eps; with a and b rounded separately that error would add up coherently
-    // over the k factors.
-    if (basis == BASIS_PGF && k >= LONG_SCALED_MIN_K) {
-      build_long_scaled(k, cr, ci, out);
-    } else if (basis == BASIS_PGF) {
-      push4(out, cr[0], 0, 0, 0);
-      if (odd) {
-        push4(out, 1.0, 0.0, 1.0, 0.0);
-        push4(out, cr[mid], 0.0, cr[mid], 0.0);
-      }
-      for (int j = 1; j <= k / 2; ++j) {
-        double wc, ws;
-        unit_root(j, N, wc, ws);
-        const double br = 0.5 * (1.0 - wc), bi = -0.5 * ws;
-        const double dr = 2.0 * (cr[j] * br - ci[j] * bi), di = 2.0 * (cr[j] * bi + ci[j] * br);
-        push4(out, 1.0, 0.0, br, bi);
-        push4(out, dr, di, 2.0 * cr[j], 2.0 * ci[j]);
-      }
-    } else {
-      push4(out, 0.0, 0, 0, 0);
-      push4(out, 2.0, 0.0, 1.0, 0.0);     // 1 + l
-      push4(out, cr[0], 0.0, cr[0], 0.0);
-      if (odd) {
-        push4(out, 0.0, 0.0, -1.0, 0.0);  // 1 - l
-        push4(out, -cr[mid], 0.0, cr[mid], 0.0);
-      }
-      for (int j = 1; j <= k / 2; ++j) {
-        double wc, ws;
-        unit_root(j, N, wc, ws);
-        const double dr = 2.0 * (cr[j] * wc - ci[j] * ws), di = 2.0 * (cr[j] * ws + ci[j] * wc);
-        push4(out, 1.0 + wc, ws, wc, ws);  // 1 + w^j l
-        push4(out, dr, di, 2.0 * cr[j], 2.0 * ci[j]);
-      }
+    // paper basis: every root, real or complex, is two granules {A, b},
+    // {D, E} with the factor 1 + w^j l written A - b (1 - l), A = 1 + w^j
+    push4(out, 0.0, 0, 0, 0);
+    push4(out, 2.0, 0.0, 1.0, 0.0);     // 1 + l
+    push4(out, cr[0], 0.0, cr[0], 0.0);
+    if (odd) {
+      push4(out, 0.0, 0.0, -1.0, 0.0);  // 1 - l
+      push4(out, -cr[mid], 0.0, cr[mid], 0.0);
+    }
+    for (int j = 1; j <= k / 2; ++j) {
+      double wc, ws;
+      unit_root(j, N, wc, ws);
+      const double dr = 2.0 * (cr[j] * wc - ci[j] * ws), di = 2.0 * (cr[j] * ws + ci[j] * wc);
+      push4(out, 1.0 + wc, ws, wc, ws);  // 1 + w^j l
+      push4(out, dr, di, 2.0 * cr[j], 2.0 * ci[j]);
     }
   }
 }

@@ -8,13 +8,12 @@ namespace afs {
 enum { BASIS_PGF = 0, BASIS_ESP = 1 };
 enum { FORM_SHORT = 0, FORM_LONG = 1 };
 
-// Long probability-generating tables use the scaled factor form from this
-// length on (below it the direct form, whose products need no exponent
-// tracking, costs less per pass).
-constexpr int LONG_SCALED_MIN_K = 129;
-// Largest factor modulus a scaled long-table root may reach for |l| <= 1:
-// 16 such factors (one checkpoint segment) stay below 2^126.
-constexpr double LONG_FACTOR_BOUND = 234.0;
+// Literals per segment of the long kernel's walks: running products are
+// brought back to their true size at segment boundaries (long table below).
+constexpr int LONG_SEG = 16;
+// A pass of long-table roots uses factor form B when one of its roots has
+// cos(theta) below this (s^16 would leave FP32's normal range in form A).
+constexpr double LONG_FORM_B_COS = 1.0 / 64.0;
 
 // Constraints with k <= KSHORT use the register (short) kernels and the
 // short table layout; longer ones use the shared-memory (long) kernel.
@@ -53,18 +52,26 @@ void esp_coefficients(const Shape& s, std::vector<double>& c);
 //     the kernel evaluates  FE   = c0 + sum_r E_r prod_i (l_i + alpha_r)
 //                                     + sum_j Re(E_j prod_i (l_i + alpha_j + i gamma_j))
 //                          dFE/dl_i = sum_r E_r prod_{i'!=i} (...) + sum_j Re(E_j prod_{i'!=i} (...))
-//  long form, paper basis and probability-generating basis below
-//              LONG_SCALED_MIN_K: {c0,0,0,0}, per root (real roots first,
-//              imaginary parts 0) {A.re, A.im, b.re, b.im}, {D.re, D.im, E.re, E.im}
-//     with the factor a + b l = A - b (1 - l), A = a + b:
+//  long form, paper basis: {0,0,0,0}, per root (real roots first, imaginary
+//              parts 0) {A.re, A.im, b.re, b.im}, {D.re, D.im, E.re, E.im}
+//     with the factor 1 + w^j l = A - b (1 - l):
 //     FE = c0 + sum Re(E prod_i F_i),  dFE/dl_i = sum Re(D prod_{i'!=i} F_i')
-//  long form, probability-generating basis from LONG_SCALED_MIN_K on:
-//     {c0, n stored, n complex, 0},
-//     per stored root {p, q, eb, form}, {D'.re, D'.im, E'.re, E'.im} with the
-//     scaled factor g(l) = p l + i q (form 1: p = tan, q = 1; form 0: p = 1,
-//     q = cot, 0 for the real root), the form the same for each run of 32
-//     roots:  FE = c0 + sum 2^eb Re(E' prod_i g_i),
-//             dFE/dl_i = sum 2^eb Re(D' prod_{i'!=i} g_i')
+//  long form, probability-generating basis (every k > KSHORT):
+//     head {c0, n kept complex roots, c_mid, has_real}, {first form-B root, 0, 0, 0};
+//     per kept complex root (nonzero coefficient, increasing angle) four
+//     granules {p, s7.re, s7.im, 0}, {s16.re, s16.im, sa.re, sa.im},
+//     {sc.re, sc.im, D'.re, D'.im}, {E'.re, E'.im, 0, 0}.
+//     The factor of literal i at the root is s g(l_i), g = p l + i (form A,
+//     roots before the first form-B root; p = tan of the root's half angle in
+//     FP32) or g = l + i p (form B; p = cot); the coefficients are solved for
+//     the nodes that p defines. The first form-B root is a multiple of 32.
+//     With n_last = k - 16 floor((k-1)/16), a = floor((n_last-1)/2),
+//     b = n_last - 1 - a, c = 8 - b + n_last: s7 = s^7, s16 = s^16, sa = s^a,
+//     sc = s^c, D' = D s^b, E' = E s^n_last, E = 2 c'_j, D = E (1 - z'_j)/2,
+//     with the rounding of s^16 over the segments compensated in E', D', sa.
+//     The real root (odd k, has_real = 1) has the factor l_i and the
+//     coefficient c_mid (value and gradient weight).
+//     FE = c0 + sum Re(E s^k prod_i g_i) + c_mid prod_i l_i
 void build_table(const Shape& s, int basis, int form, std::vector<float>& out);
 
 // Algorithmic FP32 lane instructions of one FE+gradient evaluation of a

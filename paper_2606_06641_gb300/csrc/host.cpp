@@ -139,6 +139,7 @@ struct Group {
   int rpl;          // restarts per lane (short kernel tile)
   int cpw;          // constraints per warp (short kernel tile)
   bool fused = false;  // k == KFUSE: derivatives recomputed in the fused pass
+  int lw = 32, lnw = 4;  // long probability-generating kernel tile: lanes per restart, warps per CTA
 };
 
 }  // namespace
@@ -369,10 +370,8 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   auto cons_work = [&](int g) {
     const int k = gk[g];
     const float* head = &coef[4 * static_cast<size_t>(cons_tab_load[g])];
-    if (h->p.basis == AFS_BASIS_PGF && k >= LONG_SCALED_MIN_K) {
-      const int stored = static_cast<int>(head[1]), cplx = static_cast<int>(head[2]);
-      return work_instr(k, cplx, stored - cplx);
-    }
+    if (h->p.basis == AFS_BASIS_PGF && k > KSHORT)
+      return work_instr(k, static_cast<int>(head[1]), head[3] > 0.5f ? 1 : 0);
     const bool scaled = h->p.basis == AFS_BASIS_PGF && k <= KSCALED_MAX;
     return work_instr(k, scaled ? static_cast<int>(head[1]) : k / 2);
   };
@@ -575,6 +574,42 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   CK(cudaStreamCreateWithFlags(&h->fus_s, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&h->ev_fus, cudaEventDisableTiming));
   if (!prepare_kernels()) return fail(AFS_E_CUDA, "kernel attribute setup: %s", cudaGetErrorString(cudaGetLastError()));
+  // long probability-generating groups: the tile whose lane-root slots
+  // (passes of W roots per restart) cover the group's roots with the least
+  // idle lanes, then the CTA size with the most resident warps
+  if (h->p.basis == AFS_BASIS_PGF) {
+    const int xt = h->p.x_storage == AFS_X_BF16 ? XT_BF16 : XT_F32;
+    for (auto& g : h->groups) {
+      if (!g.is_long) continue;
+      double best_cost = 0.0;
+      int best_w = 32;
+      for (int wl : {32, 16, 8}) {
+        double cost = 0.0;
+        for (int c = g.c_begin; c < g.c_begin + g.c_count; ++c) {
+          const int lg = b_orig[c];
+          const int roots = static_cast<int>(coef[4 * static_cast<size_t>(cons_tab_load[lg]) + 1]);
+          cost += static_cast<double>((roots + wl - 1) / wl * wl) * gk[lg];
+        }
+        if (wl == 32 || cost < 0.97 * best_cost) {
+          best_cost = cost;
+          best_w = wl;
+        }
+      }
+      int best_nw = 0, best_warps = -1;
+      for (int si = 0; si < LONG_PGF_NSHAPES; ++si) {
+        if (LONG_PGF_SHAPES[si][0] != best_w) continue;
+        const int nw = LONG_PGF_SHAPES[si][1];
+        const int warps = long_pgf_resident_warps(xt, g.k, best_w, nw);
+        if (warps > best_warps || (warps == best_warps && nw > best_nw)) {
+          best_warps = warps;
+          best_nw = nw;
+        }
+      }
+      if (best_warps <= 0) return fail(AFS_E_LEN, "long group of length %d: no kernel tile fits", g.k);
+      g.lw = best_w;
+      g.lnw = best_nw;
+    }
+  }
   *out = h.release();
   return AFS_OK;
 }
@@ -615,7 +650,8 @@ static int launch_fe_group(afs_handle* h, const Group& g, const void* x, int xt,
   a.vec = vec_enabled() && (x_pitch % 32) == 0 && (b0 % 32) == 0 && (go_pitch % 32) == 0 &&
           (reinterpret_cast<uintptr_t>(x) % 16) == 0 && (reinterpret_cast<uintptr_t>(go) % 16) == 0;
   if (g.is_long) {
-    launch_fe_long(a, xt, h->p.basis, 8, s);
+    if (!launch_fe_long(a, xt, h->p.basis, g.lw, g.lnw, s))
+      return fail(AFS_E_ARG, "no long kernel for tile %dx%d", g.lw, g.lnw);
   } else {
     bool ok;
     const bool esp = h->p.basis == AFS_BASIS_ESP;
@@ -916,7 +952,7 @@ static bool tune_log() {
 
 struct TuneVal {
   int Bc;
-  std::vector<int> rpl, cpw;
+  std::vector<int> rpl, cpw, lw, lnw;
 };
 static std::map<TuneKey, TuneVal>& tune_cache() {
   static std::map<TuneKey, TuneVal> c;
@@ -952,6 +988,8 @@ static int autotune(afs_handle* h, cudaStream_t s) {
     for (size_t i = 0; i < h->groups.size(); ++i) {
       h->groups[i].rpl = it->second.rpl[i];
       h->groups[i].cpw = it->second.cpw[i];
+      h->groups[i].lw = it->second.lw[i];
+      h->groups[i].lnw = it->second.lnw[i];
     }
     return alloc_go(h, h->Bc);
   }
@@ -1031,12 +1069,48 @@ static int autotune(afs_handle* h, cudaStream_t s) {
     g.rpl = best_rpl;
     g.cpw = best_cpw;
   }
+  // 3. tile of each long probability-generating group (lanes per restart and
+  // warps per CTA among the kernel's shapes that fit), single FE launches
+  // over at most 512 restarts timed (the work is linear in the restarts)
+  if (pgf) {
+    const int nbl = std::min(nb, 512);
+    for (Group& g : h->groups) {
+      if (!g.is_long) continue;
+      double bt = 1e30;
+      int bw = g.lw, bn = g.lnw;
+      for (int si = 0; si < LONG_PGF_NSHAPES; ++si) {
+        const int wl = LONG_PGF_SHAPES[si][0], nw = LONG_PGF_SHAPES[si][1];
+        if (long_pgf_resident_warps(h->xt, g.k, wl, nw) <= 0) continue;
+        g.lw = wl;
+        g.lnw = nw;
+        double t = 1e30;
+        for (int rep = 0; rep < 2; ++rep) {
+          CK(cudaEventRecord(e0, s));
+          rc = launch_fe_group(h, g, h->xcur(), h->xt, h->pitch, 0, nbl, h->go.as<float>(), h->Bc, nullptr, 0, s);
+          if (rc) return rc;
+          CK(cudaEventRecord(e1, s));
+          t = std::min(t, time_ms(s, e0, e1));
+        }
+        if (tune_log())
+          std::fprintf(stderr, "[afs autotune] long k<=%d tile %dx%d: %.2f us\n", g.k, wl, nw, 1e3 * t);
+        if (t < bt * 0.97) {
+          bt = t;
+          bw = wl;
+          bn = nw;
+        }
+      }
+      g.lw = bw;
+      g.lnw = bn;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  TuneVal val{h->Bc, {}, {}};
+  TuneVal val{h->Bc, {}, {}, {}, {}};
   for (auto& g : h->groups) {
     val.rpl.push_back(g.rpl);
     val.cpw.push_back(g.cpw);
+    val.lw.push_back(g.lw);
+    val.lnw.push_back(g.lnw);
   }
   tune_cache()[key] = val;
   return AFS_OK;
@@ -1714,6 +1788,52 @@ int afs_set_tiles(afs_handle* h, int32_t chunk, const int32_t* rpl_by_k, const i
     if (g.is_long || g.k >= kcap) continue;
     if (rpl_by_k && rpl_by_k[g.k]) g.rpl = rpl_by_k[g.k];
     if (cpw_by_k && cpw_by_k[g.k]) g.cpw = cpw_by_k[g.k];
+  }
+  h->drop_graphs();
+  return AFS_OK;
+}
+
+int afs_long_tiles(const afs_handle* h, int32_t* lanes, int32_t* warps, int32_t* kmax, int32_t cap, int32_t* n) {
+  if (!h || !n) return fail(AFS_E_ARG, "NULL argument");
+  int i = 0;
+  for (const Group& g : h->groups) {
+    if (!g.is_long) continue;
+    if (i < cap) {
+      if (lanes) lanes[i] = g.lw;
+      if (warps) warps[i] = g.lnw;
+      if (kmax) kmax[i] = g.k;
+    }
+    ++i;
+  }
+  *n = i;
+  return AFS_OK;
+}
+
+int afs_set_long_tiles(afs_handle* h, const int32_t* lanes, const int32_t* warps, int32_t n) {
+  if (!h || (n > 0 && (!lanes || !warps))) return fail(AFS_E_ARG, "NULL argument");
+  if (h->p.basis != AFS_BASIS_PGF) return fail(AFS_E_ARG, "long tiles apply to the probability-generating basis");
+  const int xt = h->p.x_storage == AFS_X_BF16 ? XT_BF16 : XT_F32;
+  int i = 0;
+  for (const Group& g : h->groups) {  // validate everything before changing anything
+    if (!g.is_long) continue;
+    if (i < n && (lanes[i] || warps[i])) {
+      bool known = false;
+      for (int si = 0; si < LONG_PGF_NSHAPES; ++si)
+        known |= LONG_PGF_SHAPES[si][0] == lanes[i] && LONG_PGF_SHAPES[si][1] == warps[i];
+      if (!known) return fail(AFS_E_ARG, "no long kernel tile %dx%d", lanes[i], warps[i]);
+      if (long_pgf_resident_warps(xt, g.k, lanes[i], warps[i]) <= 0)
+        return fail(AFS_E_ARG, "long tile %dx%d does not fit length %d", lanes[i], warps[i], g.k);
+    }
+    ++i;
+  }
+  i = 0;
+  for (Group& g : h->groups) {
+    if (!g.is_long) continue;
+    if (i < n && (lanes[i] || warps[i])) {
+      g.lw = lanes[i];
+      g.lnw = warps[i];
+    }
+    ++i;
   }
   h->drop_graphs();
   return AFS_OK;

@@ -9,62 +9,18 @@
 #include <map>
 #include <mutex>
 
+#include "afsat.h"
 #include "afsat_internal.h"
+#include "bulk_copy.cuh"
 #include "fe_short.cuh"
 
 namespace afs {
 
-// ---------------------------------------------------------------------------
-// Asynchronous bulk copies (global -> shared) completed on an mbarrier.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Wait for phase `parity` of the barrier for at most ~`limit` SM cycles.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, long long limit) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > limit) return false;
-  }
-  return true;
-}
-
-constexpr int DEV_ERR_TIMEOUT = 1;
-constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
 // ---------------------------------------------------------------------------
-// Long constraints (k > 32): one CTA per (constraint, 8 restarts).
-//
-// Same expansion as the short kernel. The probability-generating tables give
-// each root's factor in a scaled form p l + i q (a complex multiply is three
-// or four FP32 instructions; zero-coefficient roots are not stored); the
-// paper's basis keeps the direct form a_j + b_j l_i.
+// Long constraints (k > 32) in the paper's basis (the probability-generating
+// basis has its own kernel, long_pgf.cu): one CTA per (constraint, RT
+// restarts). Factors 1 + w^j l_i, written A - b (1 - l_i).
 // Warp w owns restart w of the tile and its lanes own 32 roots at a time.
 // The forward pass keeps one prefix checkpoint per LONG_SEG-literal segment
 // in shared memory; the backward pass rebuilds a segment's prefixes (and its
@@ -72,13 +28,12 @@ constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 // at the gradient weight D_j) and stores each lane's (root's) contributions
 // as a row of a per-warp shared-memory tile, whose columns the lanes then
 // sum, so lane t ends with literal t of the segment summed over the 32 roots.
-// Scaled factors (up to 234 in modulus) and the paper's basis (up to 2) make
-// running products leave the FP32 range, so they are renormalised at segment
-// boundaries into a mantissa and an integer power of two (exponent field of
-// the IEEE encoding) and the contributions are rescaled before the root sum.
-// The literal list is staged with cp.async.bulk; the coefficient table is
-// read through L1. Exponents are 16-bit (at most 8 bits of growth per
-// literal, k <= 1024).
+// The factors reach 2 in modulus, so running products leave the FP32 range:
+// they are renormalised at segment boundaries into a mantissa and an integer
+// power of two (exponent field of the IEEE encoding) and the contributions
+// are rescaled before the root sum. The literal list is staged with
+// cp.async.bulk; the coefficient table is read through L1. Exponents are
+// 16-bit (at most 1 bit of growth per literal).
 // ---------------------------------------------------------------------------
 constexpr int LONG_RT = 8;  // restarts (warps) per CTA; 4 for the longest groups (shared memory)
 
@@ -94,7 +49,6 @@ __device__ __forceinline__ void renorm(float& r, float& i, int& e) {
   e += sh;
 }
 
-constexpr int LONG_SEG = 16;   // literals per prefix checkpoint (prefixes and factors held in registers)
 constexpr int LONG_TP = 17;    // row pitch of the transpose tile (conflict-free columns)
 
 // el[t] = u_t = 1 - l_t; the factor is A - b u, passed as (ar, ai) = A and
@@ -148,95 +102,6 @@ __device__ __forceinline__ void long_segment(const float* el, int n, float ar, f
   }
 }
 
-// The probability-generating tables' scaled factor g = p l + i q (form A: q
-// = 1, three FP32 instructions per complex multiply; form B: p = 1, four).
-// Same walk as long_segment; the checkpoint Q arrives pre-scaled by its share
-// of the power of two, and sc (the rest) scales each contribution.
-template <bool FULL, bool FA, bool CF>
-__device__ __forceinline__ void long_segment_scaled(const float* el, int n, float p, float q, float Qr, float Qi,
-                                                    float& Sr, float& Si, float sc, float* trow) {
-  float pr[LONG_SEG], pi[LONG_SEG], wv[CF ? LONG_SEG : 1];
-  pr[0] = Qr;
-  pi[0] = Qi;
-  // the segment's literal values as four 16-byte broadcast reads (a segment
-  // starts 16-byte aligned; a partial one reads past n inside the CTA's
-  // shared memory and ignores those values)
-  const float4* e4 = reinterpret_cast<const float4*>(el);
-  float ev[LONG_SEG];
-#pragma unroll
-  for (int u = 0; u < LONG_SEG / 4; ++u) {
-    const float4 v = e4[u];
-    ev[4 * u] = v.x;
-    ev[4 * u + 1] = v.y;
-    ev[4 * u + 2] = v.z;
-    ev[4 * u + 3] = v.w;
-  }
-#pragma unroll
-  for (int t = 0; t < LONG_SEG; ++t) {
-    if (FULL || t < n) {
-      const float w = FA ? ev[t] * p : ev[t];
-      if constexpr (CF) wv[t] = w;
-      if (t + 1 < LONG_SEG) {
-        if constexpr (FA) {
-          pr[t + 1] = fmaf(pr[t], w, -pi[t]);
-          pi[t + 1] = fmaf(pi[t], w, pr[t]);
-        } else {
-          pr[t + 1] = fmaf(pr[t], w, -pi[t] * q);
-          pi[t + 1] = fmaf(pi[t], w, pr[t] * q);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int t = LONG_SEG - 1; t >= 0; --t) {
-    float v = 0.0f;
-    if (FULL || t < n) {
-      v = fmaf(pr[t], Sr, -pi[t] * Si) * sc;
-      const float w = CF ? wv[t] : (FA ? ev[t] * p : ev[t]);
-      float nr, ni;
-      if constexpr (FA) {
-        nr = fmaf(Sr, w, -Si);
-        ni = fmaf(Si, w, Sr);
-      } else {
-        nr = fmaf(Sr, w, -Si * q);
-        ni = fmaf(Si, w, Sr * q);
-      }
-      Sr = nr;
-      Si = ni;
-    }
-    trow[t] = v;
-  }
-}
-
-// Forward walk of one segment in the scaled form (prefix only).
-template <bool FA>
-__device__ __forceinline__ void long_forward_step(float l, float p, float q, float& Pr, float& Pi) {
-  const float w = FA ? l * p : l;
-  float nr, ni;
-  if constexpr (FA) {
-    nr = fmaf(Pr, w, -Pi);
-    ni = fmaf(Pi, w, Pr);
-  } else {
-    nr = fmaf(Pr, w, -Pi * q);
-    ni = fmaf(Pi, w, Pr * q);
-  }
-  Pr = nr;
-  Pi = ni;
-}
-template <bool FA>
-__device__ __forceinline__ void long_forward_scaled(const float* el, int n, float p, float q, float& Pr, float& Pi) {
-  // four literals per 16-byte broadcast read (el is 16-byte aligned)
-  int t = 0;
-  for (; t + 4 <= n; t += 4) {
-    const float4 v = *reinterpret_cast<const float4*>(el + t);
-    long_forward_step<FA>(v.x, p, q, Pr, Pi);
-    long_forward_step<FA>(v.y, p, q, Pr, Pi);
-    long_forward_step<FA>(v.z, p, q, Pr, Pi);
-    long_forward_step<FA>(v.w, p, q, Pr, Pi);
-  }
-  for (; t < n; ++t) long_forward_step<FA>(el[t], p, q, Pr, Pi);
-}
-
 // 2^e as a float for -126 <= e <= 127.
 __device__ __forceinline__ float exp2_int(int e) { return __int_as_float((e + 127) << 23); }
 
@@ -270,15 +135,8 @@ struct LongLayout {
   }
 };
 
-// MODE: LONG_PGF (direct factors), LONG_ESP (paper basis, renormalised) or
-// LONG_PGF_SCALED (scaled factors, renormalised; lengths from
-// LONG_SCALED_MIN_K on, which is a length-class boundary, so a group never
-// mixes the two probability-generating layouts).
-enum { LONG_PGF = 0, LONG_ESP = 1, LONG_PGF_SCALED = 2 };
-
-template <typename XT, int MODE, int RT>
+template <typename XT, int RT>
 __global__ void __launch_bounds__(RT * 32) fe_grad_long_kernel(FeGroupArgs a, int kmax) {
-  constexpr bool ESP = MODE == LONG_ESP, SCALED = MODE == LONG_PGF_SCALED;
   // the groups that run 4 restarts per CTA (the longest) keep a segment's
   // factors in registers: fewer instructions, more registers per thread
   constexpr bool CF = RT == 4;
@@ -294,8 +152,7 @@ __global__ void __launch_bounds__(RT * 32) fe_grad_long_kernel(FeGroupArgs a, in
   const int k = __ldg(a.cons_k + cb);
   const int litoff = __ldg(a.cons_lit + cb);
   const int tab_off = __ldg(a.cons_tab + cb);
-  // a probability-generating table stores its root count (zero roots dropped)
-  const int nroots = SCALED ? static_cast<int>(__ldg(a.coef + tab_off).y) : k / 2 + (k & 1) + (ESP ? 1 : 0);
+  const int nroots = k / 2 + (k & 1) + 1;
 
   const float4* tab = a.coef + tab_off;  // read through L1
   int2* lits = reinterpret_cast<int2*>(smem);
@@ -325,8 +182,7 @@ __global__ void __launch_bounds__(RT * 32) fe_grad_long_kernel(FeGroupArgs a, in
     return;
   }
 
-  // stage u[r][i] = 1 - s_i x[v_i][b] (direct factors) or l[r][i] = s_i x[v_i][b]
-  // (scaled factors): RT consecutive threads read one row segment
+  // stage u[r][i] = 1 - s_i x[v_i][b]: RT consecutive threads read one row segment
   const XT* x = static_cast<const XT*>(a.x);
   const int bt = tile * RT;
   for (int idx = tid; idx < k * RT; idx += blockDim.x) {
@@ -336,7 +192,7 @@ __global__ void __launch_bounds__(RT * 32) fe_grad_long_kernel(FeGroupArgs a, in
     const float xv =
         bl < a.nb ? load_x<XT>(x + static_cast<long long>(li.x >> 1) * a.x_pitch + a.b0 + bl) : 0.0f;
     const float lv = (li.x & 1) ? -xv : xv;
-    ell[r * L.kpad + i] = SCALED ? lv : 1.0f - lv;
+    ell[r * L.kpad + i] = 1.0f - lv;
   }
   __syncthreads();
 
@@ -348,131 +204,65 @@ __global__ void __launch_bounds__(RT * 32) fe_grad_long_kernel(FeGroupArgs a, in
   const int nseg = (k + LONG_SEG - 1) / LONG_SEG;
   float fe_part = 0.0f;
 
-  if constexpr (SCALED) {
-    for (int rg = 0; rg < nroots; rg += 32) {
-      const int j = rg + lane;
-      float p = 0.f, q = 0.f, dr = 0.f, di = 0.f, er = 0.f, ei = 0.f, fa = 0.f;
-      int eb = 0;
-      if (j < nroots) {
-        const float4 t0 = __ldg(tab + 1 + 2 * j), t1 = __ldg(tab + 2 + 2 * j);
-        p = t0.x; q = t0.y; eb = static_cast<int>(t0.z); fa = t0.w;
-        dr = t1.x; di = t1.y; er = t1.z; ei = t1.w;
-      }
-      // the table gives every root of a 32-root pass the same form
-      const bool form_a = __shfl_sync(0xffffffffu, fa, 0) > 0.5f;
-      // forward: prefix checkpoints (mantissa, power of two) at segment starts
-      float Pr = 1.0f, Pi = 0.0f;
-      int Pe = 0;
-      for (int seg = 0; seg < nseg; ++seg) {
-        myck[seg * 32 + lane] = make_float2(Pr, Pi);
-        myce[seg * 32 + lane] = static_cast<short>(Pe);
-        const int i0 = seg * LONG_SEG;
-        const int n = min(LONG_SEG, k - i0);
-        if (form_a)
-          long_forward_scaled<true>(el + i0, n, p, q, Pr, Pi);
-        else
-          long_forward_scaled<false>(el + i0, n, p, q, Pr, Pi);
-        renorm(Pr, Pi, Pe);
-      }
-      // this pass's value, summed over its roots (every lane gets the sum)
-      float fe_pass = ldexpf(fmaf(er, Pr, -ei * Pi), Pe + eb);
-#pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) fe_pass += __shfl_xor_sync(0xffffffffu, fe_pass, o);
-      fe_part += fe_pass;
-
-      // backward: suffix from D', segment by segment; a contribution's power of
-      // two (checkpoint + suffix + table) is split between the checkpoint
-      // (down to 2^-126) and a per-contribution factor
-      float Sr = dr, Si = di;
-      int Se = 0;
-      renorm(Sr, Si, Se);
-      for (int seg = nseg - 1; seg >= 0; --seg) {
-        const int i0 = seg * LONG_SEG;
-        const int n = min(LONG_SEG, k - i0);
-        const float2 Q = myck[seg * 32 + lane];
-        const int escale = myce[seg * 32 + lane] + Se + eb;
-        const int e1 = min(max(escale, -126), 127), e2 = escale - e1;
-        const float s1 = exp2_int(e1), s2 = e2 >= -126 ? exp2_int(min(e2, 127)) : 0.0f;
-        float* trow = tpw + lane * LONG_TP;
-        if (form_a) {
-          if (n == LONG_SEG)
-            long_segment_scaled<true, true, CF>(el + i0, n, p, q, Q.x * s1, Q.y * s1, Sr, Si, s2, trow);
-          else
-            long_segment_scaled<false, true, CF>(el + i0, n, p, q, Q.x * s1, Q.y * s1, Sr, Si, s2, trow);
-        } else {
-          if (n == LONG_SEG)
-            long_segment_scaled<true, false, CF>(el + i0, n, p, q, Q.x * s1, Q.y * s1, Sr, Si, s2, trow);
-          else
-            long_segment_scaled<false, false, CF>(el + i0, n, p, q, Q.x * s1, Q.y * s1, Sr, Si, s2, trow);
-        }
-        renorm(Sr, Si, Se);
-        __syncwarp();
-        const float sum = long_column_sum(tpw, lane);
-        if (lane < n) gr[i0 + lane] += sum;
-        __syncwarp();  // the tile is read before the next segment's rows
-      }
+  for (int rg = 0; rg < nroots; rg += 32) {
+    const int j = rg + lane;
+    float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f, dr = 0.f, di = 0.f, er = 0.f, ei = 0.f;
+    if (j < nroots) {  // factor A - b u: keep (A, -b)
+      const float4 t0 = __ldg(tab + 1 + 2 * j), t1 = __ldg(tab + 2 + 2 * j);
+      ar = t0.x; ai = t0.y; br = -t0.z; bi = -t0.w;
+      dr = t1.x; di = t1.y; er = t1.z; ei = t1.w;
     }
-  } else {
-    for (int rg = 0; rg < nroots; rg += 32) {
-      const int j = rg + lane;
-      float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f, dr = 0.f, di = 0.f, er = 0.f, ei = 0.f;
-      if (j < nroots) {  // factor A - b u: keep (A, -b)
-        const float4 t0 = __ldg(tab + 1 + 2 * j), t1 = __ldg(tab + 2 + 2 * j);
-        ar = t0.x; ai = t0.y; br = -t0.z; bi = -t0.w;
-        dr = t1.x; di = t1.y; er = t1.z; ei = t1.w;
+    // forward: prefix checkpoints at segment starts
+    float Pr = 1.0f, Pi = 0.0f;
+    int Pe = 0;
+    for (int seg = 0; seg < nseg; ++seg) {
+      myck[seg * 32 + lane] = make_float2(Pr, Pi);
+      myce[seg * 32 + lane] = static_cast<short>(Pe);
+      const int i0 = seg * LONG_SEG;
+      const int n = min(LONG_SEG, k - i0);
+      // four literals per 16-byte broadcast read (segments start aligned)
+      auto fstep = [&](float ll) {
+        const float Fr = fmaf(br, ll, ar), Fi = fmaf(bi, ll, ai);
+        const float nr = fmaf(Pr, Fr, -Pi * Fi);
+        const float ni = fmaf(Pr, Fi, Pi * Fr);
+        Pr = nr;
+        Pi = ni;
+      };
+      int t = 0;
+      for (; t + 4 <= n; t += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(el + i0 + t);
+        fstep(v.x);
+        fstep(v.y);
+        fstep(v.z);
+        fstep(v.w);
       }
-      // forward: prefix checkpoints at segment starts
-      float Pr = 1.0f, Pi = 0.0f;
-      int Pe = 0;
-      for (int seg = 0; seg < nseg; ++seg) {
-        myck[seg * 32 + lane] = make_float2(Pr, Pi);
-        if (ESP) myce[seg * 32 + lane] = static_cast<short>(Pe);
-        const int i0 = seg * LONG_SEG;
-        const int n = min(LONG_SEG, k - i0);
-        // four literals per 16-byte broadcast read (segments start aligned)
-        auto fstep = [&](float ll) {
-          const float Fr = fmaf(br, ll, ar), Fi = fmaf(bi, ll, ai);
-          const float nr = fmaf(Pr, Fr, -Pi * Fi);
-          const float ni = fmaf(Pr, Fi, Pi * Fr);
-          Pr = nr;
-          Pi = ni;
-        };
-        int t = 0;
-        for (; t + 4 <= n; t += 4) {
-          const float4 v = *reinterpret_cast<const float4*>(el + i0 + t);
-          fstep(v.x);
-          fstep(v.y);
-          fstep(v.z);
-          fstep(v.w);
-        }
-        for (; t < n; ++t) fstep(el[i0 + t]);
-        if (ESP) renorm(Pr, Pi, Pe);
-      }
-      float val = fmaf(er, Pr, -ei * Pi);
-      if (ESP) val = ldexpf(val, Pe);
+      for (; t < n; ++t) fstep(el[i0 + t]);
+      renorm(Pr, Pi, Pe);
+    }
+    const float val0 = fmaf(er, Pr, -ei * Pi);
+    float val = ldexpf(val0, Pe);
 #pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
-      fe_part += val;
+    for (int o = 16; o >= 1; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+    fe_part += val;
 
-      // backward: suffix from the gradient weight, segment by segment
-      float Sr = dr, Si = di;
-      int Se = 0;
-      for (int seg = nseg - 1; seg >= 0; --seg) {
-        const int i0 = seg * LONG_SEG;
-        const int n = min(LONG_SEG, k - i0);
-        const float2 Q = myck[seg * 32 + lane];
-        const int escale = ESP ? myce[seg * 32 + lane] + Se : 0;
-        float* trow = tpw + lane * LONG_TP;
-        if (n == LONG_SEG)
-          long_segment<true, ESP, CF>(el + i0, n, ar, ai, br, bi, Q.x, Q.y, Sr, Si, escale, trow);
-        else
-          long_segment<false, ESP, CF>(el + i0, n, ar, ai, br, bi, Q.x, Q.y, Sr, Si, escale, trow);
-        if (ESP) renorm(Sr, Si, Se);
-        __syncwarp();
-        const float s = long_column_sum(tpw, lane);
-        if (lane < n) gr[i0 + lane] += s;
-        __syncwarp();  // the tile is read before the next segment's rows
-      }
+    // backward: suffix from the gradient weight, segment by segment
+    float Sr = dr, Si = di;
+    int Se = 0;
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+      const int i0 = seg * LONG_SEG;
+      const int n = min(LONG_SEG, k - i0);
+      const float2 Q = myck[seg * 32 + lane];
+      const int escale = myce[seg * 32 + lane] + Se;
+      float* trow = tpw + lane * LONG_TP;
+      if (n == LONG_SEG)
+        long_segment<true, true, CF>(el + i0, n, ar, ai, br, bi, Q.x, Q.y, Sr, Si, escale, trow);
+      else
+        long_segment<false, true, CF>(el + i0, n, ar, ai, br, bi, Q.x, Q.y, Sr, Si, escale, trow);
+      renorm(Sr, Si, Se);
+      __syncwarp();
+      const float s = long_column_sum(tpw, lane);
+      if (lane < n) gr[i0 + lane] += s;
+      __syncwarp();  // the tile is read before the next segment's rows
     }
   }
   // value: fe_part holds the sum over all roots in every lane
@@ -489,34 +279,22 @@ __global__ void __launch_bounds__(RT * 32) fe_grad_long_kernel(FeGroupArgs a, in
   }
 }
 
-// Long groups whose shared memory at 8 restarts per CTA exceeds LONG_RT4_BYTES
-// run 4 restarts per CTA, so that more CTAs fit on an SM (and the longest
-// constraints fit at all).
+// Paper-basis long groups whose shared memory at 8 restarts per CTA exceeds
+// LONG_RT4_BYTES run 4 restarts per CTA, so that more CTAs fit on an SM (and
+// the longest constraints fit at all).
 constexpr size_t LONG_RT4_BYTES = 64 * 1024;
 
-size_t long_smem_bytes(int kmax, bool esp) {
-  const size_t b8 = LongLayout(kmax, 8).bytes(esp);
-  return b8 > LONG_RT4_BYTES ? LongLayout(kmax, 4).bytes(esp) : b8;
-}
-
-
-template <typename XT, int MODE>
-static void launch_long_t(const FeGroupArgs& a, cudaStream_t s) {
-  const bool rt4 = LongLayout(a.k, 8).bytes(MODE == LONG_ESP) > LONG_RT4_BYTES;
+template <typename XT>
+static void launch_long_esp_t(const FeGroupArgs& a, cudaStream_t s) {
+  const bool rt4 = LongLayout(a.k, 8).bytes(true) > LONG_RT4_BYTES;
   const int rt = rt4 ? 4 : 8;
-  const size_t smem = LongLayout(a.k, rt).bytes(MODE == LONG_ESP);
+  const size_t smem = LongLayout(a.k, rt).bytes(true);
   const int tiles = (a.nb + rt - 1) / rt;
   const long long blocks = static_cast<long long>(tiles) * a.c_count;
-  if constexpr (MODE == LONG_PGF) {
-    // direct probability-generating groups are at most LONG_SCALED_MIN_K - 1
-    // long, which always fits 8 restarts per CTA
-    launch_pdl(fe_grad_long_kernel<XT, MODE, 8>, dim3(static_cast<unsigned>(blocks)), dim3(256), smem, s, a, a.k);
-  } else {
-    if (rt4)
-      launch_pdl(fe_grad_long_kernel<XT, MODE, 4>, dim3(static_cast<unsigned>(blocks)), dim3(128), smem, s, a, a.k);
-    else
-      launch_pdl(fe_grad_long_kernel<XT, MODE, 8>, dim3(static_cast<unsigned>(blocks)), dim3(256), smem, s, a, a.k);
-  }
+  if (rt4)
+    launch_pdl(fe_grad_long_kernel<XT, 4>, dim3(static_cast<unsigned>(blocks)), dim3(128), smem, s, a, a.k);
+  else
+    launch_pdl(fe_grad_long_kernel<XT, 8>, dim3(static_cast<unsigned>(blocks)), dim3(256), smem, s, a, a.k);
 }
 
 template <typename K>
@@ -535,18 +313,13 @@ bool pdl_enabled() {
   return on;
 }
 
-// a.k carries the group's longest constraint for the long kernel
-void launch_fe_long(const FeGroupArgs& a, int xt, int basis, int /*rt*/, cudaStream_t s) {
-  const int mode = basis != 0 ? LONG_ESP : (a.k >= LONG_SCALED_MIN_K ? LONG_PGF_SCALED : LONG_PGF);
-  if (xt == XT_F32) {
-    if (mode == LONG_PGF) launch_long_t<float, LONG_PGF>(a, s);
-    else if (mode == LONG_ESP) launch_long_t<float, LONG_ESP>(a, s);
-    else launch_long_t<float, LONG_PGF_SCALED>(a, s);
-  } else {
-    if (mode == LONG_PGF) launch_long_t<__nv_bfloat16, LONG_PGF>(a, s);
-    else if (mode == LONG_ESP) launch_long_t<__nv_bfloat16, LONG_ESP>(a, s);
-    else launch_long_t<__nv_bfloat16, LONG_PGF_SCALED>(a, s);
-  }
+// a.k carries the group's longest constraint for the long kernels; (wl, nw)
+// is the probability-generating kernel's tile (lanes per restart, warps)
+bool launch_fe_long(const FeGroupArgs& a, int xt, int basis, int wl, int nw, cudaStream_t s) {
+  if (basis == 0) return launch_fe_long_pgf(a, xt, wl, nw, s);
+  if (xt == XT_F32) launch_long_esp_t<float>(a, s);
+  else launch_long_esp_t<__nv_bfloat16>(a, s);
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -1481,18 +1254,12 @@ bool prepare_kernels() {
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
-  if (LongLayout(1024, 4).bytes(true) + 64 > static_cast<size_t>(optin)) return false;
-  bool ok = true;
-  ok &= raise_smem_cap(fe_grad_long_kernel<float, LONG_PGF, 8>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<float, LONG_ESP, 8>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<float, LONG_ESP, 4>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<float, LONG_PGF_SCALED, 8>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<float, LONG_PGF_SCALED, 4>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, LONG_PGF, 8>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, LONG_ESP, 8>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, LONG_ESP, 4>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, LONG_PGF_SCALED, 8>, optin);
-  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, LONG_PGF_SCALED, 4>, optin);
+  if (LongLayout(AFS_MAX_LEN, 4).bytes(true) + 64 > static_cast<size_t>(optin)) return false;
+  bool ok = prepare_long_pgf(optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<float, 8>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<float, 4>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, 8>, optin);
+  ok &= raise_smem_cap(fe_grad_long_kernel<__nv_bfloat16, 4>, optin);
   return ok;
 }
 

@@ -75,38 +75,55 @@ def test_every_short_length(k):
         _check_eval(inst, synth.uniform_x0(inst.n, 45, k))
 
 
-@pytest.mark.parametrize("k", [33, 40, 63, 64, 65, 100, 128, 255, 256, 512, 1024])
+@pytest.mark.parametrize("k", [33, 40, 47, 48, 63, 64, 65, 100, 101, 128, 129, 255, 256, 257, 480, 511, 512])
 def test_long_lengths(k):
-    """Up to k = 512 (the longest constraints of the workloads) the 1e-5 bar
-    holds. The worst-case FP32 error of a value is (rounding of a k-factor
-    product, ~k) x (number of roots summed, ~k/2), so beyond k = 512 the bar
-    scales as (k / 512)^2."""
-    tol = TOL * max(1.0, (k / 512) ** 2)
+    """Every length class of the long kernel up to AFS_MAX_LEN = 512 (the
+    longest constraints of the workloads), tails of 1..16 literals in the last
+    segment, at uniform, near-vertex and vertex points: within 1e-5."""
     for t, op, r in ((synth.CARD, synth.GE, k // 2), (synth.EK, 0, k // 3), (synth.AMO, 0, 0),
                      (synth.CARD, synth.LT, 3 * k // 4)):
         inst = synth.single_type(t, k, 3, k + 7, index=k, op=op, param=r)
-        _check_eval(inst, synth.uniform_x0(inst.n, 19, k), tol=tol)
-        _check_eval(inst, synth.near_vertex_x0(inst.n, 11, k, spread=0.02), tol=tol)
+        _check_eval(inst, synth.uniform_x0(inst.n, 19, k))
+        _check_eval(inst, synth.near_vertex_x0(inst.n, 11, k, spread=0.02))
+        _check_eval(inst, synth.vertex_x0(inst.n, 6, k))
 
 
-@pytest.mark.parametrize("k", [129, 130, 391, 392, 393, 785])
-def test_long_scaled_form_boundaries(k):
-    """Lengths where the long probability-generating tables switch to the
-    scaled factor form (129) and where a 32-root pass switches form (k near
-    392: the last pass of roots close to pi/2; odd k: the real root), for
-    parity (odd k keeps the real root only, even k every complex root), NAE,
-    EO and a threshold, at uniform and near-vertex points."""
-    tol = TOL * max(1.0, (k / 512) ** 2)
+@pytest.mark.parametrize("k", [100, 101, 102, 127, 200, 393, 480])
+def test_long_form_boundaries(k):
+    """Lengths where the long tables switch the passes of roots near pi/2 to
+    the second factor form (from about k = 100 on), for parity (odd k keeps
+    only the real root, even k every complex root), NAE, EO and a threshold,
+    at uniform and near-vertex points."""
     for t, op, r, par in ((synth.XOR, 0, 0, 1), (synth.XOR, 0, 0, 0), (synth.NAE, 0, 0, 1), (synth.EO, 0, 0, 1),
                           (synth.CARD, synth.GE, k // 2, 1)):
         inst = synth.single_type(t, k, 2, k + 5, index=k + t, op=op, param=r, parity=par)
-        _check_eval(inst, synth.uniform_x0(inst.n, 13, k), tol=tol)
-        _check_eval(inst, synth.near_vertex_x0(inst.n, 7, k, spread=0.02), tol=tol)
+        _check_eval(inst, synth.uniform_x0(inst.n, 13, k))
+        _check_eval(inst, synth.near_vertex_x0(inst.n, 7, k, spread=0.02))
 
 
-def test_bf16_storage_long_scaled():
-    """BF16 state with long constraints in both long layouts (k = 100 direct,
-    k = 300 scaled): arithmetic at the dequantised point within 1e-5."""
+def test_every_long_tile():
+    """Every tile of the long kernel (8, 16 or 32 lanes per restart; 2, 4 or 8
+    warps per CTA) on a mix of long lengths and types, ragged restart count."""
+    inst = synth.long_card_n10000(3, n=600, n_clauses=200, n_long=10, kmin=33, kmax=300)
+    x = synth.uniform_x0(inst.n, 29, 5)
+    h = bd.load_instance(inst)
+    groups = bd.long_tiles(h)
+    assert groups and all(t[2] > 32 for t in groups)
+    fe_ref, go_ref, g_ref = O.evaluate(inst, x.astype(np.float64))
+    for tile in ((32, 4), (32, 8), (16, 2), (16, 4), (8, 2)):
+        bd.set_long_tiles(h, [tile] * len(groups))
+        assert all(t[:2] == tile for t in bd.long_tiles(h))
+        fe, g = bd.eval_fe_grad(h, _dev(x))
+        fe_err = np.abs(fe.cpu().numpy() - fe_ref) / np.maximum(1.0, np.abs(fe_ref))
+        g_err = np.abs(g.cpu().numpy() - g_ref) / _grad_scale(inst, go_ref)
+        assert fe_err.max() <= TOL and g_err.max() <= TOL, (tile, fe_err.max(), g_err.max())
+    with pytest.raises(bd.AfsError):
+        bd.set_long_tiles(h, [(8, 4)] * len(groups))
+
+
+def test_bf16_storage_long():
+    """BF16 state with long constraints (k = 100 and 300): arithmetic at the
+    dequantised point within 1e-5."""
     for k in (100, 300):
         inst = synth.single_type(synth.CARD, k, 2, k + 9, index=k, op=synth.GE, param=k // 2)
         x = synth.uniform_x0(inst.n, 24, k)

@@ -140,9 +140,9 @@ def test_longest_constraint_all_counts():
     rng = np.random.default_rng(7)
     B = 1100
     insts, xs = [], []
-    for ctype, args in ((synth.CARD, {"op": synth.GE, "param": 600}), (synth.EK, {"param": 1000}),
+    for ctype, args in ((synth.CARD, {"op": synth.GE, "param": 300}), (synth.EK, {"param": 500}),
                         (synth.XOR, {"parity": 1})):
-        inst, x = _single_constraint_case(ctype, 1024, B, rng, **args)
+        inst, x = _single_constraint_case(ctype, 512, B, rng, **args)
         insts.append(inst)
         xs.append(x)
     _run_check(insts, xs, B)
