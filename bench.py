@@ -1,33 +1,38 @@
 """Benchmark of the Fourier-expansion CLS hot path on GB300.
 
-Default workload (``--workload hybrid``): the hybrid mixed-type instance
-(n=2000 variables; 8000 random 3-clauses, 400 XOR of length 5 with a fair
-parity, 200 CARD of length 20 with threshold >= 10, 100 NAE of length 4),
-B=1024 restarts per GPU, FP32 state. A step is one pass of the whole hot path
-for all restarts: FE and analytic gradient of every constraint with the fused
-exact check of the state read, the solved fold, the CSR gather and projected
-step. Metric: literal-evals/s = literal occurrences x restarts x steps / s.
+Headline workload (``--workload long``, the default): the long-constraint
+instance (n=10000 variables; 30000 random 3-clauses + 500 CARD >= r / EK = r
+constraints of length uniform in [64, 512], r uniform in [k/4, 3k/4]),
+B=4096 restarts per GPU, FP32 state: the largest single-GPU configuration. A
+step is one pass of the whole hot path for all restarts: FE and analytic
+gradient of every constraint, the per-step exact check of the state read, the
+CSR gather and projected step. Metric: literal-evals/s = literal occurrences x
+restarts x steps / s.
+
+The same JSON line carries the other two throughput workloads under
+``workloads``: ``hybrid`` (n=2000; 8000 3-clauses, 400 XOR(5), 200 CARD(20)
+>= 10, 100 NAE(4); B=1024) and ``batch`` (256 instances, n log-uniform in
+[100, 20000], B=64 each, one handle), each with its own timing, roofline,
+end-to-end figure and CPU baseline, plus ``time_to_solve`` (random 3-SAT
+n=50: plain CLS against the batched form at an equal solve rate).
 
 Timing: W untimed warm-up steps; K timed steps as K/S replays of an S-step
 CUDA graph (S = --steps-per-graph), each replay bracketed by CUDA events on
-the launching stream, with L2 flushed (a 512 MB write) between replays. Under
-torchrun every rank runs its own restarts (weak scaling, no collective on the
-data path); the timed region is bracketed by a barrier and device syncs and
-the max over ranks is reported.
+the launching stream, with L2 flushed (a 512 MB write) between replays; a
+``sustained`` figure repeats replays until at least --sustained-s seconds of
+device time. Under torchrun every rank runs its own restarts (weak scaling,
+no collective on the data path); the timed region is bracketed by a barrier
+and device syncs and the max over ranks is reported.
 
-The default line also carries ``time_to_solve``: random 3-SAT instances of
-n=50, m=213 solved by plain CLS (one instance at a time, un-captured launches,
-solved flag read every step) and by the batched form (all instances in one
-handle, graph replays), from identical starting points, so both follow the
-same trajectories and reach the same solve rate.
-
-Other workloads: ``long`` (n=10000, 30000 3-clauses + 500 CARD/EK of length
-64..512, B=4096; adds a precision report of the FP32 PGF basis, the paper's
-ESP basis and BF16 state against the FP64 oracle) and ``batch`` (256
-instances of n log-uniform in [100, 20000], B=64 each, one handle).
+Roofline: the dominant kernel of each workload (the kernel with the largest
+share of FE+gradient time) is timed per launch with CUDA events on the
+launching stream (afs_group_times) and rated at its algorithmic FP32
+instructions (16 per (literal, root) plus 2 per root, R(k) = floor((k+1)/2);
+3 per occurrence for the fused 3-literal pass) against SMs x 128 FP32 lanes x
+the maximum SM clock.
 
 --impl reference times the CPU oracle (FP64 numpy, Poisson-binomial
-recurrence) on a bounded sample of the same workload.
+recurrence) on a bounded sample of the same workload, on all host cores.
 """
 from __future__ import annotations
 
@@ -55,7 +60,6 @@ WORKLOADS = {
 METRIC = "FE+grad literal-evals/s"
 LINE_SEARCH = (1.0, 0.5, 1e-4, 6)   # first step, backtracking factor, sufficient-decrease constant, trials
 UNIT = "literal-evals/s"
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fe_grad_traffic.json")
 KERNEL_SOURCES = ["paper_2606_06641_gb300/csrc/fe_short.cuh", "paper_2606_06641_gb300/csrc/kernels.cu",
                   "paper_2606_06641_gb300/csrc/coef.cpp", "paper_2606_06641_gb300/csrc/coef.h",
                   "paper_2606_06641_gb300/csrc/afsat_internal.h"]
@@ -159,15 +163,20 @@ def make_workload(name: str):
     raise ValueError(name)
 
 
-def cpu_oracle_sample(insts, B_sample: int, budget_s: float, seed: int = 0):
-    """The oracle's FE + gradient + projected step + exact check on B_sample
-    restarts of the first instance, repeated for about budget_s seconds."""
+def _single_thread():
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+
+
+def _oracle_worker(task):
+    """One host core: the oracle's full step (FE, gradient, projected step,
+    exact check) on B_w restarts of one instance, repeated until budget_s."""
+    inst, B_w, budget_s, seed = task
     import numpy as np
 
     from oracle import fe_oracle as O
     from paper_2606_06641_gb300 import synth
-    inst = insts[0]
-    x = synth.uniform_x0(inst.n, B_sample, seed).astype(np.float64)
+    x = synth.uniform_x0(inst.n, B_w, seed).astype(np.float64)
     reps = 0
     t0 = time.perf_counter()
     while True:
@@ -177,32 +186,82 @@ def cpu_oracle_sample(insts, B_sample: int, budget_s: float, seed: int = 0):
         el = time.perf_counter() - t0
         if el >= budget_s:
             break
-    return inst.n_lits * B_sample * reps / el, reps, el
+    return inst.n_lits * B_w * reps, el, reps
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_oracle_sample(insts, B_sample: int, budget_s: float, cores: int = 0, seed: int = 0):
+    """The oracle's step on every host core at once (a spawned process per
+    core, one numpy thread each): core w runs B_sample restarts of instance
+    w mod len(insts) for about budget_s seconds. Returns the summed rate in
+    literal-evals/s, the cores used and a description of the sample."""
+    import multiprocessing as mp
+    cores = cores or host_cores()
+    tasks = [(insts[w % len(insts)], B_sample, budget_s, seed + w) for w in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_single_thread) as pool:
+        res = pool.map(_oracle_worker, tasks)
+    rate = sum(evals / el for evals, el, _ in res)
+    steps = sum(r for _, _, r in res)
+    n_inst = min(cores, len(insts))
+    sample = (f"FP64 oracle step (FE, gradient, projected step, exact check) on {B_sample} restarts per core of "
+              f"{n_inst} instance(s), {cores} cores in parallel for {budget_s:.0f} s ({steps} steps in total)")
+    return rate, cores, sample
 
 
 def run_reference(args):
+    """The oracle as it stands, on all host cores: each of the K timed steps is
+    a bounded sample of the workload (every core runs the oracle's step on its
+    own restarts for --ref-step-s seconds); value = summed literal-evals/s."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     insts = make_workload(args.workload)
     desc, B_full = WORKLOADS[args.workload]
     B_sample = 8 if args.workload == "hybrid" else 2
+    cores = host_cores()
     for _ in range(max(args.warmup, 0)):
-        cpu_oracle_sample(insts, B_sample, 0.0)
+        cpu_oracle_sample(insts, B_sample, 0.0, cores)
+    rates = []
     t_all = time.perf_counter()
     for _ in range(args.steps):
-        cpu_oracle_sample(insts, B_sample, 0.0)
+        r, cores, sample = cpu_oracle_sample(insts, B_sample, args.ref_step_s, cores)
+        rates.append(r)
     el = time.perf_counter() - t_all
-    value = insts[0].n_lits * B_sample * args.steps / el
+    value = statistics.mean(rates)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": desc, "sample": f"{B_sample} of {B_full} restarts of the first instance per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"FP64 oracle step (FE, gradient, projected step, exact check) on "
-                                   f"{B_sample} restarts per step, {args.steps} steps"},
+        "config": {"workload": desc, "sample": f"{B_sample} of {B_full} restarts per core per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu": cpu_model(), "kind": "oracle",
+                         "sample": sample + f"; {args.steps} such steps"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -361,32 +420,80 @@ def precision_report(inst, n_restarts: int = 4):
     return {"restarts": n_restarts, **out}
 
 
-def run_ours(args):
+KIND_NAMES = {0: "fe_grad_short_kernel", 1: "fe_grad_long_pgf_kernel", 2: "fused_grad_kernel"}
+COUNTERS_FILE = os.path.join(ROOT, "profiles", "kernel_counters.json")
+
+
+def load_counters(workload: str):
+    """ncu counters of the dominant kernel recorded for this workload (executed
+    warp instructions and DRAM bytes per restart per step), if they were taken
+    on the current kernel sources."""
+    if not os.path.exists(COUNTERS_FILE):
+        return None
+    with open(COUNTERS_FILE) as fh:
+        c = json.load(fh)
+    if c.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return c.get("workloads", {}).get(workload)
+
+
+def dominant_kernel(groups, B: int, chunk: int, peak_tinst: float, peak_src: str, sm_max: float, sms: int,
+                    counters):
+    """Roofline object of the kernel with the largest FE+gradient time per
+    step: achieved = its algorithmic instructions per launch / its event-timed
+    duration per launch (launches over the same chunk of restarts)."""
+    launches_per_step = (B + chunk - 1) // chunk
+    per_kind = {}
+    for kind, kmax, ms, work in groups:
+        d = per_kind.setdefault(kind, {"ms": 0.0, "work": 0.0, "launches": 0, "kmax": []})
+        d["ms"] += ms
+        d["work"] += work
+        d["launches"] += 1
+        d["kmax"].append(kmax)
+    kind = max(per_kind, key=lambda k: per_kind[k]["ms"])
+    d = per_kind[kind]
+    total_ms = sum(v["ms"] for v in per_kind.values())
+    achieved = d["work"] / (d["ms"] * 1e-3) / 1e12
+    out = {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
+           "frac": achieved / peak_tinst, "traffic": None,
+           "kernel": KIND_NAMES[kind],
+           "launches_per_step": d["launches"] * launches_per_step,
+           "ms_per_step": d["ms"] * launches_per_step,
+           "share_of_fe_time": d["ms"] / total_ms if total_ms else None,
+           "group_lengths": d["kmax"],
+           "work_instr_per_step": d["work"] * launches_per_step,
+           "accounting": "algorithmic FP32 lane instructions: 16 per (literal, root) + 2 per root, "
+                         "R(k) = floor((k+1)/2); fused 3-literal pass: 3 per occurrence",
+           "timing": "CUDA events on the launching stream around each launch group of the step "
+                     "(afs_group_times, 5 launches per group over one restart chunk, current state)",
+           "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock, {peak_src})"}
+    if counters and counters.get("kernel") == KIND_NAMES[kind]:
+        wi = counters["warp_inst_per_restart_step"] * B
+        out["executed_lane_instr_per_step"] = 32.0 * wi
+        out["issue_frac"] = 32.0 * wi / (out["ms_per_step"] * 1e-3) / 1e12 / peak_tinst
+        out["traffic"] = counters.get("dram_bytes_per_restart_step", 0.0) * B / out["launches_per_step"]
+        out["counters_source"] = counters.get("source")
+    return out
+
+
+def measure_workload(name: str, args, rank: int, world: int, stream, want_cpu: bool, want_e2e: bool,
+                     sample_clocks: bool, dev: int):
+    """Time one workload: K steps as graph replays (the contract's figure), a
+    sustained figure over >= --sustained-s of replays, the dominant kernel's
+    roofline, the end-to-end figure through host buffers, the CPU oracle."""
     import torch
 
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.cuda.current_device()
-
     from paper_2606_06641_gb300 import binding as bd
-    from paper_2606_06641_gb300 import build as _b
-    if rank == 0 or world == 1:
-        _b.build()
-    if world > 1:
-        torch.distributed.barrier()
-
-    desc, B_default = WORKLOADS[args.workload]
-    B = args.restarts or B_default
-    insts = make_workload(args.workload)
+    desc, B_default = WORKLOADS[name]
+    B = (args.restarts if name == args.workload else 0) or B_default
+    insts = make_workload(name)
     params = bd.default_params(eta=0.1, verify_every=1, chunk=args.chunk, autotune=0 if args.tiles else 1)
     h = bd.load_instance(insts[0], params) if len(insts) == 1 else bd.load_batch(insts, params)
     bd.init_restarts(h, B, seed=1000 + rank)
-    if args.tiles:
+    if args.tiles and name == args.workload:
         bd.set_tiles(h, *bd.parse_tiles(args.tiles))
-    stream = torch.cuda.current_stream()
+    if args.long_tiles and name == args.workload:
+        bd.set_long_tiles(h, [tuple(int(v) for v in t.split("x")) for t in args.long_tiles.split(",")])
     S = max(1, min(args.steps_per_graph, args.steps))
     R = max(1, args.steps // S)
     K = R * S
@@ -400,30 +507,46 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(R)]
-    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(R)]
-    sampler = ClockSampler(gpu_id_for(dev)) if rank == 0 else None
+    sampler = ClockSampler(gpu_id_for(dev)) if (rank == 0 and sample_clocks) else None
     if sampler:
         sampler.start()
         time.sleep(0.4)
+
+    def replays(count):
+        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(count)]
+        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(count)]
+        n_launch = 0
+        for r in range(count):
+            flush.fill_(float(r))
+            e0[r].record(stream)
+            bd.step(h, S)
+            # each replay ends, as a solver's poll does, with the exact count of
+            # the state it left (two kernels: the counting check and the fold)
+            bd.get_verify(h)
+            e1[r].record(stream)
+            n_launch += bd.last_launch_count(h) + 2
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in zip(e0, e1)), n_launch
+
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    launches = 0
-    for r in range(R):
-        flush.fill_(float(r))
-        e0[r].record(stream)
-        bd.step(h, S)
-        # each replay ends, as a solver's poll does, with the exact count of
-        # the state it left (two kernels: the counting check and the fold)
-        bd.get_verify(h)
-        e1[r].record(stream)
-        launches += bd.last_launch_count(h) + 2
-    torch.cuda.synchronize()
+    dev_ms, launches = replays(R)
     if world > 1:
         torch.distributed.barrier()
+    # sustained: replays until at least --sustained-s of device time
+    sus_ms, sus_steps = dev_ms, K
+    while sus_ms < 1e3 * args.sustained_s:
+        more = max(1, int((1e3 * args.sustained_s - sus_ms) / max(sus_ms / (sus_steps / S), 1e-3)) + 1)
+        m_ms, _ = replays(min(more, 5000))
+        sus_ms += m_ms
+        sus_steps += min(more, 5000) * S
     clocks = sampler.stop() if sampler else None
-    dev_ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1))
+    t = torch.tensor([dev_ms, sus_ms / sus_steps * K], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    dev_ms, sus_equiv = float(t[0].item()), float(t[1].item())
+
     # phase breakdown from an instrumented replay of the same length: event
     # nodes inside the graph around the FE phase and the CSR pass of every
     # step (they serialise the graph, so they stay out of the timed replays)
@@ -431,46 +554,33 @@ def run_ours(args):
     bd.step(h, S)
     torch.cuda.synchronize()
     bd.set_kernel_timing(h, True)  # reset the sums, keep the instrumented graph
-    ph0 = torch.cuda.Event(enable_timing=True)
-    ph1 = torch.cuda.Event(enable_timing=True)
-    inst_ms = 0.0
     for r in range(R):
         flush.fill_(float(r))
-        ph0.record(stream)
         bd.step(h, S)
-        ph1.record(stream)
-        torch.cuda.synchronize()
-        inst_ms += ph0.elapsed_time(ph1)
+    torch.cuda.synchronize()
     fe_ms, fe_n, csr_ms, csr_n = bd.kernel_timing(h)
     bd.set_kernel_timing(h, False)
-    t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    dev_ms = float(t.item())
 
-    value = L * B * K * world / (dev_ms * 1e-3)
-    work = bd.work_per_restart(h) * B          # FP32 lane instructions per step
-    fe_ms_step = fe_ms / K
+    # per launch group: event-timed launches on this stream, algorithmic work
+    groups = bd.group_times(h, reps=5, stream=stream)
     props = torch.cuda.get_device_properties(dev)
     peaks, peak_src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tinst = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
-    # the FE+gradient work is done by the FE launches of the length buckets,
-    # the fused pass (the derivatives of 3-literal constraints, recomputed
-    # per variable beside them) and the CSR pass, which with the check make
-    # up the step: the rate is taken over the whole timed step
-    step_ms = dev_ms / K
-    achieved = work / (step_ms * 1e-3) / 1e12 if step_ms > 0 else 0.0
-    traffic = None
-    if os.path.exists(TRAFFIC_FILE):
-        with open(TRAFFIC_FILE) as fh:
-            tr = json.load(fh)
-        if tr.get("kernel_source_hash") == kernel_source_hash() and tr.get("workload") == args.workload:
-            traffic = tr.get("bytes_per_step")
+    sms = props.multi_processor_count
+    peak_tinst = sms * 128 * sm_max * 1e6 / 1e12
+    chunk, rpl = bd.tuning(h)
+    roof = dominant_kernel(groups, B, chunk, peak_tinst, peak_src, sm_max, sms, load_counters(name))
+    step_work = sum(w for _, _, _, w in groups) * ((B + chunk - 1) // chunk)
+    roof["step_work_instr"] = step_work
+    roof["step_frac"] = step_work / (dev_ms / K * 1e-3) / 1e12 / peak_tinst
+    roof["fe_ms_per_step"] = fe_ms / K
+    roof["csr_ms_per_step"] = csr_ms / K
+    roof["phases_measured"] = ("FE phase (length buckets, fused pass, per-step check; concurrent) and CSR pass "
+                               "from an instrumented replay of the same steps (event nodes in the graph)")
 
     # end to end through the public API: pinned host x in, one step, x and unsat counts out
     e2e = None
-    if not args.no_e2e:
+    if want_e2e:
         x_host = bd.get_x(h).cpu().pin_memory()
         for _ in range(2):
             bd.step_host(h, x_host, x_host)
@@ -481,53 +591,73 @@ def run_ours(args):
             bd.step_host(h, x_host, x_host)
         el = time.perf_counter() - t0
         e2e = {"value": L * B * E * world / el, "unit": UNIT, "h2d_bytes_per_step": n_total * B * 4,
-               "d2h_bytes_per_step": n_total * B * 4 + len(insts) * B * 4}
-    chunk, rpl = bd.tuning(h)
+               "d2h_bytes_per_step": n_total * B * 4 + len(insts) * B * 4, "steps": E}
     tiles = bd.format_tiles(*bd.tiles(h))
+    long_tiles = [f"k<={km}:{lw}x{nw}" for lw, nw, km in bd.long_tiles(h)]
     h.free()
+    del flush
+    torch.cuda.empty_cache()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        Bs = 8 if args.workload == "hybrid" else 2
-        v, reps, el = cpu_oracle_sample(insts, Bs, args.cpu_seconds)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"FP64 oracle step (FE, gradient, projected step, exact check) on {Bs} of {B} restarts"
-                         f" of the first instance, {reps} steps in {el:.1f} s"}
+    if want_cpu:
+        Bs = 8 if name == "hybrid" else 2
+        v, cores, sample = cpu_oracle_sample(insts, Bs, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "cpu": cpu_model(), "kind": "oracle", "sample": sample}
 
+    return {
+        "value": L * B * K * world / (dev_ms * 1e-3), "ms_per_step": dev_ms / K, "steps": K,
+        "sustained": {"value": L * B * K * world / (sus_equiv * 1e-3), "ms_per_step": sus_equiv / K,
+                      "steps": sus_steps, "device_s": sus_ms / 1e3},
+        "config": {"workload": desc, "restarts": B, "literals": L, "instances": len(insts),
+                   "l2": f"flushed (512 MB write) between timed CUDA-graph replays of {S} steps",
+                   "chunk_restarts": chunk, "restarts_per_lane": rpl, "tiles": tiles, "long_tiles": long_tiles,
+                   "tiles_source": "given" if (args.tiles and name == args.workload) else "autotuned",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+    }
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+
+    from paper_2606_06641_gb300 import build as _b
+    if rank == 0 or world == 1:
+        _b.build()
+    if world > 1:
+        torch.distributed.barrier()
+    stream = torch.cuda.current_stream()
+    solo = rank == 0 and world == 1
+    head = measure_workload(args.workload, args, rank, world, stream, solo and not args.no_cpu,
+                            not args.no_e2e, True, dev)
+    extras = {}
+    for name in [w for w in args.extras.split(",") if w and w != args.workload]:
+        extras[name] = measure_workload(name, args, rank, world, stream, solo and not args.no_cpu,
+                                        not args.no_e2e, True, dev)
     tts = None
-    if rank == 0 and args.workload == "hybrid" and not args.no_tts:
+    if rank == 0 and not args.no_tts:
         tts = measure_time_to_solve(args.tts_instances, 32, args.tts_eta, 500)
     precision = None
     if rank == 0 and args.workload == "long" and not args.no_cpu:
-        precision = precision_report(insts[0])
+        precision = precision_report(make_workload("long")[0])
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-            "warmup": max(args.warmup, 3), "ms_per_step": dev_ms / K, "higher_is_better": True,
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": head["steps"],
+            "warmup": max(args.warmup, 3), "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": desc, "restarts": B, "literals": L, "instances": len(insts),
-                       "l2": f"flushed (512 MB write) between timed CUDA-graph replays of {S} steps",
-                       "chunk_restarts": chunk, "restarts_per_lane": rpl,
-                       "tiles": tiles, "tiles_source": "given" if args.tiles else "autotuned",
-                       "parallelism": f"replicas x{world}"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
-                         "frac": achieved / peak_tinst if peak_tinst else None, "traffic": traffic,
-                         "kernel": "FE+gradient work of a step (the FE launches of the length buckets, the "
-                                   "fused pass for 3-literal constraints, the CSR pass), rated over the whole "
-                                   "timed step, which also holds the per-step exact check",
-                         "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
-                                       f"(max SM clock, {peak_src})",
-                         "fe_ms_per_step": fe_ms_step, "csr_ms_per_step": csr_ms / K,
-                         "phases_measured": "FE phase (buckets, fused pass, check; concurrent) and CSR pass "
-                                            "from an instrumented replay of the same steps, whose step takes "
-                                            f"{inst_ms / K:.4f} ms (the event nodes serialise the graph)",
-                         "work_instr_per_step": work},
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "clocks": clocks,
-            "gpu_launches": launches,
+            "config": head["config"], "roofline": head["roofline"], "cpu_baseline": head["cpu_baseline"],
+            "e2e": head["e2e"], "clocks": head["clocks"], "gpu_launches": head["gpu_launches"],
+            "sustained": head["sustained"],
         }
+        if extras:
+            line["workloads"] = {k: {kk: vv for kk, vv in v.items() if kk != "steps"} for k, v in extras.items()}
         if tts is not None:
             line["time_to_solve"] = tts
         if precision is not None:
@@ -584,10 +714,14 @@ def run_batch_sweep(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hybrid", choices=sorted(WORKLOADS) + ["learned"])
+    ap.add_argument("--workload", default="long", choices=sorted(WORKLOADS) + ["learned"])
+    ap.add_argument("--extras", default="hybrid,batch",
+                    help="comma-separated further workloads measured into the same line ('' for none)")
+    ap.add_argument("--sustained-s", type=float, default=1.0, help="device seconds of the sustained figure")
+    ap.add_argument("--ref-step-s", type=float, default=4.0, help="reference arm: seconds per sampled step")
     ap.add_argument("--learned-train", type=int, default=10000)
     ap.add_argument("--learned-test", type=int, default=512)
     ap.add_argument("--learned-epochs", type=int, default=30)
@@ -596,6 +730,7 @@ def main():
     ap.add_argument("--steps-per-graph", type=int, default=10)
     ap.add_argument("--chunk", type=int, default=0, help="restarts per chunk (0 = autotuned)")
     ap.add_argument("--tiles", default="", help="fixed chunk and tiles, 'chunk:k=RPLxCPW,...' (no autotuning)")
+    ap.add_argument("--long-tiles", default="", help="fixed long-group tiles, 'LANESxWARPS,...' longest group first")
     ap.add_argument("--sweep-b", default="", help="comma-separated restart counts: throughput against B")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--tts-instances", type=int, default=128)
@@ -606,7 +741,7 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         if args.workload == "learned":
-            args.workload = "hybrid"
+            args.workload = "long"
         return run_reference(args)
     if args.workload == "learned":
         return run_learned(args)

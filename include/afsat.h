@@ -327,6 +327,20 @@ int afs_tiles(const afs_handle* h, int32_t* chunk, int32_t* rpl_by_k, int32_t* c
  * changes and AFS_E_ARG is returned. Cached step graphs are dropped. */
 int afs_set_tiles(afs_handle* h, int32_t chunk, const int32_t* rpl_by_k, const int32_t* cpw_by_k, int32_t kcap);
 
+/* afs_group_times: event-timed FE+gradient launches of each launch group of
+ * the step (bucket order) over the current restart chunk of the current
+ * state, on `stream`: reps launches per group, ms[i] = mean milliseconds per
+ * launch. kind[i] = 0 short bucket (k <= 32), 1 long group (k > 32), 2 the
+ * fused pass of the 3-literal constraints; kmax[i] = the group's (longest)
+ * length; work[i] = algorithmic FP32 instructions of one launch: per
+ * constraint and restart 16 per (literal, root) plus 2 per root with
+ * R(k) = floor((k+1)/2) roots (Sec. 2.1.2's products at the roots, mirrored
+ * pairs counted once), or 3 per occurrence for the fused pass (its level
+ * form). The derivative rows written are scratch; the state is not changed.
+ * Writes min(cap, groups) entries (arrays may be NULL) and the number of
+ * groups to *n. Synchronises on the launches' completion. */
+int afs_group_times(afs_handle* h, int32_t reps, double* ms, int32_t* kind, int32_t* kmax, double* work,
+                    int32_t cap, int32_t* n, void* stream);
 /* afs_long_tiles: the kernel tile of each long-constraint group (k > 32) in
  * bucket order (longest first): lanes per restart (8, 16 or 32; a pass of the
  * probability-generating kernel evaluates that many roots of one restart)

@@ -70,6 +70,7 @@ SIGNATURES = {
     "afs_step_ls": (_I32, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I32, _P, _P]),
     "afs_set_tiles": (_I32, [_P, _I32, _P, _P, _I32]),
     "afs_long_tiles": (_I32, [_P, _P, _P, _P, _I32, _P]),
+    "afs_group_times": (_I32, [_P, _I32, _P, _P, _P, _P, _I32, _P, _P]),
     "afs_set_long_tiles": (_I32, [_P, _P, _P, _I32]),
     "afs_coef_table": (_I32, [_I32, _I32, _I32, _I32, _I32, _I32, _I32, _P, _I32, _P]),
     "afs_esp_coefficients": (_I32, [_I32, _I32, _I32, _I32, _I32, _P]),
@@ -443,6 +444,20 @@ def set_tiles(h: Handle, chunk: int = 0, tiles=None):
         rpl[int(k)] = int(r)
         cpw[int(k)] = int(c)
     _check(lib().afs_set_tiles(h.ptr, int(chunk), rpl, cpw, 33))
+
+
+def group_times(h: Handle, reps: int = 3, stream=None):
+    """[(kind, kmax, ms per launch, algorithmic FP32 instructions per launch)]
+    of every FE launch group (kind 0 short, 1 long, 2 fused 3-literal pass)."""
+    n = ctypes.c_int32()
+    _check(lib().afs_group_times(h.ptr, 1, None, None, None, None, 0, ctypes.byref(n), _stream(stream)))
+    cnt = max(1, n.value)
+    ms = (ctypes.c_double * cnt)()
+    kind = (ctypes.c_int32 * cnt)()
+    km = (ctypes.c_int32 * cnt)()
+    work = (ctypes.c_double * cnt)()
+    _check(lib().afs_group_times(h.ptr, int(reps), ms, kind, km, work, n.value, ctypes.byref(n), _stream(stream)))
+    return [(kind[i], km[i], ms[i], work[i]) for i in range(n.value)]
 
 
 def long_tiles(h: Handle):

@@ -140,6 +140,10 @@ struct Group {
   int cpw;          // constraints per warp (short kernel tile)
   bool fused = false;  // k == KFUSE: derivatives recomputed in the fused pass
   int lw = 32, lnw = 4;  // long probability-generating kernel tile: lanes per restart, warps per CTA
+  // algorithmic FP32 instructions per restart of the group's FE+gradient:
+  // 16 per (literal, root) plus 2 per root with R(k) = floor((k+1)/2) roots
+  // (a fused 3-literal group: 3 per occurrence, its level form)
+  double work_alg = 0.0;
 };
 
 }  // namespace
@@ -408,6 +412,10 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
       last->c_count++;
     } else {
       h->groups.push_back(Group{is_long, k, pos, 1, static_cast<long long>(b_lit[pos]), 1, 1, fused_k(k)});
+    }
+    {
+      const double R = static_cast<double>((k + 1) / 2);
+      h->groups.back().work_alg += fused_k(k) ? 3.0 * k : 16.0 * k * R + 2.0 * R;
     }
   }
   {
@@ -1790,6 +1798,43 @@ int afs_set_tiles(afs_handle* h, int32_t chunk, const int32_t* rpl_by_k, const i
     if (cpw_by_k && cpw_by_k[g.k]) g.cpw = cpw_by_k[g.k];
   }
   h->drop_graphs();
+  return AFS_OK;
+}
+
+int afs_group_times(afs_handle* h, int32_t reps, double* ms, int32_t* kind, int32_t* kmax, double* work,
+                    int32_t cap, int32_t* n, void* stream) {
+  if (!h || !n) return fail(AFS_E_ARG, "NULL argument");
+  if (h->B <= 0) return fail(AFS_E_STATE, "afs_init_restarts has not been called");
+  if (reps <= 0) return fail(AFS_E_ARG, "reps must be positive");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nb = std::min(h->Bc, h->B);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int i = 0, rc = AFS_OK;
+  for (const Group& g : h->groups) {
+    if (i < cap) {
+      CK(cudaEventRecord(e0, s));
+      for (int r = 0; r < reps && rc == AFS_OK; ++r)
+        rc = g.fused ? launch_fused(h, h->xcur(), 0, nb, s)
+                     : launch_fe_group(h, g, h->xcur(), h->xt, h->pitch, 0, nb, h->go.as<float>(), h->Bc, nullptr,
+                                       0, s);
+      if (rc) break;
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float t = 0.0f;
+      CK(cudaEventElapsedTime(&t, e0, e1));
+      if (ms) ms[i] = t / reps;
+      if (kind) kind[i] = g.fused ? 2 : (g.is_long ? 1 : 0);
+      if (kmax) kmax[i] = g.k;
+      if (work) work[i] = g.work_alg * nb;
+    }
+    ++i;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  *n = i;
   return AFS_OK;
 }
 
