@@ -61,6 +61,7 @@ METRIC = "FE+grad literal-evals/s"
 LINE_SEARCH = (1.0, 0.5, 1e-4, 6)   # first step, backtracking factor, sufficient-decrease constant, trials
 UNIT = "literal-evals/s"
 KERNEL_SOURCES = ["paper_2606_06641_gb300/csrc/fe_short.cuh", "paper_2606_06641_gb300/csrc/kernels.cu",
+                  "paper_2606_06641_gb300/csrc/long_pgf.cu",
                   "paper_2606_06641_gb300/csrc/coef.cpp", "paper_2606_06641_gb300/csrc/coef.h",
                   "paper_2606_06641_gb300/csrc/afsat_internal.h"]
 
