@@ -267,13 +267,15 @@ int afs_mpnn_get_params(afs_mpnn* net, float* theta_dev, void* stream);
 int afs_mpnn_set_params(afs_mpnn* net, const float* theta_dev, void* stream);
 /* mu_dev[n_total] = the network's output for the handle's variables */
 int afs_mpnn_forward(afs_mpnn* net, afs_handle* h, float* mu_dev, void* stream);
-/* Loss = sum_v w_v BCE(p_v, y_v) / wsum with p_v = (1 - mu_v)/2 the predicted
- * probability that v is True and y_dev[n_total] soft labels in [0, 1]
- * (w_dev nullable = all ones). Writes the parameter gradient into the net's
+/* Loss = sum_v w_v BCE(p_v, y_v) / max(sum_v w_v, 1) with p_v = (1 - mu_v)/2
+ * the predicted probability that v is True, y_dev[n_total] soft labels in
+ * [0, 1] and w_dev[n_total] a label mask (nullable = all ones); the mask sum
+ * is taken on the device. Writes the parameter gradient into the net's
  * gradient buffer (and grad_dev if not NULL) and the loss into *loss_host
- * (nullable; when given the stream is synchronised). */
-int afs_mpnn_loss_grad(afs_mpnn* net, afs_handle* h, const float* y_dev, const float* w_dev, float wsum,
-                       float* grad_dev, float* loss_host, void* stream);
+ * (nullable; when given the stream is synchronised). Every cross-CTA sum is
+ * done in a fixed order, so repeated calls give bit-identical results. */
+int afs_mpnn_loss_grad(afs_mpnn* net, afs_handle* h, const float* y_dev, const float* w_dev, float* grad_dev,
+                       float* loss_host, void* stream);
 /* One Adam step (beta 0.9/0.999, eps 1e-8, bias-corrected) with the last gradient. */
 int afs_mpnn_adam_step(afs_mpnn* net, float lr, void* stream);
 /* Overwrite the handle's restart state (after afs_init_restarts with the
@@ -283,6 +285,12 @@ int afs_mpnn_adam_step(afs_mpnn* net, float lr, void* stream);
  * remaining restarts stay uniform on [-1, 1) as the fallback. */
 int afs_mpnn_init_restarts(afs_mpnn* net, afs_handle* h, int32_t B, uint64_t seed, float uniform_frac,
                            float sigma_min, float sigma_max, void* stream);
+/* Nudge the handle's current restart state (e.g. afs_init_restarts' uniform
+ * starts) toward the network's proposal: x = clamp(x + alpha_b mu_v, -1, 1)
+ * with alpha_b ramped linearly from alpha_min (restart 0) to alpha_max
+ * (restart B - 1), so the low restarts stay close to their uniform starts
+ * and the high ones lean on the network. */
+int afs_mpnn_nudge_restarts(afs_mpnn* net, afs_handle* h, float alpha_min, float alpha_max, void* stream);
 
 /* ---- failure detection -------------------------------------------------
  * Device waits are bounded: the long-constraint kernel waits for its bulk

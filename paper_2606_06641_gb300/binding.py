@@ -52,8 +52,9 @@ SIGNATURES = {
     "afs_mpnn_get_params": (_I32, [_P, _P, _P]),
     "afs_mpnn_set_params": (_I32, [_P, _P, _P]),
     "afs_mpnn_forward": (_I32, [_P, _P, _P, _P]),
-    "afs_mpnn_loss_grad": (_I32, [_P, _P, _P, _P, ctypes.c_float, _P, _P, _P]),
+    "afs_mpnn_loss_grad": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
     "afs_mpnn_adam_step": (_I32, [_P, ctypes.c_float, _P]),
+    "afs_mpnn_nudge_restarts": (_I32, [_P, _P, ctypes.c_float, ctypes.c_float, _P]),
     "afs_mpnn_init_restarts": (_I32, [_P, _P, _I32, ctypes.c_uint64, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_float, _P]),
     "afs_device_error": (_I32, [_P, _P, _P]),
@@ -177,29 +178,34 @@ def load_instance(inst: Instance, params: Optional[Params] = None, stream=None) 
 
 
 def load_batch(insts: Sequence[Instance], params: Optional[Params] = None, stream=None) -> Handle:
-    recs, lits, begin, count, nv = [], [], [], [], []
-    c0 = l0 = 0
-    for inst in insts:
-        r = cons_records(inst)
-        r["lit_offset"] += l0
-        recs.append(r)
-        lits.append(inst.lits.astype(np.int32))
-        begin.append(c0)
-        count.append(inst.m)
-        nv.append(inst.n)
-        c0 += inst.m
-        l0 += inst.n_lits
-    rec = np.concatenate(recs) if recs else np.zeros(0, CONS_DTYPE)
-    lit = np.ascontiguousarray(np.concatenate(lits) if lits else np.zeros(0, np.int32))
-    begin = np.asarray(begin, np.int32)
-    count = np.asarray(count, np.int32)
-    nv = np.asarray(nv, np.int32)
+    count = np.fromiter((i.m for i in insts), np.int32, len(insts))
+    nv = np.fromiter((i.n for i in insts), np.int32, len(insts))
+    nl = np.fromiter((i.n_lits for i in insts), np.int64, len(insts))
+    begin = np.zeros(len(insts), np.int32)
+    np.cumsum(count[:-1], out=begin[1:])
+    lit_base = np.zeros(len(insts), np.int64)
+    np.cumsum(nl[:-1], out=lit_base[1:])
+    m = int(count.sum())
+    rec = np.zeros(m, dtype=CONS_DTYPE)
+    if m:
+        rec["type"] = np.concatenate([i.ctype for i in insts])
+        rec["op"] = np.concatenate([i.op for i in insts])
+        rec["parity"] = np.concatenate([i.parity for i in insts])
+        rec["param"] = np.concatenate([i.param for i in insts])
+        offs = np.concatenate([i.lit_off for i in insts])      # m + n_inst entries (each instance's m + 1)
+        last = np.cumsum(count + 1) - 1                          # the closing offset of each instance
+        keep = np.ones(offs.shape[0], bool)
+        keep[last] = False
+        rec["lit_offset"] = offs[keep] + np.repeat(lit_base, count)
+        rec["len"] = offs[1:][keep[:-1]] - offs[:-1][keep[:-1]]
+    lit = np.ascontiguousarray(np.concatenate([i.lits for i in insts]).astype(np.int32, copy=False)) \
+        if len(insts) else np.zeros(0, np.int32)
     out = ctypes.c_void_p()
     _check(lib().afs_load_batch(rec.ctypes.data, begin.ctypes.data, count.ctypes.data, lit.ctypes.data,
                                 lit.shape[0], nv.ctypes.data, len(insts),
                                 ctypes.byref(params) if params is not None else None, _stream(stream),
                                 ctypes.byref(out)))
-    return Handle(out.value, int(nv.sum()), int(count.sum()), len(insts))
+    return Handle(out.value, int(nv.sum()), m, len(insts))
 
 
 def init_restarts(h: Handle, B: int, seed: int = 0, x0=None, stream=None) -> None:
@@ -364,8 +370,7 @@ class Mpnn:
         import torch
         g = torch.empty(self.n_params, dtype=torch.float32, device="cuda") if want_grad else None
         loss = ctypes.c_float()
-        wsum = float(w.sum().item()) if w is not None else float(h.n)
-        _check(lib().afs_mpnn_loss_grad(self.ptr, h.ptr, _ptr(y), _ptr(w), wsum, _ptr(g), ctypes.byref(loss),
+        _check(lib().afs_mpnn_loss_grad(self.ptr, h.ptr, _ptr(y), _ptr(w), _ptr(g), ctypes.byref(loss),
                                         _stream(stream)))
         return loss.value, g
 
@@ -376,6 +381,10 @@ class Mpnn:
                       sigma_min: float = 0.3, sigma_max: float = 1.5, stream=None) -> None:
         _check(lib().afs_mpnn_init_restarts(self.ptr, h.ptr, B, seed, uniform_frac, sigma_min, sigma_max,
                                             _stream(stream)))
+
+    def nudge_restarts(self, h: Handle, alpha_min: float = 0.0, alpha_max: float = 1.0, stream=None):
+        """x = clamp(x + alpha_b mu, -1, 1) on the current state, alpha ramped over the restarts."""
+        _check(lib().afs_mpnn_nudge_restarts(self.ptr, h.ptr, alpha_min, alpha_max, _stream(stream)))
 
 
 def device_error(h: Handle, stream=None) -> int:

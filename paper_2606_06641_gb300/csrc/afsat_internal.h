@@ -205,6 +205,12 @@ struct GraphView {
   const int* cparity;
   const int* inst_vbegin;   // host: [n_inst + 1]
   const int* var_inst_dev;  // device: instance of each variable, then first variable per instance
+  // device copies of the instance graph (built at load):
+  const int* lit_off_dev;   // [m + 1] constraint-major occurrence offsets (load order)
+  const int* lit_enc_dev;   // [L] var << 1 | negated
+  const int* v_off_dev;     // [n + 1] variable-major occurrence offsets
+  const int* v_enc_dev;     // [L] constraint << 1 | negated, constraints in load order per variable
+  const int4* cinfo_dev;    // [m] {type, op, param, parity} per constraint (load order)
   void* x;                  // device state (after afs_init_restarts), pitch columns per variable
   long long pitch;
   int B, xt;

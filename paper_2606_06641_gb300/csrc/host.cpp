@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstring>
 #include <array>
+#include <chrono>
 #include <map>
 #include <memory>
 #include <string>
@@ -102,11 +103,13 @@ static double l2_bytes() {
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  bool owned = true;  // false: a span of another buffer (an arena), not freed here
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p && owned) cudaFree(p);
     p = nullptr;
     bytes = 0;
+    owned = true;
   }
   int alloc(size_t n) {
     release();
@@ -121,6 +124,39 @@ struct DevBuf {
   }
   template <typename T>
   T* as() const { return static_cast<T*>(p); }
+};
+
+// Many host arrays uploaded as spans of one device allocation with one copy
+// (instance loading makes one cudaMalloc and one transfer, not one each).
+struct ArenaUpload {
+  struct Item {
+    DevBuf* dst;
+    const void* src;
+    size_t bytes, off;
+  };
+  std::vector<Item> items;
+  size_t total = 0;
+  template <typename T>
+  void add(DevBuf& d, const std::vector<T>& h) {
+    const size_t bytes = std::max<size_t>(h.size() * sizeof(T), 16);
+    items.push_back(Item{&d, h.empty() ? nullptr : h.data(), h.size() * sizeof(T), total});
+    total += (bytes + 255) / 256 * 256;
+  }
+  int run(DevBuf& arena, cudaStream_t s) {
+    int rc = arena.alloc(total);
+    if (rc) return rc;
+    std::vector<char> host(total, 0);
+    for (const Item& it : items) {
+      if (it.bytes) std::memcpy(host.data() + it.off, it.src, it.bytes);
+      it.dst->release();
+      it.dst->p = static_cast<char*>(arena.p) + it.off;
+      it.dst->bytes = it.bytes;
+      it.dst->owned = false;
+    }
+    CK(cudaMemcpyAsync(arena.p, host.data(), total, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // the staging vector goes out of scope
+    return AFS_OK;
+  }
 };
 
 template <typename T>
@@ -171,8 +207,12 @@ struct afs_handle {
   std::vector<int> order, step_order;
   double work_per_restart = 0.0;
   // device instance data
+  // (spans of inst_arena, which is declared first so that it is freed last)
+  DevBuf inst_arena;
   DevBuf litslot, cons_tab, cons_orig, cons_k, cons_lit, coef, csr_off, lit_enc, lit_off, viol_off, viol,
       var_inst, err, chk_em, chk_ranges, fus_off, fus, cinst;
+  // the instance graph by variable and per-constraint records (the learned initialiser's inputs)
+  DevBuf v_off, v_enc, cinfo;
   int n_chk_ranges = 0;
   // restart state
   int B = 0, xt = XT_F32;
@@ -257,9 +297,23 @@ struct afs_handle {
 // ---------------------------------------------------------------------------
 // loading
 // ---------------------------------------------------------------------------
+// Phase durations of instance loading, printed when AFS_LOAD_PROFILE is set.
+struct LoadClock {
+  bool on = std::getenv("AFS_LOAD_PROFILE") != nullptr;
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  void mark(const char* what) {
+    if (!on) return;
+    const auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "[afs load] %-28s %8.3f ms\n", what,
+                 std::chrono::duration<double, std::milli>(now - t).count());
+    t = now;
+  }
+};
+
 static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const int32_t* cons_count,
                         const int32_t* lits, int64_t n_lits, const int32_t* n_vars, int32_t n_inst,
                         const afs_params* prm, cudaStream_t s, afs_handle** out) {
+  LoadClock lclk;
   if (!out) return fail(AFS_E_ARG, "out is NULL");
   *out = nullptr;
   if (n_inst <= 0) return fail(AFS_E_ARG, "n_inst must be positive");
@@ -326,6 +380,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     return (v << 1) | (lit < 0 ? 1 : 0);
   };
 
+  lclk.mark("records");
   // ---- distinct shapes: coefficient tables (both forms as needed) and truth tables ----
   std::map<std::pair<Shape, int>, int> tab_index;  // (shape, form) -> float4 offset
   std::map<Shape, int> viol_index;
@@ -333,6 +388,11 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   std::vector<uint8_t> violv;
   std::vector<int> cons_tab_load(m), viol_off(m);
   for (int g = 0; g < m; ++g) {
+    if (g > 0 && shape[g] == shape[g - 1]) {  // same shape as the previous constraint: same tables
+      cons_tab_load[g] = cons_tab_load[g - 1];
+      viol_off[g] = viol_off[g - 1];
+      continue;
+    }
     const int form = gk[g] <= KSHORT ? FORM_SHORT : FORM_LONG;
     auto key = std::make_pair(shape[g], form);
     auto it = tab_index.find(key);
@@ -359,15 +419,18 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     viol_off[g] = vt->second;
   }
 
+  lclk.mark("tables");
   // ---- bucket order: short constraints by length, then long ones by decreasing length ----
+  // (a stable counting sort: the key is the length, short ones ascending,
+  // then long ones descending)
   std::vector<int> order(m);
-  for (int g = 0; g < m; ++g) order[g] = g;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    const bool la = gk[a] > KSHORT, lb = gk[b] > KSHORT;
-    if (la != lb) return !la;
-    if (!la) return gk[a] < gk[b];
-    return gk[a] > gk[b];
-  });
+  {
+    auto key = [](int k) { return k <= KSHORT ? k : KSHORT + 1 + (AFS_MAX_LEN - k); };
+    std::vector<int> start(KSHORT + 2 + AFS_MAX_LEN, 0);
+    for (int g = 0; g < m; ++g) start[key(gk[g]) + 1]++;
+    for (size_t i = 1; i < start.size(); ++i) start[i] += start[i - 1];
+    for (int g = 0; g < m; ++g) order[start[key(gk[g])]++] = g;
+  }
   std::vector<int> b_tab(m), b_orig(m), b_k(m), b_lit(m);
   // the work model counts the complex roots a short scaled table keeps
   // (and the roots a long probability-generating table keeps)
@@ -429,6 +492,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     for (int gi : h->order)
       if (!h->groups[gi].fused) h->step_order.push_back(gi);
   }
+  lclk.mark("bucket order");
   // ---- CSR: slots in variable-major order, occurrences of a variable in
   // bucket order; occurrences in fused constraints get an entry
   // {other literal, other literal, table, negated} instead of a slot ----
@@ -461,8 +525,14 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   };
   {
     std::vector<int> fill(csr.begin(), csr.end() - 1), ffill(fcsr.begin(), fcsr.end() - 1);
+    const std::vector<double>* cl_last = nullptr;
+    Shape sh_last{-1, -1, -1, -1, -1};
     for (int pos = 0; pos < m; ++pos) {
       const int k = b_k[pos];
+      if (fused_k(k) && !(shape[b_orig[pos]] == sh_last)) {  // consecutive constraints mostly share a shape
+        sh_last = shape[b_orig[pos]];
+        cl_last = &levels_of(sh_last);
+      }
       for (int t = 0; t < k; ++t) {
         int2& ls = litslot[b_lit[pos] + t];
         if (!fused_k(k)) {
@@ -476,7 +546,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
         // expansion FE = sum_S c_|S| prod_{i in S} l_i with l = s x:
         //   s_self (c1 + c2 (s1 x1 + s2 x2) + c3 s1 s2 x1 x2)
         //   = x1 (A x2 + B1) + B2 x2 + C,   entry {A, B1, B2, C}, {v1, v2}
-        const std::vector<double>& cl = levels_of(shape[b_orig[pos]]);
+        const std::vector<double>& cl = *cl_last;
         const double s1 = (other[0] & 1) ? -1.0 : 1.0, s2 = (other[1] & 1) ? -1.0 : 1.0;
         const double ss = (ls.x & 1) ? -1.0 : 1.0;
         const size_t fe = 2 * static_cast<size_t>(ffill[ls.x >> 1]++);
@@ -493,6 +563,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   }
   h->Lgo = csr[h->n];
   h->n_fused = n_fused;
+  lclk.mark("csr + fused");
   // ---- exact-check structures (load order) ----
   h->h_lit_enc.resize(L);
   h->h_lit_off.assign(m + 1, 0);
@@ -524,6 +595,10 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   for (int g = 0; g < m; ++g) {
     const int k = gk[g];
     if (k > 62) continue;
+    if (g > 0 && viol_off[g] == viol_off[g - 1]) {  // same truth table as the previous constraint
+      chk_em[g] = chk_em[g - 1];
+      continue;
+    }
     unsigned long long vm = 0ull;
     for (int t = 0; t <= k; ++t)
       if (violv[viol_off[g] + t]) vm |= 1ull << t;
@@ -549,27 +624,47 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   std::vector<int> var_inst_ext(h->h_var_inst);
   var_inst_ext.insert(var_inst_ext.end(), h->inst_vbegin.begin(), h->inst_vbegin.end());
 
-  // ---- upload ----
-  int rc;
-  if ((rc = upload(h->litslot, litslot, s))) return rc;
-  if ((rc = upload(h->cons_tab, b_tab, s))) return rc;
-  if ((rc = upload(h->cons_orig, b_orig, s))) return rc;
-  if ((rc = upload(h->cons_k, b_k, s))) return rc;
-  if ((rc = upload(h->cons_lit, b_lit, s))) return rc;
-  if ((rc = upload(h->coef, coef, s))) return rc;
-  if ((rc = upload(h->csr_off, csr, s))) return rc;
-  if ((rc = upload(h->fus_off, fcsr, s))) return rc;
-  if ((rc = upload(h->cinst, ginst, s))) return rc;
-  if ((rc = upload(h->fus, fus, s))) return rc;
-  if ((rc = upload(h->lit_enc, h->h_lit_enc, s))) return rc;
-  if ((rc = upload(h->lit_off, h->h_lit_off, s))) return rc;
-  if ((rc = upload(h->viol_off, viol_off, s))) return rc;
-  if ((rc = upload(h->viol, violv, s))) return rc;
-  if ((rc = upload(h->var_inst, var_inst_ext, s))) return rc;
-  if ((rc = upload(h->chk_em, chk_em, s))) return rc;
-  if ((rc = upload(h->chk_ranges, chk_ranges, s))) return rc;
+  lclk.mark("check structures");
+  // the graph by variable (occurrences of each variable, constraints in load
+  // order) and the constraint records, for the learned initialiser
+  std::vector<int> v_off_h(h->n + 1, 0), v_enc_h(L);
+  std::vector<int4> cinfo_h(m);
+  {
+    for (long long e = 0; e < L; ++e) v_off_h[(h->h_lit_enc[e] >> 1) + 1]++;
+    for (int v = 0; v < h->n; ++v) v_off_h[v + 1] += v_off_h[v];
+    std::vector<int> fill(v_off_h.begin(), v_off_h.end() - 1);
+    for (int c = 0; c < m; ++c)
+      for (int e = h->h_lit_off[c]; e < h->h_lit_off[c + 1]; ++e)
+        v_enc_h[fill[h->h_lit_enc[e] >> 1]++] = (c << 1) | (h->h_lit_enc[e] & 1);
+    for (int c = 0; c < m; ++c) cinfo_h[c] = make_int4(shape[c].type, shape[c].op, shape[c].param, shape[c].parity);
+  }
+  lclk.mark("variable graph");
+  // ---- upload (one allocation, one copy) ----
   std::vector<int> zero1(1, 0);
-  if ((rc = upload(h->err, zero1, s))) return rc;
+  ArenaUpload up;
+  up.add(h->litslot, litslot);
+  up.add(h->cons_tab, b_tab);
+  up.add(h->cons_orig, b_orig);
+  up.add(h->cons_k, b_k);
+  up.add(h->cons_lit, b_lit);
+  up.add(h->coef, coef);
+  up.add(h->csr_off, csr);
+  up.add(h->fus_off, fcsr);
+  up.add(h->cinst, ginst);
+  up.add(h->fus, fus);
+  up.add(h->lit_enc, h->h_lit_enc);
+  up.add(h->lit_off, h->h_lit_off);
+  up.add(h->viol_off, viol_off);
+  up.add(h->viol, violv);
+  up.add(h->var_inst, var_inst_ext);
+  up.add(h->chk_em, chk_em);
+  up.add(h->chk_ranges, chk_ranges);
+  up.add(h->err, zero1);
+  up.add(h->v_off, v_off_h);
+  up.add(h->v_enc, v_enc_h);
+  up.add(h->cinfo, cinfo_h);
+  int rc = up.run(h->inst_arena, s);
+  if (rc) return rc;
   CK(cudaStreamSynchronize(s));
   CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
   for (int i = 0; i < afs_handle::NAUX; ++i) {
@@ -1151,6 +1246,11 @@ int afs::graph_view(const afs_handle* h, GraphView* out) {
   out->cparity = h->h_cparity.data();
   out->inst_vbegin = h->inst_vbegin.data();
   out->var_inst_dev = h->var_inst.as<int>();
+  out->lit_off_dev = h->lit_off.as<int>();
+  out->lit_enc_dev = h->lit_enc.as<int>();
+  out->v_off_dev = h->v_off.as<int>();
+  out->v_enc_dev = h->v_enc.as<int>();
+  out->cinfo_dev = h->cinfo.as<int4>();
   out->x = h->xcur();
   out->pitch = h->pitch;
   out->B = h->B;

@@ -13,10 +13,14 @@
 // Dense products run on the tensor cores (mma.sync m16n8k16, BF16 operands
 // rounded from the FP32 masters and activations, FP32 accumulation); the
 // segment means are deterministic gathers over edge lists; the backward pass
-// mirrors the forward; Adam keeps FP32 moments.
+// mirrors the forward; Adam keeps FP32 moments. Every reduction across CTAs
+// (the weight gradients' K slices, bias and head gradients, the loss and the
+// label-mask sum) writes per-CTA partials that one final pass adds in a fixed
+// order, so a gradient is bit-identical from run to run.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <random>
@@ -61,7 +65,7 @@ struct GemmArgs {
   int M, N, K;
   const float* bias;
   int relu;
-  int mode;  // 0: C = r, 1: C += r, 2: atomicAdd(C, r)
+  int mode;  // 0: C = r, 1: C += r, 2: slice partial (C + blockIdx.z * M * N, row pitch N)
   int k_split;
 };
 
@@ -125,10 +129,10 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
         const int col = col0 + nt * 8 + 2 * tig + q;
         if (row < g.M && col < g.N) {
           float v = acc[nt][2 * hh + q];
-          float* dst = g.C + row * g.ldc + col;
           if (g.mode == 2) {
-            atomicAdd(dst, v);
+            g.C[(static_cast<long long>(blockIdx.z) * g.M + row) * g.N + col] = v;
           } else {
+            float* dst = g.C + row * g.ldc + col;
             if (g.bias) v += g.bias[col];
             if (g.relu) v = fmaxf(v, 0.f);
             *dst = g.mode == 1 ? *dst + v : v;
@@ -139,17 +143,42 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
   }
 }
 
+// C[i][j] += sum_z part[z][i][j], z in order
+__global__ void slice_sum_kernel(const float* part, int slices, long long mn, int N, float* C, long long ldc) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= mn) return;
+  float acc = 0.f;
+  for (int z = 0; z < slices; ++z) acc += part[z * mn + i];
+  const long long r = i / N, c = i - r * N;
+  C[r * ldc + c] += acc;
+}
+
+constexpr int WGRAD_KSPLIT = 1024;  // inner-dimension slice of a weight-gradient product
+
+// Slices of a weight-gradient product over K (graph nodes) and the scratch they need.
+inline int wgrad_slices(int K) { return (K + WGRAD_KSPLIT - 1) / WGRAD_KSPLIT; }
+
+// mode 0: C = A B (+bias, relu); mode 1: C += A B; mode 2 (weight gradients,
+// K = graph nodes): C += A B with the inner dimension split into slices of
+// WGRAD_KSPLIT over CTAs, each slice's product written to `scratch` and the
+// slices added in order (deterministic).
 void gemm(const float* A, long long sa0, long long sa1, const float* B, long long sb0, long long sb1, float* C,
-          long long ldc, int M, int N, int K, const float* bias, bool relu, int mode, cudaStream_t s) {
+          long long ldc, int M, int N, int K, const float* bias, bool relu, int mode, cudaStream_t s,
+          float* scratch = nullptr) {
   if (M <= 0 || N <= 0 || K <= 0) return;  // empty product (weight gradients of an empty graph stay zero)
   GemmArgs g{A, sa0, sa1, B, sb0, sb1, C, ldc, M, N, K, bias, relu ? 1 : 0, mode, K};
   int zsplit = 1;
-  if (mode == 2) {  // weight gradients: split the long inner dimension over CTAs
-    g.k_split = 1024;
-    zsplit = (K + g.k_split - 1) / g.k_split;
+  if (mode == 2) {
+    g.k_split = WGRAD_KSPLIT;
+    zsplit = wgrad_slices(K);
+    g.C = scratch;
   }
   dim3 grid((M + 63) / 64, (N + 63) / 64, zsplit);
   gemm_bf16_kernel<<<grid, 128, 0, s>>>(g);
+  if (mode == 2) {
+    const long long mn = static_cast<long long>(M) * N;
+    slice_sum_kernel<<<static_cast<unsigned>((mn + 255) / 256), 256, 0, s>>>(scratch, zsplit, mn, N, C, ldc);
+  }
 }
 
 // out[r*ldo + j] = rowscale[r] * sum_{e in [off[r], off[r+1])} s_e * srcscale[src] * src[src*lds + j]
@@ -196,21 +225,70 @@ void copy_mask(const float* src, long long lds, const float* ref, long long ldr,
   copy_mask_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(src, lds, ref, ldr, dst, ldd, rows);
 }
 
-// out[j] += sum_r x[r*ld + j] (column sums of a rows x 64 block)
-__global__ void colsum_kernel(const float* x, long long ld, int rows, float* out) {
-  const int j = threadIdx.x;  // 64 columns
+// Fixed-order column sums of a rows x 64 block (optionally weighted per row):
+// CTA b adds rows [b*chunk, (b+1)*chunk) in increasing order per thread row
+// lane and writes part[b][j]; colsum_final adds the CTA partials in order.
+constexpr int RED_CTAS = 128;
+
+inline int red_ctas(int rows) { return std::max(1, std::min(RED_CTAS, (rows + 255) / 256)); }
+
+__global__ void colsum_part_kernel(const float* x, long long ld, int rows, const float* rw, float* part) {
+  const int j = threadIdx.x, y = threadIdx.y;  // 64 x 4 threads
+  const int chunk = (rows + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
   float acc = 0.f;
-  for (int r = blockIdx.x * blockDim.y + threadIdx.y; r < rows; r += gridDim.x * blockDim.y) acc += x[r * ld + j];
-  __shared__ float part[4][H];
-  part[threadIdx.y][j] = acc;
+  for (int r = r0 + y; r < r1; r += 4) acc = rw ? fmaf(rw[r], x[r * ld + j], acc) : acc + x[r * ld + j];
+  __shared__ float p[4][H];
+  p[y][j] = acc;
   __syncthreads();
-  if (threadIdx.y == 0) atomicAdd(out + j, part[0][j] + part[1][j] + part[2][j] + part[3][j]);
+  if (y == 0) part[blockIdx.x * H + j] = ((p[0][j] + p[1][j]) + p[2][j]) + p[3][j];
 }
 
-void colsum(const float* x, long long ld, int rows, float* out, cudaStream_t s) {
+__global__ void colsum_final_kernel(const float* part, int ctas, float* out) {
+  const int j = threadIdx.x;
+  float acc = 0.f;
+  for (int b = 0; b < ctas; ++b) acc += part[b * H + j];
+  out[j] += acc;
+}
+
+// out[j] += sum_r x[r][j] (rw: sum_r rw[r] x[r][j]); `part` holds RED_CTAS x 64 floats
+void colsum(const float* x, long long ld, int rows, float* out, float* part, cudaStream_t s,
+            const float* rw = nullptr) {
   if (rows <= 0) return;
-  const int blocks = std::min(256, (rows + 3) / 4);
-  colsum_kernel<<<blocks, dim3(H, 4), 0, s>>>(x, ld, rows, out);
+  const int ctas = red_ctas(rows);
+  colsum_part_kernel<<<ctas, dim3(H, 4), 0, s>>>(x, ld, rows, rw, part);
+  colsum_final_kernel<<<1, H, 0, s>>>(part, ctas, out);
+}
+
+// Fixed-order sum of n values (or of a[i] * b[i]): CTA partials then one pass.
+__global__ void sum_part_kernel(const float* a, const float* b, int n, float* part) {
+  const int chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  float acc = 0.f;
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += b ? a[i] * b[i] : a[i];
+  for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ float w[8];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int k = 0; k < static_cast<int>(blockDim.x >> 5); ++k) t += w[k];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void sum_final_kernel(const float* part, int ctas, float* out, int accumulate) {
+  if (threadIdx.x != 0) return;
+  float t = 0.f;
+  for (int b = 0; b < ctas; ++b) t += part[b];
+  out[0] = accumulate ? out[0] + t : t;
+}
+
+// out[0] (=, +=) sum_i a[i] (* b[i]); `part` holds RED_CTAS floats
+void vsum(const float* a, const float* b, int n, float* out, bool accumulate, float* part, cudaStream_t s) {
+  const int ctas = red_ctas(n);
+  if (n > 0) sum_part_kernel<<<ctas, 256, 0, s>>>(a, b, n, part);
+  sum_final_kernel<<<1, 32, 0, s>>>(part, n > 0 ? ctas : 0, out, accumulate ? 1 : 0);
 }
 
 // z = h w + b, mu = tanh(z)
@@ -224,36 +302,27 @@ __global__ void head_kernel(const float* hv, long long ld, const float* w, const
   if (mu) mu[v] = tanhf(acc);
 }
 
-// loss += sum_v w_v (softplus(t) - y t) / wsum with t = -2 z; dz = -2 w (sigmoid(t) - y) / wsum
-__global__ void loss_kernel(const float* z, const float* y, const float* wm, float inv_wsum, float* dz, float* loss,
+// l[v] = w_v (softplus(t) - y t) / wsum and dz[v] = -2 w_v (sigmoid(t) - y) / wsum
+// with t = -2 z and wsum = max(sum_v w_v, 1) read from the device
+__global__ void loss_kernel(const float* z, const float* y, const float* wm, const float* wsum, float* dz, float* l,
                             int n) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  float l = 0.f;
-  if (v < n) {
-    const float t = -2.f * z[v];
-    const float wv = wm ? wm[v] : 1.f;
-    const float sp = fmaxf(t, 0.f) + log1pf(expf(-fabsf(t)));
-    l = wv * (sp - y[v] * t) * inv_wsum;
-    const float sig = 1.f / (1.f + expf(-t));
-    dz[v] = -2.f * wv * (sig - y[v]) * inv_wsum;
-  }
-  for (int o = 16; o >= 1; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(loss, l);
+  if (v >= n) return;
+  const float inv = 1.f / fmaxf(wm ? wsum[0] : static_cast<float>(n), 1.f);
+  const float t = -2.f * z[v];
+  const float wv = wm ? wm[v] : 1.f;
+  const float sp = fmaxf(t, 0.f) + log1pf(expf(-fabsf(t)));
+  l[v] = wv * (sp - y[v] * t) * inv;
+  const float sig = 1.f / (1.f + expf(-t));
+  dz[v] = -2.f * wv * (sig - y[v]) * inv;
 }
 
-// dh[v][j] = dz[v] w[j]; gw[j] += sum_v dz[v] h[v][j]; gb += sum_v dz[v]
-__global__ void head_bwd_kernel(const float* dz, const float* hv, long long ld, const float* w, float* dh, float* gw,
-                                float* gb, int n) {
-  const int j = threadIdx.x;
-  float acc = 0.f, accb = 0.f;
-  for (int v = blockIdx.x * blockDim.y + threadIdx.y; v < n; v += gridDim.x * blockDim.y) {
-    const float d = dz[v];
-    dh[v * H + j] = d * w[j];
-    acc = fmaf(d, hv[v * ld + j], acc);
-    if (j == 0) accb += d;
-  }
-  atomicAdd(gw + j, acc);
-  if (j == 0) atomicAdd(gb, accb);
+// dh[v][j] = dz[v] w[j]
+__global__ void head_dh_kernel(const float* dz, const float* w, float* dh, int n) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= static_cast<long long>(n) * H) return;
+  const long long v = i / H;
+  dh[i] = dz[v] * w[i - v * H];
 }
 
 __global__ void adam_kernel(float* th, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
@@ -309,6 +378,60 @@ __global__ void sample_kernel(const float* mu, XT* x, long long pitch, int n, in
   }
 }
 
+// Restart b of variable v (B restarts per instance, state already set):
+// x = clamp(x + alpha_b mu_v, -1, 1), alpha_b ramped from alpha_min (b = 0)
+// to alpha_max (b = B - 1).
+template <typename XT>
+__global__ void nudge_kernel(const float* mu, XT* x, long long pitch, int n, int B, float amin, float amax) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= static_cast<long long>(n) * B) return;
+  const int v = static_cast<int>(i / B), b = static_cast<int>(i - static_cast<long long>(v) * B);
+  const float a = B > 1 ? amin + (amax - amin) * static_cast<float>(b) / (B - 1) : amin;
+  XT* p = x + static_cast<long long>(v) * pitch + b;
+  if constexpr (sizeof(XT) == 4) {
+    *p = fminf(fmaxf(fmaf(a, mu[v], *p), -1.f), 1.f);
+  } else {
+    *p = __float2bfloat16_rn(fminf(fmaxf(fmaf(a, mu[v], __bfloat162float(*p)), -1.f), 1.f));
+  }
+}
+
+// Features from the instance graph: variable v (degree deg, signed balance
+// bal): f_v = (deg/8, bal/max(deg,1), 1, 0), deg_inv = 1/deg (0 if isolated);
+// constraint c (length k): f_c = (one-hot type, k/8, param/k for EK and CARD,
+// parity for XOR, op for CARD, 1, 0...), k_inv = 1/k.
+__global__ void features_kernel(int n, int m, const int* v_off, const int* v_enc, const int* c_off, const int4* cinfo,
+                                float* fv, float* deg_inv, float* fc, float* k_inv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const int e0 = v_off[i], e1 = v_off[i + 1];
+    float bal = 0.f;
+    for (int e = e0; e < e1; ++e) bal += (v_enc[e] & 1) ? -1.f : 1.f;
+    const float deg = static_cast<float>(e1 - e0);
+    deg_inv[i] = deg > 0 ? 1.f / deg : 0.f;
+    fv[static_cast<long long>(i) * FV + 0] = deg / 8.f;
+    fv[static_cast<long long>(i) * FV + 1] = bal / fmaxf(deg, 1.f);
+    fv[static_cast<long long>(i) * FV + 2] = 1.f;
+    fv[static_cast<long long>(i) * FV + 3] = 0.f;
+  }
+  if (i < m) {
+    const int4 ci = cinfo[i];  // {type, op, param, parity}
+    const float k = static_cast<float>(c_off[i + 1] - c_off[i]);
+    k_inv[i] = k > 0 ? 1.f / k : 0.f;
+    float f[FC];
+#pragma unroll
+    for (int q = 0; q < FC; ++q) f[q] = 0.f;
+    f[ci.x] = 1.f;
+    f[7] = k / 8.f;
+    f[8] = (ci.x == AFS_EK || ci.x == AFS_CARD) ? static_cast<float>(ci.z) / fmaxf(k, 1.f) : 0.f;
+    f[9] = ci.x == AFS_XOR ? static_cast<float>(ci.w) : 0.f;
+    f[10] = ci.x == AFS_CARD ? static_cast<float>(ci.y) : 0.f;
+    f[11] = 1.f;
+    float4* dst = reinterpret_cast<float4*>(fc + static_cast<long long>(i) * FC);
+#pragma unroll
+    for (int q = 0; q < FC / 4; ++q) dst[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // per-graph buffers (kept in the handle's extension slot)
 // ---------------------------------------------------------------------------
@@ -332,17 +455,33 @@ struct Dev {
   }
 };
 
+// Device buffers of one graph, carved from a single allocation (one
+// cudaMalloc per bound handle instead of one per buffer).
+template <typename T>
+struct Span {
+  T* p = nullptr;
+  size_t n = 0;
+};
+
+// One handle's graph as the network sees it: the instance's device arrays
+// (built at load) and spans of the network's workspace for the features and
+// activations (attached per call).
 struct Graph {
   int n = 0, m = 0, layers = 0;
-  Dev<int> c_off, c_enc, v_off, v_enc;
-  Dev<float> k_inv, deg_inv, fv, fc;
-  std::vector<Dev<float>> Xv, Xc;  // layers + 1 each: [n x 128], [m x 128]
-  Dev<float> P, Q, z, mu, dz, dhv, dhc, dpre_v, dpre_c, dXv, dXc, dP, dQ, loss;
+  const int *c_off = nullptr, *c_enc = nullptr, *v_off = nullptr, *v_enc = nullptr;
+  const int4* cinfo = nullptr;
+  Span<float> k_inv, deg_inv, fv, fc;
+  std::vector<Span<float>> Xv, Xc;  // layers + 1 each: [n x 128], [m x 128]
+  Span<float> P, Q, z, mu, dz, dhv, dhc, dpre_v, dpre_c, dXv, dXc, dP, dQ, loss;
+  // fixed-order reductions: weight-gradient slices, CTA partials, per-variable
+  // loss terms, the label-mask sum
+  Span<float> wslices, part, lterm, wsum;
 };
 
 void release_graph(void* p) { delete static_cast<Graph*>(p); }
 
 int bind_graph(afs_handle* h, int layers, cudaStream_t s, Graph** out) {
+  (void)s;
   Graph* g = static_cast<Graph*>(handle_ext(h));
   if (g && g->layers == layers) {
     *out = g;
@@ -355,85 +494,56 @@ int bind_graph(afs_handle* h, int layers, cudaStream_t s, Graph** out) {
   g->n = gv.n;
   g->m = gv.m;
   g->layers = layers;
-  const int n = gv.n, m = gv.m;
-  const long long E = gv.lit_off[m];
-  std::vector<int> c_off(gv.lit_off, gv.lit_off + m + 1), c_enc(gv.lit_enc, gv.lit_enc + E);
-  std::vector<int> v_off(n + 1, 0), v_enc(E);
-  std::vector<float> k_inv(m), deg_inv(n), fv(static_cast<size_t>(n) * FV, 0.f), fc(static_cast<size_t>(m) * FC, 0.f);
-  std::vector<float> bal(n, 0.f);
-  for (long long e = 0; e < E; ++e) {
-    const int v = gv.lit_enc[e] >> 1;
-    v_off[v + 1]++;
-    bal[v] += (gv.lit_enc[e] & 1) ? -1.f : 1.f;
-  }
-  for (int v = 0; v < n; ++v) v_off[v + 1] += v_off[v];
-  {
-    std::vector<int> fill(v_off.begin(), v_off.end() - 1);
-    for (int c = 0; c < m; ++c)
-      for (int e = gv.lit_off[c]; e < gv.lit_off[c + 1]; ++e) {
-        const int v = gv.lit_enc[e] >> 1;
-        v_enc[fill[v]++] = (c << 1) | (gv.lit_enc[e] & 1);
-      }
-  }
-  for (int v = 0; v < n; ++v) {
-    const float deg = static_cast<float>(v_off[v + 1] - v_off[v]);
-    deg_inv[v] = deg > 0 ? 1.f / deg : 0.f;
-    fv[static_cast<size_t>(v) * FV + 0] = deg / 8.f;
-    fv[static_cast<size_t>(v) * FV + 1] = bal[v] / std::max(deg, 1.f);
-    fv[static_cast<size_t>(v) * FV + 2] = 1.f;
-  }
-  for (int c = 0; c < m; ++c) {
-    const float k = static_cast<float>(gv.lit_off[c + 1] - gv.lit_off[c]);
-    k_inv[c] = k > 0 ? 1.f / k : 0.f;
-    float* f = &fc[static_cast<size_t>(c) * FC];
-    f[gv.ctype[c]] = 1.f;
-    f[7] = k / 8.f;
-    f[8] = (gv.ctype[c] == AFS_EK || gv.ctype[c] == AFS_CARD) ? gv.cparam[c] / std::max(k, 1.f) : 0.f;
-    f[9] = gv.ctype[c] == AFS_XOR ? static_cast<float>(gv.cparity[c]) : 0.f;
-    f[10] = gv.ctype[c] == AFS_CARD ? static_cast<float>(gv.cop[c]) : 0.f;
-    f[11] = 1.f;
-  }
-  cudaError_t e = cudaSuccess;
-  auto chk = [&](cudaError_t x) {
-    if (x != cudaSuccess && e == cudaSuccess) e = x;
-  };
-  chk(g->c_off.upload(c_off, s));
-  chk(g->c_enc.upload(c_enc, s));
-  chk(g->v_off.upload(v_off, s));
-  chk(g->v_enc.upload(v_enc, s));
-  chk(g->k_inv.upload(k_inv, s));
-  chk(g->deg_inv.upload(deg_inv, s));
-  chk(g->fv.upload(fv, s));
-  chk(g->fc.upload(fc, s));
-  g->Xv.resize(layers + 1);
-  g->Xc.resize(layers + 1);
-  for (int l = 0; l <= layers; ++l) {
-    chk(g->Xv[l].alloc(static_cast<size_t>(n) * 2 * H));
-    chk(g->Xc[l].alloc(static_cast<size_t>(m) * 2 * H));
-  }
-  const size_t nH = static_cast<size_t>(n) * H, mH = static_cast<size_t>(m) * H;
-  chk(g->P.alloc(nH));
-  chk(g->Q.alloc(mH));
-  chk(g->z.alloc(n));
-  chk(g->mu.alloc(n));
-  chk(g->dz.alloc(n));
-  chk(g->dhv.alloc(nH));
-  chk(g->dhc.alloc(mH));
-  chk(g->dpre_v.alloc(nH));
-  chk(g->dpre_c.alloc(mH));
-  chk(g->dXv.alloc(2 * nH));
-  chk(g->dXc.alloc(2 * mH));
-  chk(g->dP.alloc(nH));
-  chk(g->dQ.alloc(mH));
-  chk(g->loss.alloc(1));
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) {
-    delete g;
-    return set_error(AFS_E_CUDA, "mpnn graph buffers: %s", cudaGetErrorString(e));
-  }
+  g->c_off = gv.lit_off_dev;
+  g->c_enc = gv.lit_enc_dev;
+  g->v_off = gv.v_off_dev;
+  g->v_enc = gv.v_enc_dev;
+  g->cinfo = gv.cinfo_dev;
   set_handle_ext(h, g, release_graph);
   *out = g;
   return AFS_OK;
+}
+
+// The activation and reduction buffers of one forward/backward over graph g,
+// carved from a workspace of at least the returned bytes.
+size_t carve_workspace(Graph* g, char* base) {
+  const int n = g->n, m = g->m, layers = g->layers;
+  size_t at = 0;
+  auto take = [&](Span<float>& sp, size_t count) {
+    sp.n = count;
+    if (base) sp.p = reinterpret_cast<float*>(base + at);
+    at += (sizeof(float) * std::max<size_t>(count, 1) + 255) / 256 * 256;
+  };
+  take(g->k_inv, m);
+  take(g->deg_inv, n);
+  take(g->fv, static_cast<size_t>(n) * FV);
+  take(g->fc, static_cast<size_t>(m) * FC);
+  g->Xv.resize(layers + 1);
+  g->Xc.resize(layers + 1);
+  for (int l = 0; l <= layers; ++l) {
+    take(g->Xv[l], static_cast<size_t>(n) * 2 * H);
+    take(g->Xc[l], static_cast<size_t>(m) * 2 * H);
+  }
+  const size_t nH = static_cast<size_t>(n) * H, mH = static_cast<size_t>(m) * H;
+  take(g->P, nH);
+  take(g->Q, mH);
+  take(g->z, n);
+  take(g->mu, n);
+  take(g->dz, n);
+  take(g->dhv, nH);
+  take(g->dhc, mH);
+  take(g->dpre_v, nH);
+  take(g->dpre_c, mH);
+  take(g->dXv, 2 * nH);
+  take(g->dXc, 2 * mH);
+  take(g->dP, nH);
+  take(g->dQ, mH);
+  take(g->loss, 1);
+  take(g->wslices, static_cast<size_t>(wgrad_slices(std::max(n, m))) * H * 2 * H);
+  take(g->part, static_cast<size_t>(RED_CTAS) * H);
+  take(g->lterm, n);
+  take(g->wsum, 1);
+  return at;
 }
 
 }  // namespace
@@ -446,6 +556,13 @@ struct afs_mpnn {
   int layers = 3;
   long long n_params = 0;
   afs::Dev<float> theta, grad, m1, m2;
+  // activation workspace, grown to the largest graph seen and reused by every
+  // call on this network (calls on one network are stream-ordered)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  ~afs_mpnn() {
+    if (ws) cudaFree(ws);
+  }
   long long t = 0;
   // offsets into theta
   long long oAv, oav, oAc, oac, ow, ob;
@@ -453,6 +570,32 @@ struct afs_mpnn {
 };
 
 using afs::H;
+
+// The handle's graph with this network's workspace attached (grown if needed).
+static int bind(afs_mpnn* net, afs_handle* h, cudaStream_t s, afs::Graph** out) {
+  afs::Graph* g = nullptr;
+  int rc = afs::bind_graph(h, net->layers, s, &g);
+  if (rc) return rc;
+  const size_t need = afs::carve_workspace(g, nullptr);
+  if (need > net->ws_bytes) {
+    if (net->ws) {
+      cudaError_t e = cudaStreamSynchronize(s);  // earlier work on the old workspace completes first
+      if (e == cudaSuccess) e = cudaFree(net->ws);
+      net->ws = nullptr;
+      net->ws_bytes = 0;
+      if (e != cudaSuccess) return afs::set_error(AFS_E_CUDA, "mpnn workspace: %s", cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaMalloc(&net->ws, need);
+    if (e != cudaSuccess) {
+      net->ws = nullptr;
+      return afs::set_error(AFS_E_CUDA, "mpnn workspace (%zu bytes): %s", need, cudaGetErrorString(e));
+    }
+    net->ws_bytes = need;
+  }
+  afs::carve_workspace(g, static_cast<char*>(net->ws));
+  *out = g;
+  return AFS_OK;
+}
 
 static long long layout(afs_mpnn* net) {
   long long at = 0;
@@ -488,19 +631,24 @@ static int mpnn_forward(afs_mpnn* net, afs::Graph* g, cudaStream_t s) {
   using namespace afs;
   const float* th = net->theta.p;
   const int n = g->n, m = g->m;
+  if (n > 0 || m > 0) {
+    const int items = std::max(n, m);
+    features_kernel<<<(items + 255) / 256, 256, 0, s>>>(n, m, g->v_off, g->v_enc, g->c_off, g->cinfo, g->fv.p,
+                                                        g->deg_inv.p, g->fc.p, g->k_inv.p);
+  }
   // embeddings into the first halves of the layer-0 inputs
   gemm(g->fv.p, FV, 1, th + net->oAv, 1, FV, g->Xv[0].p, 2 * H, n, H, FV, th + net->oav, true, 0, s);
   gemm(g->fc.p, FC, 1, th + net->oAc, 1, FC, g->Xc[0].p, 2 * H, m, H, FC, th + net->oac, true, 0, s);
   for (int l = 0; l < net->layers; ++l) {
     // P = h_v U^T; m_c = mean s P[v]
     gemm(g->Xv[l].p, 2 * H, 1, th + net->oU[l], 1, H, g->P.p, H, n, H, H, nullptr, false, 0, s);
-    edge_mean(g->c_off.p, g->c_enc.p, g->P.p, H, g->k_inv.p, nullptr, g->Xc[l].p + H, 2 * H, m, s);
+    edge_mean(g->c_off, g->c_enc, g->P.p, H, g->k_inv.p, nullptr, g->Xc[l].p + H, 2 * H, m, s);
     // h_c' = relu([h_c, m_c] Wc^T + bc)
     gemm(g->Xc[l].p, 2 * H, 1, th + net->oWc[l], 1, 2 * H, g->Xc[l + 1].p, 2 * H, m, H, 2 * H, th + net->obc[l], true,
          0, s);
     // Q = h_c' V^T; q_v = mean s Q[c]
     gemm(g->Xc[l + 1].p, 2 * H, 1, th + net->oV[l], 1, H, g->Q.p, H, m, H, H, nullptr, false, 0, s);
-    edge_mean(g->v_off.p, g->v_enc.p, g->Q.p, H, g->deg_inv.p, nullptr, g->Xv[l].p + H, 2 * H, n, s);
+    edge_mean(g->v_off, g->v_enc, g->Q.p, H, g->deg_inv.p, nullptr, g->Xv[l].p + H, 2 * H, n, s);
     // h_v' = relu([h_v, q_v] Wv^T + bv)
     gemm(g->Xv[l].p, 2 * H, 1, th + net->oWv[l], 1, 2 * H, g->Xv[l + 1].p, 2 * H, n, H, 2 * H, th + net->obv[l], true,
          0, s);
@@ -518,41 +666,46 @@ static int mpnn_backward(afs_mpnn* net, afs::Graph* g, cudaStream_t s) {
   float* gr = net->grad.p;
   const int n = g->n, m = g->m, L = net->layers;
   MCK(cudaMemsetAsync(gr, 0, sizeof(float) * net->n_params, s));
+  float* ws = g->wslices.p;
+  float* pt = g->part.p;
+  // head: gw = sum_v dz_v h_v, gb = sum_v dz_v, dh_v = dz_v w
+  colsum(g->Xv[L].p, 2 * H, n, gr + net->ow, pt, s, g->dz.p);
+  vsum(g->dz.p, nullptr, n, gr + net->ob, true, pt, s);
   if (n > 0)
-    head_bwd_kernel<<<std::min(256, (n + 3) / 4), dim3(H, 4), 0, s>>>(g->dz.p, g->Xv[L].p, 2 * H, th + net->ow,
-                                                                       g->dhv.p, gr + net->ow, gr + net->ob, n);
+    head_dh_kernel<<<static_cast<unsigned>((static_cast<long long>(n) * H + 255) / 256), 256, 0, s>>>(
+        g->dz.p, th + net->ow, g->dhv.p, n);
   MCK(cudaMemsetAsync(g->dhc.p, 0, sizeof(float) * static_cast<size_t>(m) * H, s));
   for (int l = L - 1; l >= 0; --l) {
     // variable update: h_v' = relu(Xv Wv^T + bv)
     copy_mask(g->dhv.p, H, g->Xv[l + 1].p, 2 * H, g->dpre_v.p, H, n, s);
-    gemm(g->dpre_v.p, 1, H, g->Xv[l].p, 2 * H, 1, gr + net->oWv[l], 2 * H, H, 2 * H, n, nullptr, false, 2, s);
-    colsum(g->dpre_v.p, H, n, gr + net->obv[l], s);
+    gemm(g->dpre_v.p, 1, H, g->Xv[l].p, 2 * H, 1, gr + net->oWv[l], 2 * H, H, 2 * H, n, nullptr, false, 2, s, ws);
+    colsum(g->dpre_v.p, H, n, gr + net->obv[l], pt, s);
     gemm(g->dpre_v.p, H, 1, th + net->oWv[l], 2 * H, 1, g->dXv.p, 2 * H, n, 2 * H, H, nullptr, false, 0, s);
     // q_v = mean_{e at v} s Q[c]  ->  dQ[c] = sum_{e in c} s dq[v] / deg_v
-    edge_mean(g->c_off.p, g->c_enc.p, g->dXv.p + H, 2 * H, nullptr, g->deg_inv.p, g->dQ.p, H, m, s);
+    edge_mean(g->c_off, g->c_enc, g->dXv.p + H, 2 * H, nullptr, g->deg_inv.p, g->dQ.p, H, m, s);
     // Q = h_c' V^T
-    gemm(g->dQ.p, 1, H, g->Xc[l + 1].p, 2 * H, 1, gr + net->oV[l], H, H, H, m, nullptr, false, 2, s);
+    gemm(g->dQ.p, 1, H, g->Xc[l + 1].p, 2 * H, 1, gr + net->oV[l], H, H, H, m, nullptr, false, 2, s, ws);
     gemm(g->dQ.p, H, 1, th + net->oV[l], H, 1, g->dhc.p, H, m, H, H, nullptr, false, 1, s);
     // constraint update: h_c' = relu(Xc Wc^T + bc)
     copy_mask(g->dhc.p, H, g->Xc[l + 1].p, 2 * H, g->dpre_c.p, H, m, s);
-    gemm(g->dpre_c.p, 1, H, g->Xc[l].p, 2 * H, 1, gr + net->oWc[l], 2 * H, H, 2 * H, m, nullptr, false, 2, s);
-    colsum(g->dpre_c.p, H, m, gr + net->obc[l], s);
+    gemm(g->dpre_c.p, 1, H, g->Xc[l].p, 2 * H, 1, gr + net->oWc[l], 2 * H, H, 2 * H, m, nullptr, false, 2, s, ws);
+    colsum(g->dpre_c.p, H, m, gr + net->obc[l], pt, s);
     gemm(g->dpre_c.p, H, 1, th + net->oWc[l], 2 * H, 1, g->dXc.p, 2 * H, m, 2 * H, H, nullptr, false, 0, s);
     copy_mask(g->dXc.p, 2 * H, nullptr, 0, g->dhc.p, H, m, s);
     // m_c = mean_{e in c} s P[v]  ->  dP[v] = sum_{e at v} s dm[c] / k_c
-    edge_mean(g->v_off.p, g->v_enc.p, g->dXc.p + H, 2 * H, nullptr, g->k_inv.p, g->dP.p, H, n, s);
+    edge_mean(g->v_off, g->v_enc, g->dXc.p + H, 2 * H, nullptr, g->k_inv.p, g->dP.p, H, n, s);
     // P = h_v U^T
-    gemm(g->dP.p, 1, H, g->Xv[l].p, 2 * H, 1, gr + net->oU[l], H, H, H, n, nullptr, false, 2, s);
+    gemm(g->dP.p, 1, H, g->Xv[l].p, 2 * H, 1, gr + net->oU[l], H, H, H, n, nullptr, false, 2, s, ws);
     copy_mask(g->dXv.p, 2 * H, nullptr, 0, g->dhv.p, H, n, s);
     gemm(g->dP.p, H, 1, th + net->oU[l], H, 1, g->dhv.p, H, n, H, H, nullptr, false, 1, s);
   }
   // embeddings
   copy_mask(g->dhv.p, H, g->Xv[0].p, 2 * H, g->dpre_v.p, H, n, s);
-  gemm(g->dpre_v.p, 1, H, g->fv.p, FV, 1, gr + net->oAv, FV, H, FV, n, nullptr, false, 2, s);
-  colsum(g->dpre_v.p, H, n, gr + net->oav, s);
+  gemm(g->dpre_v.p, 1, H, g->fv.p, FV, 1, gr + net->oAv, FV, H, FV, n, nullptr, false, 2, s, ws);
+  colsum(g->dpre_v.p, H, n, gr + net->oav, pt, s);
   copy_mask(g->dhc.p, H, g->Xc[0].p, 2 * H, g->dpre_c.p, H, m, s);
-  gemm(g->dpre_c.p, 1, H, g->fc.p, FC, 1, gr + net->oAc, FC, H, FC, m, nullptr, false, 2, s);
-  colsum(g->dpre_c.p, H, m, gr + net->oac, s);
+  gemm(g->dpre_c.p, 1, H, g->fc.p, FC, 1, gr + net->oAc, FC, H, FC, m, nullptr, false, 2, s, ws);
+  colsum(g->dpre_c.p, H, m, gr + net->oac, pt, s);
   MCKL();
   return AFS_OK;
 }
@@ -625,7 +778,7 @@ int afs_mpnn_forward(afs_mpnn* net, afs_handle* h, float* mu_dev, void* stream) 
   if (!net || !h) return afs::set_error(AFS_E_ARG, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   afs::Graph* g = nullptr;
-  int rc = afs::bind_graph(h, net->layers, s, &g);
+  int rc = bind(net, h, s, &g);
   if (rc) return rc;
   rc = mpnn_forward(net, g, s);
   if (rc) return rc;
@@ -634,19 +787,20 @@ int afs_mpnn_forward(afs_mpnn* net, afs_handle* h, float* mu_dev, void* stream) 
   return AFS_OK;
 }
 
-int afs_mpnn_loss_grad(afs_mpnn* net, afs_handle* h, const float* y_dev, const float* w_dev, float wsum,
-                       float* grad_dev, float* loss_host, void* stream) {
+int afs_mpnn_loss_grad(afs_mpnn* net, afs_handle* h, const float* y_dev, const float* w_dev, float* grad_dev,
+                       float* loss_host, void* stream) {
   if (!net || !h || !y_dev) return afs::set_error(AFS_E_ARG, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   afs::Graph* g = nullptr;
-  int rc = afs::bind_graph(h, net->layers, s, &g);
+  int rc = bind(net, h, s, &g);
   if (rc) return rc;
   rc = mpnn_forward(net, g, s);
   if (rc) return rc;
-  MCK(cudaMemsetAsync(g->loss.p, 0, sizeof(float), s));
-  const float inv = 1.0f / (wsum > 1.0f ? wsum : 1.0f);
+  // the label-mask sum and the loss are fixed-order device reductions
+  if (w_dev) afs::vsum(w_dev, nullptr, g->n, g->wsum.p, false, g->part.p, s);
   if (g->n > 0)
-    afs::loss_kernel<<<(g->n + 255) / 256, 256, 0, s>>>(g->z.p, y_dev, w_dev, inv, g->dz.p, g->loss.p, g->n);
+    afs::loss_kernel<<<(g->n + 255) / 256, 256, 0, s>>>(g->z.p, y_dev, w_dev, g->wsum.p, g->dz.p, g->lterm.p, g->n);
+  afs::vsum(g->lterm.p, nullptr, g->n, g->loss.p, false, g->part.p, s);
   MCKL();
   rc = mpnn_backward(net, g, s);
   if (rc) return rc;
@@ -682,7 +836,7 @@ int afs_mpnn_init_restarts(afs_mpnn* net, afs_handle* h, int32_t B, uint64_t see
   if (rc) return rc;
   if (gv.B != B || gv.x == nullptr) return afs::set_error(AFS_E_STATE, "afs_init_restarts(B) must come first");
   afs::Graph* g = nullptr;
-  rc = afs::bind_graph(h, net->layers, s, &g);
+  rc = bind(net, h, s, &g);
   if (rc) return rc;
   rc = mpnn_forward(net, g, s);
   if (rc) return rc;
@@ -696,6 +850,32 @@ int afs_mpnn_init_restarts(afs_mpnn* net, afs_handle* h, int32_t B, uint64_t see
     else
       afs::sample_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(g->mu.p, static_cast<__nv_bfloat16*>(gv.x), gv.pitch,
                                                                gv.n, B, B_learn, sigma_min, sigma_max, seed);
+  }
+  MCKL();
+  return afs::state_written(h, s);
+}
+
+int afs_mpnn_nudge_restarts(afs_mpnn* net, afs_handle* h, float alpha_min, float alpha_max, void* stream) {
+  if (!net || !h) return afs::set_error(AFS_E_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  afs::GraphView gv{};
+  int rc = afs::graph_view(h, &gv);
+  if (rc) return rc;
+  if (gv.B <= 0 || gv.x == nullptr) return afs::set_error(AFS_E_STATE, "afs_init_restarts must come first");
+  afs::Graph* g = nullptr;
+  rc = bind(net, h, s, &g);
+  if (rc) return rc;
+  rc = mpnn_forward(net, g, s);
+  if (rc) return rc;
+  const long long total = static_cast<long long>(gv.n) * gv.B;
+  if (total > 0) {
+    const unsigned blocks = static_cast<unsigned>((total + 255) / 256);
+    if (gv.xt == afs::XT_F32)
+      afs::nudge_kernel<float><<<blocks, 256, 0, s>>>(g->mu.p, static_cast<float*>(gv.x), gv.pitch, gv.n, gv.B,
+                                                      alpha_min, alpha_max);
+    else
+      afs::nudge_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(g->mu.p, static_cast<__nv_bfloat16*>(gv.x), gv.pitch,
+                                                              gv.n, gv.B, alpha_min, alpha_max);
   }
   MCKL();
   return afs::state_written(h, s);

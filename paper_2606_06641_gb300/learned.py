@@ -9,8 +9,9 @@ only sequences the calls:
 * ``train``: mini-batch Adam over handles that each hold a group of labelled
   instances (the message passing runs over the disjoint union).
 * ``evaluate``: the same held-out instances and the same step budget, solved
-  from learned starts (mu plus ramped noise, a fixed fraction of restarts kept
-  uniform) and from uniform starts.
+  from learned starts (the uniform starts nudged toward mu with a strength
+  ramped over the restarts, or mu plus ramped noise with a share of restarts
+  kept uniform) and from uniform starts.
 """
 from __future__ import annotations
 
@@ -88,9 +89,16 @@ def train(net: bd.Mpnn, batches, epochs: int, lr: float, seed: int = 0, log_ever
     return hist
 
 
+# Starting points from the network: ("nudge", alpha_min, alpha_max) moves the
+# uniform starts toward mu (x = clamp(u + alpha_b mu), alpha ramped over the
+# restarts, the uniform draws the same as the plain form's); ("sample",
+# uniform_frac, sigma_min, sigma_max) draws x = clamp(mu + sigma_b eps) for
+# a share of the restarts and keeps the rest uniform.
+DEFAULT_START = ("nudge", 0.0, 0.5)
+
+
 def evaluate(net: Optional[bd.Mpnn], insts: Sequence[Instance], B: int, eta: float, max_steps: int,
-             seed: int = 0, steps_per_poll: int = 10, uniform_frac: float = 0.5,
-             sigma_min: float = 0.3, sigma_max: float = 1.5):
+             seed: int = 0, steps_per_poll: int = 10, start=DEFAULT_START):
     """Batched solve of `insts` from learned starts (net given) or uniform starts
     (net None). Returns (solved[bool], steps[int], seconds per instance, total)."""
     import torch
@@ -99,8 +107,10 @@ def evaluate(net: Optional[bd.Mpnn], insts: Sequence[Instance], B: int, eta: flo
     h = bd.load_batch(insts, bd.default_params(eta=eta, verify_every=1, autotune=0))
     bd.init_restarts(h, B, seed=seed)
     if net is not None:
-        net.init_restarts(h, B, seed=seed + 1, uniform_frac=uniform_frac, sigma_min=sigma_min,
-                          sigma_max=sigma_max)
+        if start[0] == "nudge":
+            net.nudge_restarts(h, alpha_min=start[1], alpha_max=start[2])
+        else:
+            net.init_restarts(h, B, seed=seed + 1, uniform_frac=start[1], sigma_min=start[2], sigma_max=start[3])
     solved = np.zeros(n, bool)
     steps = np.full(n, max_steps, np.int64)
     secs = np.zeros(n)

@@ -1,11 +1,14 @@
-"""What the trained initialiser gains over uniform starts (small scale).
+"""What the trained initialiser gains over uniform starts.
 
-Labels come from the descent's own solutions on training instances of the
-n=50, m=213 random 3-SAT distribution; held-out instances are solved from
-learned and from uniform starts with the same restarts and step budget.
-The network must fit better than an untrained one on held-out labels, and
-learned starts (with a quarter of the restarts kept uniform) must not lose
-solves; the measured solve rates and step counts are printed.
+The learned-initialiser configuration at full size: 10000 training instances
+of the n=50, m=213 random 3-SAT distribution labelled with the distinct
+solutions the descent itself finds, 512 held-out instances, B=256 restarts,
+500 steps. Held-out instances are solved from uniform starts and from the same
+uniform starts nudged toward the network's proposal (x = clamp(u + alpha_b mu),
+alpha ramped from 0 to 0.5 over the restarts). The learned starts must solve
+at least as many held-out instances and take fewer steps on the instances both
+forms solve; the network must also fit the held-out labels better than an
+untrained one. Every reported solution is re-checked exactly by the solver.
 """
 import numpy as np
 import pytest
@@ -32,26 +35,26 @@ def _held_out_loss(net, batches):
 
 
 def test_learned_starts_gain_over_uniform():
-    eta, steps = 0.1, 500
-    train = [synth.learned_split(i, "train") for i in range(1500)]
-    test = [synth.learned_split(i, "test") for i in range(160)]
+    eta, steps, B = 0.1, 500, 256
+    train = [synth.learned_split(i, "train") for i in range(10000)]
+    test = [synth.learned_split(i, "test") for i in range(512)]
     lab_tr = learned.harvest(train, 64, eta, steps, seed=1)
     lab_te = learned.harvest(test, 64, eta, steps, seed=2)
-    assert len(lab_tr.insts) > 200 and len(lab_te.insts) > 20
+    assert len(lab_tr.insts) > 2000 and len(lab_te.insts) > 100
     tr_b = learned.make_batches(lab_tr, 64)
     te_b = learned.make_batches(lab_te, 64)
     untrained = bd.Mpnn(layers=3, seed=7)
     net = bd.Mpnn(layers=3, seed=7)
     loss0 = _held_out_loss(untrained, te_b)
-    hist = learned.train(net, tr_b, 25, 3e-3)
+    hist = learned.train(net, tr_b, 30, 3e-3)
     loss1 = _held_out_loss(net, te_b)
-    assert hist[-1] < hist[0]
-    assert loss1 < loss0, (loss0, loss1)
-    s_u, st_u, _, _ = learned.evaluate(None, test, 64, eta, steps, seed=3)
-    s_l, st_l, _, _ = learned.evaluate(net, test, 64, eta, steps, seed=3)
+    assert hist[-1] < hist[0] and loss1 < loss0, (hist[0], hist[-1], loss0, loss1)
+    s_u, st_u, _, _ = learned.evaluate(None, test, B, eta, steps, seed=3)
+    s_l, st_l, _, _ = learned.evaluate(net, test, B, eta, steps, seed=3, start=learned.DEFAULT_START)
     both = s_u & s_l
-    print(f"\nheld-out BCE untrained {loss0:.4f} trained {loss1:.4f}; solve rate uniform {s_u.mean():.3f} "
-          f"learned {s_l.mean():.3f}; median steps uniform {np.median(st_u[s_u]) if s_u.any() else None} "
-          f"learned {np.median(st_l[s_l]) if s_l.any() else None}; paired step gain on both-solved "
-          f"{np.median(st_u[both] - st_l[both]) if both.any() else None}")
-    assert s_l.sum() >= 0.8 * s_u.sum()
+    gain = st_u[both] - st_l[both]
+    print(f"\nheld-out BCE untrained {loss0:.4f} trained {loss1:.4f}; solved uniform {int(s_u.sum())} "
+          f"learned {int(s_l.sum())} of {len(test)}; median steps uniform {np.median(st_u[s_u])} learned "
+          f"{np.median(st_l[s_l])}; paired step gain median {np.median(gain)} mean {gain.mean():.2f}")
+    assert s_l.sum() >= s_u.sum()
+    assert np.median(gain) > 0 and gain.mean() > 0

@@ -1,10 +1,13 @@
 """GPU checks of the learned initialiser's kernels against the FP64 reference.
 
-The reference rounds every matrix-product operand to bfloat16, as the tensor
-core path does, so the remaining differences come from FP32 accumulation and
-from FP32 activations landing on the other side of a bfloat16 rounding
-boundary: outputs agree to 3e-3, gradients to 3e-2 per tensor (relative L2)
-with cosine similarity above 0.999.
+The reference is run twice: rounding every dense-layer operand to bfloat16
+(the operand precision the network is specified with: BF16 weights and
+activations, FP32 accumulation) and in plain FP64. Forward outputs are
+compared element by element (3e-3 and 3e-2); gradients element by element per
+parameter entry with the criteria of ``mpnn_criteria`` (every entry within
+atol * scale + rtol * |ref|, 95% of entries within a tighter atol). The
+gradient must also be bit-identical from call to call (fixed-order
+reductions).
 """
 import numpy as np
 import pytest
@@ -14,6 +17,8 @@ torch = pytest.importorskip("torch")
 from oracle import mpnn_oracle as M
 from paper_2606_06641_gb300 import binding as bd
 from paper_2606_06641_gb300 import synth
+
+from mpnn_criteria import BF16_REF, FP64_REF, grad_mismatches
 
 pytestmark = pytest.mark.gpu
 
@@ -48,27 +53,27 @@ def test_forward_matches_reference():
     assert np.abs(mu - mu64).max() <= 3e-2
 
 
-def test_loss_and_gradient_match_reference():
+@pytest.mark.parametrize("seed", [2, 3, 4])
+def test_loss_and_gradient_match_reference(seed):
     insts, union = _graph()
     h = bd.load_batch(insts)
-    net = bd.Mpnn(layers=3, seed=2)
-    rng = np.random.default_rng(0)
+    net = bd.Mpnn(layers=3, seed=seed)
+    rng = np.random.default_rng(seed)
     y = rng.uniform(0, 1, union.n).astype(np.float32)
     w = (rng.random(union.n) < 0.7).astype(np.float32)
-    loss, g = net.loss_grad(h, torch.from_numpy(y).cuda(), torch.from_numpy(w).cuda(), want_grad=True)
+    yd, wd = torch.from_numpy(y).cuda(), torch.from_numpy(w).cuda()
+    loss, g = net.loss_grad(h, yd, wd, want_grad=True)
+    loss2, g2 = net.loss_grad(h, yd, wd, want_grad=True)
+    assert torch.equal(g, g2) and loss == loss2          # deterministic reductions
     g = g.cpu().numpy().astype(np.float64)
     theta = net.get_params().cpu().numpy().astype(np.float64)
+    shapes = M.param_shapes(64, 3)
     ref_loss, ref_g, _ = M.loss_and_grad(union, theta, y.astype(np.float64), w.astype(np.float64), 64, 3, bf16=True)
-    assert abs(loss - ref_loss) <= 1e-3 * max(1.0, abs(ref_loss))
-    cos = g @ ref_g / (np.linalg.norm(g) * np.linalg.norm(ref_g))
-    assert cos > 0.999, cos
-    at = 0
-    for name, shp in M.param_shapes(64, 3):
-        size = int(np.prod(shp))
-        a, b = g[at:at + size], ref_g[at:at + size]
-        at += size
-        if np.linalg.norm(b) > 1e-6:
-            assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b), name
+    assert abs(loss - ref_loss) <= 1e-4 * max(1.0, abs(ref_loss))
+    assert grad_mismatches(g, ref_g, shapes, **BF16_REF) == []
+    l64, g64, _ = M.loss_and_grad(union, theta, y.astype(np.float64), w.astype(np.float64), 64, 3, bf16=False)
+    assert abs(loss - l64) <= 1e-2 * max(1.0, abs(l64))
+    assert grad_mismatches(g, g64, shapes, **FP64_REF) == []
 
 
 def test_adam_step_matches_reference():

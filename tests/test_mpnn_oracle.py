@@ -67,3 +67,39 @@ def test_adam_first_step_is_sign_times_lr():
     g = np.array([0.5, -2.0, 1e-3])
     new, m, v = M.adam_step(th, g, np.zeros(3), np.zeros(3), 1, 0.01)
     np.testing.assert_allclose(new, -0.01 * np.sign(g), rtol=1e-4)
+
+
+def test_gradient_criteria_detect_planted_errors():
+    """The element-wise criteria the GPU test applies accept the bfloat16-operand
+    reference against the plain FP64 one (the FP64 criterion) and reject a
+    gradient with one large entry's sign flipped or a weight gradient
+    transposed (both planted in the oracle's own gradient)."""
+    from mpnn_criteria import BF16_REF, FP64_REF, grad_mismatches
+    H, L = 64, 3
+    inst = synth.concat_instances([synth.random_3sat_n50(i) for i in range(2)])
+    shapes = M.param_shapes(H, L)
+    n_par = sum(int(np.prod(s)) for _, s in shapes)
+    rng = np.random.default_rng(3)
+    theta = np.concatenate([rng.uniform(-1, 1, int(np.prod(s))) * np.sqrt(3.0 / (s[-1] if len(s) > 1 else H))
+                            for _, s in shapes])
+    assert theta.size == n_par
+    y = rng.uniform(0, 1, inst.n)
+    w = (rng.random(inst.n) < 0.7).astype(np.float64)
+    _, g_bf, _ = M.loss_and_grad(inst, theta, y, w, H, L, bf16=True)
+    _, g64, _ = M.loss_and_grad(inst, theta, y, w, H, L, bf16=False)
+    assert grad_mismatches(g_bf, g_bf, shapes, **BF16_REF) == []
+    assert grad_mismatches(g_bf, g64, shapes, **FP64_REF) == []
+    at = 0
+    for name, shp in shapes:
+        size = int(np.prod(shp))
+        seg = g_bf[at:at + size]
+        if np.abs(seg).max() > 0:
+            bad = g_bf.copy()
+            i = at + int(np.argmax(np.abs(seg)))
+            bad[i] = -bad[i]
+            assert name in grad_mismatches(bad, g_bf, shapes, **BF16_REF), name
+            if len(shp) == 2 and shp[0] == shp[1]:
+                bad = g_bf.copy()
+                bad[at:at + size] = seg.reshape(shp).T.ravel()
+                assert name in grad_mismatches(bad, g_bf, shapes, **BF16_REF), name
+        at += size
