@@ -209,9 +209,11 @@ int afs_set_fixed(afs_handle* h, const int8_t* values_host, int32_t n_groups, vo
 int afs_get_step_check(const afs_handle* h, uint32_t* out_dev, int32_t* words_per_inst, void* stream);
 
 /* afs_eval_fe_grad: evaluate, for the restarts given in x_dev, every
- * constraint's expansion fe_dev[c * B + b] (constraints in load order,
- * nullable) and the objective's gradient grad_dev[v * B + b] (nullable), with
- * the same kernels as afs_step but without updating anything. x_dtype is
+ * constraint's Fourier expansion fe_dev[c * B + b] (Eq. 1 evaluated as
+ * products at the roots of unity, Sec. 2.1.2; constraints in load order,
+ * nullable) and the gradient of the objective sum_c FE_c (Sec. 2.1.1)
+ * grad_dev[v * B + b] (nullable), with the same kernels as afs_step but
+ * without updating anything. x_dtype is
  * AFS_X_F32 (x_dev is float) or AFS_X_BF16 (x_dev is bfloat16). B may differ
  * from the handle's restart count. */
 int afs_eval_fe_grad(afs_handle* h, const void* x_dev, int32_t x_dtype, int32_t B, float* fe_dev,

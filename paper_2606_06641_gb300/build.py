@@ -2,9 +2,11 @@
 
 Every translation unit under csrc/ is compiled in parallel with nvcc
 (``-gencode arch=compute_103a,code=sm_103a``), then linked into
-``_lib/libafsat.so`` with the CUDA runtime linked statically. Objects live in
-``_build/``; a unit is recompiled when it or any header is newer than its
-object.
+``_lib/libafsat.so`` with the CUDA runtime linked statically. The short
+FE+gradient kernel's dispatch (csrc/short_dispatch.cuh) is instantiated in
+four generated translation units, one per (basis, state type), written to
+``_build/gen/`` so that they compile in parallel. Objects live in ``_build/``;
+a unit is recompiled when it or any header is newer than its object.
 """
 from __future__ import annotations
 
@@ -23,8 +25,28 @@ LIB_PATH = os.path.join(LIB_DIR, "libafsat.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-O2", f"-I{INCLUDE}", f"-I{CSRC}"]
-SOURCES = ["host.cpp", "coef.cpp", "kernels.cu", "long_pgf.cu", "short_pgf_f32.cu", "short_pgf_bf16.cu",
-           "short_esp_f32.cu", "short_esp_bf16.cu", "noalloc.cu", "mpnn.cu"]
+SOURCES = ["host.cpp", "coef.cpp", "kernels.cu", "long_pgf.cu", "noalloc.cu", "mpnn.cu"]
+# generated units: (name, state type, paper basis)
+SHORT_UNITS = [("short_pgf_f32", "float", "false"), ("short_pgf_bf16", "__nv_bfloat16", "false"),
+               ("short_esp_f32", "float", "true"), ("short_esp_bf16", "__nv_bfloat16", "true")]
+
+
+def _generate_short_units() -> list:
+    gen = os.path.join(BUILD_DIR, "gen")
+    os.makedirs(gen, exist_ok=True)
+    paths = []
+    for name, xt, esp in SHORT_UNITS:
+        text = ("// generated by build.py: the short kernel's dispatch for one (basis, state type)\n"
+                '#include "short_dispatch.cuh"\n'
+                f"namespace afs {{\nbool launch_{name}(const FeGroupArgs& a, int rpl, int warps, cudaStream_t s) {{\n"
+                f"  return launch_short<{xt}, {esp}>(a, rpl, warps, s);\n}}\n}}  // namespace afs\n")
+        p = os.path.join(gen, name + ".cu")
+        old = open(p).read() if os.path.exists(p) else None
+        if old != text:
+            with open(p, "w") as fh:
+                fh.write(text)
+        paths.append(p)
+    return paths
 
 
 def _nvcc() -> str:
@@ -47,9 +69,8 @@ def build(verbose: bool = False, force: bool = False, jobs: int = 0) -> str:
     hdr = _headers_mtime()
     todo = []
     objs = []
-    for src in SOURCES:
-        sp = os.path.join(CSRC, src)
-        op = os.path.join(BUILD_DIR, src + ".o")
+    for sp in [os.path.join(CSRC, src) for src in SOURCES] + _generate_short_units():
+        op = os.path.join(BUILD_DIR, os.path.basename(sp) + ".o")
         objs.append(op)
         if force or not os.path.exists(op) or os.path.getmtime(op) < max(os.path.getmtime(sp), hdr):
             todo.append((sp, op))

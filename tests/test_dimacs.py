@@ -1,6 +1,7 @@
 """The DIMACS / hybrid-format reader (Appendix A): grammar, type identifiers,
-CARD normalisation, the simplifier's reductions, and a round trip. Inputs are
-written here for these checks (they are not the appendix's example file)."""
+CARD normalisation, the simplifier's reductions, a round trip, and the
+appendix's own worked example (tests/golden/appendix_a_example.txt, parsed
+verbatim). The other inputs are written here for these checks."""
 import numpy as np
 import pytest
 
@@ -127,3 +128,39 @@ def test_round_trip_through_the_writer():
 def test_malformed_input_is_rejected(text):
     with pytest.raises(dimacs.ParseError):
         dimacs.parse(text)
+
+
+def _appendix_blocks():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "appendix_a_example.txt")
+    with open(path) as fh:
+        blocks = fh.read().split("\n\n")
+    # keep the blocks that hold more than comment lines ('c' as the first token)
+    return [b for b in blocks if any(ln.split() and ln.split()[0] != "c" for ln in b.splitlines())]
+
+
+def test_appendix_example_blocks_parse_verbatim():
+    """The appendix's worked example (inline 'c' comments after the
+    terminating 0, the 'h' prefix, 'h d >=2', plain and signed CARD
+    thresholds) parses block by block into the constraints it describes, and
+    each constraint's truth table is the one the appendix states."""
+    cnf, hybrid, cards = [dimacs.parse(b, simplify=False) for b in _appendix_blocks()]
+    assert cnf.declared == (4, 2) and [list(cnf.inst.constraint(c)) for c in range(2)] == [[1, -2, 3], [-1, 4]]
+    assert list(cnf.inst.ctype) == [synth.OR, synth.OR]
+    assert hybrid.declared == (6, 7)
+    assert list(hybrid.inst.ctype) == [synth.OR, synth.XOR, synth.NAE, synth.AMO, synth.EO, synth.EK, synth.CARD]
+    assert [list(hybrid.inst.constraint(c)) for c in range(7)] == [[1, -2, 3], [1, 2, 3], [1, 2, 3], [1, 2, 3],
+                                                                   [4, 5, 6], [1, 2, 3], [1, 2, 3]]
+    assert int(hybrid.inst.param[5]) == 2 and (int(hybrid.inst.op[6]), int(hybrid.inst.param[6])) == (O.OP_GE, 2)
+    assert cards.declared is None and cards.inst.m == 4
+    # the semantics records list the examples in the same order (the CNF
+    # block's clauses share the first record's OR table)
+    recs = []
+    with open(__file__.replace("test_dimacs.py", "golden/appendix_a_semantics.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                recs.append([int(v) for v in line.split()[5:]])
+    got = [O.truth_table(int(p.inst.ctype[c]), int(np.diff(p.inst.lit_off)[c]), int(p.inst.op[c]),
+                         int(p.inst.param[c]), int(p.inst.parity[c])).tolist()
+           for p in (hybrid, cards) for c in range(p.inst.m)]
+    assert got == recs

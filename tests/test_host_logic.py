@@ -352,3 +352,50 @@ def test_long_pgf_table_forms_stay_in_range(k):
             assert gmax <= 1.0 / s_mod * (1 + 1e-5)        # |g| <= 1/|s| (|f| <= 1)
             assert gmax ** 8 < 2.0 ** 120
             assert abs(s16) >= 2.0 ** -100
+
+
+def _paper_basis_fp64(c, ell):
+    """Sec. 2.1.2's products in the paper's basis in FP64: the DFT over d of
+    f_hat(|S| = d) combined with prod_i (1 + w^j l_i) at the k+1 roots."""
+    k = ell.size
+    N = k + 1
+    w = np.exp(2j * np.pi * np.arange(N) / N)
+    d = np.arange(k + 1)
+    chat = np.array([np.sum(c * w[j] ** (-d)) for j in range(N)]) / N
+    return float(np.real(np.sum(chat * np.prod(1 + np.outer(w, ell), axis=1))))
+
+
+def _pgf_basis_fp64(f, ell):
+    """The probability-generating basis in FP64: DFT of the truth table
+    combined with prod_i (q_i + p_i w^j)."""
+    k = ell.size
+    N = k + 1
+    w = np.exp(2j * np.pi * np.arange(N) / N)
+    ft = np.fft.fft(f.astype(np.float64)) / N          # sum_t f(t) w^{-jt} / N
+    p = (1 - ell) / 2
+    return float(np.real(np.sum(ft * np.prod((1 - p)[None, :] + np.outer(w, p), axis=1))))
+
+
+def test_paper_basis_fp64_ceiling():
+    """Sec. 3.4's floating-point limit, reproduced from the library's exact
+    ESP coefficients: evaluated in FP64, the paper's basis loses accuracy as
+    the products reach 2^k near the all-false vertex (the satisfying region of
+    an at-most-one constraint), from about 1e-5 at k = 40 to a degenerate
+    1e-2 at k = 48 and worse beyond; the probability-generating basis stays
+    at rounding level at the same points."""
+    rng = np.random.default_rng(0)
+    worst = {}
+    for k in (32, 40, 48, 56, 64):
+        c = bd.esp_coefficients(O.T_AMO, k)
+        f = O.truth_table(O.T_AMO, k)
+        e_paper, e_pgf = [], []
+        for _ in range(10):
+            ell = 1.0 - 0.05 * rng.random(k)
+            ref = O.fe(f, ell[None])[0]
+            e_paper.append(abs(_paper_basis_fp64(c, ell) - ref))
+            e_pgf.append(abs(_pgf_basis_fp64(f, ell) - ref))
+        worst[k] = max(e_paper)
+        assert max(e_pgf) < 1e-12, (k, max(e_pgf))
+    assert worst[32] < 1e-5 and worst[40] < 1e-3
+    assert worst[48] > 1e-3 and worst[56] > 1e-1 and worst[64] > 1.0
+    assert worst[32] < worst[40] < worst[48] < worst[56] < worst[64]
