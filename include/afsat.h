@@ -233,9 +233,12 @@ int afs_eval_fe_grad(afs_handle* h, const void* x_dev, int32_t x_dtype, int32_t 
  * in constraints of length 3 (probability-generating basis) need no row:
  * their derivatives are recomputed in the gather. The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture. All calls share the one array
- * and its contents carry over from the last call, so calls whose work
- * overlaps on the GPU (different streams, or different handles at once)
+ * that first call before any stream capture. The address is kept for the
+ * life of the process: after a device reset (cudaDeviceReset, or another
+ * component resetting the primary context) it is stale, so do not use the
+ * entry point on that device again in the same process. All calls share the
+ * one array and its contents carry over from the last call, so calls whose
+ * work overlaps on the GPU (different streams, or different handles at once)
  * race; serialise them. */
 int afs_eval_fe_grad_noalloc(afs_handle* h, const float* x_dev, int32_t B, float* fe_dev, float* grad_dev,
                              void* stream);

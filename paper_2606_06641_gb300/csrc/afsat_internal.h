@@ -222,11 +222,11 @@ int state_written(afs_handle* h, cudaStream_t s);
 void* handle_ext(const afs_handle* h);
 void set_handle_ext(afs_handle* h, void* p, void (*release)(void*));
 
-// FE and gradient of FP32 x[v * B + b] into fe/grad (nullable) using the
-// caller-provided occurrence-derivative buffer `scratch` of `cap_floats`
-// floats; allocates nothing. Restarts are processed in column chunks sized
-// to fit the buffer.
-int eval_into_scratch(afs_handle* h, const float* x, int B, float* fe, float* grad, float* scratch,
+// FE and gradient of x[v * B + b] (state type xt) into fe/grad (nullable)
+// using the caller-provided occurrence-derivative buffer `scratch` of
+// `cap_floats` floats; allocates nothing. Restarts are processed in column
+// chunks of at most 256, shrunk (by 32) until a chunk fits the buffer.
+int eval_into_scratch(afs_handle* h, const void* x, int xt, int B, float* fe, float* grad, float* scratch,
                       long long cap_floats, cudaStream_t s);
 
 // Restarts per lane available for a short group of length k.

@@ -1278,7 +1278,7 @@ void afs::set_handle_ext(afs_handle* h, void* p, void (*release)(void*)) {
   h->ext_release = release;
 }
 
-int afs::eval_into_scratch(afs_handle* h, const float* x, int B, float* fe, float* grad, float* scratch,
+int afs::eval_into_scratch(afs_handle* h, const void* x, int xt, int B, float* fe, float* grad, float* scratch,
                            long long cap_floats, cudaStream_t s) {
   if (!h || !x || !scratch) return fail(AFS_E_ARG, "NULL argument");
   if (B <= 0) return fail(AFS_E_ARG, "B must be positive");
@@ -1293,11 +1293,11 @@ int afs::eval_into_scratch(afs_handle* h, const float* x, int B, float* fe, floa
   for (int b0 = 0; b0 < B; b0 += static_cast<int>(cols)) {
     const int nb = std::min(static_cast<int>(cols), B - b0);
     for (const Group& g : h->groups) {
-      int rc = launch_fe_group(h, g, x, XT_F32, B, b0, nb, scratch, cols, fe, B, s);
+      int rc = launch_fe_group(h, g, x, xt, B, b0, nb, scratch, cols, fe, B, s);
       if (rc) return rc;
     }
     if (grad) {
-      int rc = launch_csr(h, x, nullptr, XT_F32, B, b0, nb, scratch, cols, 0.0f, grad, B, false, -1, s);
+      int rc = launch_csr(h, x, nullptr, xt, B, b0, nb, scratch, cols, 0.0f, grad, B, false, -1, s);
       if (rc) return rc;
     }
   }
@@ -1597,24 +1597,16 @@ int afs_eval_fe_grad(afs_handle* h, const void* x_dev, int32_t x_dtype, int32_t 
   if (x_dtype != AFS_X_F32 && x_dtype != AFS_X_BF16) return fail(AFS_E_ARG, "unknown x dtype");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int xt = x_dtype == AFS_X_BF16 ? XT_BF16 : XT_F32;
+  // a derivative buffer for chunks of up to 256 restarts (kept by the handle),
+  // then the same chunk loop as the entry point that allocates nothing
   const int cols = std::min<int>((B + 31) / 32 * 32, 256);
-  const size_t need = sizeof(float) * static_cast<size_t>(std::max<long long>(h->Lgo, 1)) * cols;
-  if (h->eval_go.bytes < need) {
-    int rc = h->eval_go.alloc(need);
+  const long long cap = std::max<long long>(h->Lgo, 1) * cols;
+  if (h->eval_go.bytes < sizeof(float) * static_cast<size_t>(cap)) {
+    int rc = h->eval_go.alloc(sizeof(float) * static_cast<size_t>(cap));
     if (rc) return rc;
   }
-  for (int b0 = 0; b0 < B; b0 += cols) {
-    const int nb = std::min(cols, B - b0);
-    for (const Group& g : h->groups) {
-      int rc = launch_fe_group(h, g, x_dev, xt, B, b0, nb, h->eval_go.as<float>(), cols, fe_dev, B, s);
-      if (rc) return rc;
-    }
-    if (grad_dev) {
-      int rc = launch_csr(h, x_dev, nullptr, xt, B, b0, nb, h->eval_go.as<float>(), cols, 0.0f, grad_dev, B, false, -1, s);
-      if (rc) return rc;
-    }
-  }
-  return AFS_OK;
+  return eval_into_scratch(h, x_dev, xt, B, fe_dev, grad_dev, h->eval_go.as<float>(),
+                           static_cast<long long>(h->eval_go.bytes / sizeof(float)), s);
 }
 
 // FE of every constraint (load order, rows of pitch floats) and, with g, the

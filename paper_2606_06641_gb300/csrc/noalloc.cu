@@ -31,7 +31,11 @@ void* g_scratch_dev[kMaxDevices] = {};
 
 // Device address of g_scratch on the current device. In host code the name
 // g_scratch is only a host-side stand-in, so the address is looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached. A device reset
+// (cudaDeviceReset, or another component resetting the primary context)
+// unloads the library's device module and makes the cached address stale:
+// the entry point must not be used on a device after such a reset in the same
+// process.
 int scratch_address(float** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -60,6 +64,6 @@ extern "C" int afs_eval_fe_grad_noalloc(afs_handle* h, const float* x_dev, int32
   if (rc != AFS_OK) return rc;
   // Nothing in the buffer needs to start at zero: every derivative a gradient
   // sum reads is written by the FE kernels of the same column chunk first.
-  return afs::eval_into_scratch(h, x_dev, B, fe_dev, grad_dev, scratch, kScratchFloats,
+  return afs::eval_into_scratch(h, x_dev, afs::XT_F32, B, fe_dev, grad_dev, scratch, kScratchFloats,
                                 static_cast<cudaStream_t>(stream));
 }

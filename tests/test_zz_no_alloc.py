@@ -92,3 +92,24 @@ def test_noalloc_takes_large_instances_of_short_constraints():
     bd.eval_fe_grad_noalloc(h, x, fe, g)
     torch.cuda.synchronize()
     assert torch.equal(fe, fe_ref) and torch.equal(g, g_ref)
+
+
+def test_noalloc_shrinks_chunks_to_the_array():
+    """40000 occurrences of 4-clauses (each with a derivative row): a chunk of
+    256 restarts would need 40 MB, so the entry point shrinks its chunks to 96
+    restarts (96 x 40000 x 4 bytes fits 16 MiB) and walks B = 300 restarts in
+    four chunks (96, 96, 96, 12); results equal the allocating entry point's."""
+    inst = synth.random_ksat(5000, 10000, 4, synth.rng_for(400, 2))
+    assert 16384 < inst.n_lits <= 131072
+    h = bd.load_instance(inst)
+    B = 300
+    for call, seed in enumerate((5, 6)):
+        x = _dev(synth.uniform_x0(inst.n, B, seed))
+        fe_ref, g_ref = bd.eval_fe_grad(h, x)
+        fe = torch.full((inst.m, B), float("nan"), device="cuda")
+        g = torch.full((inst.n, B), float("nan"), device="cuda")
+        bd.eval_fe_grad_noalloc(h, x, fe, g)
+        torch.cuda.synchronize()
+        fe_err = (fe - fe_ref).abs().max().item()
+        g_err = (g - g_ref).abs().max().item()
+        assert fe_err <= TOL and g_err <= TOL, (call, fe_err, g_err)
