@@ -723,6 +723,12 @@ def run_batch_sweep(args):
     L = sum(i.n_lits for i in insts)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    # half a second of device work first, so that the first point does not
+    # run at the idle clocks
+    t_end = time.time() + 0.5
+    while time.time() < t_end:
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
     rows = []
     for B in [int(b) for b in args.sweep_b.split(",")]:
         params = bd.default_params(eta=0.1, verify_every=1)

@@ -88,7 +88,11 @@ typedef struct afs_params {
   int32_t autotune;     /* 1 = time tile shapes per bucket at init           */
   int32_t use_graph;    /* 1 = replay afs_step (and repeated afs_step_ls
                            calls) as captured CUDA graphs                   */
-  int32_t reserved;
+  int32_t persistent;   /* steps as one persistent launch (every constraint
+                           of length <= 32, probability-generating basis,
+                           all restarts in one chunk): 0 = the autotuner
+                           times it against graph replay, 1 = on where
+                           possible, -1 = off                               */
 } afs_params;
 
 typedef struct afs_handle afs_handle;
@@ -340,6 +344,12 @@ int afs_tiles(const afs_handle* h, int32_t* chunk, int32_t* rpl_by_k, int32_t* c
  * changes and AFS_E_ARG is returned. Cached step graphs are dropped. */
 int afs_set_tiles(afs_handle* h, int32_t chunk, const int32_t* rpl_by_k, const int32_t* cpw_by_k, int32_t kcap);
 
+/* afs_step_mode: whether afs_step runs its steps as one persistent
+ * cooperative launch (*persistent = 1; *blocks = its grid) or as the
+ * per-step launches of the length buckets, the check and the CSR pass
+ * (replayed as graphs). Decided at afs_init_restarts (afs_params.persistent,
+ * timed by the autotuner when 0). No device work. */
+int afs_step_mode(const afs_handle* h, int32_t* persistent, int32_t* blocks);
 /* afs_group_times: event-timed FE+gradient launches of each launch group of
  * the step (bucket order) over the current restart chunk of the current
  * state, on `stream`: reps launches per group, ms[i] = mean milliseconds per

@@ -72,6 +72,7 @@ SIGNATURES = {
     "afs_set_tiles": (_I32, [_P, _I32, _P, _P, _I32]),
     "afs_long_tiles": (_I32, [_P, _P, _P, _P, _I32, _P]),
     "afs_group_times": (_I32, [_P, _I32, _P, _P, _P, _P, _I32, _P, _P]),
+    "afs_step_mode": (_I32, [_P, _P, _P]),
     "afs_set_long_tiles": (_I32, [_P, _P, _P, _I32]),
     "afs_coef_table": (_I32, [_I32, _I32, _I32, _I32, _I32, _I32, _I32, _P, _I32, _P]),
     "afs_esp_coefficients": (_I32, [_I32, _I32, _I32, _I32, _I32, _P]),
@@ -88,7 +89,7 @@ class AfsError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("eta", ctypes.c_float), ("basis", _I32), ("x_storage", _I32), ("verify_every", _I32),
-                ("chunk", _I32), ("autotune", _I32), ("use_graph", _I32), ("reserved", _I32)]
+                ("chunk", _I32), ("autotune", _I32), ("use_graph", _I32), ("persistent", _I32)]
 
 
 _lib = None
@@ -453,6 +454,14 @@ def set_tiles(h: Handle, chunk: int = 0, tiles=None):
         rpl[int(k)] = int(r)
         cpw[int(k)] = int(c)
     _check(lib().afs_set_tiles(h.ptr, int(chunk), rpl, cpw, 33))
+
+
+def step_mode(h: Handle):
+    """(persistent, blocks): whether afs_step runs as one persistent launch, and its grid."""
+    p = ctypes.c_int32()
+    bl = ctypes.c_int32()
+    _check(lib().afs_step_mode(h.ptr, ctypes.byref(p), ctypes.byref(bl)))
+    return bool(p.value), bl.value
 
 
 def group_times(h: Handle, reps: int = 3, stream=None):

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(LIB_DIR, "libafsat.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-O2", f"-I{INCLUDE}", f"-I{CSRC}"]
-SOURCES = ["host.cpp", "coef.cpp", "kernels.cu", "long_pgf.cu", "noalloc.cu", "mpnn.cu"]
+SOURCES = ["host.cpp", "coef.cpp", "kernels.cu", "long_pgf.cu", "persist.cu", "noalloc.cu", "mpnn.cu"]
 # generated units: (name, state type, paper basis)
 SHORT_UNITS = [("short_pgf_f32", "float", "false"), ("short_pgf_bf16", "__nv_bfloat16", "false"),
                ("short_esp_f32", "float", "true"), ("short_esp_bf16", "__nv_bfloat16", "true")]

@@ -119,6 +119,13 @@ struct CheckArgs {
   int B;                    // restarts per instance (count mode)
 };
 void launch_check_bits(const CheckArgs& a, cudaStream_t s);
+// The per-step check for few restart words (W <= CHECK_WIDE_MAX_W) and
+// constraints of at most 62 literals, one constraint per lane: `ranges` are
+// then runs of <= 31 constraints of one instance with <= CHECK_WIDE_STAGE
+// literals in all, for the words w0 .. w0 + wc - 1 (count mode with unsat).
+constexpr int CHECK_WIDE_STAGE = 256;
+constexpr int CHECK_WIDE_MAX_W = 8;
+void launch_check_wide(const CheckArgs& a, cudaStream_t s);
 
 // Line search (afs_step_ls). Per-restart objective: out[inst * B + b] =
 // sum of fe[c * pitch + b] over the constraints c of each instance (cinst[c]
@@ -151,6 +158,42 @@ void launch_solved_words(const unsigned* vword, int n_inst, int W, int B, unsign
 // p[0..n) = v
 void launch_fill_int(int* p, int v, long long n, cudaStream_t s);
 
+
+// Persistent step kernel (persist.cu): S whole steps in one cooperative
+// launch for handles whose constraints are all short (k <= 32), one chunk of
+// all B restarts. Short groups run one restart per lane and one constraint
+// per warp unit.
+constexpr int PERSIST_MAX_GROUPS = 32;
+constexpr int PERSIST_WARPS = 8;  // warps per block of the persistent kernel
+struct PersistGroup {
+  int k, c_begin, c_count;
+  unsigned unit0, units;    // the group's units in phase A: unit0 .. unit0 + units - 1
+  long long lit_base;
+};
+struct PersistArgs {
+  FeGroupArgs fe;           // common FE arguments (x, k and the group range set per unit)
+  const PersistGroup* groups;
+  int ng;
+  // phase A's units: the FE groups' (group table unit0 .. + count), the fused
+  // sums' (fus0 .. + fus_units) and the check's (chk0 .. + chk_units), a_units
+  // in all, numbered in decreasing expected cost
+  unsigned a_units, chk0, chk_units, chk_chunks, fus0, fus_units, csr_units;
+  int chk_wide;             // the check's units are (wide run, word) pairs: chk_chunks = W
+  CheckArgs chk;            // vword set per step
+  CsrArgs fus;              // fused sums into gf (x set per step)
+  CsrArgs csr;              // step-mode CSR (x, x_out, vcur, vnext set per step)
+  void* xb0;                // the double-buffered state (step t reads parity (parity0 + t) & 1)
+  void* xb1;
+  unsigned* vw0;            // check words of parity 0 and 1
+  unsigned* vw1;
+  int parity0, nsteps, check, B;
+  unsigned* bar;            // grid barrier: {arrivals, generation}
+  int* err;
+  long long wait_limit;
+};
+// Blocks of the persistent kernel resident on the whole device (0 on error).
+int persistent_grid(int xt);
+cudaError_t launch_persistent(const PersistArgs& a, int xt, int blocks, cudaStream_t s);
 
 // Launch wrappers (kernels.cu / short_*.cu).
 // Return false if no kernel exists for (k, rpl).

@@ -26,49 +26,89 @@
 
 namespace afs {
 
-template <typename XT>
+// State loads. COH = false: through the read-only data cache (__ldg), for
+// data no thread writes during the kernel. COH = true: L2-coherent loads
+// (__ldcg, bypassing L1), for data written by other thread blocks earlier in
+// the same (persistent) kernel.
+template <bool COH>
+__device__ __forceinline__ float ld_f(const float* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ unsigned short ld_u16(const unsigned short* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ float2 ld_f2(const float2* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ float4 ld_f4(const float4* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ unsigned ld_u32(const unsigned* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ uint2 ld_u2(const uint2* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+
+template <typename XT, bool COH = false>
 __device__ __forceinline__ float load_x(const XT* p);
 template <>
-__device__ __forceinline__ float load_x<float>(const float* p) {
-  return __ldg(p);
+__device__ __forceinline__ float load_x<float, false>(const float* p) {
+  return ld_f<false>(p);
 }
 template <>
-__device__ __forceinline__ float load_x<__nv_bfloat16>(const __nv_bfloat16* p) {
-  const unsigned short u = __ldg(reinterpret_cast<const unsigned short*>(p));
-  return __uint_as_float(static_cast<unsigned int>(u) << 16);
+__device__ __forceinline__ float load_x<float, true>(const float* p) {
+  return ld_f<true>(p);
+}
+template <>
+__device__ __forceinline__ float load_x<__nv_bfloat16, false>(const __nv_bfloat16* p) {
+  return __uint_as_float(static_cast<unsigned int>(ld_u16<false>(reinterpret_cast<const unsigned short*>(p))) << 16);
+}
+template <>
+__device__ __forceinline__ float load_x<__nv_bfloat16, true>(const __nv_bfloat16* p) {
+  return __uint_as_float(static_cast<unsigned int>(ld_u16<true>(reinterpret_cast<const unsigned short*>(p))) << 16);
 }
 
 // N consecutive state values with one vector load (N = 2 or 4; 16-byte or
 // 8-byte alignment for FP32, 8- or 4-byte for BF16)
-template <typename XT, int N>
-__device__ __forceinline__ void load_xvec(const XT* p, float (&v)[N]);
-template <>
-__device__ __forceinline__ void load_xvec<float, 2>(const float* p, float (&v)[2]) {
-  const float2 t = __ldg(reinterpret_cast<const float2*>(p));
-  v[0] = t.x;
-  v[1] = t.y;
-}
-template <>
-__device__ __forceinline__ void load_xvec<float, 4>(const float* p, float (&v)[4]) {
-  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
-  v[0] = t.x;
-  v[1] = t.y;
-  v[2] = t.z;
-  v[3] = t.w;
-}
-template <>
-__device__ __forceinline__ void load_xvec<__nv_bfloat16, 2>(const __nv_bfloat16* p, float (&v)[2]) {
-  const unsigned t = __ldg(reinterpret_cast<const unsigned*>(p));
-  v[0] = __uint_as_float(t << 16);
-  v[1] = __uint_as_float(t & 0xffff0000u);
-}
-template <>
-__device__ __forceinline__ void load_xvec<__nv_bfloat16, 4>(const __nv_bfloat16* p, float (&v)[4]) {
-  const uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
-  v[0] = __uint_as_float(t.x << 16);
-  v[1] = __uint_as_float(t.x & 0xffff0000u);
-  v[2] = __uint_as_float(t.y << 16);
-  v[3] = __uint_as_float(t.y & 0xffff0000u);
+template <typename XT, int N, bool COH = false>
+__device__ __forceinline__ void load_xvec(const XT* p, float (&v)[N]) {
+  if constexpr (sizeof(XT) == 4) {
+    if constexpr (N == 2) {
+      const float2 t = ld_f2<COH>(reinterpret_cast<const float2*>(p));
+      v[0] = t.x;
+      v[1] = t.y;
+    } else {
+      const float4 t = ld_f4<COH>(reinterpret_cast<const float4*>(p));
+      v[0] = t.x;
+      v[1] = t.y;
+      v[2] = t.z;
+      v[3] = t.w;
+    }
+  } else {
+    if constexpr (N == 2) {
+      const unsigned t = ld_u32<COH>(reinterpret_cast<const unsigned*>(p));
+      v[0] = __uint_as_float(t << 16);
+      v[1] = __uint_as_float(t & 0xffff0000u);
+    } else {
+      const uint2 t = ld_u2<COH>(reinterpret_cast<const uint2*>(p));
+      v[0] = __uint_as_float(t.x << 16);
+      v[1] = __uint_as_float(t.x & 0xffff0000u);
+      v[2] = __uint_as_float(t.y << 16);
+      v[3] = __uint_as_float(t.y & 0xffff0000u);
+    }
+  }
 }
 template <int N>
 __device__ __forceinline__ void store_fvec(float* p, const float (&v)[N]);
@@ -94,12 +134,11 @@ __device__ __forceinline__ float mul_recompute(float a, float b) {
   return r;
 }
 
-template <int K, int RPL, typename XT, bool SHIFT, bool VEC>
-__global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
-  pdl_wait();
-  pdl_trigger();
-  const int lane = threadIdx.x & 31;
-  const long long warp = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+// One warp's unit of a short group: `warp` indexes (constraint chunk of
+// a.cpw constraints, tile of 32 * RPL restarts). COH: the state is read with
+// L2-coherent loads (it was written earlier in the same persistent kernel).
+template <int K, int RPL, typename XT, bool SHIFT, bool VEC, bool COH>
+__device__ __forceinline__ void short_unit(const FeGroupArgs& a, long long warp, int lane) {
   constexpr int TW = 32 * RPL;
   const int tiles = (a.nb + TW - 1) / TW;
   const long long cg = warp / tiles;
@@ -132,7 +171,7 @@ __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
       if constexpr (V) {
         float xv[RPL];
         if (act[0]) {
-          load_xvec<XT, RPL>(x + row + bl[0], xv);
+          load_xvec<XT, RPL, COH>(x + row + bl[0], xv);
         } else {
 #pragma unroll
           for (int r = 0; r < RPL; ++r) xv[r] = 0.0f;
@@ -141,7 +180,7 @@ __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
         for (int r = 0; r < RPL; ++r) l[r][i] = xv[r] * sg;
       } else {
 #pragma unroll
-        for (int r = 0; r < RPL; ++r) l[r][i] = (act[r] ? load_x<XT>(x + row + bl[r]) : 0.0f) * sg;
+        for (int r = 0; r < RPL; ++r) l[r][i] = (act[r] ? load_x<XT, COH>(x + row + bl[r]) : 0.0f) * sg;
       }
     }
 
@@ -315,6 +354,14 @@ __global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
         if (act[r]) a.fe[orow + bl[r]] = fe[r];
     }
   }
+}
+
+template <int K, int RPL, typename XT, bool SHIFT, bool VEC>
+__global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  const long long warp = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  short_unit<K, RPL, XT, SHIFT, VEC, false>(a, warp, static_cast<int>(threadIdx.x & 31));
 }
 
 template <int K, int RPL, typename XT, bool SHIFT>

@@ -210,10 +210,12 @@ struct afs_handle {
   // (spans of inst_arena, which is declared first so that it is freed last)
   DevBuf inst_arena;
   DevBuf litslot, cons_tab, cons_orig, cons_k, cons_lit, coef, csr_off, lit_enc, lit_off, viol_off, viol,
-      var_inst, err, chk_em, chk_ranges, fus_off, fus, cinst;
+      var_inst, err, chk_em, chk_ranges, chk_wide, fus_off, fus, cinst;
   // the instance graph by variable and per-constraint records (the learned initialiser's inputs)
   DevBuf v_off, v_enc, cinfo;
   int n_chk_ranges = 0;
+  int n_chk_wide = 0;       // runs of the lane-per-constraint check (chk_wide_ok)
+  bool chk_wide_ok = false;
   // restart state
   int B = 0, xt = XT_F32;
   long long pitch = 0;
@@ -237,6 +239,13 @@ struct afs_handle {
   bool step_check_valid = false;  // vword[parity ^ 1] holds the last step's check
   bool count_valid = false;       // unsat holds the exact count of the current state
   long long eval_go_cols = 0;
+  // persistent step mode (all constraints short, one chunk): S steps per
+  // cooperative launch; group table and grid-barrier words on the device
+  bool persist = false;
+  DevBuf pgroups, pbar;
+  std::vector<PersistGroup> h_pgroups;
+  int persist_B = -1, persist_Bc = -1, persist_blocks = 0;
+  unsigned persist_a_units = 0, persist_fus0 = 0, persist_chk0 = 0;
   // graphs
   cudaStream_t cap = nullptr;
   // the length buckets of a chunk are launched concurrently on these streams
@@ -618,6 +627,25 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     }
   }
   h->n_chk_ranges = static_cast<int>(chk_ranges.size());
+  // runs for the lane-per-constraint check of few restart words: <= 31
+  // constraints of one instance, <= CHECK_WIDE_STAGE literals (only when no
+  // constraint is longer than 62 literals)
+  std::vector<int4> chk_wide;
+  h->chk_wide_ok = true;
+  for (int g = 0; g < m; ++g) h->chk_wide_ok = h->chk_wide_ok && gk[g] <= 62;
+  if (h->chk_wide_ok) {
+    for (int i = 0; i < n_inst; ++i) {
+      int c = h->inst_cbegin[i];
+      const int ce = h->inst_cbegin[i + 1];
+      while (c < ce) {
+        int e = c, lits_in = 0;
+        while (e < ce && e - c < 31 && lits_in + gk[e] <= CHECK_WIDE_STAGE) lits_in += gk[e++];
+        chk_wide.push_back(make_int4(c, e, i, 0));
+        c = e;
+      }
+    }
+  }
+  h->n_chk_wide = static_cast<int>(chk_wide.size());
   h->h_var_inst.resize(h->n);
   for (int i = 0; i < n_inst; ++i)
     for (int v = h->inst_vbegin[i]; v < h->inst_vbegin[i + 1]; ++v) h->h_var_inst[v] = i;
@@ -659,6 +687,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   up.add(h->var_inst, var_inst_ext);
   up.add(h->chk_em, chk_em);
   up.add(h->chk_ranges, chk_ranges);
+  up.add(h->chk_wide, chk_wide);
   up.add(h->err, zero1);
   up.add(h->v_off, v_off_h);
   up.add(h->v_enc, v_enc_h);
@@ -840,6 +869,10 @@ static int launch_fused(afs_handle* h, const void* x, int b0, int nb, cudaStream
 
 // Standalone exact check of the state x (whose sign words are current) into
 // h->unsat: the bit-sliced check in count mode, then the solved fold.
+// The checks take one constraint per lane when the restarts fill few words
+// (a lane per word would leave most of each warp idle).
+static bool use_wide_check(const afs_handle* h) { return h->chk_wide_ok && h->W <= CHECK_WIDE_MAX_W; }
+
 static int launch_check(afs_handle* h, const void* x, cudaStream_t s) {
   (void)x;
   CK(cudaMemsetAsync(h->unsat.p, 0, sizeof(int) * static_cast<size_t>(h->n_inst) * h->B, s));
@@ -857,7 +890,13 @@ static int launch_check(afs_handle* h, const void* x, cudaStream_t s) {
   c.n_ranges = h->n_chk_ranges;
   c.unsat = h->unsat.as<int>();
   c.B = h->B;
-  launch_check_bits(c, s);
+  if (use_wide_check(h)) {
+    c.ranges = h->chk_wide.as<int4>();
+    c.n_ranges = h->n_chk_wide;
+    launch_check_wide(c, s);
+  } else {
+    launch_check_bits(c, s);
+  }
   CKL();
   launch_solved(h->unsat.as<int>(), h->n_inst, h->B, h->solved.as<int>(), s);
   CKL();
@@ -889,7 +928,13 @@ static void launch_check_step(afs_handle* h, int p, cudaStream_t s) {
   c.ranges = h->chk_ranges.as<int4>();
   c.n_ranges = h->n_chk_ranges;
   c.vword = h->vword.as<unsigned>() + static_cast<size_t>(p) * h->n_inst * h->W;
-  launch_check_bits(c, s);
+  if (use_wide_check(h)) {
+    c.ranges = h->chk_wide.as<int4>();
+    c.n_ranges = h->n_chk_wide;
+    launch_check_wide(c, s);
+  } else {
+    launch_check_bits(c, s);
+  }
 }
 
 // The fused pass is enqueued before the FE launches of a chunk (true) or after
@@ -910,8 +955,172 @@ constexpr bool BUCKETS_ON_AUX = true;
 // failed the check, writes the sign words of x_{t+1}, records solved restarts
 // and clears the words of parity 1 - p. With `check`, a standalone exact
 // check of the final state ends the sequence.
+// The persistent step mode applies to probability-generating handles whose
+// constraints are all short (k <= 32) and whose restarts form one chunk.
+static bool persist_eligible(const afs_handle* h) {
+  if (h->p.basis != AFS_BASIS_PGF || h->p.persistent < 0 || h->B <= 0 || h->Bc < h->B) return false;
+  int ng = 0;
+  for (const Group& g : h->groups) {
+    if (g.is_long) return false;
+    if (!g.fused) ++ng;
+  }
+  return ng <= PERSIST_MAX_GROUPS;
+}
+
+// (Re)build the persistent mode's group table and barrier words for the
+// current restart count and chunk.
+static int persist_prepare(afs_handle* h, cudaStream_t s) {
+  if (h->persist_B == h->B && h->persist_Bc == h->Bc && h->persist_blocks > 0) return AFS_OK;
+  const unsigned tiles32 = static_cast<unsigned>((h->B + 31) / 32);
+  const unsigned tiles128 = static_cast<unsigned>((h->B + 127) / 128);
+  // phase A's units in decreasing expected cost (the kernel's warps take
+  // them in snake order, pairing the costliest with the cheapest): FE groups
+  // of k >= 8 by decreasing k, the fused sums, the check, the shorter groups
+  std::vector<int> fe_order(h->step_order);
+  std::stable_sort(fe_order.begin(), fe_order.end(),
+                   [&](int x, int y) { return h->groups[x].k > h->groups[y].k; });
+  h->h_pgroups.clear();
+  unsigned u = 0;
+  auto add_groups = [&](bool heavy) {
+    for (int gi : fe_order) {
+      const Group& g = h->groups[gi];
+      if ((g.k >= 8) != heavy) continue;
+      const unsigned nu = static_cast<unsigned>(g.c_count) * tiles32;
+      h->h_pgroups.push_back(PersistGroup{g.k, g.c_begin, g.c_count, u, nu, g.lit_base});
+      u += nu;
+    }
+  };
+  add_groups(true);
+  h->persist_fus0 = u;
+  u += h->n_fused > 0 ? static_cast<unsigned>(h->n) * tiles128 : 0u;
+  h->persist_chk0 = u;
+  u += use_wide_check(h) ? static_cast<unsigned>(h->n_chk_wide) * static_cast<unsigned>(h->W)
+                         : static_cast<unsigned>(h->n_chk_ranges) * ((h->W + 31) / 32);
+  add_groups(false);
+  h->persist_a_units = u;
+  int rc = h->pgroups.alloc(sizeof(PersistGroup) * std::max<size_t>(h->h_pgroups.size(), 1));
+  if (rc) return rc;
+  if (!h->h_pgroups.empty())
+    CK(cudaMemcpyAsync(h->pgroups.p, h->h_pgroups.data(), sizeof(PersistGroup) * h->h_pgroups.size(),
+                       cudaMemcpyHostToDevice, s));
+  if (h->pbar.bytes < 2 * sizeof(unsigned)) {
+    if ((rc = h->pbar.alloc(2 * sizeof(unsigned)))) return rc;
+    CK(cudaMemsetAsync(h->pbar.p, 0, 2 * sizeof(unsigned), s));
+  }
+  const unsigned a_units = u;
+  const unsigned b_units = static_cast<unsigned>(h->n) * tiles128;
+  const long long want = (std::max(a_units, b_units) + PERSIST_WARPS - 1) / PERSIST_WARPS;
+  const int grid = persistent_grid(h->xt);
+  if (grid <= 0) return fail(AFS_E_CUDA, "persistent step kernel: no resident blocks");
+  h->persist_blocks = static_cast<int>(std::max<long long>(1, std::min<long long>(grid, want)));
+  h->persist_B = h->B;
+  h->persist_Bc = h->Bc;
+  return AFS_OK;
+}
+
+// nsteps whole steps as one persistent launch.
+static int enqueue_persistent(afs_handle* h, int nsteps, float eta, bool check, int parity0, cudaStream_t s) {
+  int rc = persist_prepare(h, s);
+  if (rc) return rc;
+  PersistArgs a{};
+  FeGroupArgs& f = a.fe;
+  f.x_pitch = h->pitch;
+  f.b0 = 0;
+  f.nb = h->B;
+  f.litslot = h->litslot.as<int2>();
+  f.cons_tab = h->cons_tab.as<int>();
+  f.cons_orig = h->cons_orig.as<int>();
+  f.coef = h->coef.as<float4>();
+  f.cons_k = h->cons_k.as<int>();
+  f.cons_lit = h->cons_lit.as<int>();
+  f.go = h->go.as<float>();
+  f.go_pitch = h->Bc;
+  f.fe = nullptr;
+  f.err = h->err.as<int>();
+  f.cpw = 1;
+  f.vec = 0;
+  a.groups = h->pgroups.as<PersistGroup>();
+  a.ng = static_cast<int>(h->h_pgroups.size());
+  const unsigned tiles128 = static_cast<unsigned>((h->B + 127) / 128);
+  a.a_units = h->persist_a_units;
+  a.chk0 = h->persist_chk0;
+  a.fus0 = h->persist_fus0;
+  a.chk_wide = use_wide_check(h) ? 1 : 0;
+  a.chk_chunks = a.chk_wide ? static_cast<unsigned>(h->W) : static_cast<unsigned>((h->W + 31) / 32);
+  a.chk_units = static_cast<unsigned>(a.chk_wide ? h->n_chk_wide : h->n_chk_ranges) * a.chk_chunks;
+  CheckArgs& c = a.chk;
+  c.sgn = h->sgn.as<unsigned>();
+  c.W = h->W;
+  c.w0 = 0;
+  c.wc = h->W;
+  c.lit_enc = h->lit_enc.as<int>();
+  c.lit_off = h->lit_off.as<int>();
+  c.em = h->chk_em.as<unsigned long long>();
+  c.viol_off = h->viol_off.as<int>();
+  c.viol = h->viol.as<unsigned char>();
+  c.ranges = a.chk_wide ? h->chk_wide.as<int4>() : h->chk_ranges.as<int4>();
+  c.n_ranges = a.chk_wide ? h->n_chk_wide : h->n_chk_ranges;
+  CsrArgs& u = a.fus;
+  u.x_pitch = h->pitch;
+  u.b0 = 0;
+  u.nb = h->B;
+  u.v_begin = 0;
+  u.v_count = h->n;
+  u.fus_off = h->fus_off.as<int>();
+  u.fus = h->fus.as<float4>();
+  u.coef = h->coef.as<float4>();
+  u.gf = h->gf.as<float>();
+  u.gf_pitch = h->Bc;
+  a.fus_units = h->n_fused > 0 ? static_cast<unsigned>(h->n) * tiles128 : 0u;
+  CsrArgs& r = a.csr;
+  r.x_pitch = h->pitch;
+  r.b0 = 0;
+  r.nb = h->B;
+  r.csr_off = h->csr_off.as<int>();
+  r.fus_off = h->fus_off.as<int>();
+  r.fus = h->fus.as<float4>();
+  r.coef = h->coef.as<float4>();
+  r.v_begin = 0;
+  r.v_count = h->n;
+  r.go = h->go.as<float>();
+  r.go_pitch = h->Bc;
+  r.go_rows = h->Lgo;
+  r.eta = eta;
+  r.grad = nullptr;
+  r.var_inst = h->var_inst.as<int>();
+  r.n_vars = h->n;
+  r.W = h->W;
+  r.B = h->B;
+  r.solved = h->solved.as<int>();
+  r.sgn = h->sgn.as<unsigned>();
+  r.discard_go = 0;
+  r.fixv = h->fix_groups > 0 ? h->fixv.as<signed char>() : nullptr;
+  r.n_fix_groups = h->fix_groups;
+  r.gf = h->n_fused > 0 ? h->gf.as<float>() : nullptr;
+  r.gf_pitch = h->Bc;
+  a.csr_units = static_cast<unsigned>(h->n) * tiles128;
+  a.xb0 = h->xb[0].p;
+  a.xb1 = h->xb[1].p;
+  const size_t niw = static_cast<size_t>(h->n_inst) * h->W;
+  a.vw0 = h->vword.as<unsigned>();
+  a.vw1 = h->vword.as<unsigned>() + niw;
+  a.parity0 = parity0;
+  a.nsteps = nsteps;
+  a.check = check ? 1 : 0;
+  a.B = h->B;
+  a.bar = h->pbar.as<unsigned>();
+  a.err = h->err.as<int>();
+  a.wait_limit = h->dbg_wait_limit;
+  CK(launch_persistent(a, h->xt, h->persist_blocks, s));
+  return AFS_OK;
+}
+
 static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int parity0, cudaStream_t s,
                          long long* launches) {
+  if (h->persist && !h->timing) {
+    if (launches) *launches = 1;
+    return enqueue_persistent(h, nsteps, eta, check, parity0, s);
+  }
   long long nl = 0;
   int ev = 0;
   for (int t = 0; t < nsteps; ++t) {
@@ -1041,11 +1250,12 @@ static double time_ms(cudaStream_t s, cudaEvent_t a, cudaEvent_t b) {
 }
 
 struct TuneKey {
-  int dev, n, m, B, xt, basis;
+  int dev, n, m, B, xt, basis, persistent;  // (persistent: the step-mode parameter, which can force the mode)
   long long L;
   std::vector<int> ks;
   bool operator<(const TuneKey& o) const {
-    return std::tie(dev, n, m, B, xt, basis, L, ks) < std::tie(o.dev, o.n, o.m, o.B, o.xt, o.basis, o.L, o.ks);
+    return std::tie(dev, n, m, B, xt, basis, persistent, L, ks) <
+           std::tie(o.dev, o.n, o.m, o.B, o.xt, o.basis, o.persistent, o.L, o.ks);
   }
 };
 static bool tune_log() {
@@ -1056,6 +1266,7 @@ static bool tune_log() {
 struct TuneVal {
   int Bc;
   std::vector<int> rpl, cpw, lw, lnw;
+  bool persist = false;
 };
 static std::map<TuneKey, TuneVal>& tune_cache() {
   static std::map<TuneKey, TuneVal> c;
@@ -1083,7 +1294,7 @@ static int autotune(afs_handle* h, cudaStream_t s) {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  TuneKey key{dev, h->n, h->m, h->B, h->xt, h->p.basis, h->L, {}};
+  TuneKey key{dev, h->n, h->m, h->B, h->xt, h->p.basis, h->p.persistent, h->L, {}};
   for (auto& g : h->groups) key.ks.push_back(g.is_long ? -g.c_count : g.k * 100000 + g.c_count);
   auto it = tune_cache().find(key);
   if (it != tune_cache().end()) {
@@ -1094,6 +1305,7 @@ static int autotune(afs_handle* h, cudaStream_t s) {
       h->groups[i].lw = it->second.lw[i];
       h->groups[i].lnw = it->second.lnw[i];
     }
+    h->persist = it->second.persist && persist_eligible(h);
     return alloc_go(h, h->Bc);
   }
   cudaEvent_t e0, e1;
@@ -1206,9 +1418,47 @@ static int autotune(afs_handle* h, cudaStream_t s) {
       g.lnw = bn;
     }
   }
+  // 4. the persistent step mode against graph replay of the same 10 steps
+  // (eta = 0): the faster one runs the steps
+  h->persist = false;
+  if (persist_eligible(h)) {
+    if (h->p.persistent == 1) {
+      h->persist = true;
+    } else {
+      cudaGraph_t graph;
+      cudaGraphExec_t exec;
+      CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+      rc = enqueue_steps(h, 10, 0.0f, true, 0, h->cap, nullptr);
+      cudaError_t ce = cudaStreamEndCapture(h->cap, &graph);
+      if (rc) return rc;
+      if (ce != cudaSuccess) return fail(AFS_E_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) return fail(AFS_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+      double tg = 1e30, tp = 1e30;
+      for (int rep = 0; rep < 3; ++rep) {
+        CK(cudaEventRecord(e0, s));
+        CK(cudaGraphLaunch(exec, s));
+        CK(cudaEventRecord(e1, s));
+        tg = std::min(tg, time_ms(s, e0, e1));
+      }
+      cudaGraphExecDestroy(exec);
+      h->persist = true;
+      for (int rep = 0; rep < 4; ++rep) {  // the first launch also builds the persistent tables
+        CK(cudaEventRecord(e0, s));
+        rc = enqueue_steps(h, 10, 0.0f, true, 0, s, nullptr);
+        if (rc) return rc;
+        CK(cudaEventRecord(e1, s));
+        if (rep > 0) tp = std::min(tp, time_ms(s, e0, e1));
+      }
+      h->persist = tp < 0.97 * tg;
+      if (tune_log())
+        std::fprintf(stderr, "[afs autotune] 10 steps: graph %.1f us, persistent %.1f us\n", 1e3 * tg, 1e3 * tp);
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  TuneVal val{h->Bc, {}, {}, {}, {}};
+  TuneVal val{h->Bc, {}, {}, {}, {}, h->persist};
   for (auto& g : h->groups) {
     val.rpl.push_back(g.rpl);
     val.cpw.push_back(g.cpw);
@@ -1391,7 +1641,9 @@ int afs_init_restarts(afs_handle* h, int32_t B, uint64_t seed, const float* x0_d
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (Group& g : h->groups)
       if (!g.is_long) g.cpw = default_cpw(g, std::min(h->Bc, h->B), g.rpl, sms);
+    h->persist = h->p.persistent == 1 && persist_eligible(h);
   }
+  if (h->persist && (rc = persist_prepare(h, s))) return rc;
   // the autotuner's steps leave x unchanged but touch the check buffers and flags
   CK(cudaMemsetAsync(h->unsat.p, 0, h->unsat.bytes, s));
   CK(cudaMemsetAsync(h->vword.p, 0, h->vword.bytes, s));
@@ -1414,7 +1666,8 @@ int afs_step(afs_handle* h, int32_t nsteps, void* stream) {
   h->parity = (h->parity + nsteps) & 1;
   h->step_check_valid = check;
   h->count_valid = false;
-  if (!h->p.use_graph) {
+  // (a persistent launch already covers all nsteps: no graph)
+  if (!h->p.use_graph || (h->persist && !h->timing)) {
     int rc = enqueue_steps(h, nsteps, h->p.eta, check, p0, s, &h->last_launches);
     if (rc) return rc;
     if (h->timing) collect_timing(h);
@@ -1889,6 +2142,7 @@ int afs_set_tiles(afs_handle* h, int32_t chunk, const int32_t* rpl_by_k, const i
     if (rpl_by_k && rpl_by_k[g.k]) g.rpl = rpl_by_k[g.k];
     if (cpw_by_k && cpw_by_k[g.k]) g.cpw = cpw_by_k[g.k];
   }
+  if (h->persist && !persist_eligible(h)) h->persist = false;  // (a smaller chunk ends the persistent mode)
   h->drop_graphs();
   return AFS_OK;
 }
@@ -1927,6 +2181,13 @@ int afs_group_times(afs_handle* h, int32_t reps, double* ms, int32_t* kind, int3
   cudaEventDestroy(e1);
   if (rc) return rc;
   *n = i;
+  return AFS_OK;
+}
+
+int afs_step_mode(const afs_handle* h, int32_t* persistent, int32_t* blocks) {
+  if (!h) return fail(AFS_E_ARG, "NULL handle");
+  if (persistent) *persistent = h->persist ? 1 : 0;
+  if (blocks) *blocks = h->persist ? h->persist_blocks : 0;
   return AFS_OK;
 }
 

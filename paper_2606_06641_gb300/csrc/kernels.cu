@@ -13,6 +13,7 @@
 #include "afsat_internal.h"
 #include "bulk_copy.cuh"
 #include "fe_short.cuh"
+#include "step_units.cuh"
 
 namespace afs {
 
@@ -328,148 +329,6 @@ bool launch_fe_long(const FeGroupArgs& a, int xt, int basis, int wl, int nw, cud
 // x <- clamp(x - eta g, -1, 1), or g written out in evaluation mode.
 // One lane per restart, one warp per (variable, 32 restarts).
 // ---------------------------------------------------------------------------
-template <typename XT>
-__device__ __forceinline__ void store_x(XT* p, float v);
-template <>
-__device__ __forceinline__ void store_x<float>(float* p, float v) {
-  *p = v;
-}
-template <>
-__device__ __forceinline__ void store_x<__nv_bfloat16>(__nv_bfloat16* p, float v) {
-  *p = __float2bfloat16_rn(v);
-}
-template <typename XT>
-__device__ __forceinline__ float load_x_rw(const XT* p);
-template <>
-__device__ __forceinline__ float load_x_rw<float>(const float* p) {
-  return *p;
-}
-template <>
-__device__ __forceinline__ float load_x_rw<__nv_bfloat16>(const __nv_bfloat16* p) {
-  return __bfloat162float(*p);
-}
-
-// The value a state entry holds once stored (BF16 storage rounds).
-template <typename XT>
-__device__ __forceinline__ float stored_value(float v);
-template <>
-__device__ __forceinline__ float stored_value<float>(float v) {
-  return v;
-}
-template <>
-__device__ __forceinline__ float stored_value<__nv_bfloat16>(float v) {
-  return __bfloat162float(__float2bfloat16_rn(v));
-}
-
-// Fused constraints (k = KFUSE = 3, probability-generating tables): the
-// derivative of occurrence `self` is s_self * dFE/dl_self, recomputed from the
-// two other literals' state: the real root w = -1 contributes E l1 l2, the
-// complex pair (scaled form) Re(E' tan (l1 tan + i)(l2 tan + i)) -- the same
-// products at the roots as the FE kernel's gradient, without the self factor.
-// Each entry carries the root constants with the other literals' signs
-// folded in ({E s1 s2, tan s1, tan s2, E'r tan}, {E'i tan, s_self, v1, v2}),
-// read with uniform loads (the warp's lanes share them); the gathers of FB
-// occurrences are in flight at a time, R consecutive restarts per lane
-// starting at column col.
-template <typename XT, int R, int FB, bool OFF32 = false>
-__device__ __forceinline__ void fused_sum(const CsrArgs& a, int v, long long col, bool act, float (&acc)[R]) {
-  const int f0 = __ldg(a.fus_off + v), f1 = __ldg(a.fus_off + v + 1);
-  const XT* xc = static_cast<const XT*>(a.x) + col;
-  // lists are padded to pairs: with FB == FUS_PAD every entry of a batch
-  // exists, and col (clamped to the launch's first restart on idle lanes) is
-  // a valid column, so the loads need no guard
-  constexpr bool PAIRS = FB == FUS_PAD;
-  float cs = 0.0f;  // sum of the entries' constant terms (the same for every restart)
-  for (int f = f0; f < f1; f += FB) {  // uniform per warp
-    float4 c[FB];
-    float x1[FB][R], x2[FB][R];
-#pragma unroll
-    for (int u = 0; u < FB; ++u) {
-      const bool ok = PAIRS || f + u < f1;
-      c[u] = ok ? __ldg(a.fus + 2 * (f + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
-      const int2 vv = ok ? __ldg(reinterpret_cast<const int2*>(a.fus + 2 * (f + u) + 1)) : make_int2(0, 0);
-      const bool ld = PAIRS || (act && ok);
-      // OFF32: the launch checked that every row offset v * x_pitch fits 32 bits
-      const XT* p1 = OFF32 ? xc + static_cast<unsigned>(vv.x) * static_cast<unsigned>(a.x_pitch)
-                           : xc + static_cast<long long>(vv.x) * a.x_pitch;
-      const XT* p2 = OFF32 ? xc + static_cast<unsigned>(vv.y) * static_cast<unsigned>(a.x_pitch)
-                           : xc + static_cast<long long>(vv.y) * a.x_pitch;
-      if constexpr (R == 4) {
-        if (ld) {
-          load_xvec<XT, 4>(p1, x1[u]);
-          load_xvec<XT, 4>(p2, x2[u]);
-        } else {
-#pragma unroll
-          for (int r = 0; r < R; ++r) x1[u][r] = x2[u][r] = 0.0f;
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          x1[u][r] = ld ? load_x<XT>(p1 + r) : 0.0f;
-          x2[u][r] = ld ? load_x<XT>(p2 + r) : 0.0f;
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < FB; ++u) {
-      // the level expansion of the entry's derivative, x1 (A x2 + B1) + B2 x2
-      // (+ C, summed once); an absent occurrence has all constants 0
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const float t1 = fmaf(c[u].x, x2[u][r], c[u].y);
-        acc[r] = fmaf(x1[u][r], t1, acc[r]);
-        acc[r] = fmaf(c[u].z, x2[u][r], acc[r]);
-      }
-      cs += c[u].w;
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) acc[r] += cs;
-}
-
-// Invalidate the 128-byte L2 line at p (128-byte aligned) without writing it
-// back. `after` is a value loaded from that line: the operand makes the
-// discard wait for the load.
-__device__ __forceinline__ void l2_discard_line(const void* p, float after) {
-  asm volatile("discard.global.L2 [%0], 128;" ::"l"(p), "f"(after));
-}
-
-// Bookkeeping of the step's check, done once per (instance, word) by the
-// warps of the instance's first variable: record the lowest solved restart
-// and clear the word the next step's check will OR into.
-__device__ __forceinline__ void csr_first_var_duty(const CsrArgs& a, int inst, int word, long long wi) {
-  if (a.vcur != nullptr) {
-    const int valid = min(32, a.B - word * 32);
-    const unsigned ok = ~a.vcur[wi] & (valid >= 32 ? ~0u : ((1u << valid) - 1u));
-    if (ok) atomicMin(a.solved + inst, word * 32 + __ffs(static_cast<int>(ok)) - 1);
-  }
-  if (a.vnext != nullptr) a.vnext[wi] = 0u;
-}
-
-// Store n <= 4 consecutive state values (one vector store when n == 4).
-template <typename XT>
-__device__ __forceinline__ void store_xvec(XT* p, const float (&v)[4], int n);
-template <>
-__device__ __forceinline__ void store_xvec<float>(float* p, const float (&v)[4], int n) {
-  if (n == 4) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  } else {
-    for (int e = 0; e < n; ++e) p[e] = v[e];
-  }
-}
-template <>
-__device__ __forceinline__ void store_xvec<__nv_bfloat16>(__nv_bfloat16* p, const float (&v)[4], int n) {
-  if (n == 4) {
-    const __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]), hi = __floats2bfloat162_rn(v[2], v[3]);
-    uint2 u;
-    u.x = *reinterpret_cast<const unsigned*>(&lo);
-    u.y = *reinterpret_cast<const unsigned*>(&hi);
-    *reinterpret_cast<uint2*>(p) = u;
-  } else {
-    for (int e = 0; e < n; ++e) p[e] = __float2bfloat16_rn(v[e]);
-  }
-}
-
 // One lane per restart. Evaluation mode (grad != nullptr) writes the summed
 // gradient; step mode moves the unsolved restarts and, with sgn, writes the
 // sign word of the warp's 32 restarts (the chunk start is a multiple of 32).
@@ -535,98 +394,6 @@ __global__ void __launch_bounds__(256) csr_update_kernel(CsrArgs a) {
   if (a.sgn != nullptr && lane == 0) a.sgn[static_cast<long long>(v) * a.W + word] = bits;
 }
 
-// Step-path variant: each lane owns 4 consecutive restarts, so a warp reads
-// 512 contiguous bytes of every occurrence row (16-byte vector loads), four
-// rows in flight, and updates 4 states. The state, the solved word and the
-// instance's first variable are read before the gather so their latency
-// overlaps it; 8 lanes together write one sign word. 64 registers (four
-// 256-thread blocks per SM) measured faster than squeezing to five blocks.
-// The grid is persistent (one wave of resident blocks)
-// and warps stride over the (variable, 128-restart tile) tasks, so no partial
-// last wave idles the machine. Needs the state's row pitch and the chunk
-// start to be multiples of 32 and the buffers 16-byte aligned (true for the
-// library's own state and occurrence buffers); lanes past nb are masked.
-// OFF32: the launch checked that every state and row offset fits 32 bits.
-template <typename XT, bool OFF32>
-__device__ __forceinline__ void csr_vec4_task(const CsrArgs& a, int vl, int tile, int lane) {
-  const int bl = tile * 128 + lane * 4;
-  const bool act = bl < a.nb;
-  const int v = a.v_begin + vl;
-  const int s0 = __ldg(a.csr_off + v), s1 = __ldg(a.csr_off + v + 1);
-  const int inst = __ldg(a.var_inst + v);
-  const int first_var = __ldg(a.var_inst + a.n_vars + inst);
-  const int word = (a.b0 + bl) >> 5;
-  const long long wi = static_cast<long long>(inst) * a.W + word;
-  unsigned sw = 0u;  // solved (or fixed) bits of this lane's restarts
-  if (act && a.vcur != nullptr) sw = ~(a.vcur[wi] >> (bl & 31));
-  if (act && a.fixv != nullptr) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const long long g = static_cast<long long>(a.b0 + bl + e) * a.n_fix_groups / a.B;
-      if (bl + e < a.nb && a.fixv[g * a.n_vars + v] != 0) sw |= 1u << e;
-    }
-  }
-  const long long xi = OFF32 ? static_cast<long long>(static_cast<unsigned>(v) * static_cast<unsigned>(a.x_pitch) +
-                                                     static_cast<unsigned>(a.b0 + bl))
-                            : static_cast<long long>(v) * a.x_pitch + a.b0 + bl;
-  float xo[4] = {0.f, 0.f, 0.f, 0.f};
-  if (act) load_xvec<XT, 4>(static_cast<const XT*>(a.x) + xi, xo);
-  const float* col = a.go + (act ? bl : 0);
-  float4 acc[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-  // fused occurrences: summed by the fused pass beside the FE launches (the
-  // step path always provides gf when the instance has fused occurrences)
-  const float* gfp = a.gf != nullptr && act ? a.gf + static_cast<long long>(v) * a.gf_pitch + bl : nullptr;
-  const bool dis = a.discard_go && act && (lane & 7) == 0;
-  // most variables have few rows: batches of four, the summation order
-  // (row j into acc[j mod 4]) fixed by the slot order
-  for (int s = s0; s < s1; s += 4) {
-    float4 t[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const float* rp = OFF32 ? col + static_cast<unsigned>(s + u) * static_cast<unsigned>(a.go_pitch)
-                              : col + static_cast<long long>(s + u) * a.go_pitch;
-      t[u] = s + u < s1 ? __ldg(reinterpret_cast<const float4*>(rp)) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      acc[u & 3].x += t[u].x;
-      acc[u & 3].y += t[u].y;
-      acc[u & 3].z += t[u].z;
-      acc[u & 3].w += t[u].w;
-    }
-  }
-  const float4 gf = gfp != nullptr ? __ldg(reinterpret_cast<const float4*>(gfp)) : make_float4(0.f, 0.f, 0.f, 0.f);
-  const float g[4] = {gf.x + ((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x)),
-                      gf.y + ((acc[0].y + acc[1].y) + (acc[2].y + acc[3].y)),
-                      gf.z + ((acc[0].z + acc[1].z) + (acc[2].z + acc[3].z)),
-                      gf.w + ((acc[0].w + acc[1].w) + (acc[2].w + acc[3].w))};
-  // the rows are dead once read (the next FE pass rewrites them): drop their
-  // 128-byte L2 lines without a write-back, so that they make room for rows
-  // still to be read instead of costing DRAM writes (g depends on every load)
-  if (dis)
-    for (int s = s0; s < s1; ++s) l2_discard_line(col + static_cast<long long>(s) * a.go_pitch, g[0]);
-  unsigned nib = 0u;
-  float xn[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    // a solved restart keeps x_t; restarts past nb only fill the vector
-    xn[e] = ((sw >> e) & 1u) ? xo[e] : stored_value<XT>(fminf(fmaxf(fmaf(-a.eta, g[e], xo[e]), -1.0f), 1.0f));
-    if (act && bl + e < a.nb) nib |= static_cast<unsigned>(xn[e] < 0.0f) << e;
-  }
-  if (act) store_xvec<XT>(static_cast<XT*>(a.x_out) + xi, xn, min(4, a.nb - bl));
-  // 8 lanes x 4 restarts = one word
-  unsigned wv = nib << ((lane & 7) * 4);
-  wv |= __shfl_xor_sync(0xffffffffu, wv, 1);
-  wv |= __shfl_xor_sync(0xffffffffu, wv, 2);
-  wv |= __shfl_xor_sync(0xffffffffu, wv, 4);
-  if ((lane & 7) == 0 && act) {
-    if (a.sgn != nullptr) a.sgn[static_cast<long long>(v) * a.W + word] = wv;
-    if (v == first_var) csr_first_var_duty(a, inst, word, wi);
-  }
-}
-
 template <typename XT, bool OFF32>
 __global__ void __launch_bounds__(256, 4) csr_update_vec4_kernel(CsrArgs a) {
   pdl_wait();
@@ -651,13 +418,14 @@ __global__ void __launch_bounds__(256, 4) csr_update_vec4_kernel(CsrArgs a) {
 // resident warps beat deeper per-warp batches for these L2 gathers)
 template <typename XT>
 constexpr int FUSED_FB = 2;
+constexpr int FUSED_PF_MAX_B = 256;  // restart chunks up to this size take the prefetching sums
 constexpr int FUSED_THREADS = 128;
 // the persistent grid takes 1/FUSED_GRID_DIV of the resident-block slots (0:
 // one block per 4 tasks, no persistent grid, which measured best: the FE
 // launches beside it then share the SMs block by block)
 constexpr int FUSED_GRID_DIV = 0;
 
-template <typename XT, bool OFF32>
+template <typename XT, bool OFF32, bool PF>
 __global__ void __launch_bounds__(FUSED_THREADS) fused_grad_kernel(CsrArgs a) {
   pdl_wait();
   pdl_trigger();
@@ -671,7 +439,10 @@ __global__ void __launch_bounds__(FUSED_THREADS) fused_grad_kernel(CsrArgs a) {
     const int bl = static_cast<int>(task - vl * tiles) * 128 + lane * 4;
     const bool act = bl < a.nb;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    fused_sum<XT, 4, FUSED_FB<XT>, OFF32>(a, v, a.b0 + (act ? bl : 0), act, acc);
+    if constexpr (PF)
+      fused_sum_pf<XT, FUSED_PF_BATCH, OFF32>(a, v, a.b0 + (act ? bl : 0), act, lane, acc);
+    else
+      fused_sum<XT, 4, FUSED_FB<XT>, OFF32>(a, v, a.b0 + (act ? bl : 0), act, acc);
     if (act)
       *reinterpret_cast<float4*>(a.gf + static_cast<long long>(v) * a.gf_pitch + bl) =
           make_float4(acc[0], acc[1], acc[2], acc[3]);
@@ -696,9 +467,9 @@ static long long resident_blocks(K kernel, int threads, size_t smem = 0) {
   return it->second;
 }
 
-template <typename XT, bool OFF32>
+template <typename XT, bool OFF32, bool PF>
 static void launch_fused_t(const CsrArgs& a, long long blocks, cudaStream_t s) {
-  auto kern = fused_grad_kernel<XT, OFF32>;
+  auto kern = fused_grad_kernel<XT, OFF32, PF>;
   if (FUSED_GRID_DIV > 0)
     blocks = std::min(blocks, std::max(1LL, resident_blocks(kern, FUSED_THREADS) / FUSED_GRID_DIV));
   launch_pdl(kern, dim3(static_cast<unsigned>(blocks)), dim3(FUSED_THREADS), 0, s, a);
@@ -713,16 +484,21 @@ void launch_fused_grad(const CsrArgs& a, int xt, cudaStream_t s) {
   // row offsets v * x_pitch in 32 bits when the whole state fits
   const bool off32 = static_cast<unsigned long long>(a.n_vars) * static_cast<unsigned long long>(a.x_pitch) <
                      (1ull << 32);
+  // few restarts: the latency of each variable's list dominates (prefetched
+  // entries); many: the throughput of the plain batches
+  const bool pf = a.nb <= FUSED_PF_MAX_B;
   if (xt == XT_F32) {
     if (off32)
-      launch_fused_t<float, true>(a, blocks, s);
+      pf ? launch_fused_t<float, true, true>(a, blocks, s) : launch_fused_t<float, true, false>(a, blocks, s);
     else
-      launch_fused_t<float, false>(a, blocks, s);
+      pf ? launch_fused_t<float, false, true>(a, blocks, s) : launch_fused_t<float, false, false>(a, blocks, s);
   } else {
     if (off32)
-      launch_fused_t<__nv_bfloat16, true>(a, blocks, s);
+      pf ? launch_fused_t<__nv_bfloat16, true, true>(a, blocks, s)
+         : launch_fused_t<__nv_bfloat16, true, false>(a, blocks, s);
     else
-      launch_fused_t<__nv_bfloat16, false>(a, blocks, s);
+      pf ? launch_fused_t<__nv_bfloat16, false, true>(a, blocks, s)
+         : launch_fused_t<__nv_bfloat16, false, false>(a, blocks, s);
   }
 }
 
@@ -823,70 +599,6 @@ void launch_pack_signs(const void* x, int xt, long long x_pitch, int n, int B, u
 // AND_p (u_p ? P_p : ~P_p); longer constraints unpack t per restart and read
 // the violation table.
 // ---------------------------------------------------------------------------
-constexpr int CHECK_PLANES = 11;  // counts up to 2047 >= the longest constraint
-constexpr int CHECK_STAGE = 32;   // literal words a warp stages at a time
-constexpr int CHECK_WARPS = 4;
-
-template <int MAXP>
-__device__ __forceinline__ void add_words(unsigned (&P)[CHECK_PLANES], const unsigned* sw, int n, int np) {
-  for (int i = 0; i < n; ++i) {
-    unsigned carry = sw[i * 32];
-#pragma unroll
-    for (int p = 0; p < MAXP; ++p) {
-      if (p < np) {
-        const unsigned t = P[p] & carry;
-        P[p] ^= carry;
-        carry = t;
-      }
-    }
-  }
-}
-
-// Violation word of one constraint from its count planes.
-__device__ __forceinline__ unsigned violated_word(const unsigned (&P)[CHECK_PLANES], int k, int np,
-                                                  unsigned long long em, const unsigned char* vt) {
-  if (k <= 62) {
-    unsigned long long m = em & ~(1ull << 63);
-    unsigned hit = 0u;
-    while (m) {
-      const int u = __ffsll(static_cast<long long>(m)) - 1;
-      m &= m - 1;
-      unsigned e = ~0u;
-#pragma unroll
-      for (int p = 0; p < 6; ++p)
-        if (p < np) e &= ((u >> p) & 1) ? P[p] : ~P[p];
-      hit |= e;
-    }
-    return (em >> 63) ? ~hit : hit;
-  }
-  unsigned bad = 0u;
-  for (int j = 0; j < 32; ++j) {
-    int t = 0;
-#pragma unroll
-    for (int p = 0; p < CHECK_PLANES; ++p)
-      if (p < np) t |= static_cast<int>((P[p] >> j) & 1u) << p;
-    bad |= static_cast<unsigned>(__ldg(vt + t)) << j;
-  }
-  return bad;
-}
-
-// Gather the literal words of literals [base, base + cnt) (cnt <= 32) into
-// the warp's stage, all loads in flight at once: lane j of row i holds the
-// truth of literal base + i in restarts 32w + (0..31).
-__device__ __forceinline__ void check_stage(const CheckArgs& a, const unsigned* sg, unsigned* st, int base, int cnt,
-                                            int lane) {
-  const int e = lane < cnt ? __ldg(a.lit_enc + base + lane) : 0;
-  unsigned wv[CHECK_STAGE];
-#pragma unroll
-  for (int j = 0; j < CHECK_STAGE; ++j) {
-    const int enc = __shfl_sync(0xffffffffu, e, j);
-    wv[j] = j < cnt ? __ldg(sg + static_cast<long long>(enc >> 1) * a.W) ^ (0u - static_cast<unsigned>(enc & 1)) : 0u;
-  }
-#pragma unroll
-  for (int j = 0; j < CHECK_STAGE; ++j) st[j * 32] = wv[j];
-  __syncwarp();
-}
-
 // A warp handles one range (<= 32 literals, or one longer constraint) for 32
 // words: lane j owns word w0 + 32*blockIdx.y + j. The range's literal words
 // are staged in shared memory, then the constraints are counted from there.
@@ -1008,6 +720,25 @@ __global__ void __launch_bounds__(CHECK_WARPS * 32) check_bits_kernel(CheckArgs 
     }
     if (cur >= 0 && acc) atomicOr(a.vword + static_cast<long long>(cur) * a.W + w, acc);
   }
+}
+
+// One warp per (wide run, word): blockIdx.y is the word.
+template <bool COUNT>
+__global__ void __launch_bounds__(CHECK_WARPS * 32) check_wide_kernel(CheckArgs a) {
+  __shared__ unsigned stage[CHECK_WARPS][CHECK_WIDE_STAGE];
+  pdl_wait();
+  pdl_trigger();
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int rgi = blockIdx.x * CHECK_WARPS + wp;
+  if (rgi < a.n_ranges)
+    check_wide_unit<false, COUNT>(a, rgi, a.w0 + static_cast<int>(blockIdx.y), lane, stage[wp]);
+}
+
+void launch_check_wide(const CheckArgs& a, cudaStream_t s) {
+  if (a.n_ranges == 0 || a.wc == 0) return;
+  const dim3 grid(static_cast<unsigned>((a.n_ranges + CHECK_WARPS - 1) / CHECK_WARPS), static_cast<unsigned>(a.wc));
+  if (a.unsat != nullptr) launch_pdl(check_wide_kernel<true>, grid, dim3(CHECK_WARPS * 32), 0, s, a);
+  else launch_pdl(check_wide_kernel<false>, grid, dim3(CHECK_WARPS * 32), 0, s, a);
 }
 
 void launch_check_bits(const CheckArgs& a, cudaStream_t s) {

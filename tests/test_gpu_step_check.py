@@ -136,6 +136,42 @@ def test_every_count_of_every_length(ctype, kw):
     assert got.any() and not got.all()
 
 
+@pytest.mark.parametrize("B", [200, 300])
+@pytest.mark.parametrize("ctype,kw", [
+    (synth.OR, {}), (synth.XOR, {"parity": 1}), (synth.NAE, {}), (synth.EO, {}), (synth.EK, {"param": -1}),
+    (synth.CARD, {"op": synth.GE, "param": -1}), (synth.CARD, {"op": synth.LT, "param": -1}),
+])
+def test_every_count_up_to_62_literals(ctype, kw, B):
+    """All counts t = 0..k for k <= 62, where the checks of up to 8 restart
+    words (B = 200) take one constraint per lane and wider ones (B = 300) one
+    word per lane: both must give the oracle's counts."""
+    rng = np.random.default_rng(300 + ctype + B)
+    insts, xs = [], []
+    for k in (1, 2, 3, 5, 20, 31, 32, 33, 61, 62):
+        args = dict(kw)
+        if args.get("param") == -1:
+            args["param"] = int(rng.integers(0, k + 1))
+        inst, x = _single_constraint_case(ctype, k, B, rng, **args)
+        insts.append(inst)
+        xs.append(x)
+    got = _run_check(insts, xs, B)
+    assert got.any() and not got.all()
+
+
+@pytest.mark.parametrize("B", [32, 64, 250])
+def test_planted_runs_of_long_short_constraints(B):
+    """Runs of many constraints up to 62 literals (several runs of up to 31
+    constraints and 256 literals per instance) in the lane-per-constraint check."""
+    rng = np.random.default_rng(40 + B)
+    insts, xs = [], []
+    for i in range(4):
+        inst, x = _planted_case(int(rng.integers(70, 120)), int(rng.integers(60, 140)), 62, B, rng)
+        insts.append(inst)
+        xs.append(x)
+    got = _run_check(insts, xs, B)
+    assert got[:, 0].all()
+
+
 def test_longest_constraint_all_counts():
     rng = np.random.default_rng(7)
     B = 1100
