@@ -60,15 +60,22 @@ WORKLOADS = {
 METRIC = "FE+grad literal-evals/s"
 LINE_SEARCH = (1.0, 0.5, 1e-4, 6)   # first step, backtracking factor, sufficient-decrease constant, trials
 UNIT = "literal-evals/s"
-KERNEL_SOURCES = ["paper_2606_06641_gb300/csrc/fe_short.cuh", "paper_2606_06641_gb300/csrc/kernels.cu",
-                  "paper_2606_06641_gb300/csrc/long_pgf.cu",
-                  "paper_2606_06641_gb300/csrc/coef.cpp", "paper_2606_06641_gb300/csrc/coef.h",
-                  "paper_2606_06641_gb300/csrc/afsat_internal.h"]
+# the sources each dominant kernel is built from (its counters are valid while
+# their hash is unchanged)
+_CS = "paper_2606_06641_gb300/csrc/"
+KERNEL_SOURCES = {
+    "fe_grad_short_kernel": [_CS + "fe_short.cuh", _CS + "short_dispatch.cuh", _CS + "coef.cpp", _CS + "coef.h",
+                             _CS + "afsat_internal.h"],
+    "fe_grad_long_pgf_kernel": [_CS + "long_pgf.cu", _CS + "bulk_copy.cuh", _CS + "coef.cpp", _CS + "coef.h",
+                                _CS + "afsat_internal.h"],
+    "fused_grad_kernel": [_CS + "kernels.cu", _CS + "step_units.cuh", _CS + "fe_short.cuh",
+                          _CS + "afsat_internal.h"],
+}
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, p), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -457,21 +464,21 @@ def precision_report(inst, n_restarts: int = 4):
     return {"restarts": n_restarts, **out}
 
 
+STEP_MODES = {"auto": 0, "persistent": 1, "graph": -1}   # afs_params.persistent
 KIND_NAMES = {0: "fe_grad_short_kernel", 1: "fe_grad_long_pgf_kernel", 2: "fused_grad_kernel"}
 COUNTERS_FILE = os.path.join(ROOT, "profiles", "kernel_counters.json")
 
 
 def load_counters(workload: str):
-    """ncu counters of the dominant kernel recorded for this workload (executed
-    warp instructions and DRAM bytes per restart per step), if they were taken
-    on the current kernel sources."""
+    """ncu counters recorded for this workload, per kernel (executed warp
+    instructions and DRAM bytes per restart per step): those taken on the
+    kernel's current sources."""
     if not os.path.exists(COUNTERS_FILE):
-        return None
+        return {}
     with open(COUNTERS_FILE) as fh:
-        c = json.load(fh)
-    if c.get("kernel_source_hash") != kernel_source_hash():
-        return None
-    return c.get("workloads", {}).get(workload)
+        per_kernel = json.load(fh).get("workloads", {}).get(workload, {})
+    return {k: c for k, c in per_kernel.items()
+            if k in KERNEL_SOURCES and c.get("kernel_source_hash") == kernel_source_hash(k)}
 
 
 def dominant_kernel(groups, B: int, chunk: int, peak_tinst: float, peak_src: str, sm_max: float, sms: int,
@@ -504,7 +511,8 @@ def dominant_kernel(groups, B: int, chunk: int, peak_tinst: float, peak_src: str
            "timing": "CUDA events on the launching stream around each launch group of the step "
                      "(afs_group_times, 5 launches per group over one restart chunk, current state)",
            "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock, {peak_src})"}
-    if counters and counters.get("kernel") == KIND_NAMES[kind]:
+    counters = counters.get(KIND_NAMES[kind]) if counters else None
+    if counters:
         wi = counters["warp_inst_per_restart_step"] * B
         out["executed_lane_instr_per_step"] = 32.0 * wi
         out["issue_frac"] = 32.0 * wi / (out["ms_per_step"] * 1e-3) / 1e12 / peak_tinst
@@ -524,7 +532,8 @@ def measure_workload(name: str, args, rank: int, world: int, stream, want_cpu: b
     desc, B_default = WORKLOADS[name]
     B = (args.restarts if name == args.workload else 0) or B_default
     insts = make_workload(name)
-    params = bd.default_params(eta=0.1, verify_every=1, chunk=args.chunk, autotune=0 if args.tiles else 1)
+    params = bd.default_params(eta=0.1, verify_every=1, chunk=args.chunk, autotune=0 if args.tiles else 1,
+                               persistent=STEP_MODES[args.step_mode])
     h = bd.load_instance(insts[0], params) if len(insts) == 1 else bd.load_batch(insts, params)
     bd.init_restarts(h, B, seed=1000 + rank)
     if args.tiles and name == args.workload:
@@ -568,7 +577,10 @@ def measure_workload(name: str, args, rank: int, world: int, stream, want_cpu: b
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    # (the timed replays are the profiler's capture range: ncu --profile-from-start off)
+    torch.cuda.profiler.start()
     dev_ms, launches = replays(R)
+    torch.cuda.profiler.stop()
     if world > 1:
         torch.distributed.barrier()
     # sustained: replays until at least --sustained-s of device time
@@ -631,6 +643,7 @@ def measure_workload(name: str, args, rank: int, world: int, stream, want_cpu: b
                "d2h_bytes_per_step": n_total * B * 4 + len(insts) * B * 4, "steps": E}
     tiles = bd.format_tiles(*bd.tiles(h))
     long_tiles = [f"k<={km}:{lw}x{nw}" for lw, nw, km in bd.long_tiles(h)]
+    pmode, pblocks = bd.step_mode(h)
     h.free()
     del flush
     torch.cuda.empty_cache()
@@ -646,7 +659,9 @@ def measure_workload(name: str, args, rank: int, world: int, stream, want_cpu: b
         "sustained": {"value": L * B * K * world / (sus_equiv * 1e-3), "ms_per_step": sus_equiv / K,
                       "steps": sus_steps, "device_s": sus_ms / 1e3},
         "config": {"workload": desc, "restarts": B, "literals": L, "instances": len(insts),
-                   "l2": f"flushed (512 MB write) between timed CUDA-graph replays of {S} steps",
+                   "l2": f"flushed (512 MB write) between timed replays of {S} steps",
+                   "step_mode": (f"persistent ({pblocks} cooperative blocks, one launch per replay)" if pmode
+                                 else "CUDA-graph replay of the per-step launches"),
                    "chunk_restarts": chunk, "restarts_per_lane": rpl, "tiles": tiles, "long_tiles": long_tiles,
                    "tiles_source": "given" if (args.tiles and name == args.workload) else "autotuned",
                    "parallelism": f"replicas x{world}"},
@@ -783,6 +798,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--tts-instances", type=int, default=128)
     ap.add_argument("--tts-eta", type=float, default=0.1)
+    ap.add_argument("--step-mode", default="auto", choices=sorted(STEP_MODES),
+                    help="steps as graph-replayed per-step launches, one persistent launch, or the faster (autotuned)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tts", action="store_true")

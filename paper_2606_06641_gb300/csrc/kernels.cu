@@ -418,7 +418,9 @@ __global__ void __launch_bounds__(256, 4) csr_update_vec4_kernel(CsrArgs a) {
 // resident warps beat deeper per-warp batches for these L2 gathers)
 template <typename XT>
 constexpr int FUSED_FB = 2;
-constexpr int FUSED_PF_MAX_B = 256;  // restart chunks up to this size take the prefetching sums
+// launches of up to this many (variable, 128-restart) tasks, which leave each
+// warp's occurrence list on the critical path, take the prefetching sums
+constexpr long long FUSED_PF_MAX_TASKS = 16384;
 constexpr int FUSED_THREADS = 128;
 // the persistent grid takes 1/FUSED_GRID_DIV of the resident-block slots (0:
 // one block per 4 tasks, no persistent grid, which measured best: the FE
@@ -484,9 +486,9 @@ void launch_fused_grad(const CsrArgs& a, int xt, cudaStream_t s) {
   // row offsets v * x_pitch in 32 bits when the whole state fits
   const bool off32 = static_cast<unsigned long long>(a.n_vars) * static_cast<unsigned long long>(a.x_pitch) <
                      (1ull << 32);
-  // few restarts: the latency of each variable's list dominates (prefetched
+  // few tasks: the latency of each variable's list dominates (prefetched
   // entries); many: the throughput of the plain batches
-  const bool pf = a.nb <= FUSED_PF_MAX_B;
+  const bool pf = tasks <= FUSED_PF_MAX_TASKS;
   if (xt == XT_F32) {
     if (off32)
       pf ? launch_fused_t<float, true, true>(a, blocks, s) : launch_fused_t<float, true, false>(a, blocks, s);
