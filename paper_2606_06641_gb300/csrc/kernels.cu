@@ -420,7 +420,7 @@ template <typename XT>
 constexpr int FUSED_FB = 2;
 // launches of up to this many (variable, 128-restart) tasks, which leave each
 // warp's occurrence list on the critical path, take the prefetching sums
-constexpr long long FUSED_PF_MAX_TASKS = 16384;
+constexpr long long FUSED_PF_MAX_TASKS = 4096;
 constexpr int FUSED_THREADS = 128;
 // the persistent grid takes 1/FUSED_GRID_DIV of the resident-block slots (0:
 // one block per 4 tasks, no persistent grid, which measured best: the FE
