@@ -28,7 +28,8 @@ Roofline: the dominant kernel of each workload (the kernel with the largest
 share of FE+gradient time) is timed per launch with CUDA events on the
 launching stream (afs_group_times) and rated at its algorithmic FP32
 instructions (16 per (literal, root) plus 2 per root, R(k) = floor((k+1)/2);
-3 per occurrence for the fused 3-literal pass) against SMs x 128 FP32 lanes x
+the level form's operations per occurrence for the fused 3- to 5-literal
+pass) against SMs x 128 FP32 lanes x
 the maximum SM clock.
 
 --impl reference times the CPU oracle (FP64 numpy, Poisson-binomial
@@ -507,7 +508,8 @@ def dominant_kernel(groups, B: int, chunk: int, peak_tinst: float, peak_src: str
            "group_lengths": d["kmax"],
            "work_instr_per_step": d["work"] * launches_per_step,
            "accounting": "algorithmic FP32 lane instructions: 16 per (literal, root) + 2 per root, "
-                         "R(k) = floor((k+1)/2); fused 3-literal pass: 3 per occurrence",
+                         "R(k) = floor((k+1)/2); fused pass (3- to 5-literal constraints): its level form's "
+                         "operations per occurrence, 3 / 8 / 13 for k = 3 / 4 / 5",
            "timing": "CUDA events on the launching stream around each launch group of the step "
                      "(afs_group_times, 5 launches per group over one restart chunk, current state)",
            "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock, {peak_src})"}

@@ -126,6 +126,27 @@ __device__ __forceinline__ void store_fvec<4>(float* p, const float (&v)[4]) {
 // the state's row pitch, the chunk start and the derivative pitch to be
 // multiples of 32 (the library's own state and buffers); a vector that starts
 // below nb then stays inside the padded row, and values past nb are ignored.
+// Approximate reciprocal (PTX rcp.approx, within one unit in the last place)
+// of a number >= 1.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// Gradient of the scaled short form: 0 from stored prefix and running suffix
+// products; 1 by dividing each literal's factor out of the full product,
+// keeping w = l / gamma; 2 the same recomputing w (fewer registers).
+constexpr int SCALED_GRAD_FORM = 2;
+constexpr int SHORT_MIN_BLOCKS_SCALED = 6;
+constexpr bool SCALED_GRAD_BY_DIVISION = SCALED_GRAD_FORM > 0;
+// Blocks of 4 warps per SM the short kernel is compiled for (register cap):
+// one restart per lane on the scaled form, where the division form needs
+// about 2k registers.
+template <int K, int RPL>
+constexpr int short_min_blocks() {
+  return (SCALED_GRAD_FORM == 2 && RPL == 1 && K <= KSCALED_MAX) ? SHORT_MIN_BLOCKS_SCALED : 1;
+}
+
 // a * b, computed again where the compiler would otherwise keep the first
 // product of the same operands live (k registers) across the forward pass
 __device__ __forceinline__ float mul_recompute(float a, float b) {
@@ -234,33 +255,58 @@ __device__ __forceinline__ void short_unit(const FeGroupArgs& a, long long warp,
       const float ia = cc.x;  // 1 / gamma
 #pragma unroll
       for (int r = 0; r < RPL; ++r) {
-        float pr[K], pi[K];
-        float Pr = cc.z * ia, Pi = cc.w * ia;
+        if constexpr (SCALED_GRAD_BY_DIVISION) {
+          // the full product T = E' prod (w_i + i), then each literal's
+          // gradient term ia Re(T / (w_i + i)) = ia (Tr w_i + Ti) / (w_i^2 + 1):
+          // |w_i + i| >= 1, so dividing a factor out cannot amplify the error,
+          // and no prefix products are kept (K registers instead of 2K)
+          float w[SCALED_GRAD_FORM == 1 ? K : 1];
+          float Tr = cc.z, Ti = cc.w;
 #pragma unroll
-        for (int i = 0; i < K; ++i) {
-          pr[i] = Pr;
-          pi[i] = Pi;
-          if (i + 1 < K) {
-            const float w = l[r][i] * ia;
-            const float nr = fmaf(Pr, w, -Pi);
-            const float ni = fmaf(Pi, w, Pr);
-            Pr = nr;
-            Pi = ni;
+          for (int i = 0; i < K; ++i) {
+            const float wi = l[r][i] * ia;
+            if constexpr (SCALED_GRAD_FORM == 1) w[i] = wi;
+            const float nr = fmaf(Tr, wi, -Ti);
+            const float ni = fmaf(Ti, wi, Tr);
+            Tr = nr;
+            Ti = ni;
           }
-        }
-        g[r][K - 1] += pr[K - 1];
-        float Sr = l[r][K - 1] * ia, Si = 1.0f;
+          fe[r] += Tr;
+          const float Ur = Tr * ia, Ui = Ti * ia;
 #pragma unroll
-        for (int i = K - 2; i >= 0; --i) {
-          g[r][i] = fmaf(pr[i], Sr, g[r][i]);
-          g[r][i] = fmaf(-pi[i], Si, g[r][i]);
-          const float w = K > 8 ? mul_recompute(l[r][i], ia) : l[r][i] * ia;
-          const float nr = fmaf(Sr, w, -Si);
-          const float ni = fmaf(Si, w, Sr);
-          Sr = nr;
-          Si = ni;
+          for (int i = 0; i < K; ++i) {
+            const float wi = SCALED_GRAD_FORM == 1 ? w[i] : mul_recompute(l[r][i], ia);
+            g[r][i] = fmaf(fmaf(Ur, wi, Ui), rcp_approx(fmaf(wi, wi, 1.0f)), g[r][i]);
+          }
+        } else {
+          float pr[K], pi[K];
+          float Pr = cc.z * ia, Pi = cc.w * ia;
+#pragma unroll
+          for (int i = 0; i < K; ++i) {
+            pr[i] = Pr;
+            pi[i] = Pi;
+            if (i + 1 < K) {
+              const float w = l[r][i] * ia;
+              const float nr = fmaf(Pr, w, -Pi);
+              const float ni = fmaf(Pi, w, Pr);
+              Pr = nr;
+              Pi = ni;
+            }
+          }
+          g[r][K - 1] += pr[K - 1];
+          float Sr = l[r][K - 1] * ia, Si = 1.0f;
+#pragma unroll
+          for (int i = K - 2; i >= 0; --i) {
+            g[r][i] = fmaf(pr[i], Sr, g[r][i]);
+            g[r][i] = fmaf(-pi[i], Si, g[r][i]);
+            const float w = K > 8 ? mul_recompute(l[r][i], ia) : l[r][i] * ia;
+            const float nr = fmaf(Sr, w, -Si);
+            const float ni = fmaf(Si, w, Sr);
+            Sr = nr;
+            Si = ni;
+          }
+          fe[r] = fmaf(cc.z, Sr, fmaf(-cc.w, Si, fe[r]));
         }
-        fe[r] = fmaf(cc.z, Sr, fmaf(-cc.w, Si, fe[r]));
       }
     }
 
@@ -332,7 +378,7 @@ __device__ __forceinline__ void short_unit(const FeGroupArgs& a, long long warp,
     for (int i = 0; i < K; ++i) {
       const float sg = ((negm >> i) & 1u) ? -1.0f : 1.0f;
       const int slot = __ldg(&ls[i].y);
-      if (K == KFUSE && slot < 0) continue;  // fused constraint: no derivative row
+      if (K <= KFUSE_MAX && slot < 0) continue;  // fused constraint: no derivative row
       float* row = a.go + static_cast<long long>(slot) * a.go_pitch;
       if constexpr (V) {
         if (act[0]) {
@@ -357,7 +403,7 @@ __device__ __forceinline__ void short_unit(const FeGroupArgs& a, long long warp,
 }
 
 template <int K, int RPL, typename XT, bool SHIFT, bool VEC>
-__global__ void __launch_bounds__(128) fe_grad_short_kernel(FeGroupArgs a) {
+__global__ void __launch_bounds__(128, short_min_blocks<K, RPL>()) fe_grad_short_kernel(FeGroupArgs a) {
   pdl_wait();
   pdl_trigger();
   const long long warp = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);

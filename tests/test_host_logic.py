@@ -321,6 +321,34 @@ def test_length3_level_expansion_derivative():
             np.testing.assert_allclose(got, want, atol=1e-14, rtol=0)
 
 
+@pytest.mark.parametrize("k", [4, 5])
+def test_length4_5_level_expansion_derivative(k):
+    """The fused pass's derivative of a 4- or 5-literal constraint in its first
+    variable: s (c1 + c2 e1 + c3 e2 + c4 e3 [+ c5 e4]) with e_d the elementary
+    symmetric sums of the other literals l = s x, built one literal at a time
+    as the device does (e_d += l e_{d-1}, highest d first), equals the
+    oracle's s * dFE/dl for every shape and sign pattern; parities have only
+    the top level, so their entries take the product of the other literals."""
+    rng = np.random.default_rng(40 + k)
+    x = rng.uniform(-1, 1, (7, k))
+    for (ct, op, r, par) in _shapes(k):
+        f = O.truth_table(ct, k, op, r, par)
+        c = bd.esp_coefficients(ct, k, op, r, par)
+        if ct == O.T_XOR:
+            assert np.all(np.abs(c[1:k]) < 1e-13) and abs(c[k]) > 0.5
+        for _ in range(4):
+            s = rng.choice([-1.0, 1.0], size=k)
+            _, g = O.fe_and_dfe(f, x * s)
+            want = s[0] * g[:, 0]
+            lo = x[:, 1:] * s[1:]
+            e = [np.ones(len(x))] + [np.zeros(len(x)) for _ in range(k - 1)]
+            for j in range(k - 1):
+                for d in range(j + 1, 0, -1):
+                    e[d] = e[d] + lo[:, j] * e[d - 1]
+            got = s[0] * sum(c[d + 1] * e[d] for d in range(k))
+            np.testing.assert_allclose(got, want, atol=1e-13, rtol=0)
+
+
 @pytest.mark.parametrize("k", list(range(33, 513, 29)) + [63, 64, 65, 100, 101, 128, 255, 256, 257, 480, 511, 512])
 def test_long_pgf_table_forms_stay_in_range(k):
     """Layout of a long probability-generating table: the kept roots are
