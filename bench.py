@@ -28,8 +28,7 @@ Roofline: the dominant kernel of each workload (the kernel with the largest
 share of FE+gradient time) is timed per launch with CUDA events on the
 launching stream (afs_group_times) and rated at its algorithmic FP32
 instructions (16 per (literal, root) plus 2 per root, R(k) = floor((k+1)/2);
-the level form's operations per occurrence for the fused 3- to 5-literal
-pass) against SMs x 128 FP32 lanes x
+3 per occurrence for the fused 3-literal pass) against SMs x 128 FP32 lanes x
 the maximum SM clock.
 
 --impl reference times the CPU oracle (FP64 numpy, Poisson-binomial
@@ -508,11 +507,17 @@ def dominant_kernel(groups, B: int, chunk: int, peak_tinst: float, peak_src: str
            "group_lengths": d["kmax"],
            "work_instr_per_step": d["work"] * launches_per_step,
            "accounting": "algorithmic FP32 lane instructions: 16 per (literal, root) + 2 per root, "
-                         "R(k) = floor((k+1)/2); fused pass (3- to 5-literal constraints): its level form's "
-                         "operations per occurrence, 3 / 8 / 13 for k = 3 / 4 / 5",
+                         "R(k) = floor((k+1)/2); fused 3-literal pass: 3 per occurrence",
            "timing": "CUDA events on the launching stream around each launch group of the step "
                      "(afs_group_times, 5 launches per group over one restart chunk, current state)",
            "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock, {peak_src})"}
+    if kind == 1 or (kind == 0 and max(d["kmax"]) <= 24):
+        # the kernel's own algorithm (gradient by division): per (literal,
+        # root) 3 FP32 instructions for the forward product and 5 for the
+        # derivative (w = p l, numerator, denominator, reciprocal, sum)
+        out["division_form"] = {"instr_per_literal_root": 8,
+                                "frac": achieved / peak_tinst * 8.0 / 16.0,
+                                "note": "the frac above counts 16 per (literal, root), the prefix/suffix work model"}
     counters = counters.get(KIND_NAMES[kind]) if counters else None
     if counters:
         wi = counters["warp_inst_per_restart_step"] * B

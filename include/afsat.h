@@ -234,8 +234,8 @@ int afs_eval_fe_grad(afs_handle* h, const void* x_dev, int32_t x_dtype, int32_t 
  * processed in chunks of 32..256 columns sized to that array; an instance
  * whose occurrences with derivative rows x 32 restarts x 4 bytes exceed
  * 16 MiB (more than 131072 of them) is rejected with AFS_E_ARG. Occurrences
- * in constraints of length 3 to 5 (probability-generating basis) need no
- * row: their derivatives are recomputed in the gather. The first call on each
+ * in constraints of length 3 (probability-generating basis) need no row:
+ * their derivatives are recomputed in the gather. The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture. The address is kept for the
  * life of the process: after a device reset (cudaDeviceReset, or another
@@ -354,14 +354,12 @@ int afs_step_mode(const afs_handle* h, int32_t* persistent, int32_t* blocks);
  * the step (bucket order) over the current restart chunk of the current
  * state, on `stream`: reps launches per group, ms[i] = mean milliseconds per
  * launch. kind[i] = 0 short bucket (k <= 32), 1 long group (k > 32), 2 the
- * fused pass of the 3- to 5-literal constraints (one pass for all of them:
- * timed at the first fused group, which carries their work, the others
- * report 0 ms and 0 work); kmax[i] = the group's (longest)
+ * fused pass of the 3-literal constraints; kmax[i] = the group's (longest)
  * length; work[i] = algorithmic FP32 instructions of one launch: per
  * constraint and restart 16 per (literal, root) plus 2 per root with
  * R(k) = floor((k+1)/2) roots (Sec. 2.1.2's products at the roots, mirrored
- * pairs counted once), or per occurrence for the fused pass its level
- * form's operations: 3 (k = 3), 8 (k = 4), 13 (k = 5). The derivative rows written are scratch; the state is not changed.
+ * pairs counted once), or 3 per occurrence for the fused pass (its level
+ * form). The derivative rows written are scratch; the state is not changed.
  * Writes min(cap, groups) entries (arrays may be NULL) and the number of
  * groups to *n. Synchronises on the launches' completion. */
 int afs_group_times(afs_handle* h, int32_t reps, double* ms, int32_t* kind, int32_t* kmax, double* work,

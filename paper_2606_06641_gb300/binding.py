@@ -466,8 +466,7 @@ def step_mode(h: Handle):
 
 def group_times(h: Handle, reps: int = 3, stream=None):
     """[(kind, kmax, ms per launch, algorithmic FP32 instructions per launch)]
-    of every FE launch group (kind 0 short, 1 long, 2 the fused pass of the 3- to
-    5-literal constraints, timed once at the first fused group)."""
+    of every FE launch group (kind 0 short, 1 long, 2 fused 3-literal pass)."""
     n = ctypes.c_int32()
     _check(lib().afs_group_times(h.ptr, 1, None, None, None, None, 0, ctypes.byref(n), _stream(stream)))
     cnt = max(1, n.value)

@@ -19,15 +19,6 @@ constexpr int KFUSE = 3;
 // constants 0, both other literals the variable itself) to a multiple of
 // FUS_PAD, so that the pass reads them in pairs without bounds selects.
 constexpr int FUS_PAD = 2;
-// Constraints of length 4 and 5 (probability-generating basis) are fused too:
-// the derivative in the self literal's variable is s (c1 + c2 e1 + c3 e2 +
-// c4 e3 + c5 e4), e_d the elementary symmetric sums of the other literals'
-// values l = s x (Eq. 1's level form), from an entry of three float4:
-//   {s c1, s c2, s c3, s c4}, {s c5, o1, o2, o3}, {o4 or -1, product, s c_k, 0}
-// with o = (other variable << 1) | negated as int bits, o4 = -1 for k = 4,
-// and product = 1 when only the top level is nonzero (parities), where the
-// derivative is s c_k times the product of the other literals.
-constexpr int KFUSE_MAX = 5;
 
 // One FE+gradient launch over a group of constraints that share a length k
 // and are stored contiguously in bucket order: constraint c of the group owns
@@ -68,8 +59,6 @@ struct CsrArgs {
   const int* fus_off;       // fused occurrences of v: fus[fus_off[v] .. fus_off[v+1])
   const float4* fus;        // 2 per entry: {A, B1, B2, C}, {v1, v2 (int bits), 0, 0}: the derivative
                             // in v of the entry's constraint is x1 (A x2 + B1) + B2 x2 + C
-  const int* fw_off;        // nullable: fused 4- and 5-literal occurrences of v: fw[3 fw_off[v] .. 3 fw_off[v+1])
-  const float4* fw;         // (entries of three float4, layout at KFUSE_MAX)
   const float4* coef;       // coefficient tables (short form)
   int v_begin, v_count;
   const float* go;

@@ -207,32 +207,26 @@ static void push4(std::vector<float>& o, double a, double b, double c, double d)
 // b' = (1 - z')/2 and a'/b' = i cot(theta'), so a' + b' l = s g(l) with
 // s = b'/p (form A, |s| = cos theta') or s = b' (form B, |s| = sin theta').
 // The kernel walks the literals in segments of LONG_SEG = 16 (the last
-// segment n_last long) and keeps running products at their true size at
-// segment boundaries with powers of s: forward, P <- P prod_seg g then
-// P <- P s^16 (full segments); backward, a segment of n literals starts from
-// the checkpoint times s^a and the suffix carried as S s^b (a + b = n - 1:
-// a = 7, b = 8 for a full segment), so Re(prefix * suffix) is the true
-// contribution; after the walk the suffix is multiplied by s^16 (full) or by
-// s^(8 - b + n) (the last segment, walked first). Within a segment
-// |g| <= 1/|s| and the split keeps both running products within 2^126.
+// segment n_last long) and keeps the running product at its true size at
+// segment boundaries: P <- P prod_seg g, then P <- P s^16 after every full
+// segment; within a segment |g| <= 1/|s| and |s|^16 >= 2^-100 keep P within
+// FP32. The root's value is Re(E' P) and each literal's derivative is
+// Re(E' P dg/dl / g(l_i)), the factor divided out of the full product
+// (|g| >= 1 in form A, >= p in form B, so never zero).
 // Roots take form A (one FP32 instruction fewer per complex multiply) up to
 // the first block of 32 kept roots that holds a root with cos(theta) below
 // LONG_FORM_B_COS (there s^16 would leave FP32's normal range), form B from
 // that block on; kernel passes of 8, 16 or 32 roots never straddle it.
 //
-// FP32 rounding of the powers. A stored power s^e is rounded once, but the
-// kernel applies s^16 once per segment, so its rounding would add up over
-// the segments. It is the same factor for every point, so it is compensated
-// in the values that close each chain: E' makes the value exact with the
-// rounded s^16 applied nseg - 1 times, D' makes every full segment's
-// contributions exact with the rounded s^7, s^c and nseg - 2 rounded s^16,
-// and s^a makes the last segment's exact with D' and nseg - 1 rounded s^16.
-// Per kept root (by increasing angle) four granules
-//   {p, s^7}, {s^16, s^a}, {s^c, D'}, {E', 0, 0}
-// with E = 2 c'_j, D = E b'. Head: {c'_0, kept complex roots, c'_mid (the
-// real root's coefficient, odd k), 1 if the real root is present},
-// {first form-B root (a multiple of 32; = kept roots if none), 0, 0, 0}.
-// The real root's factor is l itself (a = 0, b = 1).
+// FP32 rounding of s^16. It is stored rounded once but applied once per
+// segment, so its rounding would add up over the segments. It is the same
+// factor for every point, so it is compensated in E': with the rounded s^16
+// applied nseg - 1 times, E' P is exact.
+// Per kept root (by increasing angle) two granules {p, s^16, 0}, {E', 0, 0}
+// with E = 2 c'_j. Head: {c'_0, kept complex roots, c'_mid (the real root's
+// coefficient, odd k), 1 if the real root is present}, {first form-B root (a
+// multiple of 32; = kept roots if none), 0, 0, 0}. The real root's factor is
+// l itself.
 namespace {
 struct Cx {
   double r, i;
@@ -330,7 +324,6 @@ static void build_long_pgf(const Shape& s, std::vector<float>& out) {
   }
   const int nseg = (k + LONG_SEG - 1) / LONG_SEG;
   const int n_last = k - LONG_SEG * (nseg - 1);
-  const int a_last = (n_last - 1) / 2, b_last = n_last - 1 - a_last, c_last = 8 - b_last + n_last;
   out.clear();
   push4(out, cr[0], nk, has_real ? cmid : 0.0, has_real ? 1.0 : 0.0);
   push4(out, form_b_from, 0, 0, 0);
@@ -339,21 +332,14 @@ static void build_long_pgf(const Shape& s, std::vector<float>& out) {
     const double p = pv[j];
     const Cx b{0.5 * (1.0 - z[j].r), -0.5 * z[j].i};  // b' = (1 - z')/2
     const Cx E{2.0 * cr[j], 2.0 * ci[j]};
-    const Cx D = cmul(E, b);
     const Cx sc = formb[j] ? b : Cx{b.r / p, b.i / p};
     if (1.0 / std::hypot(sc.r, sc.i) >= 32768.0) throw std::invalid_argument("long table: root factor bound exceeded");
-    const Cx s7 = f32(cpow(sc, 7)), s16 = f32(cpow(sc, 16)), scl = f32(cpow(sc, c_last));
+    const Cx s16 = f32(cpow(sc, 16));
     const Cx r16 = cdiv(cpow(sc, 16), s16);  // exact / rounded s^16
-    // E' = E s^n_last (s^16 / fl(s^16))^(nseg-1)
+    // E' = E s^n_last (s^16 / fl(s^16))^(nseg-1): with the rounded s^16 at
+    // the segment boundaries, E' prod_i g_i is the root's exact product
     const Cx Ep = cmul(cmul(E, cpow(sc, n_last)), cpow(r16, nseg - 1));
-    // D' = D s^b (s^7/fl(s^7)) (s^c/fl(s^c)) (s^16/fl(s^16))^(nseg-2)
-    const Cx Dp = f32(cmul(cmul(cmul(D, cpow(sc, b_last)), cmul(cdiv(cpow(sc, 7), s7), cdiv(cpow(sc, c_last), scl))),
-                           cpow(r16, nseg - 2)));
-    // s^a = D s^(b+a) (s^16/fl(s^16))^(nseg-1) / D'
-    const Cx Sa = cdiv(cmul(cmul(D, cpow(sc, b_last + a_last)), cpow(r16, nseg - 1)), Dp);
-    push4(out, p, s7.r, s7.i, 0.0);
-    push4(out, s16.r, s16.i, Sa.r, Sa.i);
-    push4(out, scl.r, scl.i, Dp.r, Dp.i);
+    push4(out, p, s16.r, s16.i, 0.0);
     push4(out, Ep.r, Ep.i, 0.0, 0.0);
   }
 }

@@ -58,17 +58,16 @@ void esp_coefficients(const Shape& s, std::vector<double>& c);
 //     FE = c0 + sum Re(E prod_i F_i),  dFE/dl_i = sum Re(D prod_{i'!=i} F_i')
 //  long form, probability-generating basis (every k > KSHORT):
 //     head {c0, n kept complex roots, c_mid, has_real}, {first form-B root, 0, 0, 0};
-//     per kept complex root (nonzero coefficient, increasing angle) four
-//     granules {p, s7.re, s7.im, 0}, {s16.re, s16.im, sa.re, sa.im},
-//     {sc.re, sc.im, D'.re, D'.im}, {E'.re, E'.im, 0, 0}.
+//     per kept complex root (nonzero coefficient, increasing angle) two
+//     granules {p, s16.re, s16.im, 0}, {E'.re, E'.im, 0, 0}.
 //     The factor of literal i at the root is s g(l_i), g = p l + i (form A,
 //     roots before the first form-B root; p = tan of the root's half angle in
 //     FP32) or g = l + i p (form B; p = cot); the coefficients are solved for
 //     the nodes that p defines. The first form-B root is a multiple of 32.
-//     With n_last = k - 16 floor((k-1)/16), a = floor((n_last-1)/2),
-//     b = n_last - 1 - a, c = 8 - b + n_last: s7 = s^7, s16 = s^16, sa = s^a,
-//     sc = s^c, D' = D s^b, E' = E s^n_last, E = 2 c'_j, D = E (1 - z'_j)/2,
-//     with the rounding of s^16 over the segments compensated in E', D', sa.
+//     With n_last = k - 16 floor((k-1)/16): s16 = s^16 rounded to FP32,
+//     E' = E s^n_last (s^16 / s16)^(nseg - 1), E = 2 c'_j, so that a walk
+//     multiplying the g's and s16 after every full segment of 16 literals
+//     ends at the root's true product over E'.
 //     The real root (odd k, has_real = 1) has the factor l_i and the
 //     coefficient c_mid (value and gradient weight).
 //     FE = c0 + sum Re(E s^k prod_i g_i) + c_mid prod_i l_i

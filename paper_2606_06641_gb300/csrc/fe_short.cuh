@@ -378,7 +378,7 @@ __device__ __forceinline__ void short_unit(const FeGroupArgs& a, long long warp,
     for (int i = 0; i < K; ++i) {
       const float sg = ((negm >> i) & 1u) ? -1.0f : 1.0f;
       const int slot = __ldg(&ls[i].y);
-      if (K <= KFUSE_MAX && slot < 0) continue;  // fused constraint: no derivative row
+      if (K == KFUSE && slot < 0) continue;  // fused constraint: no derivative row
       float* row = a.go + static_cast<long long>(slot) * a.go_pitch;
       if constexpr (V) {
         if (act[0]) {

@@ -78,14 +78,6 @@ bool fuse_enabled() {
   const char* e = std::getenv("AFS_FUSE");
   return !(e != nullptr && e[0] == '0');
 }
-// The same for the 4- and 5-literal constraints, on with AFS_FUSE_WIDE=1:
-// measured level with their FE launches on the hybrid workload (each
-// occurrence gathers k - 1 other states, more L2 traffic than the row it
-// replaces), so off by default.
-bool fuse_wide_enabled() {
-  const char* e = std::getenv("AFS_FUSE_WIDE");
-  return e != nullptr && e[0] == '1';
-}
 
 // Dropping consumed occurrence rows from L2 in the CSR pass (off when
 // AFS_DISCARD=0, for A/B timing).
@@ -198,7 +190,6 @@ struct afs_handle {
   long long L = 0;  // literal occurrences
   long long Lgo = 0;  // occurrences with a derivative row (not in fused constraints)
   long long n_fused = 0;  // occurrences in fused constraints
-  long long n_fused_wide = 0;  // of which in fused 4- and 5-literal constraints
   std::vector<int> inst_vbegin, inst_cbegin;
   // host copies for the independent re-check
   std::vector<int> h_lit_enc, h_lit_off, h_viol_off, h_cons_inst, h_var_inst;
@@ -219,7 +210,7 @@ struct afs_handle {
   // (spans of inst_arena, which is declared first so that it is freed last)
   DevBuf inst_arena;
   DevBuf litslot, cons_tab, cons_orig, cons_k, cons_lit, coef, csr_off, lit_enc, lit_off, viol_off, viol,
-      var_inst, err, chk_em, chk_ranges, chk_wide, fus_off, fus, fw_off, fw, cinst;
+      var_inst, err, chk_em, chk_ranges, chk_wide, fus_off, fus, cinst;
   // the instance graph by variable and per-constraint records (the learned initialiser's inputs)
   DevBuf v_off, v_enc, cinfo;
   int n_chk_ranges = 0;
@@ -467,12 +458,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   // occurrence rows: the CSR pass recomputes their derivatives from the
   // other literals' state
   const bool can_fuse = h->p.basis == AFS_BASIS_PGF && fuse_enabled();
-  const bool can_fuse_wide = h->p.basis == AFS_BASIS_PGF && fuse_wide_enabled();
-  auto fused_k = [&](int k) { return (can_fuse && k == KFUSE) || (can_fuse_wide && k > KFUSE && k <= KFUSE_MAX); };
-  // level-form operations per occurrence of a fused constraint: three FMAs
-  // for k = 3; the symmetric-sum recurrence over the k - 1 other literals
-  // and its combination with the k constants for k = 4, 5 (8 and 13)
-  auto fused_ops = [](int k) { return k == KFUSE ? 3.0 : (k - 1) * k / 2 - 1 + (k - 1); };
+  auto fused_k = [&](int k) { return can_fuse && k == KFUSE; };
   for (int pos = 0; pos < m; ++pos) {
     const int g = order[pos];
     const int k = gk[g];
@@ -501,7 +487,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     }
     {
       const double R = static_cast<double>((k + 1) / 2);
-      h->groups.back().work_alg += fused_k(k) ? fused_ops(k) * k : 16.0 * k * R + 2.0 * R;
+      h->groups.back().work_alg += fused_k(k) ? 3.0 * k : 16.0 * k * R + 2.0 * R;
     }
   }
   {
@@ -519,21 +505,15 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   // ---- CSR: slots in variable-major order, occurrences of a variable in
   // bucket order; occurrences in fused constraints get an entry
   // {other literal, other literal, table, negated} instead of a slot ----
-  std::vector<int> csr(h->n + 1, 0), fcsr(h->n + 1, 0), wcsr(h->n + 1, 0);
-  for (int pos = 0; pos < m; ++pos) {
-    const int k = b_k[pos];
-    std::vector<int>& list = !fused_k(k) ? csr : (k == KFUSE ? fcsr : wcsr);
-    for (int t = 0; t < k; ++t) list[(litslot[b_lit[pos] + t].x >> 1) + 1]++;
-  }
+  std::vector<int> csr(h->n + 1, 0), fcsr(h->n + 1, 0);
+  for (int pos = 0; pos < m; ++pos)
+    for (int t = 0; t < b_k[pos]; ++t) (fused_k(b_k[pos]) ? fcsr : csr)[(litslot[b_lit[pos] + t].x >> 1) + 1]++;
   long long n_fused = 0;
   for (int v = 0; v < h->n; ++v) {
     csr[v + 1] += csr[v];
-    n_fused += fcsr[v + 1] + wcsr[v + 1];
+    n_fused += fcsr[v + 1];
     fcsr[v + 1] = fcsr[v] + (fcsr[v + 1] + FUS_PAD - 1) / FUS_PAD * FUS_PAD;
-    wcsr[v + 1] += wcsr[v];
   }
-  std::vector<float4> fw(3 * static_cast<size_t>(wcsr[h->n]));
-  h->n_fused_wide = wcsr[h->n];
   // padding entries: zero constants, both other literals the variable itself
   std::vector<float4> fus(2 * static_cast<size_t>(fcsr[h->n]), make_float4(0.f, 0.f, 0.f, 0.f));
   for (int v = 0; v < h->n; ++v) {
@@ -553,8 +533,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     return it->second;
   };
   {
-    std::vector<int> fill(csr.begin(), csr.end() - 1), ffill(fcsr.begin(), fcsr.end() - 1),
-        wfill(wcsr.begin(), wcsr.end() - 1);
+    std::vector<int> fill(csr.begin(), csr.end() - 1), ffill(fcsr.begin(), fcsr.end() - 1);
     const std::vector<double>* cl_last = nullptr;
     Shape sh_last{-1, -1, -1, -1, -1};
     for (int pos = 0; pos < m; ++pos) {
@@ -567,28 +546,6 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
         int2& ls = litslot[b_lit[pos] + t];
         if (!fused_k(k)) {
           ls.y = fill[ls.x >> 1]++;
-          continue;
-        }
-        if (k > KFUSE) {
-          // {s c1, s c2, s c3, s c4}, {s c5, o1, o2, o3}, {o4 or -1, product, s c_k, 0}
-          int o[4] = {0, 0, 0, -1}, no = 0;
-          for (int u = 0; u < k; ++u)
-            if (u != t) o[no++] = litslot[b_lit[pos] + u].x;
-          const std::vector<double>& cl = *cl_last;
-          const double ss = (ls.x & 1) ? -1.0 : 1.0;
-          bool product = true;
-          for (int d = 1; d < k; ++d) product = product && std::fabs(cl[d]) < 1e-13;
-          auto fb = [](int i) {
-            float f;
-            std::memcpy(&f, &i, 4);
-            return f;
-          };
-          const size_t fe = 3 * static_cast<size_t>(wfill[ls.x >> 1]++);
-          fw[fe] = make_float4(static_cast<float>(ss * cl[1]), static_cast<float>(ss * cl[2]),
-                               static_cast<float>(ss * cl[3]), static_cast<float>(ss * cl[4]));
-          fw[fe + 1] = make_float4(k >= 5 ? static_cast<float>(ss * cl[5]) : 0.0f, fb(o[0]), fb(o[1]), fb(o[2]));
-          fw[fe + 2] = make_float4(fb(k >= 5 ? o[3] : -1), fb(product ? 1 : 0), static_cast<float>(ss * cl[k]), 0.0f);
-          ls.y = -1;
           continue;
         }
         int other[2] = {0, 0}, no = 0;
@@ -721,10 +678,6 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   up.add(h->coef, coef);
   up.add(h->csr_off, csr);
   up.add(h->fus_off, fcsr);
-  if (h->n_fused_wide > 0) {
-    up.add(h->fw_off, wcsr);
-    up.add(h->fw, fw);
-  }
   up.add(h->cinst, ginst);
   up.add(h->fus, fus);
   up.add(h->lit_enc, h->h_lit_enc);
@@ -859,8 +812,6 @@ static int launch_csr(afs_handle* h, const void* x, void* xout, int xt, long lon
   a.csr_off = h->csr_off.as<int>();
   a.fus_off = h->fus_off.as<int>();
   a.fus = h->fus.as<float4>();
-  a.fw_off = h->n_fused_wide > 0 ? h->fw_off.as<int>() : nullptr;
-  a.fw = h->fw.as<float4>();
   a.coef = h->coef.as<float4>();
   a.v_begin = 0;
   a.v_count = h->n;
@@ -908,8 +859,6 @@ static int launch_fused(afs_handle* h, const void* x, int b0, int nb, cudaStream
   a.v_count = h->n;
   a.fus_off = h->fus_off.as<int>();
   a.fus = h->fus.as<float4>();
-  a.fw_off = h->n_fused_wide > 0 ? h->fw_off.as<int>() : nullptr;
-  a.fw = h->fw.as<float4>();
   a.coef = h->coef.as<float4>();
   a.gf = h->gf.as<float>();
   a.gf_pitch = h->Bc;
@@ -1119,8 +1068,6 @@ static int enqueue_persistent(afs_handle* h, int nsteps, float eta, bool check, 
   u.v_count = h->n;
   u.fus_off = h->fus_off.as<int>();
   u.fus = h->fus.as<float4>();
-  u.fw_off = h->n_fused_wide > 0 ? h->fw_off.as<int>() : nullptr;
-  u.fw = h->fw.as<float4>();
   u.coef = h->coef.as<float4>();
   u.gf = h->gf.as<float>();
   u.gf_pitch = h->Bc;

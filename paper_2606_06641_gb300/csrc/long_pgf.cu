@@ -4,8 +4,7 @@
 // Sec. 2.1.2: a symmetric constraint's expansion is a combination, with the
 // constraint's DFT coefficients, of products over its literals at the roots
 // of unity; the gradient of literal i at a root is the product of the other
-// literals' factors, taken here as prefix x suffix (no division, so zero
-// factors are safe). Sec. 3.5: conjugate roots are paired, so only the roots
+// literals' factors. Sec. 3.5: conjugate roots are paired, so only the roots
 // of one half-plane are evaluated (each complex one counted twice through
 // the real part) plus, for odd k, the real root w = -1.
 //
@@ -17,24 +16,26 @@
 // broadcast loads.
 //
 // Factor form (coefficient table built on the host): at every complex root
-// the literal factor is s (p l + i), so a complex multiply of a running
-// product by it is three FP32 instructions (w = p l, two FMAs). Walks go in
-// segments of LONG_SEG literals; at each segment boundary running products
-// are at their true size (|prod| <= 1), which the table's powers of s
-// restore: inside a segment the checkpoint carries s^7 and the suffix s^8,
-// so that Re(prefix * suffix) is the true contribution and neither running
-// product leaves the FP32 range. No exponent bookkeeping is needed.
+// the literal factor is s g(l), g = p l + i (form A) or l + i p (form B), so
+// a complex multiply of a running product by it is three (four) FP32
+// instructions. The forward walk goes in segments of LONG_SEG literals and
+// multiplies by the table's s^16 after each full one, so the running product
+// is at its true size (|prod| <= 1) at every segment boundary and stays
+// within FP32 inside a segment; no exponent bookkeeping is needed.
 //
-// Per pass and lane: a forward walk stores one prefix checkpoint per segment
-// in shared memory; the backward walk, segment by segment from the end,
-// rebuilds the segment's prefixes in registers from the checkpoint, walks the
-// suffix down from the gradient weight and writes each contribution
-// Re(prefix_t * suffix_t) to a per-warp shared-memory tile (column = lane,
-// row = literal); the lanes then sum the tile's rows over the slot's roots
-// with 16-byte reads and add them to the slot's gradient row. The sum order
-// is fixed (deterministic). The real root's factor is l itself: its product
-// and leave-one-out products are real and take a prefix/suffix scan over the
-// slot's lanes after the passes.
+// Gradient by division. With T = E' prod g the root's exact product, the
+// derivative in literal i is Re(T g'(l_i) / g(l_i)): the factor divided out
+// of the full product. |g| >= 1 in form A and >= p in form B (p at least
+// tan(pi / (2 (k + 1))) there), so the division never meets a zero and keeps
+// the product's relative error; per (literal, root) it costs the forward
+// multiply plus about four FP32 instructions and one approximate reciprocal,
+// instead of rebuilding prefix and suffix products. The lanes then swap
+// roles: each lane takes 4 literals of its slot at a time and walks the
+// slot's W roots (their constants broadcast from shared memory), summing in
+// registers and adding each literal's sum to the slot's gradient row once
+// per pass (fixed order, deterministic). The real root's factor is l itself,
+// which can be zero: its leave-one-out products take a prefix/suffix scan
+// over the slot's lanes after the passes.
 #include <cuda_bf16.h>
 
 #include "afsat.h"
@@ -47,12 +48,11 @@ namespace afs {
 
 namespace {
 
-constexpr int LTP = 36;  // tile row pitch in floats (16-byte column reads hit distinct banks)
 
 // Shared memory of one CTA.
 struct LongPgfLayout {
-  int kpad, nseg, rt, ep, gp;
-  size_t off_ell, off_gs, off_ck, off_tile, bytes;
+  int kpad, nseg, rt, ep, gp, ckw;
+  size_t off_ell, off_gs, off_ck, off_rc, bytes;
   __host__ __device__ LongPgfLayout(int kmax, int W, int NW) {
     kpad = (kmax + LONG_SEG - 1) / LONG_SEG * LONG_SEG;
     nseg = kpad / LONG_SEG;
@@ -60,13 +60,22 @@ struct LongPgfLayout {
     const int k32 = (kpad + 31) & ~31;
     ep = k32 + 8;                   // literal-value rows: the slots' 16-byte reads fall in distinct banks
     gp = k32 + (W < 32 ? W : 0);    // gradient rows: the slots' column updates fall in distinct banks
+    ckw = (kpad + W - 1) / W * 32;  // per warp: the real root's within-chunk suffixes
     off_ell = static_cast<size_t>(kpad) * 8;                         // literal list (int2)
     off_gs = off_ell + static_cast<size_t>(rt) * ep * 4;            // literal values
     off_ck = off_gs + static_cast<size_t>(rt) * gp * 4;             // gradient accumulators
-    off_tile = off_ck + static_cast<size_t>(NW) * nseg * 32 * 8;    // prefix checkpoints
-    bytes = off_tile + static_cast<size_t>(NW) * LONG_SEG * LTP * 4;  // contribution tiles
+    off_rc = off_ck + static_cast<size_t>(NW) * ckw * 4;            // per-warp scratch
+    bytes = off_rc + static_cast<size_t>(NW) * 32 * 16;              // each warp's root constants
   }
 };
+
+// Approximate reciprocal (PTX rcp.approx, within one unit in the last place)
+// of a normal positive number.
+__device__ __forceinline__ float rcp_apx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 // P <- P (w + i)
 __device__ __forceinline__ void gmul(float w, float& r, float& i) {
@@ -96,109 +105,33 @@ __device__ __forceinline__ void cmul(float& r, float& i, float br, float bi) {
   i = ni;
 }
 
-// Backward walk of one segment of N literals: prefixes rebuilt from the
-// scaled checkpoint Q, suffix S (scaled) walked down, contribution of literal
-// t written to tcol[t * LTP]. el is 16-byte aligned; the row is padded, so
-// the last vector read may pass N. Form A keeps w = p l per literal in
-// registers (computed once for both walks), form B the literal values.
-template <int N, bool FB>
-__device__ __forceinline__ void pgf_segment(const float* el, float p, float Qr, float Qi, float& Sr, float& Si,
-                                            float* tcol) {
-  float wv[N], pr[N], pi[N];
-  const float sc = FB ? 1.0f : p;
-#pragma unroll
-  for (int t = 0; t < N; t += 4) {
-    const float4 v = *reinterpret_cast<const float4*>(el + t);
-    wv[t] = v.x * sc;
-    if (t + 1 < N) wv[t + 1] = v.y * sc;
-    if (t + 2 < N) wv[t + 2] = v.z * sc;
-    if (t + 3 < N) wv[t + 3] = v.w * sc;
-  }
-  pr[0] = Qr;
-  pi[0] = Qi;
-#pragma unroll
-  for (int t = 0; t + 1 < N; ++t) {
-    pr[t + 1] = pr[t];
-    pi[t + 1] = pi[t];
-    if constexpr (FB) bmul(wv[t], p, pr[t + 1], pi[t + 1]);
-    else gmul(wv[t], pr[t + 1], pi[t + 1]);
-  }
-#pragma unroll
-  for (int t = N - 1; t >= 0; --t) {
-    tcol[t * LTP] = fmaf(pr[t], Sr, -pi[t] * Si);
-    if constexpr (FB) bmul(wv[t], p, Sr, Si);
-    else gmul(wv[t], Sr, Si);
-  }
-}
-
-template <bool FB>
-__device__ __forceinline__ void pgf_tail_segment(int n, const float* el, float p, float Qr, float Qi, float& Sr,
-                                                 float& Si, float* tcol) {
-  switch (n) {
-#define AFS_TAIL_CASE(N) \
-  case N:                \
-    pgf_segment<N, FB>(el, p, Qr, Qi, Sr, Si, tcol); \
-    break;
-    AFS_TAIL_CASE(1) AFS_TAIL_CASE(2) AFS_TAIL_CASE(3) AFS_TAIL_CASE(4) AFS_TAIL_CASE(5) AFS_TAIL_CASE(6)
-    AFS_TAIL_CASE(7) AFS_TAIL_CASE(8) AFS_TAIL_CASE(9) AFS_TAIL_CASE(10) AFS_TAIL_CASE(11) AFS_TAIL_CASE(12)
-    AFS_TAIL_CASE(13) AFS_TAIL_CASE(14) AFS_TAIL_CASE(15) AFS_TAIL_CASE(16)
-#undef AFS_TAIL_CASE
-    default:
-      break;
-  }
-}
-
-// Sums of the warp tile's rows (literals of the segment) over each slot's
-// roots, added to the slot's gradient row gseg (n literals in the segment).
-template <int W>
-__device__ __forceinline__ void tile_column_sums(const float* tw, int lane, float* gseg, int n) {
-  if constexpr (W == 8) {
-    const int h = lane >> 3, c = lane & 7;
-#pragma unroll
-    for (int cc = 0; cc < 2; ++cc) {
-      const int col = c + 8 * cc;
-      const float4* q = reinterpret_cast<const float4*>(tw + col * LTP + h * 8);
-      const float4 u0 = q[0], u1 = q[1];
-      const float s = ((u0.x + u0.y) + (u0.z + u0.w)) + ((u1.x + u1.y) + (u1.z + u1.w));
-      if (col < n) gseg[col] += s;
-    }
-  } else {
-    const int h = lane >> 4, c = lane & 15;
-    const float4* q = reinterpret_cast<const float4*>(tw + c * LTP + h * 16);
-    const float4 u0 = q[0], u1 = q[1], u2 = q[2], u3 = q[3];
-    float s = (((u0.x + u0.y) + (u0.z + u0.w)) + ((u1.x + u1.y) + (u1.z + u1.w))) +
-              (((u2.x + u2.y) + (u2.z + u2.w)) + ((u3.x + u3.y) + (u3.z + u3.w)));
-    if constexpr (W == 32) {
-      s += __shfl_xor_sync(0xffffffffu, s, 16);
-      if (lane < n) gseg[lane] += s;
-    } else {
-      if (c < n) gseg[c] += s;
-    }
-  }
-}
-
-// One pass: the slot's W lanes evaluate roots j0 .. j0 + W - 1 of the table
-// for their restart (forward checkpoints, value, backward contributions
-// added to the gradient row gr); returns the pass's value summed over the
-// slot's roots.
+// One pass: the slot's W lanes take roots j0 .. j0 + W - 1. A forward walk
+// gives the full product P (true size at every segment boundary, restored by
+// s^16) and T = E' P, whose real part is the root's value; the derivative in
+// literal t is then Re(U / g_t), U = T dg/dl (p for form A, 1 for form B):
+// (U_r w + U_i) / (w^2 + 1) with w = p l in form A, (U_r l + T_i p) /
+// (l^2 + p^2) in form B. For the gradient the lanes swap roles: each lane
+// publishes its root's {U_r, U_i', p, p^2} to the warp's shared row, then the
+// slot's lanes take 4 W literals at a time (4 per lane, values in registers)
+// and walk the slot's W roots (broadcast reads), summing in registers and
+// adding each literal's sum to the gradient row once per pass (fixed order).
+// Lanes past the table's roots get a zero weight and bounded factors.
 template <int W, bool FB>
 __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0, int rl, int lane, const float* el,
-                                          float* gr, float2* myck, float* tw, int nseg, int n_last) {
+                                          float* gr, float4* rc, int k, int nseg, int n_last) {
   const int j = j0 + rl;
-  float p = 0.f, s7r = 0.f, s7i = 0.f, s16r = 0.f, s16i = 0.f, sar = 0.f, sai = 0.f, scr = 0.f, sci = 0.f;
-  float dr = 0.f, di = 0.f, er = 0.f, ei = 0.f;
+  float p = FB ? 1.0f : 0.0f, s16r = FB ? 0.00390625f : 1.0f, s16i = 0.f, er = 0.f, ei = 0.f;
   if (j < nroots) {
-    const float4* rg = tab + 2 + 4 * j;
-    const float4 g0 = __ldg(rg), g1 = __ldg(rg + 1), g2 = __ldg(rg + 2), g3 = __ldg(rg + 3);
-    p = g0.x; s7r = g0.y; s7i = g0.z;
-    s16r = g1.x; s16i = g1.y; sar = g1.z; sai = g1.w;
-    scr = g2.x; sci = g2.y; dr = g2.z; di = g2.w;
-    er = g3.x; ei = g3.y;
+    const float4* rg = tab + 2 + 2 * j;
+    const float4 g0 = __ldg(rg), g1 = __ldg(rg + 1);
+    p = g0.x;
+    s16r = g0.y;
+    s16i = g0.z;
+    er = g1.x;
+    ei = g1.y;
   }
-  // forward: one checkpoint (true size) per segment start
   float Pr = 1.0f, Pi = 0.0f;
   for (int sg = 0; sg + 1 < nseg; ++sg) {
-    myck[sg * 32 + lane] = make_float2(Pr, Pi);
     const float4* e4 = reinterpret_cast<const float4*>(el + sg * LONG_SEG);
 #pragma unroll
     for (int u = 0; u < LONG_SEG / 4; ++u) {
@@ -210,41 +143,58 @@ __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0,
     }
     cmul(Pr, Pi, s16r, s16i);
   }
-  myck[(nseg - 1) * 32 + lane] = make_float2(Pr, Pi);
   {
     const float* e = el + (nseg - 1) * LONG_SEG;
     for (int t = 0; t < n_last; ++t) fmul<FB>(e[t], p, Pr, Pi);
   }
-  // the pass's value, summed over the slot's roots (every lane of the slot)
-  float v = fmaf(er, Pr, -ei * Pi);
+  const float Tr = fmaf(er, Pr, -ei * Pi), Ti = fmaf(er, Pi, ei * Pr);
+  float v = Tr;
 #pragma unroll
   for (int o = W / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-
-  // backward: the last segment first, then the full ones
-  float Sr = dr, Si = di;
-  {
-    float2 Q = myck[(nseg - 1) * 32 + lane];
-    cmul(Q.x, Q.y, sar, sai);
-    pgf_tail_segment<FB>(n_last, el + (nseg - 1) * LONG_SEG, p, Q.x, Q.y, Sr, Si, tw + lane);
-    cmul(Sr, Si, scr, sci);
-    __syncwarp();
-    tile_column_sums<W>(tw, lane, gr + (nseg - 1) * LONG_SEG, n_last);
-    __syncwarp();  // the tile is read before the next segment's rows
+  // form A: U = T p; form B: U = T, and the numerator's T_i p (both: Ti p)
+  rc[lane] = make_float4(FB ? Tr : Tr * p, Ti * p, p, p * p);
+  __syncwarp();
+  const float4* rs = rc + (lane & ~(W - 1));  // the slot's W roots
+  for (int c0 = 0; c0 < k; c0 += 4 * W) {
+    float lv[4], g[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = c0 + q * W + rl;
+      lv[q] = i < k ? el[i] : 0.0f;
+      g[q] = 0.0f;
+    }
+#pragma unroll 4
+    for (int jj = 0; jj < W; ++jj) {
+      const float4 c = rs[jj];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float num, den;
+        if constexpr (FB) {
+          num = fmaf(c.x, lv[q], c.y);
+          den = fmaf(lv[q], lv[q], c.w);
+        } else {
+          const float w = lv[q] * c.z;
+          num = fmaf(c.x, w, c.y);
+          den = fmaf(w, w, 1.0f);
+        }
+        g[q] = fmaf(num, rcp_apx(den), g[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = c0 + q * W + rl;
+      if (i < k) gr[i] += g[q];
+    }
   }
-  for (int sg = nseg - 2; sg >= 0; --sg) {
-    float2 Q = myck[sg * 32 + lane];
-    cmul(Q.x, Q.y, s7r, s7i);
-    pgf_segment<LONG_SEG, FB>(el + sg * LONG_SEG, p, Q.x, Q.y, Sr, Si, tw + lane);
-    cmul(Sr, Si, s16r, s16i);
-    __syncwarp();
-    tile_column_sums<W>(tw, lane, gr + sg * LONG_SEG, LONG_SEG);
-    __syncwarp();
-  }
+  __syncwarp();  // the root row is read before the next pass writes it
   return v;
 }
 
+// resident warps per SM the kernel is compiled for (register cap)
+constexpr int LONG_WARPS_PER_SM = 32;
+
 template <typename XT, int W, int NW>
-__global__ void __launch_bounds__(NW * 32, 24 / NW) fe_grad_long_pgf_kernel(FeGroupArgs a) {
+__global__ void __launch_bounds__(NW * 32, LONG_WARPS_PER_SM / NW) fe_grad_long_pgf_kernel(FeGroupArgs a) {
   constexpr int SL = 32 / W;   // restarts per warp
   constexpr int RT = NW * SL;  // restarts per CTA
   extern __shared__ __align__(16) unsigned char smem[];
@@ -267,7 +217,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW) fe_grad_long_pgf_kernel(FeGr
   float* ell = reinterpret_cast<float*>(smem + L.off_ell);
   float* gs = reinterpret_cast<float*>(smem + L.off_gs);
   float2* ck = reinterpret_cast<float2*>(smem + L.off_ck);
-  float* tls = reinterpret_cast<float*>(smem + L.off_tile);
+  float4* rcs = reinterpret_cast<float4*>(smem + L.off_rc);
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const unsigned lit_bytes = static_cast<unsigned>((k + 1) & ~1) * 8u;
@@ -307,8 +257,8 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW) fe_grad_long_pgf_kernel(FeGr
   const int r = w * SL + slot;
   const float* el = ell + r * L.ep;
   float* gr = gs + r * L.gp;
-  float2* myck = ck + static_cast<size_t>(w) * L.nseg * 32;
-  float* tw = tls + w * LONG_SEG * LTP;
+  float* myck = reinterpret_cast<float*>(ck) + static_cast<size_t>(w) * L.ckw;
+  float4* rcw = rcs + w * 32;
   const int nseg = (k + LONG_SEG - 1) / LONG_SEG;
   const int n_last = k - LONG_SEG * (nseg - 1);
   float fe_part = 0.0f;
@@ -318,19 +268,19 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW) fe_grad_long_pgf_kernel(FeGr
   const int first_b = static_cast<int>(__ldg(tab + 1).x);
   for (int j0 = 0; j0 < nroots; j0 += W) {
     if (j0 < first_b)
-      fe_part += pgf_pass<W, false>(tab, nroots, j0, rl, lane, el, gr, myck, tw, nseg, n_last);
+      fe_part += pgf_pass<W, false>(tab, nroots, j0, rl, lane, el, gr, rcw, k, nseg, n_last);
     else
-      fe_part += pgf_pass<W, true>(tab, nroots, j0, rl, lane, el, gr, myck, tw, nseg, n_last);
+      fe_part += pgf_pass<W, true>(tab, nroots, j0, rl, lane, el, gr, rcw, k, nseg, n_last);
   }
 
   if (has_real) {
     // the real root: value c_mid prod l, gradient c_mid prod_{i' != i} l_i'.
     // The slot's lanes split the literals into W contiguous chunks; the
-    // within-chunk suffixes go to this warp's (now free) checkpoint area.
+    // within-chunk suffixes go to this warp's scratch area.
     const float em = head.z;
     const int chunk = (k + W - 1) / W;
     const int i0 = min(k, rl * chunk), i1 = min(k, i0 + chunk);
-    float* scr = reinterpret_cast<float*>(myck);
+    float* scr = myck;
     float sl = 1.0f;
     for (int i = i1 - 1; i >= i0; --i) {
       scr[(i - i0) * 32 + lane] = sl;

@@ -20,8 +20,8 @@ namespace {
 // 16 MiB of device memory, held on every GPU that loads the library until the
 // process exits. It holds (literal occurrences) x (restarts per chunk) floats;
 // chunks of 32..256 restarts are used, so instances up to 131072 literal
-// occurrences with derivative rows (those outside 3- to 5-literal
-// constraints) fit.
+// occurrences with derivative rows (those outside 3-literal constraints)
+// fit.
 constexpr long long kScratchBytes = 16LL << 20;
 constexpr long long kScratchFloats = kScratchBytes / static_cast<long long>(sizeof(float));
 static __device__ __align__(256) float g_scratch[kScratchFloats];

@@ -45,97 +45,6 @@ __device__ __forceinline__ float stored_value<__nv_bfloat16>(float v) {
   return __bfloat162float(__float2bfloat16_rn(v));
 }
 
-// Fused 4- and 5-literal constraints: the derivative of occurrence `self` is
-// s_self * sum_d c_{d+1} e_d(l_others) (the level form of Eq. 1), the
-// elementary symmetric sums e_d of the other literals' values l = s x built
-// one literal at a time (e_d += l e_{d-1}, highest d first) and combined with
-// the entry's constants (the self sign folded in); parities (only the top
-// level nonzero) take the product of the other literals directly. Entries are
-// read two at a time (their state loads in flight together) and added to acc
-// in list order, the constants summed once at the end. R consecutive restarts
-// per lane from column col.
-template <typename XT, int R, bool OFF32 = false, bool COH = false>
-__device__ __forceinline__ void fused_wide_sum(const CsrArgs& a, int v, long long col, bool act, float (&acc)[R]) {
-  if (a.fw_off == nullptr) return;
-  const int f0 = __ldg(a.fw_off + v), f1 = __ldg(a.fw_off + v + 1);
-  const XT* xc = static_cast<const XT*>(a.x) + col;
-  constexpr int WB = 2;
-  float cs = 0.0f;
-  for (int f = f0; f < f1; f += WB) {  // uniform per warp
-    float4 q0[WB], q1[WB], q2[WB];
-    float l[WB][4][R];
-#pragma unroll
-    for (int u = 0; u < WB; ++u) {
-      const bool ok = f + u < f1;
-      q0[u] = ok ? __ldg(a.fw + 3 * (f + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
-      q1[u] = ok ? __ldg(a.fw + 3 * (f + u) + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-      q2[u] = ok ? __ldg(a.fw + 3 * (f + u) + 2) : make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);
-      const int o[4] = {__float_as_int(q1[u].y), __float_as_int(q1[u].z), __float_as_int(q1[u].w),
-                        __float_as_int(q2[u].x)};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const bool ld = ok && act && (j < 3 || o[3] >= 0);
-        const int vj = ld ? (o[j] >> 1) : 0;
-        const XT* p = OFF32 ? xc + static_cast<unsigned>(vj) * static_cast<unsigned>(a.x_pitch)
-                            : xc + static_cast<long long>(vj) * a.x_pitch;
-        float t[R];
-        if constexpr (R == 4) {
-          if (ld) {
-            load_xvec<XT, 4, COH>(p, t);
-          } else {
-#pragma unroll
-            for (int r = 0; r < R; ++r) t[r] = 0.0f;
-          }
-        } else {
-#pragma unroll
-          for (int r = 0; r < R; ++r) t[r] = ld ? load_x<XT, COH>(p + r) : 0.0f;
-        }
-        const bool neg = ld && (o[j] & 1);
-#pragma unroll
-        for (int r = 0; r < R; ++r) l[u][j][r] = neg ? -t[r] : t[r];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < WB; ++u) {
-      if (f + u >= f1) continue;  // uniform per warp
-      const bool four = __float_as_int(q2[u].x) >= 0;
-      if (__float_as_int(q2[u].y) != 0) {  // a parity: s c_k times the product of the others
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          float pr = l[u][0][r] * l[u][1][r];
-          pr *= l[u][2][r];
-          if (four) pr *= l[u][3][r];
-          acc[r] = fmaf(q2[u].z, pr, acc[r]);
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          float e1 = l[u][0][r];
-          float e2 = e1 * l[u][1][r];
-          e1 += l[u][1][r];
-          float e3 = e2 * l[u][2][r];
-          e2 = fmaf(e1, l[u][2][r], e2);
-          e1 += l[u][2][r];
-          float e4 = 0.0f;
-          if (four) {
-            e4 = e3 * l[u][3][r];
-            e3 = fmaf(e2, l[u][3][r], e3);
-            e2 = fmaf(e1, l[u][3][r], e2);
-            e1 += l[u][3][r];
-          }
-          float t = fmaf(q0[u].y, e1, acc[r]);
-          t = fmaf(q0[u].z, e2, t);
-          t = fmaf(q0[u].w, e3, t);
-          acc[r] = four ? fmaf(q1[u].x, e4, t) : t;
-        }
-      }
-      cs += q0[u].x;
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) acc[r] += cs;
-}
-
 // Fused constraints (k = KFUSE = 3, probability-generating tables): the
 // derivative of occurrence `self` is s_self * dFE/dl_self, recomputed from the
 // two other literals' state: the real root w = -1 contributes E l1 l2, the
@@ -200,7 +109,6 @@ __device__ __forceinline__ void fused_sum(const CsrArgs& a, int v, long long col
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) acc[r] += cs;
-  fused_wide_sum<XT, R, OFF32, COH>(a, v, col, act, acc);
 }
 
 // fused_sum for few restarts, where a variable's occurrence list is a chain
@@ -260,7 +168,6 @@ __device__ __forceinline__ void fused_sum_pf(const CsrArgs& a, int v, long long 
   }
 #pragma unroll
   for (int r = 0; r < 4; ++r) acc[r] += cs;
-  fused_wide_sum<XT, 4, OFF32, COH>(a, v, col, act, acc);
 }
 constexpr int FUSED_PF_BATCH = 4;  // occurrences whose state loads are in flight together (fused_sum_pf)
 

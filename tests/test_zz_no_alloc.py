@@ -66,8 +66,8 @@ def test_noalloc_mixed_long_constraints():
 
 
 def test_noalloc_rejects_instances_beyond_the_array():
-    # 180000 occurrences of 6-clauses (each with a derivative row; 3- to
-    # 5-literal constraints have none) x 32 restarts x 4 bytes > 16 MiB
+    # 180000 occurrences of 6-clauses (each with a derivative row) x 32
+    # restarts x 4 bytes > 16 MiB
     inst = synth.random_ksat(20000, 30000, 6, synth.rng_for(400, 0))
     assert inst.n_lits > 131072
     h = bd.load_instance(inst)
