@@ -111,10 +111,11 @@ __device__ __forceinline__ void cmul(float& r, float& i, float br, float bi) {
 // literal t is then Re(U / g_t), U = T dg/dl (p for form A, 1 for form B):
 // (U_r w + U_i) / (w^2 + 1) with w = p l in form A, (U_r l + T_i p) /
 // (l^2 + p^2) in form B. For the gradient the lanes swap roles: each lane
-// publishes its root's {U_r, U_i', p, p^2} to the warp's shared row, then the
-// slot's lanes take 4 W literals at a time (4 per lane, values in registers)
-// and walk the slot's W roots (broadcast reads), summing in registers and
-// adding each literal's sum to the gradient row once per pass (fixed order).
+// publishes its root's four derivative constants to the warp's shared row,
+// then the slot's lanes take 4 W literals at a time (4 per lane, l and l^2 in
+// registers) and walk the slot's W roots (broadcast reads): per (literal,
+// root) three FMAs and a reciprocal, summed in registers and added to the
+// gradient row once per pass (fixed order).
 // Lanes past the table's roots get a zero weight and bounded factors.
 template <int W, bool FB>
 __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0, int rl, int lane, const float* el,
@@ -151,34 +152,28 @@ __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0,
   float v = Tr;
 #pragma unroll
   for (int o = W / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  // form A: U = T p; form B: U = T, and the numerator's T_i p (both: Ti p)
-  rc[lane] = make_float4(FB ? Tr : Tr * p, Ti * p, p, p * p);
+  // the derivative as (A l + B') / (alpha l^2 + beta): form A (U = T p,
+  // w = p l) A = T_r p^2, B' = T_i p, alpha = p^2, beta = 1; form B (U = T)
+  // A = T_r, B' = T_i p, alpha = 1, beta = p^2
+  const float p2 = p * p;
+  rc[lane] = FB ? make_float4(Tr, Ti * p, 1.0f, p2) : make_float4(Tr * p2, Ti * p, p2, 1.0f);
   __syncwarp();
   const float4* rs = rc + (lane & ~(W - 1));  // the slot's W roots
   for (int c0 = 0; c0 < k; c0 += 4 * W) {
-    float lv[4], g[4];
+    float lv[4], l2[4], g[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int i = c0 + q * W + rl;
       lv[q] = i < k ? el[i] : 0.0f;
+      l2[q] = lv[q] * lv[q];
       g[q] = 0.0f;
     }
 #pragma unroll 4
     for (int jj = 0; jj < W; ++jj) {
       const float4 c = rs[jj];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float num, den;
-        if constexpr (FB) {
-          num = fmaf(c.x, lv[q], c.y);
-          den = fmaf(lv[q], lv[q], c.w);
-        } else {
-          const float w = lv[q] * c.z;
-          num = fmaf(c.x, w, c.y);
-          den = fmaf(w, w, 1.0f);
-        }
-        g[q] = fmaf(num, rcp_apx(den), g[q]);
-      }
+      for (int q = 0; q < 4; ++q)
+        g[q] = fmaf(fmaf(c.x, lv[q], c.y), rcp_apx(fmaf(c.z, l2[q], c.w)), g[q]);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
