@@ -513,10 +513,12 @@ def dominant_kernel(groups, B: int, chunk: int, peak_tinst: float, peak_src: str
            "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock, {peak_src})"}
     if kind == 1 or (kind == 0 and max(d["kmax"]) <= 24):
         # the kernel's own algorithm (gradient by division): per (literal,
-        # root) 3 FP32 instructions for the forward product and 5 for the
-        # derivative (w = p l, numerator, denominator, reciprocal, sum)
-        out["division_form"] = {"instr_per_literal_root": 8,
-                                "frac": achieved / peak_tinst * 8.0 / 16.0,
+        # root) 3 FP32 instructions for the forward product and, for the
+        # derivative, numerator, denominator, reciprocal and sum (long) or
+        # those and w = l / gamma (short)
+        own = 7 if kind == 1 else 8
+        out["division_form"] = {"instr_per_literal_root": own,
+                                "frac": achieved / peak_tinst * own / 16.0,
                                 "note": "the frac above counts 16 per (literal, root), the prefix/suffix work model"}
     counters = counters.get(KIND_NAMES[kind]) if counters else None
     if counters:
