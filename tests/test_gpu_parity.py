@@ -88,6 +88,25 @@ def test_long_lengths(k):
         _check_eval(inst, synth.vertex_x0(inst.n, 6, k))
 
 
+@pytest.mark.parametrize("k", [64, 101, 256, 301, 512])
+def test_long_lengths_at_exact_zeros(k):
+    """The long kernel divides each literal's factor out of the root's full
+    product. Points where literal values are exactly 0 make the second-form
+    factors l + i p as small as they get (i p), and the real root's factor
+    (odd k) exactly 0; points mixing 0 with the vertices -1, +1 and interior
+    values must still match the oracle within 1e-5."""
+    rng = np.random.default_rng(700 + k)
+    for t, op, r, par in ((synth.CARD, synth.GE, k // 2, 1), (synth.XOR, 0, 0, 1), (synth.EK, 0, k // 3, 1),
+                          (synth.NAE, 0, 0, 1)):
+        inst = synth.single_type(t, k, 2, k + 3, index=k + 3 * t, op=op, param=r, parity=par)
+        B = 12
+        x = rng.choice(np.array([0.0, -1.0, 1.0, 0.3, -0.7]), size=(inst.n, B), p=[0.4, 0.15, 0.15, 0.15, 0.15])
+        x[:, 0] = 0.0                      # every literal exactly 0
+        x[: inst.n // 2, 1] = 0.0          # half of them 0, the rest interior
+        x[inst.n // 2:, 1] = rng.uniform(-1, 1, inst.n - inst.n // 2)
+        _check_eval(inst, x.astype(np.float32))
+
+
 @pytest.mark.parametrize("k", [100, 101, 102, 127, 200, 393, 480])
 def test_long_form_boundaries(k):
     """Lengths where the long tables switch the passes of roots near pi/2 to
