@@ -210,12 +210,12 @@ struct afs_handle {
   // (spans of inst_arena, which is declared first so that it is freed last)
   DevBuf inst_arena;
   DevBuf litslot, cons_tab, cons_orig, cons_k, cons_lit, coef, csr_off, lit_enc, lit_off, viol_off, viol,
-      var_inst, err, chk_em, chk_ranges, chk_wide, fus_off, fus, cinst;
+      var_inst, err, chk_em, chk_ranges, chk_wide, chk_longr, fus_off, fus, cinst;
   // the instance graph by variable and per-constraint records (the learned initialiser's inputs)
   DevBuf v_off, v_enc, cinfo;
   int n_chk_ranges = 0;
-  int n_chk_wide = 0;       // runs of the lane-per-constraint check (chk_wide_ok)
-  bool chk_wide_ok = false;
+  int n_chk_wide = 0;       // runs of the lane-per-constraint check (k <= 62)
+  int n_chk_longr = 0;      // ranges of one constraint each (k > 62) beside them
   // restart state
   int B = 0, xt = XT_F32;
   long long pitch = 0;
@@ -627,25 +627,28 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
     }
   }
   h->n_chk_ranges = static_cast<int>(chk_ranges.size());
-  // runs for the lane-per-constraint check of few restart words: <= 31
-  // constraints of one instance, <= CHECK_WIDE_STAGE literals (only when no
-  // constraint is longer than 62 literals)
-  std::vector<int4> chk_wide;
-  h->chk_wide_ok = true;
-  for (int g = 0; g < m; ++g) h->chk_wide_ok = h->chk_wide_ok && gk[g] <= 62;
-  if (h->chk_wide_ok) {
-    for (int i = 0; i < n_inst; ++i) {
-      int c = h->inst_cbegin[i];
-      const int ce = h->inst_cbegin[i + 1];
-      while (c < ce) {
-        int e = c, lits_in = 0;
-        while (e < ce && e - c < 31 && lits_in + gk[e] <= CHECK_WIDE_STAGE) lits_in += gk[e++];
-        chk_wide.push_back(make_int4(c, e, i, 0));
-        c = e;
+  // for the lane-per-constraint check of few restart words: runs of <= 31
+  // constraints of one instance with at most 62 literals each and
+  // <= CHECK_WIDE_STAGE literals in all; each longer constraint is a range of
+  // its own for the lane-per-word kernel
+  std::vector<int4> chk_wide, chk_longr;
+  for (int i = 0; i < n_inst; ++i) {
+    int c = h->inst_cbegin[i];
+    const int ce = h->inst_cbegin[i + 1];
+    while (c < ce) {
+      if (gk[c] > 62) {
+        chk_longr.push_back(make_int4(c, c + 1, i, 0));
+        ++c;
+        continue;
       }
+      int e = c, lits_in = 0;
+      while (e < ce && gk[e] <= 62 && e - c < 31 && lits_in + gk[e] <= CHECK_WIDE_STAGE) lits_in += gk[e++];
+      chk_wide.push_back(make_int4(c, e, i, 0));
+      c = e;
     }
   }
   h->n_chk_wide = static_cast<int>(chk_wide.size());
+  h->n_chk_longr = static_cast<int>(chk_longr.size());
   h->h_var_inst.resize(h->n);
   for (int i = 0; i < n_inst; ++i)
     for (int v = h->inst_vbegin[i]; v < h->inst_vbegin[i + 1]; ++v) h->h_var_inst[v] = i;
@@ -688,6 +691,7 @@ static int build_handle(const afs_cons* cons, const int32_t* cons_begin, const i
   up.add(h->chk_em, chk_em);
   up.add(h->chk_ranges, chk_ranges);
   up.add(h->chk_wide, chk_wide);
+  up.add(h->chk_longr, chk_longr);
   up.add(h->err, zero1);
   up.add(h->v_off, v_off_h);
   up.add(h->v_enc, v_enc_h);
@@ -871,7 +875,26 @@ static int launch_fused(afs_handle* h, const void* x, int b0, int nb, cudaStream
 // h->unsat: the bit-sliced check in count mode, then the solved fold.
 // The checks take one constraint per lane when the restarts fill few words
 // (a lane per word would leave most of each warp idle).
-static bool use_wide_check(const afs_handle* h) { return h->chk_wide_ok && h->W <= CHECK_WIDE_MAX_W; }
+static bool use_wide_check(const afs_handle* h) { return h->W <= CHECK_WIDE_MAX_W; }
+
+// The check as one lane-per-word launch over every range, or, for few
+// words, the lane-per-constraint launch over the runs of short constraints
+// and a lane-per-word launch over the longer constraints (one range each).
+// Returns the number of launches.
+static int launch_check_any(afs_handle* h, CheckArgs c, cudaStream_t s) {
+  if (!use_wide_check(h)) {
+    launch_check_bits(c, s);
+    return 1;
+  }
+  c.ranges = h->chk_wide.as<int4>();
+  c.n_ranges = h->n_chk_wide;
+  launch_check_wide(c, s);
+  if (h->n_chk_longr == 0) return 1;
+  c.ranges = h->chk_longr.as<int4>();
+  c.n_ranges = h->n_chk_longr;
+  launch_check_bits(c, s);
+  return 2;
+}
 
 static int launch_check(afs_handle* h, const void* x, cudaStream_t s) {
   (void)x;
@@ -890,13 +913,7 @@ static int launch_check(afs_handle* h, const void* x, cudaStream_t s) {
   c.n_ranges = h->n_chk_ranges;
   c.unsat = h->unsat.as<int>();
   c.B = h->B;
-  if (use_wide_check(h)) {
-    c.ranges = h->chk_wide.as<int4>();
-    c.n_ranges = h->n_chk_wide;
-    launch_check_wide(c, s);
-  } else {
-    launch_check_bits(c, s);
-  }
+  launch_check_any(h, c, s);
   CKL();
   launch_solved(h->unsat.as<int>(), h->n_inst, h->B, h->solved.as<int>(), s);
   CKL();
@@ -914,7 +931,7 @@ static cudaEvent_t pool_event(afs_handle* h, int idx) {
 
 // Bit-sliced exact check of the state's sign words for every restart, into
 // the violation words of parity p (cleared by the previous step's CSR pass).
-static void launch_check_step(afs_handle* h, int p, cudaStream_t s) {
+static int launch_check_step(afs_handle* h, int p, cudaStream_t s) {
   CheckArgs c{};
   c.sgn = h->sgn.as<unsigned>();
   c.W = h->W;
@@ -928,13 +945,7 @@ static void launch_check_step(afs_handle* h, int p, cudaStream_t s) {
   c.ranges = h->chk_ranges.as<int4>();
   c.n_ranges = h->n_chk_ranges;
   c.vword = h->vword.as<unsigned>() + static_cast<size_t>(p) * h->n_inst * h->W;
-  if (use_wide_check(h)) {
-    c.ranges = h->chk_wide.as<int4>();
-    c.n_ranges = h->n_chk_wide;
-    launch_check_wide(c, s);
-  } else {
-    launch_check_bits(c, s);
-  }
+  return launch_check_any(h, c, s);
 }
 
 // The fused pass is enqueued before the FE launches of a chunk (true) or after
@@ -1150,9 +1161,8 @@ static int enqueue_steps(afs_handle* h, int nsteps, float eta, bool check, int p
       }
       if (chk_now) {
         if (conc) CK(cudaStreamWaitEvent(h->chk, h->ev_fork, 0));
-        launch_check_step(h, p, conc ? h->chk : s);
+        nl += launch_check_step(h, p, conc ? h->chk : s);
         CKL();
-        ++nl;
         if (conc) CK(cudaEventRecord(h->ev_chk, h->chk));
       }
       int used = 0;
