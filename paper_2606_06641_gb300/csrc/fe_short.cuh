@@ -138,13 +138,16 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // keeping w = l / gamma; 2 the same recomputing w (fewer registers).
 constexpr int SCALED_GRAD_FORM = 2;
 constexpr int SHORT_MIN_BLOCKS_SCALED = 6;
+constexpr int SHORT_MIN_BLOCKS_UNSCALED = 5;  // probability-generating basis, KSCALED_MAX < k <= 32
 constexpr bool SCALED_GRAD_BY_DIVISION = SCALED_GRAD_FORM > 0;
 // Blocks of 4 warps per SM the short kernel is compiled for (register cap):
 // one restart per lane on the scaled form, where the division form needs
 // about 2k registers.
-template <int K, int RPL>
+template <int K, int RPL, bool SHIFT>
 constexpr int short_min_blocks() {
-  return (SCALED_GRAD_FORM == 2 && RPL == 1 && K <= KSCALED_MAX) ? SHORT_MIN_BLOCKS_SCALED : 1;
+  if (SHIFT || RPL != 1) return 1;
+  if (K <= KSCALED_MAX) return SCALED_GRAD_FORM == 2 ? SHORT_MIN_BLOCKS_SCALED : 1;
+  return SHORT_MIN_BLOCKS_UNSCALED;
 }
 
 // a * b, computed again where the compiler would otherwise keep the first
@@ -310,14 +313,41 @@ __device__ __forceinline__ void short_unit(const FeGroupArgs& a, long long warp,
       }
     }
 
-    // otherwise complex roots are factors (l + alpha) + i gamma; RPI roots per
-    // iteration are independent product chains interleaved for instruction-
+    // otherwise (the paper basis) complex roots are factors (l + alpha) + i
+    // gamma; RPI roots per iteration are independent product chains interleaved for instruction-
     // level parallelism (they share the literal values and the accumulators)
     // (two interleaved roots measured slower at k = 20: the register growth
     // costs more occupancy than the extra chains win back)
     constexpr int RPI = 1;
+    if constexpr (!SCALED && !SHIFT) {
+      // probability-generating basis above KSCALED_MAX: factor l + i gamma
+      // with |l + i gamma| >= gamma >= cot(pi k / (2 (k + 1))), never zero:
+      // the full product T = E' prod (l_i + i gamma) and each literal's term
+      // Re(T / (l_i + i gamma)) = (Tr l_i + Ti gamma) / (l_i^2 + gamma^2)
 #pragma unroll 1
-    for (int j = ns; j < (SCALED ? 0 : NC); j += RPI) {
+      for (int j = 0; j < NC; ++j) {
+        const float4 cc = __ldg(tab + 1 + NREAL + j);
+        const float gam = cc.y, g2 = gam * gam;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+          float Tr = cc.z, Ti = cc.w;
+#pragma unroll
+          for (int i = 0; i < K; ++i) {
+            const float nr = fmaf(Tr, l[r][i], -Ti * gam);
+            const float ni = fmaf(Ti, l[r][i], Tr * gam);
+            Tr = nr;
+            Ti = ni;
+          }
+          fe[r] += Tr;
+          const float tig = Ti * gam;
+#pragma unroll
+          for (int i = 0; i < K; ++i)
+            g[r][i] = fmaf(fmaf(Tr, l[r][i], tig), rcp_approx(fmaf(l[r][i], l[r][i], g2)), g[r][i]);
+        }
+      }
+    }
+#pragma unroll 1
+    for (int j = ns; j < (SCALED || !SHIFT ? 0 : NC); j += RPI) {
       float4 cc[RPI];
       bool on[RPI];
 #pragma unroll
@@ -403,7 +433,7 @@ __device__ __forceinline__ void short_unit(const FeGroupArgs& a, long long warp,
 }
 
 template <int K, int RPL, typename XT, bool SHIFT, bool VEC>
-__global__ void __launch_bounds__(128, short_min_blocks<K, RPL>()) fe_grad_short_kernel(FeGroupArgs a) {
+__global__ void __launch_bounds__(128, short_min_blocks<K, RPL, SHIFT>()) fe_grad_short_kernel(FeGroupArgs a) {
   pdl_wait();
   pdl_trigger();
   const long long warp = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
