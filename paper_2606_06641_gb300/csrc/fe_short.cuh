@@ -133,21 +133,16 @@ __device__ __forceinline__ float rcp_approx(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-// Gradient of the scaled short form: 0 from stored prefix and running suffix
-// products; 1 by dividing each literal's factor out of the full product,
-// keeping w = l / gamma; 2 the same recomputing w (fewer registers).
-constexpr int SCALED_GRAD_FORM = 2;
-constexpr int SHORT_MIN_BLOCKS_SCALED = 6;
-constexpr int SHORT_MIN_BLOCKS_UNSCALED = 5;  // probability-generating basis, KSCALED_MAX < k <= 32
-constexpr bool SCALED_GRAD_BY_DIVISION = SCALED_GRAD_FORM > 0;
-// Blocks of 4 warps per SM the short kernel is compiled for (register cap):
-// one restart per lane on the scaled form, where the division form needs
-// about 2k registers.
+// Blocks of 4 warps per SM the short kernel is compiled for (register cap)
+// with one restart per lane in the probability-generating basis, where the
+// division form holds about 2k values per lane (literal values and gradient
+// sums).
+constexpr int SHORT_MIN_BLOCKS_SCALED = 6;    // k <= KSCALED_MAX
+constexpr int SHORT_MIN_BLOCKS_UNSCALED = 5;  // KSCALED_MAX < k <= 32
 template <int K, int RPL, bool SHIFT>
 constexpr int short_min_blocks() {
   if (SHIFT || RPL != 1) return 1;
-  if (K <= KSCALED_MAX) return SCALED_GRAD_FORM == 2 ? SHORT_MIN_BLOCKS_SCALED : 1;
-  return SHORT_MIN_BLOCKS_UNSCALED;
+  return K <= KSCALED_MAX ? SHORT_MIN_BLOCKS_SCALED : SHORT_MIN_BLOCKS_UNSCALED;
 }
 
 // a * b, computed again where the compiler would otherwise keep the first
@@ -247,9 +242,8 @@ __device__ __forceinline__ void short_unit(const FeGroupArgs& a, long long warp,
 
     constexpr int NC = K / 2;
     // complex roots stored scaled (probability-generating basis, k up to
-    // KSCALED_MAX): factor gamma (w + i) with w = l / gamma, gamma^k folded into E', so
-    // a running product times the factor is two FMAs; the gradient products
-    // have k - 1 factors and start from E' / gamma
+    // KSCALED_MAX): factor gamma (w + i) with w = l / gamma, gamma^k folded
+    // into E', so a running product times the factor is two FMAs
     constexpr bool SCALED = !SHIFT && K <= KSCALED_MAX;
     const int ns = SCALED ? static_cast<int>(head.y) : 0;  // roots stored (zero ones dropped)
 #pragma unroll 1
@@ -258,67 +252,30 @@ __device__ __forceinline__ void short_unit(const FeGroupArgs& a, long long warp,
       const float ia = cc.x;  // 1 / gamma
 #pragma unroll
       for (int r = 0; r < RPL; ++r) {
-        if constexpr (SCALED_GRAD_BY_DIVISION) {
-          // the full product T = E' prod (w_i + i), then each literal's
-          // gradient term ia Re(T / (w_i + i)) = ia (Tr w_i + Ti) / (w_i^2 + 1):
-          // |w_i + i| >= 1, so dividing a factor out cannot amplify the error,
-          // and no prefix products are kept (K registers instead of 2K)
-          float w[SCALED_GRAD_FORM == 1 ? K : 1];
-          float Tr = cc.z, Ti = cc.w;
+        // the full product T = E' prod (w_i + i), then each literal's
+        // gradient term ia Re(T / (w_i + i)) = ia (Tr w_i + Ti) / (w_i^2 + 1):
+        // |w_i + i| >= 1, so dividing a factor out cannot amplify the error,
+        // and no prefix products are kept; w is recomputed rather than held
+        // (K registers fewer)
+        float Tr = cc.z, Ti = cc.w;
 #pragma unroll
-          for (int i = 0; i < K; ++i) {
-            const float wi = l[r][i] * ia;
-            if constexpr (SCALED_GRAD_FORM == 1) w[i] = wi;
-            const float nr = fmaf(Tr, wi, -Ti);
-            const float ni = fmaf(Ti, wi, Tr);
-            Tr = nr;
-            Ti = ni;
-          }
-          fe[r] += Tr;
-          const float Ur = Tr * ia, Ui = Ti * ia;
+        for (int i = 0; i < K; ++i) {
+          const float wi = l[r][i] * ia;
+          const float nr = fmaf(Tr, wi, -Ti);
+          const float ni = fmaf(Ti, wi, Tr);
+          Tr = nr;
+          Ti = ni;
+        }
+        fe[r] += Tr;
+        const float Ur = Tr * ia, Ui = Ti * ia;
 #pragma unroll
-          for (int i = 0; i < K; ++i) {
-            const float wi = SCALED_GRAD_FORM == 1 ? w[i] : mul_recompute(l[r][i], ia);
-            g[r][i] = fmaf(fmaf(Ur, wi, Ui), rcp_approx(fmaf(wi, wi, 1.0f)), g[r][i]);
-          }
-        } else {
-          float pr[K], pi[K];
-          float Pr = cc.z * ia, Pi = cc.w * ia;
-#pragma unroll
-          for (int i = 0; i < K; ++i) {
-            pr[i] = Pr;
-            pi[i] = Pi;
-            if (i + 1 < K) {
-              const float w = l[r][i] * ia;
-              const float nr = fmaf(Pr, w, -Pi);
-              const float ni = fmaf(Pi, w, Pr);
-              Pr = nr;
-              Pi = ni;
-            }
-          }
-          g[r][K - 1] += pr[K - 1];
-          float Sr = l[r][K - 1] * ia, Si = 1.0f;
-#pragma unroll
-          for (int i = K - 2; i >= 0; --i) {
-            g[r][i] = fmaf(pr[i], Sr, g[r][i]);
-            g[r][i] = fmaf(-pi[i], Si, g[r][i]);
-            const float w = K > 8 ? mul_recompute(l[r][i], ia) : l[r][i] * ia;
-            const float nr = fmaf(Sr, w, -Si);
-            const float ni = fmaf(Si, w, Sr);
-            Sr = nr;
-            Si = ni;
-          }
-          fe[r] = fmaf(cc.z, Sr, fmaf(-cc.w, Si, fe[r]));
+        for (int i = 0; i < K; ++i) {
+          const float wi = mul_recompute(l[r][i], ia);
+          g[r][i] = fmaf(fmaf(Ur, wi, Ui), rcp_approx(fmaf(wi, wi, 1.0f)), g[r][i]);
         }
       }
     }
 
-    // otherwise (the paper basis) complex roots are factors (l + alpha) + i
-    // gamma; RPI roots per iteration are independent product chains interleaved for instruction-
-    // level parallelism (they share the literal values and the accumulators)
-    // (two interleaved roots measured slower at k = 20: the register growth
-    // costs more occupancy than the extra chains win back)
-    constexpr int RPI = 1;
     if constexpr (!SCALED && !SHIFT) {
       // probability-generating basis above KSCALED_MAX: factor l + i gamma
       // with |l + i gamma| >= gamma >= cot(pi k / (2 (k + 1))), never zero:
@@ -346,6 +303,13 @@ __device__ __forceinline__ void short_unit(const FeGroupArgs& a, long long warp,
         }
       }
     }
+    // the paper basis: complex roots are factors (l + alpha) + i gamma, taken
+    // by prefix and suffix products (these factors can vanish); RPI roots per
+    // iteration are independent product chains interleaved for instruction-
+    // level parallelism (they share the literal values and the accumulators)
+    // (two interleaved roots measured slower at k = 20: the register growth
+    // costs more occupancy than the extra chains win back)
+    constexpr int RPI = 1;
 #pragma unroll 1
     for (int j = ns; j < (SCALED || !SHIFT ? 0 : NC); j += RPI) {
       float4 cc[RPI];
