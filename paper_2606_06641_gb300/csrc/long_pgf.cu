@@ -35,7 +35,7 @@
 // registers and adding each literal's sum to the slot's gradient row once
 // per pass (fixed order, deterministic). The real root's factor is l itself,
 // which can be zero: its leave-one-out products take a prefix/suffix scan
-// over the slot's lanes after the passes.
+// over the slot's lanes after the passes, in registers.
 #include <cuda_bf16.h>
 
 #include "afsat.h"
@@ -51,8 +51,8 @@ namespace {
 
 // Shared memory of one CTA.
 struct LongPgfLayout {
-  int kpad, nseg, rt, ep, gp, ckw;
-  size_t off_ell, off_gs, off_ck, off_rc, bytes;
+  int kpad, nseg, rt, ep, gp;
+  size_t off_ell, off_gs, off_rc, bytes;
   __host__ __device__ LongPgfLayout(int kmax, int W, int NW) {
     kpad = (kmax + LONG_SEG - 1) / LONG_SEG * LONG_SEG;
     nseg = kpad / LONG_SEG;
@@ -60,11 +60,9 @@ struct LongPgfLayout {
     const int k32 = (kpad + 31) & ~31;
     ep = k32 + 8;                   // literal-value rows: the slots' 16-byte reads fall in distinct banks
     gp = k32 + (W < 32 ? W : 0);    // gradient rows: the slots' column updates fall in distinct banks
-    ckw = (kpad + W - 1) / W * 32;  // per warp: the real root's within-chunk suffixes
     off_ell = static_cast<size_t>(kpad) * 8;                         // literal list (int2)
     off_gs = off_ell + static_cast<size_t>(rt) * ep * 4;            // literal values
-    off_ck = off_gs + static_cast<size_t>(rt) * gp * 4;             // gradient accumulators
-    off_rc = off_ck + static_cast<size_t>(NW) * ckw * 4;            // per-warp scratch
+    off_rc = off_gs + static_cast<size_t>(rt) * gp * 4;             // gradient accumulators
     bytes = off_rc + static_cast<size_t>(NW) * 32 * 16;              // each warp's root constants
   }
 };
@@ -211,7 +209,6 @@ __global__ void __launch_bounds__(NW * 32, LONG_WARPS_PER_SM / NW) fe_grad_long_
   int2* lits = reinterpret_cast<int2*>(smem);
   float* ell = reinterpret_cast<float*>(smem + L.off_ell);
   float* gs = reinterpret_cast<float*>(smem + L.off_gs);
-  float2* ck = reinterpret_cast<float2*>(smem + L.off_ck);
   float4* rcs = reinterpret_cast<float4*>(smem + L.off_rc);
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -252,7 +249,6 @@ __global__ void __launch_bounds__(NW * 32, LONG_WARPS_PER_SM / NW) fe_grad_long_
   const int r = w * SL + slot;
   const float* el = ell + r * L.ep;
   float* gr = gs + r * L.gp;
-  float* myck = reinterpret_cast<float*>(ck) + static_cast<size_t>(w) * L.ckw;
   float4* rcw = rcs + w * 32;
   const int nseg = (k + LONG_SEG - 1) / LONG_SEG;
   const int n_last = k - LONG_SEG * (nseg - 1);
@@ -269,18 +265,20 @@ __global__ void __launch_bounds__(NW * 32, LONG_WARPS_PER_SM / NW) fe_grad_long_
   }
 
   if (has_real) {
-    // the real root: value c_mid prod l, gradient c_mid prod_{i' != i} l_i'.
-    // The slot's lanes split the literals into W contiguous chunks; the
-    // within-chunk suffixes go to this warp's scratch area.
+    // the real root: value c_mid prod l, gradient c_mid prod over the other
+    // literals (l can be zero, so no division). The slot's lanes split the
+    // literals into W contiguous chunks (at most AFS_MAX_LEN / W); across
+    // lanes a prefix/suffix scan of the chunk products; within its chunk a
+    // lane takes sub-blocks of RR_SUB literals from the last one back, with
+    // the suffix after the sub-block carried along, the prefix before it
+    // re-multiplied from the chunk's start, and the within-block suffixes in
+    // registers.
+    constexpr int RR_SUB = 8, RR_NSUB = (AFS_MAX_LEN / W + RR_SUB - 1) / RR_SUB;
     const float em = head.z;
     const int chunk = (k + W - 1) / W;
     const int i0 = min(k, rl * chunk), i1 = min(k, i0 + chunk);
-    float* scr = myck;
     float sl = 1.0f;
-    for (int i = i1 - 1; i >= i0; --i) {
-      scr[(i - i0) * 32 + lane] = sl;
-      sl *= el[i];
-    }
+    for (int i = i0; i < i1; ++i) sl *= el[i];
     float inc = sl;
 #pragma unroll
     for (int d = 1; d < W; d <<= 1) {
@@ -298,10 +296,29 @@ __global__ void __launch_bounds__(NW * 32, LONG_WARPS_PER_SM / NW) fe_grad_long_
     }
     float suf = __shfl_down_sync(0xffffffffu, sinc, 1, W);
     if (rl == W - 1) suf = 1.0f;
-    float pl = em * pre * suf;
-    for (int i = i0; i < i1; ++i) {
-      gr[i] += pl * scr[(i - i0) * 32 + lane];
-      pl *= el[i];
+    float C = suf;  // the product after the sub-block
+#pragma unroll
+    for (int sb = RR_NSUB - 1; sb >= 0; --sb) {
+      const int b0 = i0 + sb * RR_SUB;
+      if (b0 >= i1) continue;
+      float A = em * pre;  // c_mid times the product before the sub-block
+      for (int i = i0; i < b0; ++i) A *= el[i];
+      float lv[RR_SUB], ws[RR_SUB];
+#pragma unroll
+      for (int t = 0; t < RR_SUB; ++t) lv[t] = b0 + t < i1 ? el[b0 + t] : 1.0f;
+      float w = 1.0f;
+#pragma unroll
+      for (int t = RR_SUB - 1; t >= 0; --t) {
+        ws[t] = w;
+        w *= lv[t];
+      }
+      float pl = A * C;
+#pragma unroll
+      for (int t = 0; t < RR_SUB; ++t) {
+        if (b0 + t < i1) gr[b0 + t] += pl * ws[t];
+        pl *= lv[t];
+      }
+      C *= w;
     }
     fe_part += em * tot;
   }
