@@ -566,27 +566,35 @@ void launch_apply_fixed(void* x, int xt, long long x_pitch, int n, int B, const 
 }
 
 template <typename XT>
-__global__ void pack_signs_kernel(const XT* x, long long pitch, int n, int B, unsigned* sgn, int W) {
+__global__ void pack_signs_kernel(const XT* x, long long pitch, int n, int B, unsigned* sgn, int W, int wc) {
   const int lane = threadIdx.x & 31;
   const long long warp = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (warp >= static_cast<long long>(n) * W) return;  // uniform per warp
-  const int v = static_cast<int>(warp / W);
-  const int w = static_cast<int>(warp - static_cast<long long>(v) * W);
+  if (warp >= static_cast<long long>(n) * wc) return;  // uniform per warp
+  const int v = static_cast<int>(warp / wc);
+  const int w = static_cast<int>(warp - static_cast<long long>(v) * wc);
   const int b = w * 32 + lane;
   const bool neg = b < B && load_x<XT>(x + static_cast<long long>(v) * pitch + b) < 0.0f;
   const unsigned bits = __ballot_sync(0xffffffffu, neg);
-  if (lane == 0) sgn[warp] = bits;
+  if (lane == 0) sgn[static_cast<long long>(v) * W + w] = bits;
+}
+
+// The first wc words of every row of sgn (row pitch W) from the B restarts
+// of x (row pitch x_pitch): x and sgn may point into a column range.
+void launch_pack_signs_words(const void* x, int xt, long long x_pitch, int n, int B, unsigned* sgn, int W, int wc,
+                             cudaStream_t s) {
+  const long long warps = static_cast<long long>(n) * wc;
+  if (warps == 0) return;
+  const unsigned blocks = static_cast<unsigned>((warps + 7) / 8);
+  if (xt == XT_F32)
+    pack_signs_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(x), x_pitch, n, B, sgn, W, wc);
+  else
+    pack_signs_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(x), x_pitch, n, B, sgn,
+                                                            W, wc);
 }
 
 void launch_pack_signs(const void* x, int xt, long long x_pitch, int n, int B, unsigned* sgn, int W,
                        cudaStream_t s) {
-  const long long warps = static_cast<long long>(n) * W;
-  if (warps == 0) return;
-  const unsigned blocks = static_cast<unsigned>((warps + 7) / 8);
-  if (xt == XT_F32) pack_signs_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(x), x_pitch, n, B, sgn, W);
-  else
-    pack_signs_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(x), x_pitch, n, B, sgn,
-                                                            W);
+  launch_pack_signs_words(x, xt, x_pitch, n, B, sgn, W, W, s);
 }
 
 // ---------------------------------------------------------------------------

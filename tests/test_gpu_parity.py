@@ -482,6 +482,42 @@ def test_step_host_matches_device_step():
     np.testing.assert_array_equal(un.numpy(), un_dev.cpu().numpy())
 
 
+@pytest.mark.parametrize("case", ["f32_1024", "f32_840", "bf16_1024"])
+def test_pipelined_step_host_matches_device_steps(case):
+    """States of 32 MB and more take afs_step_host in restart chunks whose
+    host copies overlap the other chunks' kernels (4 chunks of 256 restarts;
+    a ragged last chunk at B = 840; BF16 storage), here on short and long
+    constraints together. Two chained host-buffer steps must give the device
+    steps' states and exact counts bit for bit, and leave the handle's check
+    and count consistent."""
+    inst = synth.long_card_n10000(1, n=10000, n_clauses=20000, n_long=24, kmin=40, kmax=160)
+    B = 840 if case.endswith("840") else 1024
+    xs = bd.X_BF16 if case.startswith("bf16") else bd.X_F32
+    assert inst.n * B * 4 >= 32 << 20
+    x0 = synth.uniform_x0(inst.n, B, 31)
+    p = bd.default_params(eta=0.1, x_storage=xs)
+    h1 = bd.load_instance(inst, p)
+    bd.init_restarts(h1, B, x0=_dev(x0))
+    h2 = bd.load_instance(inst, p)
+    bd.init_restarts(h2, B, seed=0)
+    xh = torch.from_numpy(x0).pin_memory()
+    xo = torch.empty_like(xh).pin_memory()
+    for _ in range(2):
+        bd.step(h1, 1)
+        x_dev = bd.get_x(h1).cpu().numpy()
+        un_dev, sol_dev = bd.get_verify(h1)
+        un = bd.step_host(h2, xh, xo)
+        np.testing.assert_array_equal(xo.numpy(), x_dev)
+        np.testing.assert_array_equal(un.numpy(), un_dev.cpu().numpy())
+        un2, sol2 = bd.get_verify(h2)
+        np.testing.assert_array_equal(un2.cpu().numpy(), un_dev.cpu().numpy())
+        np.testing.assert_array_equal(sol2.cpu().numpy(), sol_dev.cpu().numpy())
+        np.testing.assert_array_equal(bd.get_step_check(h2).cpu().numpy(), bd.get_step_check(h1).cpu().numpy())
+        xh.copy_(xo)
+    h1.free()
+    h2.free()
+
+
 # ---- 3-literal constraints: derivatives recomputed in the gather --------------
 def test_fused_gradient_without_fe_values():
     """Gradient-only evaluation (no FE kernel for the k = 3 bucket) equals the

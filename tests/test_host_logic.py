@@ -42,6 +42,19 @@ def test_library_exports_every_declared_symbol():
     assert "sm_103a" in bd.version()
 
 
+def test_library_resolves_every_symbol_at_load():
+    """Loading the library with immediate binding (RTLD_NOW, a fresh process)
+    resolves every symbol it uses: a declaration with the wrong linkage or a
+    missing definition fails here instead of at its first call under lazy
+    binding."""
+    import subprocess
+    import sys
+    path = bd.lib()._name
+    code = "import ctypes, os, sys; ctypes.CDLL(sys.argv[1], mode=os.RTLD_NOW)"
+    r = subprocess.run([sys.executable, "-c", code, path], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+
+
 def _eval_short(tab, k, esp, ell):
     """FE and dFE/dl for ell[B, k] from a short-form table, in float64."""
     t = tab.astype(np.float64).reshape(-1, 4)
