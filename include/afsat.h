@@ -250,7 +250,10 @@ int afs_eval_fe_grad_noalloc(afs_handle* h, const float* x_dev, int32_t B, float
 /* afs_step_host: one step of the whole hot path through host memory: copies
  * x_host[v * B + b] (pinned host FP32) to the device, runs one afs_step with
  * the exact check, and copies back the unsat counts (unsat_host[n_inst * B])
- * and the new state (x_out_host, nullable). Synchronises `stream`. */
+ * and the new state (x_out_host, nullable). Synchronises `stream`. States of
+ * 32 MB and more without fixed variables are stepped in 4 restart chunks of
+ * at least 128 restarts, whose copies run on the handle's own copy streams
+ * beside the other chunks' kernels; the results are the same bit for bit. */
 int afs_step_host(afs_handle* h, const float* x_host, float* x_out_host, int32_t* unsat_host,
                   void* stream);
 
