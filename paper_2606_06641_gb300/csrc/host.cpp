@@ -2161,29 +2161,51 @@ int afs_step_host(afs_handle* h, const float* x_host, float* x_out_host, int32_t
   const int width = std::min(h->Bc, (h->B / STEP_HOST_CHUNKS + 31) / 32 * 32);
   if (nb >= STEP_HOST_PIPELINE_BYTES && h->fix_groups == 0 && width >= STEP_HOST_MIN_WIDTH && width < h->B)
     return step_host_chunked(h, x_host, x_out_host, unsat_host, s, width);
-  if (h->stage.bytes < nb) {
+  // FP32 state: the copies go straight to and from the state's rows (2D when
+  // the row pitch exceeds B); BF16: through an FP32 stage and a conversion
+  const bool direct = h->xt == XT_F32;
+  const size_t hp = sizeof(float) * static_cast<size_t>(h->B), dp = sizeof(float) * static_cast<size_t>(h->pitch);
+  if (!direct && h->stage.bytes < nb) {
     int rc = h->stage.alloc(nb);
     if (rc) return rc;
   }
-  CK(cudaMemcpyAsync(h->stage.p, x_host, nb, cudaMemcpyHostToDevice, s));
-  launch_convert_in(h->stage.p, XT_F32, h->B, h->xcur(), h->xt, h->pitch, h->n, h->B, s);
-  CKL();
+  if (direct) {
+    CK(cudaMemcpy2DAsync(h->xcur(), dp, x_host, hp, hp, h->n, cudaMemcpyHostToDevice, s));
+  } else {
+    CK(cudaMemcpyAsync(h->stage.p, x_host, nb, cudaMemcpyHostToDevice, s));
+    launch_convert_in(h->stage.p, XT_F32, h->B, h->xcur(), h->xt, h->pitch, h->n, h->B, s);
+    CKL();
+  }
   if (int rc0 = afs::state_written(h, s)) return rc0;
   const int ve = h->p.verify_every;
   if (ve == 0) h->p.verify_every = 1;
   int rc = afs_step(h, 1, stream);
   h->p.verify_every = ve;
   if (rc) return rc;
+  // the new state goes down on copy_out while the exact count runs on s
+  if (x_out_host) {
+    if (!direct) {
+      launch_convert_in(h->xcur(), h->xt, h->pitch, h->stage.p, XT_F32, h->B, h->n, h->B, s);
+      CKL();
+    }
+    if (h->copy_ev.empty()) {
+      cudaEvent_t e;
+      CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      h->copy_ev.push_back(e);
+    }
+    CK(cudaEventRecord(h->copy_ev[0], s));
+    CK(cudaStreamWaitEvent(h->copy_out, h->copy_ev[0], 0));
+    if (direct)
+      CK(cudaMemcpy2DAsync(x_out_host, hp, h->xcur(), dp, hp, h->n, cudaMemcpyDeviceToHost, h->copy_out));
+    else
+      CK(cudaMemcpyAsync(x_out_host, h->stage.p, nb, cudaMemcpyDeviceToHost, h->copy_out));
+  }
   if ((rc = launch_check(h, h->xcur(), s))) return rc;
   h->count_valid = true;
   CK(cudaMemcpyAsync(unsat_host, h->unsat.p, sizeof(int) * static_cast<size_t>(h->n_inst) * h->B,
                      cudaMemcpyDeviceToHost, s));
-  if (x_out_host) {
-    launch_convert_in(h->xcur(), h->xt, h->pitch, h->stage.p, XT_F32, h->B, h->n, h->B, s);
-    CKL();
-    CK(cudaMemcpyAsync(x_out_host, h->stage.p, nb, cudaMemcpyDeviceToHost, s));
-  }
   CK(cudaStreamSynchronize(s));
+  CK(cudaStreamSynchronize(h->copy_out));
   return AFS_OK;
 }
 

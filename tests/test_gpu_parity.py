@@ -463,11 +463,14 @@ def test_step_before_init_is_an_error():
     assert ei.value.code == -8
 
 
-def test_step_host_matches_device_step():
+@pytest.mark.parametrize("B,xs", [(64, bd.X_F32), (50, bd.X_F32), (50, bd.X_BF16)])
+def test_step_host_matches_device_step(B, xs):
+    """The whole-state host-buffer step (FP32 copies straight into the state's
+    rows, 2D when the row pitch exceeds B; BF16 through a stage) equals the
+    device step."""
     inst = synth.random_3sat_n50(2)
-    B = 64
     x0 = synth.uniform_x0(inst.n, B, 9)
-    p = bd.default_params(eta=0.1)
+    p = bd.default_params(eta=0.1, x_storage=xs)
     h1 = bd.load_instance(inst, p)
     bd.init_restarts(h1, B, x0=_dev(x0))
     bd.step(h1, 1)
