@@ -27,11 +27,15 @@
 // derivative in literal i is Re(T g'(l_i) / g(l_i)): the factor divided out
 // of the full product. |g| >= 1 in form A and >= p in form B (p at least
 // tan(pi / (2 (k + 1))) there), so the division never meets a zero and keeps
-// the product's relative error; per (literal, root) it costs the forward
-// multiply plus about four FP32 instructions and one approximate reciprocal,
-// instead of rebuilding prefix and suffix products. The lanes then swap
-// roles: each lane takes 4 literals of its slot at a time and walks the
-// slot's W roots (their constants broadcast from shared memory), summing in
+// the product's relative error. Each root's term is a rational function of
+// l with a quadratic denominator in l^2, so four adjacent roots' terms sum
+// to one fraction (numerator of degree 7 in l, denominator of degree 4 in
+// l^2, coefficients formed once per pass): per (literal, four roots) twelve
+// FMAs and one approximate reciprocal, three FMAs a root, where a pass walks
+// more than 4 W literals; shorter passes take one term a root (three FMAs
+// and a reciprocal). Either way no prefix and suffix products are rebuilt. The lanes then swap roles: each
+// lane takes 4 literals of its slot at a time and walks the slot's W / 4
+// root groups (their coefficients broadcast from shared memory), summing in
 // registers and adding each literal's sum to the slot's gradient row once
 // per pass (fixed order, deterministic). The real root's factor is l itself,
 // which can be zero: its leave-one-out products take a prefix/suffix scan
@@ -103,17 +107,92 @@ __device__ __forceinline__ void cmul(float& r, float& i, float br, float bi) {
   i = ni;
 }
 
+// Gradient of one pass with four adjacent roots' terms summed to one
+// fraction N(l) / D(u), u = l^2: N of degree 7 in l, D of degree 4 in u with
+// positive coefficients (the product of the four denominators). Pairs first
+// (lane ^ 1), then pairs of pairs (lane ^ 2); each lane forms the sums with
+// its own root or pair as the first operand (deterministic; the lanes of a
+// group may differ in the last bit). Per (literal, group) twelve FMAs and
+// one reciprocal. Pays off once a pass walks more than one chunk of 4 W
+// literals: the coefficients cost about seventy instructions a lane.
+template <int W>
+__device__ __forceinline__ void long_grad_groups(float ta, float tb, float da, float db, int rl, int lane,
+                                                 const float* el, float* gr, float4* rc, int k) {
+  // pair: N = n0 + n1 l + n2 l^2 + n3 l^3, D = e0 + e1 u + e2 u^2
+  const float oa = __shfl_xor_sync(0xffffffffu, ta, 1), ob = __shfl_xor_sync(0xffffffffu, tb, 1);
+  const float oda = __shfl_xor_sync(0xffffffffu, da, 1), odb = __shfl_xor_sync(0xffffffffu, db, 1);
+  const float n0 = fmaf(tb, odb, ob * db), n1 = fmaf(ta, odb, oa * db);
+  const float n2 = fmaf(tb, oda, ob * da), n3 = fmaf(ta, oda, oa * da);
+  const float e0 = db * odb, e1 = fmaf(da, odb, oda * db), e2 = da * oda;
+  // (N, D) this lane's pair, (M, F) the other one: N F + M D over D F
+  const float M0 = __shfl_xor_sync(0xffffffffu, n0, 2), M1 = __shfl_xor_sync(0xffffffffu, n1, 2);
+  const float M2 = __shfl_xor_sync(0xffffffffu, n2, 2), M3 = __shfl_xor_sync(0xffffffffu, n3, 2);
+  const float F0 = __shfl_xor_sync(0xffffffffu, e0, 2), F1 = __shfl_xor_sync(0xffffffffu, e1, 2);
+  const float F2 = __shfl_xor_sync(0xffffffffu, e2, 2);
+  // each lane of the group publishes one quarter: (Q7 Q6 Q5 Q4), (Q3 Q2 Q1 Q0), (E4 E3 E2 E1), (E0)
+  float4 piece;
+  switch (rl & 3) {
+    case 0:
+      piece = make_float4(fmaf(n3, F2, M3 * e2), fmaf(n2, F2, M2 * e2),
+                          fmaf(n3, F1, fmaf(n1, F2, fmaf(M3, e1, M1 * e2))),
+                          fmaf(n2, F1, fmaf(n0, F2, fmaf(M2, e1, M0 * e2))));
+      break;
+    case 1:
+      piece = make_float4(fmaf(n3, F0, fmaf(n1, F1, fmaf(M3, e0, M1 * e1))),
+                          fmaf(n2, F0, fmaf(n0, F1, fmaf(M2, e0, M0 * e1))), fmaf(n1, F0, M1 * e0),
+                          fmaf(n0, F0, M0 * e0));
+      break;
+    case 2:
+      piece = make_float4(e2 * F2, fmaf(e1, F2, e2 * F1), fmaf(e0, F2, fmaf(e1, F1, e2 * F0)), fmaf(e0, F1, e1 * F0));
+      break;
+    default:
+      piece = make_float4(e0 * F0, 0.0f, 0.0f, 0.0f);
+      break;
+  }
+  rc[lane] = piece;
+  __syncwarp();
+  const float4* rs = rc + (lane & ~(W - 1));  // the slot's W / 4 groups
+  for (int c0 = 0; c0 < k; c0 += 4 * W) {
+    float lv[4], u[4], v[4], g[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = c0 + q * W + rl;
+      lv[q] = i < k ? el[i] : 0.0f;
+      u[q] = lv[q] * lv[q];
+      v[q] = u[q] * u[q];
+      g[q] = 0.0f;
+    }
+#pragma unroll 2
+    for (int jq = 0; jq < W / 4; ++jq) {
+      const float4 qh = rs[4 * jq], ql = rs[4 * jq + 1], eh = rs[4 * jq + 2];
+      const float el0 = rs[4 * jq + 3].x;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float hi = fmaf(fmaf(qh.x, lv[q], qh.y), u[q], fmaf(qh.z, lv[q], qh.w));
+        const float lo = fmaf(fmaf(ql.x, lv[q], ql.y), u[q], fmaf(ql.z, lv[q], ql.w));
+        const float den = fmaf(fmaf(fmaf(eh.x, u[q], eh.y), v[q], fmaf(eh.z, u[q], eh.w)), u[q], el0);
+        g[q] = fmaf(fmaf(hi, v[q], lo), rcp_apx(den), g[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = c0 + q * W + rl;
+      if (i < k) gr[i] += g[q];
+    }
+  }
+}
+
 // One pass: the slot's W lanes take roots j0 .. j0 + W - 1. A forward walk
 // gives the full product P (true size at every segment boundary, restored by
 // s^16) and T = E' P, whose real part is the root's value; the derivative in
 // literal t is then Re(U / g_t), U = T dg/dl (p for form A, 1 for form B):
 // (U_r w + U_i) / (w^2 + 1) with w = p l in form A, (U_r l + T_i p) /
 // (l^2 + p^2) in form B. For the gradient the lanes swap roles: each lane
-// publishes its root's four derivative constants to the warp's shared row,
-// then the slot's lanes take 4 W literals at a time (4 per lane, l and l^2 in
-// registers) and walk the slot's W roots (broadcast reads): per (literal,
-// root) three FMAs and a reciprocal, summed in registers and added to the
-// gradient row once per pass (fixed order).
+// publishes its root's derivative constants (or, for long passes, each group
+// of four lanes its roots' summed fraction) to the warp's shared row, then
+// the slot's lanes take 4 W literals at a time (4 per lane, in registers)
+// and walk the slot's roots or groups (broadcast reads), summing in
+// registers and adding to the gradient row once per pass (fixed order).
 // Lanes past the table's roots get a zero weight and bounded factors.
 template <int W, bool FB>
 __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0, int rl, int lane, const float* el,
@@ -150,33 +229,38 @@ __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0,
   float v = Tr;
 #pragma unroll
   for (int o = W / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  // the derivative as (A l + B') / (alpha l^2 + beta): form A (U = T p,
-  // w = p l) A = T_r p^2, B' = T_i p, alpha = p^2, beta = 1; form B (U = T)
-  // A = T_r, B' = T_i p, alpha = 1, beta = p^2
+  // the root's derivative term (A l + B') / (alpha u + beta), u = l^2: form A
+  // (U = T p, w = p l) A = T_r p^2, B' = T_i p, alpha = p^2, beta = 1; form B
+  // (U = T) A = T_r, B' = T_i p, alpha = 1, beta = p^2
   const float p2 = p * p;
-  rc[lane] = FB ? make_float4(Tr, Ti * p, 1.0f, p2) : make_float4(Tr * p2, Ti * p, p2, 1.0f);
-  __syncwarp();
-  const float4* rs = rc + (lane & ~(W - 1));  // the slot's W roots
-  for (int c0 = 0; c0 < k; c0 += 4 * W) {
-    float lv[4], l2[4], g[4];
+  const float ta = FB ? Tr : Tr * p2, tb = Ti * p, da = FB ? 1.0f : p2, db = FB ? p2 : 1.0f;
+  if (W >= 16 && k > 4 * W) {
+    long_grad_groups<W>(ta, tb, da, db, rl, lane, el, gr, rc, k);
+  } else {
+    // one term a root: three FMAs and a reciprocal per (literal, root)
+    rc[lane] = make_float4(ta, tb, da, db);
+    __syncwarp();
+    const float4* rs = rc + (lane & ~(W - 1));  // the slot's W roots
+    for (int c0 = 0; c0 < k; c0 += 4 * W) {
+      float lv[4], l2[4], g[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = c0 + q * W + rl;
-      lv[q] = i < k ? el[i] : 0.0f;
-      l2[q] = lv[q] * lv[q];
-      g[q] = 0.0f;
-    }
+      for (int q = 0; q < 4; ++q) {
+        const int i = c0 + q * W + rl;
+        lv[q] = i < k ? el[i] : 0.0f;
+        l2[q] = lv[q] * lv[q];
+        g[q] = 0.0f;
+      }
 #pragma unroll 4
-    for (int jj = 0; jj < W; ++jj) {
-      const float4 c = rs[jj];
+      for (int jj = 0; jj < W; ++jj) {
+        const float4 c = rs[jj];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        g[q] = fmaf(fmaf(c.x, lv[q], c.y), rcp_apx(fmaf(c.z, l2[q], c.w)), g[q]);
-    }
+        for (int q = 0; q < 4; ++q) g[q] = fmaf(fmaf(c.x, lv[q], c.y), rcp_apx(fmaf(c.z, l2[q], c.w)), g[q]);
+      }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = c0 + q * W + rl;
-      if (i < k) gr[i] += g[q];
+      for (int q = 0; q < 4; ++q) {
+        const int i = c0 + q * W + rl;
+        if (i < k) gr[i] += g[q];
+      }
     }
   }
   __syncwarp();  // the root row is read before the next pass writes it
