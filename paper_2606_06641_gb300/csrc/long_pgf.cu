@@ -13,15 +13,21 @@
 // passes walk the table's roots W at a time. The literal list is staged with
 // cp.async.bulk on an mbarrier (bounded wait), the literal values l = s x of
 // the CTA's restarts in shared memory rows, read four at a time by 16-byte
-// broadcast loads.
+// loads; each warp has a shared row of 32 16-byte entries for the values its
+// lanes exchange within a pass.
 //
 // Factor form (coefficient table built on the host): at every complex root
-// the literal factor is s g(l), g = p l + i (form A) or l + i p (form B), so
-// a complex multiply of a running product by it is three (four) FP32
-// instructions. The forward walk goes in segments of LONG_SEG literals and
-// multiplies by the table's s^16 after each full one, so the running product
-// is at its true size (|prod| <= 1) at every segment boundary and stays
-// within FP32 inside a segment; no exponent bookkeeping is needed.
+// the literal factor is s g(l), g = p l + i (form A) or l + i p (form B). The
+// forward walk multiplies a running product by the factors of four literals
+// at once: their product is a polynomial in p whose coefficients are the
+// four values' elementary symmetric polynomials, formed once per pass and
+// shared by all roots of the slot, so a quad costs eight FP32 instructions
+// (two a literal; one factor at a time, three a literal in form A, is kept
+// for slots of 8 lanes, where a quad formed per lane serves only 8 roots).
+// The walk goes in segments of LONG_SEG literals and multiplies by the
+// table's s^16 after each full one, so the running product is at its true
+// size (|prod| <= 1) at every segment boundary and stays within FP32 inside
+// a segment; no exponent bookkeeping is needed.
 //
 // Gradient by division. With T = E' prod g the root's exact product, the
 // derivative in literal i is Re(T g'(l_i) / g(l_i)): the factor divided out
@@ -33,11 +39,11 @@
 // l^2, coefficients formed once per pass): per (literal, four roots) twelve
 // FMAs and one approximate reciprocal, three FMAs a root, where a pass walks
 // more than 4 W literals; shorter passes take one term a root (three FMAs
-// and a reciprocal). Either way no prefix and suffix products are rebuilt. The lanes then swap roles: each
-// lane takes 4 literals of its slot at a time and walks the slot's W / 4
-// root groups (their coefficients broadcast from shared memory), summing in
-// registers and adding each literal's sum to the slot's gradient row once
-// per pass (fixed order, deterministic). The real root's factor is l itself,
+// and a reciprocal). Either way no prefix and suffix products are rebuilt.
+// The lanes then swap roles: each lane takes 4 literals of its slot at a
+// time and walks the slot's root groups (their coefficients broadcast from
+// shared memory), summing in registers and adding each literal's sum to the
+// slot's gradient row once per pass (fixed order, deterministic). The real root's factor is l itself,
 // which can be zero: its leave-one-out products take a prefix/suffix scan
 // over the slot's lanes after the passes, in registers.
 #include <cuda_bf16.h>
@@ -182,6 +188,33 @@ __device__ __forceinline__ void long_grad_groups(float ta, float tb, float da, f
   }
 }
 
+// Elementary symmetric polynomials (e1, e2, e3, e4) of a quad of literal
+// values: the product of the quad's factors is a polynomial in p with these
+// coefficients, shared by all roots.
+__device__ __forceinline__ float4 quad_esp(float4 v) {
+  const float a = v.x + v.y, b = v.x * v.y, c = v.z + v.w, d = v.z * v.w;
+  return make_float4(a + c, fmaf(a, c, b + d), fmaf(b, c, d * a), b * d);
+}
+// P <- P prod over a quad of g(l), from the quad's symmetric polynomials e:
+// form A prod (p l + i) = (1 - p^2 e2 + p^4 e4) + i p (p^2 e3 - e1), form B
+// prod (l + i p) = (e4 - p^2 e2 + p^4) + i p (e3 - p^2 e1); eight FP32
+// instructions for four literals. The terms' magnitudes sum to at most 4
+// times the product's (each factor's |real| + |imag| is at most sqrt(2) times
+// its modulus), so the expansion keeps the product's relative accuracy.
+template <bool FB>
+__device__ __forceinline__ void qmul(float4 e, float p, float p2, float& r, float& i) {
+  float fr, fi;
+  if constexpr (FB) {
+    fr = fmaf(p2, p2 - e.y, e.w);
+    fi = p * fmaf(-p2, e.x, e.z);
+  } else {
+    fr = fmaf(p2, fmaf(p2, e.w, -e.y), 1.0f);
+    fi = p * fmaf(p2, e.z, -e.x);
+  }
+  cmul(r, i, fr, fi);
+}
+static_assert(LONG_SEG % 4 == 0, "segments hold whole quads");
+
 // One pass: the slot's W lanes take roots j0 .. j0 + W - 1. A forward walk
 // gives the full product P (true size at every segment boundary, restored by
 // s^16) and T = E' P, whose real part is the root's value; the derivative in
@@ -208,20 +241,50 @@ __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0,
     er = g1.x;
     ei = g1.y;
   }
+  const float p2 = p * p;
   float Pr = 1.0f, Pi = 0.0f;
-  for (int sg = 0; sg + 1 < nseg; ++sg) {
-    const float4* e4 = reinterpret_cast<const float4*>(el + sg * LONG_SEG);
+  if constexpr (W >= 16) {
+    // chunks of W quads (4 W literals): each lane stages the symmetric
+    // polynomials of one quad of its slot in the warp's shared row, then the
+    // slot's lanes walk the chunk's full segments, s^16 after each
+    const int nq = k >> 2;
+    const float4* e4 = reinterpret_cast<const float4*>(el);
+    const float4* rs = rc + (lane & ~(W - 1));
+    for (int c0 = 0; c0 < nq; c0 += W) {
+      const int qi = c0 + rl;
+      rc[lane] = qi < nq ? quad_esp(e4[qi]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      __syncwarp();
+      const int s1 = min((c0 + W) / (LONG_SEG / 4), nseg - 1);
+      for (int sg = c0 / (LONG_SEG / 4); sg < s1; ++sg) {
+        const float4* qs = rs + (sg * (LONG_SEG / 4) - c0);
 #pragma unroll
-    for (int u = 0; u < LONG_SEG / 4; ++u) {
-      const float4 v = e4[u];
-      fmul<FB>(v.x, p, Pr, Pi);
-      fmul<FB>(v.y, p, Pr, Pi);
-      fmul<FB>(v.z, p, Pr, Pi);
-      fmul<FB>(v.w, p, Pr, Pi);
+        for (int u = 0; u < LONG_SEG / 4; ++u) qmul<FB>(qs[u], p, p2, Pr, Pi);
+        cmul(Pr, Pi, s16r, s16i);
+      }
+      if (c0 + W < nq) __syncwarp();  // the chunk is read before the next one is staged
     }
-    cmul(Pr, Pi, s16r, s16i);
-  }
-  {
+    // the last segment: its full quads (staged in the last chunk), then the literals past them
+    if (nq > 0) {
+      const int cl = (nq - 1) / W * W;
+      for (int qq = (nseg - 1) * (LONG_SEG / 4); qq < nq; ++qq) qmul<FB>(rs[qq - cl], p, p2, Pr, Pi);
+    }
+    for (int t = 4 * nq; t < k; ++t) fmul<FB>(el[t], p, Pr, Pi);
+    __syncwarp();  // the quads are read before the root constants replace them
+  } else {
+    // narrow slots (a quad staged per lane would serve only W roots): one
+    // factor at a time, literal values read four at a time
+    for (int sg = 0; sg + 1 < nseg; ++sg) {
+      const float4* e4 = reinterpret_cast<const float4*>(el + sg * LONG_SEG);
+#pragma unroll
+      for (int u = 0; u < LONG_SEG / 4; ++u) {
+        const float4 v = e4[u];
+        fmul<FB>(v.x, p, Pr, Pi);
+        fmul<FB>(v.y, p, Pr, Pi);
+        fmul<FB>(v.z, p, Pr, Pi);
+        fmul<FB>(v.w, p, Pr, Pi);
+      }
+      cmul(Pr, Pi, s16r, s16i);
+    }
     const float* e = el + (nseg - 1) * LONG_SEG;
     for (int t = 0; t < n_last; ++t) fmul<FB>(e[t], p, Pr, Pi);
   }
@@ -232,7 +295,6 @@ __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0,
   // the root's derivative term (A l + B') / (alpha u + beta), u = l^2: form A
   // (U = T p, w = p l) A = T_r p^2, B' = T_i p, alpha = p^2, beta = 1; form B
   // (U = T) A = T_r, B' = T_i p, alpha = 1, beta = p^2
-  const float p2 = p * p;
   const float ta = FB ? Tr : Tr * p2, tb = Ti * p, da = FB ? 1.0f : p2, db = FB ? p2 : 1.0f;
   if (W >= 16 && k > 4 * W) {
     long_grad_groups<W>(ta, tb, da, db, rl, lane, el, gr, rc, k);
