@@ -59,6 +59,10 @@ namespace afs {
 namespace {
 
 
+// 16-byte entries of a warp's shared row: two per lane (a root group's
+// coefficients in duplicated pairs take eight entries)
+constexpr int LONG_ROW = 64;
+
 // Shared memory of one CTA.
 struct LongPgfLayout {
   int kpad, nseg, rt, ep, gp;
@@ -73,7 +77,7 @@ struct LongPgfLayout {
     off_ell = static_cast<size_t>(kpad) * 8;                         // literal list (int2)
     off_gs = off_ell + static_cast<size_t>(rt) * ep * 4;            // literal values
     off_rc = off_gs + static_cast<size_t>(rt) * gp * 4;             // gradient accumulators
-    bytes = off_rc + static_cast<size_t>(NW) * 32 * 16;              // each warp's root constants
+    bytes = off_rc + static_cast<size_t>(NW) * LONG_ROW * 16;        // each warp's shared row
   }
 };
 
@@ -84,6 +88,11 @@ __device__ __forceinline__ float rcp_apx(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+
+// x y + z in both halves: one paired FP32 instruction
+__device__ __forceinline__ float2 ffma2(float2 x, float2 y, float2 z) { return __ffma2_rn(x, y, z); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
 // P <- P (w + i)
 __device__ __forceinline__ void gmul(float w, float& r, float& i) {
@@ -118,9 +127,11 @@ __device__ __forceinline__ void cmul(float& r, float& i, float br, float bi) {
 // positive coefficients (the product of the four denominators). Pairs first
 // (lane ^ 1), then pairs of pairs (lane ^ 2); each lane forms the sums with
 // its own root or pair as the first operand (deterministic; the lanes of a
-// group may differ in the last bit). Per (literal, group) twelve FMAs and
-// one reciprocal. Pays off once a pass walks more than one chunk of 4 W
-// literals: the coefficients cost about seventy instructions a lane.
+// group may differ in the last bit). The coefficients are published in
+// duplicated pairs and each lane evaluates two adjacent literals at once:
+// per (literal pair, group) twelve paired FMAs and two reciprocals. Pays off
+// once a pass walks more than one chunk of 4 W literals: the coefficients
+// cost about seventy instructions a lane.
 template <int W>
 __device__ __forceinline__ void long_grad_groups(float ta, float tb, float da, float db, int rl, int lane,
                                                  const float* el, float* gr, float4* rc, int k) {
@@ -135,7 +146,8 @@ __device__ __forceinline__ void long_grad_groups(float ta, float tb, float da, f
   const float M2 = __shfl_xor_sync(0xffffffffu, n2, 2), M3 = __shfl_xor_sync(0xffffffffu, n3, 2);
   const float F0 = __shfl_xor_sync(0xffffffffu, e0, 2), F1 = __shfl_xor_sync(0xffffffffu, e1, 2);
   const float F2 = __shfl_xor_sync(0xffffffffu, e2, 2);
-  // each lane of the group publishes one quarter: (Q7 Q6 Q5 Q4), (Q3 Q2 Q1 Q0), (E4 E3 E2 E1), (E0)
+  // each lane of the group publishes one quarter, duplicated into pairs for
+  // the paired evaluation: (Q7 Q6 Q5 Q4), (Q3 Q2 Q1 Q0), (E4 E3 E2 E1), (E0)
   float4 piece;
   switch (rl & 3) {
     case 0:
@@ -155,63 +167,84 @@ __device__ __forceinline__ void long_grad_groups(float ta, float tb, float da, f
       piece = make_float4(e0 * F0, 0.0f, 0.0f, 0.0f);
       break;
   }
-  rc[lane] = piece;
+  rc[2 * lane] = make_float4(piece.x, piece.x, piece.y, piece.y);
+  rc[2 * lane + 1] = make_float4(piece.z, piece.z, piece.w, piece.w);
   __syncwarp();
-  const float4* rs = rc + (lane & ~(W - 1));  // the slot's W / 4 groups
+  // each lane takes pairs of adjacent literals (two pairs per chunk of 4 W);
+  // a group's coefficients occupy eight entries
+  const float4* rs = rc + 2 * (lane & ~(W - 1));
   for (int c0 = 0; c0 < k; c0 += 4 * W) {
-    float lv[4], u[4], v[4], g[4];
+    float2 lv[2], u[2], v[2], g[2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = c0 + q * W + rl;
-      lv[q] = i < k ? el[i] : 0.0f;
-      u[q] = lv[q] * lv[q];
-      v[q] = u[q] * u[q];
-      g[q] = 0.0f;
+    for (int q = 0; q < 2; ++q) {
+      const int i = c0 + 2 * (q * W + rl);
+      lv[q] = i < k ? *reinterpret_cast<const float2*>(el + i) : make_float2(0.0f, 0.0f);
+      u[q] = __fmul2_rn(lv[q], lv[q]);
+      v[q] = __fmul2_rn(u[q], u[q]);
+      g[q] = make_float2(0.0f, 0.0f);
     }
 #pragma unroll 2
     for (int jq = 0; jq < W / 4; ++jq) {
-      const float4 qh = rs[4 * jq], ql = rs[4 * jq + 1], eh = rs[4 * jq + 2];
-      const float el0 = rs[4 * jq + 3].x;
+      const float4* cg = rs + 8 * jq;
+      const float4 a0 = cg[0], a1 = cg[1], b0 = cg[2], b1 = cg[3], d0 = cg[4], d1 = cg[5];
+      const float2 z0 = lo2(cg[6]);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float hi = fmaf(fmaf(qh.x, lv[q], qh.y), u[q], fmaf(qh.z, lv[q], qh.w));
-        const float lo = fmaf(fmaf(ql.x, lv[q], ql.y), u[q], fmaf(ql.z, lv[q], ql.w));
-        const float den = fmaf(fmaf(fmaf(eh.x, u[q], eh.y), v[q], fmaf(eh.z, u[q], eh.w)), u[q], el0);
-        g[q] = fmaf(fmaf(hi, v[q], lo), rcp_apx(den), g[q]);
+      for (int q = 0; q < 2; ++q) {
+        const float2 hi = ffma2(ffma2(lo2(a0), lv[q], hi2(a0)), u[q], ffma2(lo2(a1), lv[q], hi2(a1)));
+        const float2 lo = ffma2(ffma2(lo2(b0), lv[q], hi2(b0)), u[q], ffma2(lo2(b1), lv[q], hi2(b1)));
+        const float2 den = ffma2(ffma2(ffma2(lo2(d0), u[q], hi2(d0)), v[q], ffma2(lo2(d1), u[q], hi2(d1))), u[q], z0);
+        g[q] = ffma2(ffma2(hi, v[q], lo), make_float2(rcp_apx(den.x), rcp_apx(den.y)), g[q]);
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = c0 + q * W + rl;
-      if (i < k) gr[i] += g[q];
+    for (int q = 0; q < 2; ++q) {
+      const int i = c0 + 2 * (q * W + rl);
+      if (i + 1 < k) {
+        float2* gp2 = reinterpret_cast<float2*>(gr + i);  // rows and i are even: 8-byte aligned
+        const float2 o = *gp2;
+        *gp2 = make_float2(o.x + g[q].x, o.y + g[q].y);
+      } else if (i < k) {
+        gr[i] += g[q].x;
+      }
     }
   }
 }
 
-// Elementary symmetric polynomials (e1, e2, e3, e4) of a quad of literal
-// values: the product of the quad's factors is a polynomial in p with these
-// coefficients, shared by all roots.
-__device__ __forceinline__ float4 quad_esp(float4 v) {
-  const float a = v.x + v.y, b = v.x * v.y, c = v.z + v.w, d = v.z * v.w;
-  return make_float4(a + c, fmaf(a, c, b + d), fmaf(b, c, d * a), b * d);
-}
-// P <- P prod over a quad of g(l), from the quad's symmetric polynomials e:
-// form A prod (p l + i) = (1 - p^2 e2 + p^4 e4) + i p (p^2 e3 - e1), form B
-// prod (l + i p) = (e4 - p^2 e2 + p^4) + i p (e3 - p^2 e1); eight FP32
-// instructions for four literals. The terms' magnitudes sum to at most 4
-// times the product's (each factor's |real| + |imag| is at most sqrt(2) times
-// its modulus), so the expansion keeps the product's relative accuracy.
+// A quad of literal values staged for the forward walk: its elementary
+// symmetric polynomials e1 .. e4, in the order the form's paired multiply
+// takes them. The product of the quad's factors is a polynomial in p with
+// these coefficients, shared by all roots: form A prod (p l + i) =
+// (1 - p^2 e2 + p^4 e4) + i p (p^2 e3 - e1), staged (e4, e3, -e2, -e1);
+// form B prod (l + i p) = (e4 - p^2 e2 + p^4) + i p (e3 - p^2 e1), staged
+// (e2, e1, e4, e3).
 template <bool FB>
-__device__ __forceinline__ void qmul(float4 e, float p, float p2, float& r, float& i) {
-  float fr, fi;
-  if constexpr (FB) {
-    fr = fmaf(p2, p2 - e.y, e.w);
-    fi = p * fmaf(-p2, e.x, e.z);
-  } else {
-    fr = fmaf(p2, fmaf(p2, e.w, -e.y), 1.0f);
-    fi = p * fmaf(p2, e.z, -e.x);
-  }
-  cmul(r, i, fr, fi);
+__device__ __forceinline__ float4 quad_stage(float4 v) {
+  const float a = v.x + v.y, b = v.x * v.y, c = v.z + v.w, d = v.z * v.w;
+  const float e1 = a + c, e2 = fmaf(a, c, b + d), e3 = fmaf(b, c, d * a), e4 = b * d;
+  return FB ? make_float4(e2, e1, e4, e3) : make_float4(e4, e3, -e2, -e1);
+}
+// a root's constant pairs for the quad multiply: t = c1 x + z on the staged
+// pairs (x, z), then (real, imag) = c2 t + c3. Form A c1 = (p^2, p^2), c2 =
+// (p^2, p), c3 = (1, 0); form B c1 = (-p^2, -p^2), c2 = (1, p), c3 = (p^4, 0).
+struct QuadConst {
+  float2 c1, c2, c3;
+};
+template <bool FB>
+__device__ __forceinline__ QuadConst quad_const(float p, float p2) {
+  QuadConst q;
+  q.c1 = FB ? make_float2(-p2, -p2) : make_float2(p2, p2);
+  q.c2 = FB ? make_float2(1.0f, p) : make_float2(p2, p);
+  q.c3 = FB ? make_float2(p2 * p2, 0.0f) : make_float2(1.0f, 0.0f);
+  return q;
+}
+// P <- P prod over a quad of g(l): two paired FMAs for the quad's factor and
+// a complex multiply, six FP32 instructions for four literals. The terms'
+// magnitudes sum to at most 4 times the product's (each factor's |real| +
+// |imag| is at most sqrt(2) times its modulus), so the expansion keeps the
+// product's relative accuracy.
+__device__ __forceinline__ void qmul(float4 e, const QuadConst& q, float& r, float& i) {
+  const float2 f = ffma2(q.c2, ffma2(q.c1, lo2(e), hi2(e)), q.c3);
+  cmul(r, i, f.x, f.y);
 }
 static_assert(LONG_SEG % 4 == 0, "segments hold whole quads");
 
@@ -248,17 +281,18 @@ __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0,
     // polynomials of one quad of its slot in the warp's shared row, then the
     // slot's lanes walk the chunk's full segments, s^16 after each
     const int nq = k >> 2;
+    const QuadConst qc = quad_const<FB>(p, p2);
     const float4* e4 = reinterpret_cast<const float4*>(el);
     const float4* rs = rc + (lane & ~(W - 1));
     for (int c0 = 0; c0 < nq; c0 += W) {
       const int qi = c0 + rl;
-      rc[lane] = qi < nq ? quad_esp(e4[qi]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      rc[lane] = qi < nq ? quad_stage<FB>(e4[qi]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       __syncwarp();
       const int s1 = min((c0 + W) / (LONG_SEG / 4), nseg - 1);
       for (int sg = c0 / (LONG_SEG / 4); sg < s1; ++sg) {
         const float4* qs = rs + (sg * (LONG_SEG / 4) - c0);
 #pragma unroll
-        for (int u = 0; u < LONG_SEG / 4; ++u) qmul<FB>(qs[u], p, p2, Pr, Pi);
+        for (int u = 0; u < LONG_SEG / 4; ++u) qmul(qs[u], qc, Pr, Pi);
         cmul(Pr, Pi, s16r, s16i);
       }
       if (c0 + W < nq) __syncwarp();  // the chunk is read before the next one is staged
@@ -266,7 +300,7 @@ __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0,
     // the last segment: its full quads (staged in the last chunk), then the literals past them
     if (nq > 0) {
       const int cl = (nq - 1) / W * W;
-      for (int qq = (nseg - 1) * (LONG_SEG / 4); qq < nq; ++qq) qmul<FB>(rs[qq - cl], p, p2, Pr, Pi);
+      for (int qq = (nseg - 1) * (LONG_SEG / 4); qq < nq; ++qq) qmul(rs[qq - cl], qc, Pr, Pi);
     }
     for (int t = 4 * nq; t < k; ++t) fmul<FB>(el[t], p, Pr, Pi);
     __syncwarp();  // the quads are read before the root constants replace them
@@ -395,7 +429,7 @@ __global__ void __launch_bounds__(NW * 32, LONG_WARPS_PER_SM / NW) fe_grad_long_
   const int r = w * SL + slot;
   const float* el = ell + r * L.ep;
   float* gr = gs + r * L.gp;
-  float4* rcw = rcs + w * 32;
+  float4* rcw = rcs + w * LONG_ROW;
   const int nseg = (k + LONG_SEG - 1) / LONG_SEG;
   const int n_last = k - LONG_SEG * (nseg - 1);
   float fe_part = 0.0f;
