@@ -122,6 +122,73 @@ __device__ __forceinline__ void cmul(float& r, float& i, float br, float bi) {
   i = ni;
 }
 
+// NP pairs of adjacent literals a lane (literals c0 + 2 (q W + rl), + 1)
+// against the slot's W / 4 root groups: per (pair, group) twelve paired
+// FMAs and two reciprocals, each pair's sums added to the gradient row.
+template <int W, int NP>
+__device__ __forceinline__ void grad_group_pairs(const float4* rs, const float* el, float* gr, int c0, int rl,
+                                                 int k) {
+  float2 lv[NP], u[NP], v[NP], g[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const int i = c0 + 2 * (q * W + rl);
+    lv[q] = i < k ? *reinterpret_cast<const float2*>(el + i) : make_float2(0.0f, 0.0f);
+    u[q] = __fmul2_rn(lv[q], lv[q]);
+    v[q] = __fmul2_rn(u[q], u[q]);
+    g[q] = make_float2(0.0f, 0.0f);
+  }
+#pragma unroll 2
+  for (int jq = 0; jq < W / 4; ++jq) {
+    const float4* cg = rs + 8 * jq;
+    const float4 a0 = cg[0], a1 = cg[1], b0 = cg[2], b1 = cg[3], d0 = cg[4], d1 = cg[5];
+    const float2 z0 = lo2(cg[6]);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const float2 hi = ffma2(ffma2(lo2(a0), lv[q], hi2(a0)), u[q], ffma2(lo2(a1), lv[q], hi2(a1)));
+      const float2 lo = ffma2(ffma2(lo2(b0), lv[q], hi2(b0)), u[q], ffma2(lo2(b1), lv[q], hi2(b1)));
+      const float2 den = ffma2(ffma2(ffma2(lo2(d0), u[q], hi2(d0)), v[q], ffma2(lo2(d1), u[q], hi2(d1))), u[q], z0);
+      g[q] = ffma2(ffma2(hi, v[q], lo), make_float2(rcp_apx(den.x), rcp_apx(den.y)), g[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const int i = c0 + 2 * (q * W + rl);
+    if (i + 1 < k) {
+      float2* gp2 = reinterpret_cast<float2*>(gr + i);  // rows and i are even: 8-byte aligned
+      const float2 o = *gp2;
+      *gp2 = make_float2(o.x + g[q].x, o.y + g[q].y);
+    } else if (i < k) {
+      gr[i] += g[q].x;
+    }
+  }
+}
+
+// NQ literals a lane (c0 + q W + rl) against the slot's W roots, one term a
+// root: three FMAs and a reciprocal per (literal, root).
+template <int W, int NQ>
+__device__ __forceinline__ void grad_root_terms(const float4* rs, const float* el, float* gr, int c0, int rl,
+                                                int k) {
+  float lv[NQ], l2[NQ], g[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int i = c0 + q * W + rl;
+    lv[q] = i < k ? el[i] : 0.0f;
+    l2[q] = lv[q] * lv[q];
+    g[q] = 0.0f;
+  }
+#pragma unroll 4
+  for (int jj = 0; jj < W; ++jj) {
+    const float4 c = rs[jj];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) g[q] = fmaf(fmaf(c.x, lv[q], c.y), rcp_apx(fmaf(c.z, l2[q], c.w)), g[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int i = c0 + q * W + rl;
+    if (i < k) gr[i] += g[q];
+  }
+}
+
 // Gradient of one pass with four adjacent roots' terms summed to one
 // fraction N(l) / D(u), u = l^2: N of degree 7 in l, D of degree 4 in u with
 // positive coefficients (the product of the four denominators). Pairs first
@@ -170,44 +237,13 @@ __device__ __forceinline__ void long_grad_groups(float ta, float tb, float da, f
   rc[2 * lane] = make_float4(piece.x, piece.x, piece.y, piece.y);
   rc[2 * lane + 1] = make_float4(piece.z, piece.z, piece.w, piece.w);
   __syncwarp();
-  // each lane takes pairs of adjacent literals (two pairs per chunk of 4 W);
-  // a group's coefficients occupy eight entries
+  // each lane takes pairs of adjacent literals, two pairs per chunk of 4 W
+  // (one in a last chunk that ends within its first 2 W); a group's
+  // coefficients occupy eight entries
   const float4* rs = rc + 2 * (lane & ~(W - 1));
-  for (int c0 = 0; c0 < k; c0 += 4 * W) {
-    float2 lv[2], u[2], v[2], g[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int i = c0 + 2 * (q * W + rl);
-      lv[q] = i < k ? *reinterpret_cast<const float2*>(el + i) : make_float2(0.0f, 0.0f);
-      u[q] = __fmul2_rn(lv[q], lv[q]);
-      v[q] = __fmul2_rn(u[q], u[q]);
-      g[q] = make_float2(0.0f, 0.0f);
-    }
-#pragma unroll 2
-    for (int jq = 0; jq < W / 4; ++jq) {
-      const float4* cg = rs + 8 * jq;
-      const float4 a0 = cg[0], a1 = cg[1], b0 = cg[2], b1 = cg[3], d0 = cg[4], d1 = cg[5];
-      const float2 z0 = lo2(cg[6]);
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const float2 hi = ffma2(ffma2(lo2(a0), lv[q], hi2(a0)), u[q], ffma2(lo2(a1), lv[q], hi2(a1)));
-        const float2 lo = ffma2(ffma2(lo2(b0), lv[q], hi2(b0)), u[q], ffma2(lo2(b1), lv[q], hi2(b1)));
-        const float2 den = ffma2(ffma2(ffma2(lo2(d0), u[q], hi2(d0)), v[q], ffma2(lo2(d1), u[q], hi2(d1))), u[q], z0);
-        g[q] = ffma2(ffma2(hi, v[q], lo), make_float2(rcp_apx(den.x), rcp_apx(den.y)), g[q]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int i = c0 + 2 * (q * W + rl);
-      if (i + 1 < k) {
-        float2* gp2 = reinterpret_cast<float2*>(gr + i);  // rows and i are even: 8-byte aligned
-        const float2 o = *gp2;
-        *gp2 = make_float2(o.x + g[q].x, o.y + g[q].y);
-      } else if (i < k) {
-        gr[i] += g[q].x;
-      }
-    }
-  }
+  int c0 = 0;
+  for (; c0 + 2 * W < k; c0 += 4 * W) grad_group_pairs<W, 2>(rs, el, gr, c0, rl, k);
+  if (c0 < k) grad_group_pairs<W, 1>(rs, el, gr, c0, rl, k);
 }
 
 // A quad of literal values staged for the forward walk: its elementary
@@ -337,27 +373,13 @@ __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0,
     rc[lane] = make_float4(ta, tb, da, db);
     __syncwarp();
     const float4* rs = rc + (lane & ~(W - 1));  // the slot's W roots
-    for (int c0 = 0; c0 < k; c0 += 4 * W) {
-      float lv[4], l2[4], g[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = c0 + q * W + rl;
-        lv[q] = i < k ? el[i] : 0.0f;
-        l2[q] = lv[q] * lv[q];
-        g[q] = 0.0f;
-      }
-#pragma unroll 4
-      for (int jj = 0; jj < W; ++jj) {
-        const float4 c = rs[jj];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) g[q] = fmaf(fmaf(c.x, lv[q], c.y), rcp_apx(fmaf(c.z, l2[q], c.w)), g[q]);
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = c0 + q * W + rl;
-        if (i < k) gr[i] += g[q];
-      }
-    }
+    // chunks of 4 W literals; a last chunk takes only the rows of W it reaches
+    int c0 = 0;
+    for (; c0 + 3 * W < k; c0 += 4 * W) grad_root_terms<W, 4>(rs, el, gr, c0, rl, k);
+    const int rows = (k - c0 + W - 1) / W;
+    if (rows == 3) grad_root_terms<W, 3>(rs, el, gr, c0, rl, k);
+    else if (rows == 2) grad_root_terms<W, 2>(rs, el, gr, c0, rl, k);
+    else if (rows == 1) grad_root_terms<W, 1>(rs, el, gr, c0, rl, k);
   }
   __syncwarp();  // the root row is read before the next pass writes it
   return v;
