@@ -17,13 +17,14 @@
 // lanes exchange within a pass.
 //
 // Factor form (coefficient table built on the host): at every complex root
-// the literal factor is s g(l), g = p l + i (form A) or l + i p (form B). The
-// forward walk multiplies a running product by the factors of four literals
-// at once: their product is a polynomial in p whose coefficients are the
-// four values' elementary symmetric polynomials, formed once per pass and
-// shared by all roots of the slot, so a quad costs eight FP32 instructions
-// (two a literal; one factor at a time, three a literal in form A, is kept
-// for slots of 8 lanes, where a quad formed per lane serves only 8 roots).
+// the literal factor is s g(l), g = p l + i (form A) or l + i p (form B). In
+// slots of 16 and 32 lanes the forward walk multiplies a running product by
+// the factors of eight literals at once: their product is a polynomial in p
+// whose coefficients are the eight values' elementary symmetric polynomials,
+// formed once per pass and shared by all roots of the slot, so an octet
+// costs twelve FP32 operations (paired FMAs where the form allows), 1.5 a
+// literal. Slots of 8 lanes, where an octet formed per lane would serve only
+// 8 roots, take one factor at a time (three FP32 instructions in form A).
 // The walk goes in segments of LONG_SEG literals and multiplies by the
 // table's s^16 after each full one, so the running product is at its true
 // size (|prod| <= 1) at every segment boundary and stays within FP32 inside
@@ -246,43 +247,65 @@ __device__ __forceinline__ void long_grad_groups(float ta, float tb, float da, f
   if (c0 < k) grad_group_pairs<W, 1>(rs, el, gr, c0, rl, k);
 }
 
-// A quad of literal values staged for the forward walk: its elementary
-// symmetric polynomials e1 .. e4, in the order the form's paired multiply
-// takes them. The product of the quad's factors is a polynomial in p with
-// these coefficients, shared by all roots: form A prod (p l + i) =
-// (1 - p^2 e2 + p^4 e4) + i p (p^2 e3 - e1), staged (e4, e3, -e2, -e1);
-// form B prod (l + i p) = (e4 - p^2 e2 + p^4) + i p (e3 - p^2 e1), staged
-// (e2, e1, e4, e3).
+
+// An octet of literal values (two quads v, w) staged for the forward walk:
+// its elementary symmetric polynomials e1 .. e8 (from the quads' by
+// convolution), in the order the form's multiply takes them. Form A prod
+// (p l + i) = (1 - p^2 e2 + p^4 e4 - p^6 e6 + p^8 e8) + i p (-e1 + p^2 e3 -
+// p^4 e5 + p^6 e7): Horner in p^2 on the pairs, staged (e8, e7, -e6, -e5),
+// (e4, e3, -e2, -e1). Form B prod (l + i p) = (e8 + q e6 + q^2 e4 + q^3 e2
+// + q^4) + i p (e7 + q e5 + q^2 e3 + q^3 e1) with q = -p^2: staged (e4, e5,
+// e6, e7), (e1, e2, e3, e8).
 template <bool FB>
-__device__ __forceinline__ float4 quad_stage(float4 v) {
-  const float a = v.x + v.y, b = v.x * v.y, c = v.z + v.w, d = v.z * v.w;
-  const float e1 = a + c, e2 = fmaf(a, c, b + d), e3 = fmaf(b, c, d * a), e4 = b * d;
-  return FB ? make_float4(e2, e1, e4, e3) : make_float4(e4, e3, -e2, -e1);
+__device__ __forceinline__ void oct_stage(float4 v, float4 w, float4& s0, float4& s1) {
+  const float pa = v.x + v.y, pb = v.x * v.y, pc = v.z + v.w, pd = v.z * v.w;
+  const float a1 = pa + pc, a2 = fmaf(pa, pc, pb + pd), a3 = fmaf(pb, pc, pd * pa), a4 = pb * pd;
+  const float qa = w.x + w.y, qb = w.x * w.y, qc = w.z + w.w, qd = w.z * w.w;
+  const float b1 = qa + qc, b2 = fmaf(qa, qc, qb + qd), b3 = fmaf(qb, qc, qd * qa), b4 = qb * qd;
+  const float e1 = a1 + b1;
+  const float e2 = fmaf(a1, b1, a2 + b2);
+  const float e3 = fmaf(a2, b1, fmaf(a1, b2, a3 + b3));
+  const float e4 = fmaf(a3, b1, fmaf(a2, b2, fmaf(a1, b3, a4 + b4)));
+  const float e5 = fmaf(a4, b1, fmaf(a3, b2, fmaf(a2, b3, a1 * b4)));
+  const float e6 = fmaf(a4, b2, fmaf(a3, b3, a2 * b4));
+  const float e7 = fmaf(a4, b3, a3 * b4);
+  const float e8 = a4 * b4;
+  if (FB) {
+    s0 = make_float4(e4, e5, e6, e7);
+    s1 = make_float4(e1, e2, e3, e8);
+  } else {
+    s0 = make_float4(e8, e7, -e6, -e5);
+    s1 = make_float4(e4, e3, -e2, -e1);
+  }
 }
-// a root's constant pairs for the quad multiply: t = c1 x + z on the staged
-// pairs (x, z), then (real, imag) = c2 t + c3. Form A c1 = (p^2, p^2), c2 =
-// (p^2, p), c3 = (1, 0); form B c1 = (-p^2, -p^2), c2 = (1, p), c3 = (p^4, 0).
-struct QuadConst {
-  float2 c1, c2, c3;
-};
+// P <- P prod over an octet of g(l): form A four paired FMAs, form B two
+// paired FMAs and four FP32 instructions, then a complex multiply (twelve
+// FP32 operations for eight literals). The terms' magnitudes sum to at most
+// 16 times the product's (each factor's |real| + |imag| is at most sqrt(2)
+// times its modulus).
 template <bool FB>
-__device__ __forceinline__ QuadConst quad_const(float p, float p2) {
-  QuadConst q;
-  q.c1 = FB ? make_float2(-p2, -p2) : make_float2(p2, p2);
-  q.c2 = FB ? make_float2(1.0f, p) : make_float2(p2, p);
-  q.c3 = FB ? make_float2(p2 * p2, 0.0f) : make_float2(1.0f, 0.0f);
-  return q;
+__device__ __forceinline__ void omul(float4 s0, float4 s1, float p, float p2, float& r, float& i) {
+  float fr, fi;
+  if constexpr (FB) {
+    const float q = -p2;
+    const float2 qq = make_float2(q, q);
+    float2 t = make_float2(q + s1.y, fmaf(q, s1.x, s1.z));
+    t = ffma2(qq, t, lo2(s0));
+    t = ffma2(qq, t, hi2(s0));
+    fr = fmaf(q, t.x, s1.w);
+    fi = p * t.y;
+  } else {
+    const float2 pp = make_float2(p2, p2);
+    float2 t = ffma2(pp, lo2(s0), hi2(s0));
+    t = ffma2(pp, t, lo2(s1));
+    t = ffma2(pp, t, hi2(s1));
+    const float2 f = ffma2(make_float2(p2, p), t, make_float2(1.0f, 0.0f));
+    fr = f.x;
+    fi = f.y;
+  }
+  cmul(r, i, fr, fi);
 }
-// P <- P prod over a quad of g(l): two paired FMAs for the quad's factor and
-// a complex multiply, six FP32 instructions for four literals. The terms'
-// magnitudes sum to at most 4 times the product's (each factor's |real| +
-// |imag| is at most sqrt(2) times its modulus), so the expansion keeps the
-// product's relative accuracy.
-__device__ __forceinline__ void qmul(float4 e, const QuadConst& q, float& r, float& i) {
-  const float2 f = ffma2(q.c2, ffma2(q.c1, lo2(e), hi2(e)), q.c3);
-  cmul(r, i, f.x, f.y);
-}
-static_assert(LONG_SEG % 4 == 0, "segments hold whole quads");
+static_assert(LONG_SEG % 8 == 0, "segments hold whole octets");
 
 // One pass: the slot's W lanes take roots j0 .. j0 + W - 1. A forward walk
 // gives the full product P (true size at every segment boundary, restored by
@@ -313,35 +336,39 @@ __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0,
   const float p2 = p * p;
   float Pr = 1.0f, Pi = 0.0f;
   if constexpr (W >= 16) {
-    // chunks of W quads (4 W literals): each lane stages the symmetric
-    // polynomials of one quad of its slot in the warp's shared row, then the
-    // slot's lanes walk the chunk's full segments, s^16 after each
-    const int nq = k >> 2;
-    const QuadConst qc = quad_const<FB>(p, p2);
+    // chunks of W octets (8 W literals): each lane stages the symmetric
+    // polynomials of one octet of its slot in two entries of the warp's
+    // shared row, then the slot's lanes walk the chunk's full segments, s^16
+    // after each
+    const int no = k >> 3;
     const float4* e4 = reinterpret_cast<const float4*>(el);
-    const float4* rs = rc + (lane & ~(W - 1));
-    for (int c0 = 0; c0 < nq; c0 += W) {
-      const int qi = c0 + rl;
-      rc[lane] = qi < nq ? quad_stage<FB>(e4[qi]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const float4* rs = rc + 2 * (lane & ~(W - 1));
+    for (int c0 = 0; c0 < no; c0 += W) {
+      const int oi = c0 + rl;
+      float4 s0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), s1 = s0;
+      if (oi < no) oct_stage<FB>(e4[2 * oi], e4[2 * oi + 1], s0, s1);
+      rc[2 * lane] = s0;
+      rc[2 * lane + 1] = s1;
       __syncwarp();
-      const int s1 = min((c0 + W) / (LONG_SEG / 4), nseg - 1);
-      for (int sg = c0 / (LONG_SEG / 4); sg < s1; ++sg) {
-        const float4* qs = rs + (sg * (LONG_SEG / 4) - c0);
+      const int s1g = min((c0 + W) / (LONG_SEG / 8), nseg - 1);
+      for (int sg = c0 / (LONG_SEG / 8); sg < s1g; ++sg) {
+        const float4* os = rs + 2 * (sg * (LONG_SEG / 8) - c0);
 #pragma unroll
-        for (int u = 0; u < LONG_SEG / 4; ++u) qmul(qs[u], qc, Pr, Pi);
+        for (int u = 0; u < LONG_SEG / 8; ++u) omul<FB>(os[2 * u], os[2 * u + 1], p, p2, Pr, Pi);
         cmul(Pr, Pi, s16r, s16i);
       }
-      if (c0 + W < nq) __syncwarp();  // the chunk is read before the next one is staged
+      if (c0 + W < no) __syncwarp();  // the chunk is read before the next one is staged
     }
-    // the last segment: its full quads (staged in the last chunk), then the literals past them
-    if (nq > 0) {
-      const int cl = (nq - 1) / W * W;
-      for (int qq = (nseg - 1) * (LONG_SEG / 4); qq < nq; ++qq) qmul(rs[qq - cl], qc, Pr, Pi);
+    // the last segment: its full octets (staged in the last chunk), then the literals past them
+    if (no > 0) {
+      const int cl = (no - 1) / W * W;
+      for (int oo = (nseg - 1) * (LONG_SEG / 8); oo < no; ++oo)
+        omul<FB>(rs[2 * (oo - cl)], rs[2 * (oo - cl) + 1], p, p2, Pr, Pi);
     }
-    for (int t = 4 * nq; t < k; ++t) fmul<FB>(el[t], p, Pr, Pi);
-    __syncwarp();  // the quads are read before the root constants replace them
+    for (int t = 8 * no; t < k; ++t) fmul<FB>(el[t], p, Pr, Pi);
+    __syncwarp();  // the octets are read before the root constants replace them
   } else {
-    // narrow slots (a quad staged per lane would serve only W roots): one
+    // narrow slots (an octet staged per lane would serve only W roots): one
     // factor at a time, literal values read four at a time
     for (int sg = 0; sg + 1 < nseg; ++sg) {
       const float4* e4 = reinterpret_cast<const float4*>(el + sg * LONG_SEG);
