@@ -225,8 +225,18 @@ static void push4(std::vector<float>& o, double a, double b, double c, double d)
 // Per kept root (by increasing angle) two granules {p, s^16, 0}, {E', 0, 0}
 // with E = 2 c'_j. Head: {c'_0, kept complex roots, c'_mid (the real root's
 // coefficient, odd k), 1 if the real root is present}, {first form-B root (a
-// multiple of 32; = kept roots if none), 0, 0, 0}. The real root's factor is
-// l itself.
+// multiple of 32; = kept roots if none), number of expanded roots (a
+// multiple of 32, all in form A), expansion terms (0, 16 or 32), 0}. After
+// the roots' granules, per expanded root its expansion terms. The real
+// root's factor is l itself.
+//
+// Expanded derivative terms. A root's derivative term (A l + B) / (alpha u
+// + beta), u = l^2, has its pole at u = -beta/alpha; for the first form-A
+// roots (p <= about 3) that pole is far enough from [0, 1] for 1 / (alpha u
+// + beta) = sum_n c_n T_n(2u - 1) to converge to FP32 accuracy in 16 or 32
+// terms, so the sum over those roots becomes sum_n T_n(2u - 1) (l X_n +
+// Y_n) with X_n = sum_r A_r c_{n,r}, Y_n = sum_r B_r c_{n,r}: per literal
+// one Chebyshev sum instead of a term per root.
 namespace {
 struct Cx {
   double r, i;
@@ -246,6 +256,30 @@ Cx cpow(Cx z, int e) {
   return r;
 }
 Cx f32(Cx z) { return {static_cast<double>(static_cast<float>(z.r)), static_cast<double>(static_cast<float>(z.i))}; }
+
+// Chebyshev expansion on u in [0, 1] of 1 / (alpha u + beta) (alpha, beta >
+// 0): with t = 2u - 1 it is (2/alpha) / (t + s), s = 1 + 2 beta / alpha > 1,
+// whose expansion is (2/q) (1/2 + sum_{n >= 1} (-r)^n T_n(t)), q =
+// sqrt(s^2 - 1), r = s - q = 1 / (s + q). Written without cancellation:
+// alpha q / 2 = sqrt(beta (alpha + beta)), r = alpha / (alpha + 2 beta + 2
+// sqrt(beta (alpha + beta))). So c_0 = 1 / m, c_n = 2 (-r)^n / m, m =
+// sqrt(beta (alpha + beta)).
+void expansion_terms(double alpha, double beta, int nc, double* c) {
+  const double m = std::sqrt(beta * (alpha + beta));
+  const double r = alpha / (alpha + 2.0 * beta + 2.0 * m);
+  double rn = 1.0;
+  for (int n = 0; n < nc; ++n) {
+    c[n] = (n == 0 ? 1.0 : 2.0 * rn) / m;
+    rn *= -r;
+  }
+}
+// The tail after nc terms, sum_{n >= nc} |c_n| = 2 r^nc / ((1 - r) m),
+// relative to the function's smallest value on [0, 1], 1 / (alpha + beta).
+double cheb_tail(double alpha, double beta, int nc) {
+  const double m = std::sqrt(beta * (alpha + beta));
+  const double r = alpha / (alpha + 2.0 * beta + 2.0 * m);
+  return 2.0 * std::pow(r, nc) / ((1.0 - r) * m) * (alpha + beta);
+}
 }  // namespace
 
 static void build_long_pgf(const Shape& s, std::vector<float>& out) {
@@ -324,9 +358,36 @@ static void build_long_pgf(const Shape& s, std::vector<float>& out) {
   }
   const int nseg = (k + LONG_SEG - 1) / LONG_SEG;
   const int n_last = k - LONG_SEG * (nseg - 1);
+  // Chebyshev expansion of the leading form-A roots' derivative terms
+  // 1 / (p^2 u + 1), u = l^2 (expansion_terms below): the roots whose tail
+  // after nc terms is within LONG_CHEB_TOL (a prefix: the pole -1/p^2 moves
+  // toward u = 0 as p grows along the table), rounded down to a multiple of
+  // 32; nc chosen for the least kernel work, in FP32 operations per literal
+  // and restart: 3 per exact root, 2 nc / k per expanded root (the per-root
+  // sums), 3.5 nc for the per-literal Chebyshev sum.
+  auto n_expandable = [&](int nc) {
+    int n = 0;
+    while (n < form_b_from) {
+      const double p = pv[kept[n]];
+      if (cheb_tail(p * p, 1.0, nc) > LONG_CHEB_TOL) break;
+      ++n;
+    }
+    return n / 32 * 32;
+  };
+  int ncheb = 0, first_x = 0;
+  double best = 3.0 * nk;
+  for (const int nc : {LONG_CHEB_SHORT, LONG_CHEB_LONG}) {
+    const int fx = n_expandable(nc);
+    const double cost = 3.0 * (nk - fx) + 2.0 * nc * fx / k + 3.5 * nc;
+    if (fx > 0 && cost < best) {
+      best = cost;
+      ncheb = nc;
+      first_x = fx;
+    }
+  }
   out.clear();
   push4(out, cr[0], nk, has_real ? cmid : 0.0, has_real ? 1.0 : 0.0);
-  push4(out, form_b_from, 0, 0, 0);
+  push4(out, form_b_from, first_x, ncheb, 0);
   for (int r = 0; r < nk; ++r) {
     const int j = kept[r];
     const double p = pv[j];
@@ -341,6 +402,13 @@ static void build_long_pgf(const Shape& s, std::vector<float>& out) {
     const Cx Ep = cmul(cmul(E, cpow(sc, n_last)), cpow(r16, nseg - 1));
     push4(out, p, s16.r, s16.i, 0.0);
     push4(out, Ep.r, Ep.i, 0.0, 0.0);
+  }
+  // per expanded root its ncheb coefficients c_0 .. c_{ncheb-1}
+  for (int r = 0; r < first_x; ++r) {
+    const double p = pv[kept[r]];
+    double c[LONG_CHEB_LONG];
+    expansion_terms(p * p, 1.0, ncheb, c);
+    for (int n = 0; n < ncheb; n += 4) push4(out, c[n], c[n + 1], c[n + 2], c[n + 3]);
   }
 }
 

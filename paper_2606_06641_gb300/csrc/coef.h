@@ -14,6 +14,14 @@ constexpr int LONG_SEG = 16;
 // A pass of long-table roots uses factor form B when one of its roots has
 // cos(theta) below this (s^16 would leave FP32's normal range in form A).
 constexpr double LONG_FORM_B_COS = 1.0 / 64.0;
+// Chebyshev expansion of the long kernel's derivative terms: a table
+// expands the derivative terms of its first roots (a multiple of 32, all in
+// form A) in LONG_CHEB_SHORT or LONG_CHEB_LONG Chebyshev terms of l^2, or
+// none, whichever costs the kernel least; a root qualifies when the
+// truncated tail stays below LONG_CHEB_TOL of the term's smallest value.
+constexpr int LONG_CHEB_SHORT = 16;
+constexpr int LONG_CHEB_LONG = 32;
+constexpr double LONG_CHEB_TOL = 1e-8;
 
 // Constraints with k <= KSHORT use the register (short) kernels and the
 // short table layout; longer ones use the shared-memory (long) kernel.

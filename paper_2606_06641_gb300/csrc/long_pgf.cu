@@ -319,9 +319,13 @@ static_assert(LONG_SEG % 8 == 0, "segments hold whole octets");
 // and walk the slot's roots or groups (broadcast reads), summing in
 // registers and adding to the gradient row once per pass (fixed order).
 // Lanes past the table's roots get a zero weight and bounded factors.
-template <int W, bool FB>
+// An expansion pass (XP) adds its roots' A and B times their Chebyshev
+// terms to the slot's sums X_n, Y_n (lane rl holds n = rl and rl + W)
+// instead of a derivative term per literal.
+template <int W, bool FB, bool XP>
 __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0, int rl, int lane, const float* el,
-                                          float* gr, float4* rc, int k, int nseg, int n_last) {
+                                          float* gr, float4* rc, int k, int nseg, int n_last, const float* cheb,
+                                          int ncheb, float (&X)[2], float (&Y)[2]) {
   const int j = j0 + rl;
   float p = FB ? 1.0f : 0.0f, s16r = FB ? 0.00390625f : 1.0f, s16i = 0.f, er = 0.f, ei = 0.f;
   if (j < nroots) {
@@ -393,7 +397,29 @@ __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0,
   // (U = T p, w = p l) A = T_r p^2, B' = T_i p, alpha = p^2, beta = 1; form B
   // (U = T) A = T_r, B' = T_i p, alpha = 1, beta = p^2
   const float ta = FB ? Tr : Tr * p2, tb = Ti * p, da = FB ? 1.0f : p2, db = FB ? p2 : 1.0f;
-  if (W >= 16 && k > 4 * W) {
+  if constexpr (XP) {
+    float2* r2 = reinterpret_cast<float2*>(rc);
+    r2[lane] = make_float2(ta, tb);
+    __syncwarp();
+    const float2* s2 = r2 + (lane & ~(W - 1));
+    const float* cj = cheb + static_cast<size_t>(j0) * ncheb;  // root-major, ncheb terms a root
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const int n = rl + m * W;
+      if (n < ncheb) {
+        float x = X[m], y = Y[m];
+#pragma unroll 8
+        for (int r = 0; r < W; ++r) {
+          const float2 ab = s2[r];
+          const float c = __ldg(cj + r * ncheb + n);
+          x = fmaf(ab.x, c, x);
+          y = fmaf(ab.y, c, y);
+        }
+        X[m] = x;
+        Y[m] = y;
+      }
+    }
+  } else if (W >= 16 && k > 4 * W) {
     long_grad_groups<W>(ta, tb, da, db, rl, lane, el, gr, rc, k);
   } else {
     // one term a root: three FMAs and a reciprocal per (literal, root)
@@ -410,6 +436,43 @@ __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0,
   }
   __syncwarp();  // the root row is read before the next pass writes it
   return v;
+}
+
+// The expanded roots' derivative terms at every literal of the slot: the
+// slot's sums (X_n, Y_n) published to the warp's row (32 entries a slot),
+// then per literal sum_n T_n(t) (l X_n + Y_n), t = 2 l^2 - 1, by Clenshaw's
+// recurrence (three FP32 operations a term), two literals a lane at a time.
+template <int W>
+__device__ __forceinline__ void cheb_grad(const float* el, float* gr, float4* rc, int lane, int rl, int k, int ncheb,
+                                          const float (&X)[2], const float (&Y)[2]) {
+  float2* cx = reinterpret_cast<float2*>(rc) + (lane / W) * 32;
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const int n = rl + m * W;
+    if (n < ncheb) cx[n] = make_float2(X[m], Y[m]);
+  }
+  __syncwarp();
+  for (int i = rl; i < k; i += 2 * W) {
+    const bool two = i + W < k;
+    const float l0 = el[i], l1 = two ? el[i + W] : 0.0f;
+    const float t0 = fmaf(2.0f * l0, l0, -1.0f), t1 = fmaf(2.0f * l1, l1, -1.0f);
+    const float d0 = 2.0f * t0, d1 = 2.0f * t1;
+    float b10 = 0.0f, b20 = 0.0f, b11 = 0.0f, b21 = 0.0f;
+#pragma unroll 4
+    for (int n = ncheb - 1; n >= 1; --n) {
+      const float2 xy = cx[n];
+      const float n0 = fmaf(d0, b10, fmaf(l0, xy.x, xy.y) - b20);
+      const float n1 = fmaf(d1, b11, fmaf(l1, xy.x, xy.y) - b21);
+      b20 = b10;
+      b10 = n0;
+      b21 = b11;
+      b11 = n1;
+    }
+    const float2 xy = cx[0];
+    gr[i] += fmaf(t0, b10, fmaf(l0, xy.x, xy.y) - b20);
+    if (two) gr[i + W] += fmaf(t1, b11, fmaf(l1, xy.x, xy.y) - b21);
+  }
+  __syncwarp();  // the row is read before it is written again
 }
 
 // resident warps per SM the kernel is compiled for (register cap)
@@ -485,13 +548,25 @@ __global__ void __launch_bounds__(NW * 32, LONG_WARPS_PER_SM / NW) fe_grad_long_
 
   // passes of W roots; from the table's first form-B root on (a multiple of
   // 32, so no pass straddles it) the passes use form B
-  const int first_b = static_cast<int>(__ldg(tab + 1).x);
+  // The table's first first_x roots (a multiple of 32, all form A) have
+  // their derivative terms expanded in ncheb Chebyshev terms; a slot of W
+  // lanes holds at most 2 W of the sums, so narrower slots take every root
+  // exactly.
+  const float4 h1 = __ldg(tab + 1);
+  const int first_b = static_cast<int>(h1.x);
+  const int ncheb = static_cast<int>(h1.z);
+  const int first_x = ncheb <= 2 * W ? static_cast<int>(h1.y) : 0;
+  const float* cheb = reinterpret_cast<const float*>(tab + 2 + 2 * nroots);
+  float X[2] = {0.0f, 0.0f}, Y[2] = {0.0f, 0.0f};
   for (int j0 = 0; j0 < nroots; j0 += W) {
-    if (j0 < first_b)
-      fe_part += pgf_pass<W, false>(tab, nroots, j0, rl, lane, el, gr, rcw, k, nseg, n_last);
+    if (j0 < first_x)
+      fe_part += pgf_pass<W, false, true>(tab, nroots, j0, rl, lane, el, gr, rcw, k, nseg, n_last, cheb, ncheb, X, Y);
+    else if (j0 < first_b)
+      fe_part += pgf_pass<W, false, false>(tab, nroots, j0, rl, lane, el, gr, rcw, k, nseg, n_last, cheb, ncheb, X, Y);
     else
-      fe_part += pgf_pass<W, true>(tab, nroots, j0, rl, lane, el, gr, rcw, k, nseg, n_last);
+      fe_part += pgf_pass<W, true, false>(tab, nroots, j0, rl, lane, el, gr, rcw, k, nseg, n_last, cheb, ncheb, X, Y);
   }
+  if (first_x > 0) cheb_grad<W>(el, gr, rcw, lane, rl, k, ncheb, X, Y);
 
   if (has_real) {
     // the real root: value c_mid prod l, gradient c_mid prod over the other

@@ -332,7 +332,8 @@ def test_long_pgf_table_forms_stay_in_range(k):
                              (O.T_OR, 0, 0, 1)]:
         t = bd.coef_table(ct, k, op, r, par, basis=bd.BASIS_PGF, form=1).astype(np.float64).reshape(-1, 4)
         n, has_real, fb = int(t[0, 1]), t[0, 3], int(t[1, 0])
-        assert t.shape[0] == 2 + 2 * n
+        nx, nc = int(t[1, 1]), int(t[1, 2])
+        assert t.shape[0] == 2 + 2 * n + nx * nc // 4
         # kept roots = nonzero exact spectrum (pairs j = 1..k/2); the real root w = -1 (odd k)
         f = O.truth_table(ct, k, op, r, par).astype(np.float64)
         N = k + 1
@@ -349,6 +350,29 @@ def test_long_pgf_table_forms_stay_in_range(k):
             gmax = np.sqrt(1 + p * p)   # |p l + i| (form A) or |l + i p| (form B) at |l| <= 1
             assert gmax <= 1.0 / s_mod * (1 + 1e-5)        # |g| <= 1/|s| (|f| <= 1)
             assert abs(s16) >= 2.0 ** -100
+        # expanded roots: a multiple of 32, all in form A, 16 or 32 terms
+        assert nx % 32 == 0 and nx <= fb and (nc in (16, 32) if nx else nc == 0)
+
+
+@pytest.mark.parametrize("k", [100, 130, 200, 256, 300, 401, 512])
+def test_long_pgf_expansion_terms_approximate_the_derivative_factor(k):
+    """The expanded roots' stored terms c_n: sum_n c_n T_n(2u - 1) evaluated
+    by numpy's Chebyshev series in FP64 equals 1 / (p^2 u + 1), the form-A
+    derivative term's denominator, on u in [0, 1] to the FP32 rounding of the
+    stored terms (relative to the function's smallest value there, 1 / (p^2 +
+    1))."""
+    t = bd.coef_table(O.T_CARD, k, O.OP_GE, k // 2, 1, basis=bd.BASIS_PGF, form=1).astype(np.float64).reshape(-1, 4)
+    n, nx, nc = int(t[0, 1]), int(t[1, 1]), int(t[1, 2])
+    if k >= 200:
+        assert nx >= 64  # long tables expand most roots
+    c = t[2 + 2 * n:].reshape(-1)
+    assert c.size == nx * nc
+    u = np.linspace(0.0, 1.0, 1001)
+    for j in range(nx):
+        p = t[2 + 2 * j, 0]
+        exact = 1.0 / (p * p * u + 1.0)
+        approx = np.polynomial.chebyshev.chebval(2.0 * u - 1.0, c[j * nc:(j + 1) * nc])
+        assert np.max(np.abs(approx - exact)) * (p * p + 1.0) < 4e-7
 
 
 def _paper_basis_fp64(c, ell):
