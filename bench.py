@@ -481,8 +481,47 @@ def load_counters(workload: str):
             if k in KERNEL_SOURCES and c.get("kernel_source_hash") == kernel_source_hash(k)}
 
 
+def long_kernel_form_ops(insts, tiles) -> float:
+    """FP32 operations per restart and step of the long kernel's own forms,
+    summed over the long constraints (k > 32) from each table's head and the
+    lanes per restart W of the constraint's length group: per root the
+    forward walk (W >= 16: twelve per octet, three per literal past the last
+    octet; W = 8: three per literal, four in form B), four per segment for
+    s^16 and six for T and the value; per exactly treated root and literal
+    3.25 (four-root fractions, W >= 16 and k > 4 W) or 4 (one term a root);
+    per expanded root 2 nc (its sums), plus 3 nc per literal for the
+    Chebyshev sum; 4 per literal for the real root's scan."""
+    import numpy as np
+
+    from paper_2606_06641_gb300 import binding as bd
+    groups = sorted((km, lw) for lw, _, km in tiles)  # shortest first
+    cache = {}
+    total = 0.0
+    for inst in insts:
+        ks = inst.lengths
+        for c in np.nonzero(ks > 32)[0]:
+            k = int(ks[c])
+            key = (int(inst.ctype[c]), k, int(inst.op[c]), int(inst.param[c]), int(inst.parity[c]))
+            if key not in cache:
+                t = bd.coef_table(*key, basis=bd.BASIS_PGF, form=1).astype(np.float64).reshape(-1, 4)
+                cache[key] = (int(t[0, 1]), t[0, 3] > 0.5, int(t[1, 0]), int(t[1, 1]), int(t[1, 2]))
+            nr, has_real, fb, nx, nc = cache[key]
+            W = next((lw for km, lw in groups if km >= k), 32)
+            nseg = (k + 15) // 16
+            fwd = (12 * (k // 8) + 3 * (k % 8) if W >= 16 else 3 * k) + 4 * (nseg - 1) + 6
+            nx = nx // W * W if nc <= 2 * W else 0
+            d_exact = (3.25 if W >= 16 and k > 4 * W else 4.0) * k
+            ops = nr * fwd + (nr - nx) * d_exact + nx * 2 * nc + (3 * nc * k if nx else 0)
+            if W < 16:
+                ops += max(0, nr - fb) * k
+            if has_real:
+                ops += 4 * k
+            total += ops
+    return total
+
+
 def dominant_kernel(groups, B: int, chunk: int, peak_tinst: float, peak_src: str, sm_max: float, sms: int,
-                    counters):
+                    counters, long_form_ops: float = 0.0):
     """Roofline object of the kernel with the largest FE+gradient time per
     step: achieved = its algorithmic instructions per launch / its event-timed
     duration per launch (launches over the same chunk of restarts)."""
@@ -511,12 +550,23 @@ def dominant_kernel(groups, B: int, chunk: int, peak_tinst: float, peak_src: str
            "timing": "CUDA events on the launching stream around each launch group of the step "
                      "(afs_group_times, 5 launches per group over one restart chunk, current state)",
            "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock, {peak_src})"}
-    if kind == 1 or (kind == 0 and max(d["kmax"]) <= 24):
-        # the kernel's own algorithm (gradient by division): per (literal,
-        # root) 3 FP32 instructions for the forward product and, for the
-        # derivative, numerator, denominator, reciprocal and sum (long) or
-        # those and w = l / gamma (short)
-        own = 7 if kind == 1 else 8
+    if kind == 1 and long_form_ops > 0:
+        # the long kernel's own forms (octet walk, gradient by division in
+        # four-root fractions, Chebyshev-expanded roots): their FP32
+        # operations per step over the same event-timed launches
+        ops = long_form_ops * B
+        out["kernel_form"] = {"ops_per_step": ops,
+                              "achieved": ops / (out["ms_per_step"] * 1e-3) / 1e12,
+                              "frac": ops / (out["ms_per_step"] * 1e-3) / 1e12 / peak_tinst,
+                              "note": "the frac above counts 16 per (literal, root), the prefix/suffix work "
+                                      "model; this one the FP32 operations the kernel's forms take "
+                                      "(long_kernel_form_ops)"}
+    elif kind == 0 and max(d["kmax"]) <= 24:
+        # the short kernel's own algorithm (gradient by division): per
+        # (literal, root) 3 FP32 instructions for the forward product and,
+        # for the derivative, w = l / gamma, numerator, denominator,
+        # reciprocal and sum
+        own = 8
         out["division_form"] = {"instr_per_literal_root": own,
                                 "frac": achieved / peak_tinst * own / 16.0,
                                 "note": "the frac above counts 16 per (literal, root), the prefix/suffix work model"}
@@ -627,7 +677,8 @@ def measure_workload(name: str, args, rank: int, world: int, stream, want_cpu: b
     sms = props.multi_processor_count
     peak_tinst = sms * 128 * sm_max * 1e6 / 1e12
     chunk, rpl = bd.tuning(h)
-    roof = dominant_kernel(groups, B, chunk, peak_tinst, peak_src, sm_max, sms, load_counters(name))
+    roof = dominant_kernel(groups, B, chunk, peak_tinst, peak_src, sm_max, sms, load_counters(name),
+                           long_kernel_form_ops(insts, bd.long_tiles(h)))
     step_work = sum(w for _, _, _, w in groups) * ((B + chunk - 1) // chunk)
     roof["step_work_instr"] = step_work
     roof["step_frac"] = step_work / (dev_ms / K * 1e-3) / 1e12 / peak_tinst
