@@ -342,23 +342,27 @@ __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0,
   if constexpr (W >= 16) {
     // chunks of W octets (8 W literals): each lane stages the symmetric
     // polynomials of one octet of its slot in two entries of the warp's
-    // shared row, then the slot's lanes walk the chunk's full segments, s^16
-    // after each
+    // shared row (halves 0..31 and 32..63), then the slot's lanes walk the
+    // chunk's full segments, s^16 after each. A chunk of wc octets covers its
+    // 2 wc quads; octet c0 + rl takes quads rl and wc + rl of them (an
+    // octet's literals need not be adjacent: any 16 literals of a segment
+    // keep the running product within its bound), so the loads and stores
+    // are consecutive 16-byte words.
     const int no = k >> 3;
     const float4* e4 = reinterpret_cast<const float4*>(el);
-    const float4* rs = rc + 2 * (lane & ~(W - 1));
+    const float4* rs = rc + (lane & ~(W - 1));
     for (int c0 = 0; c0 < no; c0 += W) {
-      const int oi = c0 + rl;
+      const int wc = min(W, no - c0);
       float4 s0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), s1 = s0;
-      if (oi < no) oct_stage<FB>(e4[2 * oi], e4[2 * oi + 1], s0, s1);
-      rc[2 * lane] = s0;
-      rc[2 * lane + 1] = s1;
+      if (rl < wc) oct_stage<FB>(e4[2 * c0 + rl], e4[2 * c0 + wc + rl], s0, s1);
+      rc[lane] = s0;
+      rc[32 + lane] = s1;
       __syncwarp();
       const int s1g = min((c0 + W) / (LONG_SEG / 8), nseg - 1);
       for (int sg = c0 / (LONG_SEG / 8); sg < s1g; ++sg) {
-        const float4* os = rs + 2 * (sg * (LONG_SEG / 8) - c0);
+        const float4* os = rs + (sg * (LONG_SEG / 8) - c0);
 #pragma unroll
-        for (int u = 0; u < LONG_SEG / 8; ++u) omul<FB>(os[2 * u], os[2 * u + 1], p, p2, Pr, Pi);
+        for (int u = 0; u < LONG_SEG / 8; ++u) omul<FB>(os[u], os[32 + u], p, p2, Pr, Pi);
         cmul(Pr, Pi, s16r, s16i);
       }
       if (c0 + W < no) __syncwarp();  // the chunk is read before the next one is staged
@@ -366,8 +370,7 @@ __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0,
     // the last segment: its full octets (staged in the last chunk), then the literals past them
     if (no > 0) {
       const int cl = (no - 1) / W * W;
-      for (int oo = (nseg - 1) * (LONG_SEG / 8); oo < no; ++oo)
-        omul<FB>(rs[2 * (oo - cl)], rs[2 * (oo - cl) + 1], p, p2, Pr, Pi);
+      for (int oo = (nseg - 1) * (LONG_SEG / 8); oo < no; ++oo) omul<FB>(rs[oo - cl], rs[32 + oo - cl], p, p2, Pr, Pi);
     }
     for (int t = 8 * no; t < k; ++t) fmul<FB>(el[t], p, Pr, Pi);
     __syncwarp();  // the octets are read before the root constants replace them
@@ -439,38 +442,38 @@ __device__ __forceinline__ float pgf_pass(const float4* tab, int nroots, int j0,
 }
 
 // The expanded roots' derivative terms at every literal of the slot: the
-// slot's sums (X_n, Y_n) published to the warp's row (32 entries a slot),
-// then per literal sum_n T_n(t) (l X_n + Y_n), t = 2 l^2 - 1, by Clenshaw's
-// recurrence (three FP32 operations a term), two literals a lane at a time.
+// slot's sums (X_n, Y_n) published to the warp's row in duplicated pairs
+// (2 W entries a slot, so at most 2 W terms), then per literal sum_n T_n(t)
+// (l X_n + Y_n), t = 2 l^2 - 1, by Clenshaw's recurrence, two literals a
+// lane on paired FMAs (three a term).
 template <int W>
 __device__ __forceinline__ void cheb_grad(const float* el, float* gr, float4* rc, int lane, int rl, int k, int ncheb,
                                           const float (&X)[2], const float (&Y)[2]) {
-  float2* cx = reinterpret_cast<float2*>(rc) + (lane / W) * 32;
+  float4* cx = rc + (lane / W) * (2 * W);
 #pragma unroll
   for (int m = 0; m < 2; ++m) {
     const int n = rl + m * W;
-    if (n < ncheb) cx[n] = make_float2(X[m], Y[m]);
+    if (n < ncheb) cx[n] = make_float4(X[m], X[m], Y[m], Y[m]);
   }
   __syncwarp();
+  const float2 m1 = make_float2(-1.0f, -1.0f);
   for (int i = rl; i < k; i += 2 * W) {
     const bool two = i + W < k;
-    const float l0 = el[i], l1 = two ? el[i + W] : 0.0f;
-    const float t0 = fmaf(2.0f * l0, l0, -1.0f), t1 = fmaf(2.0f * l1, l1, -1.0f);
-    const float d0 = 2.0f * t0, d1 = 2.0f * t1;
-    float b10 = 0.0f, b20 = 0.0f, b11 = 0.0f, b21 = 0.0f;
+    const float2 l = make_float2(el[i], two ? el[i + W] : 0.0f);
+    const float2 t = ffma2(make_float2(2.0f * l.x, 2.0f * l.y), l, m1);
+    const float2 d = make_float2(2.0f * t.x, 2.0f * t.y);
+    float2 b1 = make_float2(0.0f, 0.0f), b2 = b1;
 #pragma unroll 4
     for (int n = ncheb - 1; n >= 1; --n) {
-      const float2 xy = cx[n];
-      const float n0 = fmaf(d0, b10, fmaf(l0, xy.x, xy.y) - b20);
-      const float n1 = fmaf(d1, b11, fmaf(l1, xy.x, xy.y) - b21);
-      b20 = b10;
-      b10 = n0;
-      b21 = b11;
-      b11 = n1;
+      const float4 c = cx[n];
+      const float2 nb = ffma2(d, b1, ffma2(m1, b2, ffma2(l, lo2(c), hi2(c))));
+      b2 = b1;
+      b1 = nb;
     }
-    const float2 xy = cx[0];
-    gr[i] += fmaf(t0, b10, fmaf(l0, xy.x, xy.y) - b20);
-    if (two) gr[i + W] += fmaf(t1, b11, fmaf(l1, xy.x, xy.y) - b21);
+    const float4 c = cx[0];
+    const float2 g = ffma2(t, b1, ffma2(m1, b2, ffma2(l, lo2(c), hi2(c))));
+    gr[i] += g.x;
+    if (two) gr[i + W] += g.y;
   }
   __syncwarp();  // the row is read before it is written again
 }
