@@ -122,8 +122,11 @@ def test_long_form_boundaries(k):
 
 def test_every_long_tile():
     """Every tile of the long kernel (8, 16 or 32 lanes per restart; 2, 4 or 8
-    warps per CTA) on a mix of long lengths and types, ragged restart count."""
-    inst = synth.long_card_n10000(3, n=600, n_clauses=200, n_long=10, kmin=33, kmax=300)
+    warps per CTA) on a mix of long lengths and types, ragged restart count:
+    lengths 43..406 cover tables without expanded roots, with 16 and with 32
+    Chebyshev terms (a slot of 8 lanes takes the 32-term tables' roots
+    exactly, one of 16 holds two terms a lane)."""
+    inst = synth.long_card_n10000(3, n=600, n_clauses=200, n_long=10, kmin=33, kmax=512)
     x = synth.uniform_x0(inst.n, 29, 5)
     h = bd.load_instance(inst)
     groups = bd.long_tiles(h)
