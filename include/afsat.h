@@ -386,9 +386,10 @@ int afs_set_long_tiles(afs_handle* h, const int32_t* lanes, const int32_t* warps
 /* afs_coef_table: the FP32 coefficient table the kernels use for one
  * constraint shape (for host-side inspection and tests). form 0 = short
  * (k <= 32) layout, form 1 = long layout (in the probability-generating basis
- * the factor-form layout with per-segment scale powers; in the paper's basis
- * the direct-factor layout). Writes up to cap floats into out and the table
- * length into *len. No device work. */
+ * the factor-form layout with per-segment scale powers, followed by the
+ * Chebyshev terms of the roots whose derivative terms are expanded; in the
+ * paper's basis the direct-factor layout). Writes up to cap floats into out
+ * and the table length into *len. No device work. */
 int afs_coef_table(int32_t type, int32_t k, int32_t op, int32_t param, int32_t parity,
                    int32_t basis, int32_t form, float* out, int32_t cap, int32_t* len);
 /* afs_esp_coefficients: f_hat(|S| = d) for d = 0..k in FP64 (Eq. 1's

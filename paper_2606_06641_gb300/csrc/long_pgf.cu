@@ -13,8 +13,9 @@
 // passes walk the table's roots W at a time. The literal list is staged with
 // cp.async.bulk on an mbarrier (bounded wait), the literal values l = s x of
 // the CTA's restarts in shared memory rows, read four at a time by 16-byte
-// loads; each warp has a shared row of 32 16-byte entries for the values its
-// lanes exchange within a pass.
+// loads; each warp has a shared row of 64 16-byte entries (two a lane) for
+// the values its lanes exchange within a pass: staged octets, root constants
+// or four-root fractions, expansion sums.
 //
 // Factor form (coefficient table built on the host): at every complex root
 // the literal factor is s g(l), g = p l + i (form A) or l + i p (form B). In
@@ -41,12 +42,21 @@
 // FMAs and one approximate reciprocal, three FMAs a root, where a pass walks
 // more than 4 W literals; shorter passes take one term a root (three FMAs
 // and a reciprocal). Either way no prefix and suffix products are rebuilt.
-// The lanes then swap roles: each lane takes 4 literals of its slot at a
-// time and walks the slot's root groups (their coefficients broadcast from
-// shared memory), summing in registers and adding each literal's sum to the
-// slot's gradient row once per pass (fixed order, deterministic). The real root's factor is l itself,
-// which can be zero: its leave-one-out products take a prefix/suffix scan
-// over the slot's lanes after the passes, in registers.
+// The lanes then swap roles: each lane takes literals of its slot (pairs of
+// adjacent ones on paired FMAs for the fractions) and walks the slot's roots
+// or root groups (their constants broadcast from shared memory), summing in
+// registers and adding each literal's sum to the slot's gradient row once
+// per pass (fixed order, deterministic).
+//
+// Expanded roots. For a table's leading form-A roots the derivative term's
+// factor 1 / (p^2 l^2 + 1) is stored as a Chebyshev series in 2 l^2 - 1 (16
+// or 32 terms, tail below 1e-8): their passes skip the per-literal terms and
+// add each root's A and B times its terms to per-restart sums X_n, Y_n, and
+// one Clenshaw sum per literal, sum_n T_n (l X_n + Y_n), covers all of them.
+//
+// The real root's factor is l itself, which can be zero: its leave-one-out
+// products take a prefix/suffix scan over the slot's lanes after the passes,
+// in registers.
 #include <cuda_bf16.h>
 
 #include "afsat.h"
